@@ -1,0 +1,423 @@
+/*
+ * pms_oracle.c -- plain CPU oracle for exact planted (l,d)-motif search
+ * (the PMS problem: qPMS with quorum q = n).
+ *
+ * TEST INFRASTRUCTURE ONLY. The test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this file; the GPU library neither links
+ * nor includes it, and nothing here includes GPU code. It shares no header,
+ * helper or table with the GPU path.
+ *
+ * It is deliberately slow and literal: l-mers are compared character by
+ * character, the search space is walked with nested loops/recursion, motifs
+ * are gathered in a growable array that is sorted and de-duplicated at the
+ * end. Every entry point names the definition or observation of the paper it
+ * restates (section "Formal Definitions of qPMS", chapter "Our Approach").
+ *
+ * Conventions (the paper's readings used throughout):
+ *   - alphabet order A < C < G < T, coded 0,1,2,3 as in the paper's
+ *     compression example (AGGCTA -> 022130);
+ *   - an l-mer of s is s[j..j+l-1] for every j in 0..m-l (Definition 2 read
+ *     with its index range fixed to 1 <= i <= m-l+1);
+ *   - "within d" means Hamming distance <= d (Definition 5: no more than d);
+ *   - a motif set is reported as sorted, unique 64-bit keys holding 2 bits per
+ *     base with position 0 in the most significant used bits, so ascending
+ *     keys are lexicographic order.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+#define ORACLE_OK 0
+#define ORACLE_EINVAL (-1)
+#define ORACLE_ENOMEM (-2)
+
+static int code_of(uint8_t ch)
+{
+    switch (ch) {
+    case 'A': return 0;
+    case 'C': return 1;
+    case 'G': return 2;
+    case 'T': return 3;
+    default: return -1;
+    }
+}
+
+static const uint8_t LETTER[4] = {'A', 'C', 'G', 'T'};
+
+/* Definition 3: number of positions at which two equal-length strings differ. */
+int oracle_hamming(const uint8_t *a, const uint8_t *b, int l)
+{
+    int h = 0;
+    for (int k = 0; k < l; ++k)
+        if (a[k] != b[k])
+            h += 1;
+    return h;
+}
+
+/* Definition 4: distance from an l-mer x to a string s = minimum over the
+ * l-mers of s (all m-l+1 windows). Returns l+1 if s is shorter than x. */
+int oracle_distance_to_string(const uint8_t *x, int l, const uint8_t *s, int m)
+{
+    int best = l + 1;
+    for (int j = 0; j + l <= m; ++j) {
+        int h = oracle_hamming(x, s + j, l);
+        if (h < best)
+            best = h;
+    }
+    return best;
+}
+
+/* "d_H(x, s) <= d": true iff some window of s is within d of x. Same predicate
+ * as oracle_distance_to_string(...) <= d, stopping at the first window found. */
+static int string_has_occurrence(const uint8_t *x, int l, int d, const uint8_t *s, int m)
+{
+    for (int j = 0; j + l <= m; ++j)
+        if (oracle_hamming(x, s + j, l) <= d)
+            return 1;
+    return 0;
+}
+
+/* Definition 5 with q = n: M is an (l,d)-motif of s_1..s_n iff every string
+ * is within d of M. seqs is row-major n x m. */
+int oracle_is_motif(const uint8_t *M, int l, int d, const uint8_t *seqs, int n, int m)
+{
+    for (int i = 0; i < n; ++i)
+        if (!string_has_occurrence(M, l, d, seqs + (size_t)i * m, m))
+            return 0;
+    return 1;
+}
+
+/* ---- bit-plane compression (chapter "Our Approach", "String Compression") ----
+ * An l-mer is stored as ceil(log2 |Sigma|) = 2 groups of ceil(l/32) 32-bit
+ * words; bit g of the code of character k goes to bit (k mod 32) of word
+ * (k div 32) of group g. The distance of two compressed l-mers: XOR the two
+ * copies of each group, OR the XOR results across groups, count the set bits.
+ * out must hold 2*ceil(l/32) words: group 0 first, then group 1. */
+int oracle_compress(const uint8_t *s, int l, uint32_t *out)
+{
+    int words = (l + 31) / 32;
+    for (int w = 0; w < 2 * words; ++w)
+        out[w] = 0;
+    for (int k = 0; k < l; ++k) {
+        int c = code_of(s[k]);
+        if (c < 0)
+            return ORACLE_EINVAL;
+        for (int g = 0; g < 2; ++g)
+            if ((c >> g) & 1)
+                out[g * words + k / 32] |= (uint32_t)1 << (k % 32);
+    }
+    return ORACLE_OK;
+}
+
+static int count_set_bits(uint32_t v)
+{
+    int c = 0;
+    while (v) {
+        c += (int)(v & 1u);
+        v >>= 1;
+    }
+    return c;
+}
+
+int oracle_compressed_distance(const uint32_t *a, const uint32_t *b, int l)
+{
+    int words = (l + 31) / 32;
+    int h = 0;
+    for (int w = 0; w < words; ++w) {
+        uint32_t acc = 0;
+        for (int g = 0; g < 2; ++g)
+            acc |= a[g * words + w] ^ b[g * words + w];
+        h += count_set_bits(acc);
+    }
+    return h;
+}
+
+/* ---- result sets ---- */
+
+typedef struct {
+    uint64_t *v;
+    long n, cap;
+    int oom;
+} keyvec;
+
+static void kv_push(keyvec *kv, uint64_t key)
+{
+    if (kv->oom)
+        return;
+    if (kv->n == kv->cap) {
+        long nc = kv->cap ? 2 * kv->cap : 256;
+        uint64_t *nv = (uint64_t *)realloc(kv->v, (size_t)nc * sizeof(uint64_t));
+        if (!nv) {
+            kv->oom = 1;
+            return;
+        }
+        kv->v = nv;
+        kv->cap = nc;
+    }
+    kv->v[kv->n++] = key;
+}
+
+static int cmp_u64(const void *a, const void *b)
+{
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Sorts, removes duplicates, copies up to cap keys to out. Returns the number
+ * of unique keys (which may exceed cap: then only cap were written). */
+static long kv_finish(keyvec *kv, uint64_t *out, long cap)
+{
+    if (kv->oom) {
+        free(kv->v);
+        return ORACLE_ENOMEM;
+    }
+    qsort(kv->v, (size_t)kv->n, sizeof(uint64_t), cmp_u64);
+    long u = 0;
+    for (long i = 0; i < kv->n; ++i)
+        if (u == 0 || kv->v[i] != kv->v[u - 1])
+            kv->v[u++] = kv->v[i];
+    for (long i = 0; i < u && i < cap; ++i)
+        out[i] = kv->v[i];
+    free(kv->v);
+    return u;
+}
+
+/* Key of an l-mer: 2 bits per base, position 0 most significant. */
+uint64_t oracle_key(const uint8_t *x, int l)
+{
+    uint64_t key = 0;
+    for (int k = 0; k < l; ++k)
+        key = (key << 2) | (uint64_t)code_of(x[k]);
+    return key;
+}
+
+void oracle_decode(uint64_t key, int l, uint8_t *out)
+{
+    for (int k = l - 1; k >= 0; --k) {
+        out[k] = LETTER[key & 3u];
+        key >>= 2;
+    }
+}
+
+static int valid_input(const uint8_t *seqs, int n, int m, int l, int d)
+{
+    if (n < 1 || l < 1 || l > 32 || m < l || d < 0 || d >= l)
+        return 0;
+    for (long k = 0; k < (long)n * m; ++k)
+        if (code_of(seqs[k]) < 0)
+            return 0;
+    return 1;
+}
+
+/* ---- the d-neighbourhood B(x, d) as the tree T_d(x) of qPMSPrune ----
+ * ("Previous Works", qPMSPrune: the root is x, a child differs from its parent
+ * at one position to the right of the parent's last change, so a node at depth
+ * h is at distance h from x; depth is at most d). Every string of B(x, d) is
+ * visited exactly once. */
+
+typedef struct {
+    const uint8_t *x;   /* root l-mer */
+    uint8_t *cur;       /* the node being visited (x with some changes) */
+    int l, d;
+    /* what to do with each node */
+    const uint8_t *seqs;
+    int n, m;
+    const uint8_t *other;   /* if non-NULL: keep only nodes within d of it */
+    int mode;               /* 0: motif test, 1: collect every node */
+    keyvec *out;
+    long visited;
+} walk_t;
+
+static void visit_node(walk_t *w)
+{
+    w->visited += 1;
+    if (w->other && oracle_hamming(w->cur, w->other, w->l) > w->d)
+        return;
+    if (w->mode == 1 || oracle_is_motif(w->cur, w->l, w->d, w->seqs, w->n, w->m))
+        kv_push(w->out, oracle_key(w->cur, w->l));
+}
+
+static void walk_tree(walk_t *w, int first_pos, int depth)
+{
+    visit_node(w);
+    if (depth == w->d)
+        return;
+    for (int p = first_pos; p < w->l; ++p) {
+        uint8_t orig = w->cur[p];
+        for (int b = 0; b < 4; ++b) {
+            if (LETTER[b] == w->x[p])
+                continue;
+            w->cur[p] = LETTER[b];
+            walk_tree(w, p + 1, depth + 1);
+        }
+        w->cur[p] = orig;
+    }
+}
+
+/* B(x, d) itself, as sorted keys (notation table: the sphere B(a, R)). */
+long oracle_neighbourhood(const uint8_t *x, int l, int d, uint64_t *out, long cap)
+{
+    if (l < 1 || l > 32 || d < 0)
+        return ORACLE_EINVAL;
+    uint8_t cur[32];
+    memcpy(cur, x, (size_t)l);
+    keyvec kv = {0};
+    walk_t w = {x, cur, l, d, NULL, 0, 0, NULL, 1, &kv, 0};
+    walk_tree(&w, 0, 0);
+    return kv_finish(&kv, out, cap);
+}
+
+/* Number of nodes the tree walk of B(x, d) visits (each string once, so this
+ * equals |B(x, d)|). */
+long oracle_neighbourhood_visits(const uint8_t *x, int l, int d)
+{
+    if (l < 1 || l > 32 || d < 0)
+        return ORACLE_EINVAL;
+    uint8_t cur[32];
+    memcpy(cur, x, (size_t)l);
+    keyvec kv = {0};
+    walk_t w = {x, cur, l, d, NULL, 0, 0, NULL, 1, &kv, 0};
+    walk_tree(&w, 0, 0);
+    free(kv.v);
+    return w.visited;
+}
+
+/* |B(x, d) intersect B(r, d)|, by walking B(x, d) and testing each node. */
+long oracle_pair_intersection_size(const uint8_t *x, const uint8_t *r, int l, int d)
+{
+    uint8_t cur[32];
+    memcpy(cur, x, (size_t)l);
+    keyvec kv = {0};
+    walk_t w = {x, cur, l, d, NULL, 0, 0, r, 1, &kv, 0};
+    walk_tree(&w, 0, 0);
+    long n = kv.n;
+    free(kv.v);
+    return n;
+}
+
+/* ---- PMS solvers ---- */
+
+typedef struct {
+    const uint8_t *seqs;
+    int n, m, l, d;
+    int variant;        /* 0: seeds x in S_1; 1: pairs (x in S_1, r in S_2) */
+    int tid, nthreads;
+    long seed_lo, seed_hi;   /* range of windows of s_1 used as seeds */
+    keyvec out;
+} job_t;
+
+static void *solve_worker(void *arg)
+{
+    job_t *j = (job_t *)arg;
+    const uint8_t *s1 = j->seqs;
+    const uint8_t *s2 = j->n > 1 ? j->seqs + j->m : NULL;
+    uint8_t cur[32];
+    for (long x0 = j->seed_lo + j->tid; x0 < j->seed_hi; x0 += j->nthreads) {
+        const uint8_t *x = s1 + x0;
+        if (j->variant == 0 || s2 == NULL) {
+            /* Observation 3.1 with q = n: every motif is within d of some
+             * l-mer x of s_1, so the candidates are the union of B(x, d). */
+            memcpy(cur, x, (size_t)j->l);
+            walk_t w = {x, cur, j->l, j->d, j->seqs, j->n, j->m, NULL, 0, &j->out, 0};
+            walk_tree(&w, 0, 0);
+        } else {
+            /* Observation 3.3 with q = n: a motif is within d of an l-mer x
+             * of s_1 and of an l-mer r of s_2, so it lies in
+             * B(x, d) intersect B(r, d), and then d_H(x, r) <= 2d. */
+            for (int r0 = 0; r0 + j->l <= j->m; ++r0) {
+                const uint8_t *r = s2 + r0;
+                if (oracle_hamming(x, r, j->l) > 2 * j->d)
+                    continue;
+                memcpy(cur, x, (size_t)j->l);
+                walk_t w = {x, cur, j->l, j->d, j->seqs, j->n, j->m, r, 0, &j->out, 0};
+                walk_tree(&w, 0, 0);
+            }
+        }
+    }
+    return NULL;
+}
+
+static long run_solver(const uint8_t *seqs, int n, int m, int l, int d, int variant,
+                       long seed_lo, long seed_hi, int threads, uint64_t *out, long cap)
+{
+    if (!valid_input(seqs, n, m, l, d))
+        return ORACLE_EINVAL;
+    long W = (long)m - l + 1;
+    if (seed_lo < 0)
+        seed_lo = 0;
+    if (seed_hi > W)
+        seed_hi = W;
+    if (threads < 1)
+        threads = 1;
+    if (threads > 256)
+        threads = 256;
+    job_t *jobs = (job_t *)calloc((size_t)threads, sizeof(job_t));
+    pthread_t *th = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    if (!jobs || !th) {
+        free(jobs);
+        free(th);
+        return ORACLE_ENOMEM;
+    }
+    for (int t = 0; t < threads; ++t) {
+        jobs[t] = (job_t){seqs, n, m, l, d, variant, t, threads, seed_lo, seed_hi, {0}};
+        if (threads == 1 || pthread_create(&th[t], NULL, solve_worker, &jobs[t]) != 0) {
+            solve_worker(&jobs[t]);
+            th[t] = 0;
+        }
+    }
+    keyvec all = {0};
+    for (int t = 0; t < threads; ++t) {
+        if (th[t])
+            pthread_join(th[t], NULL);
+        if (jobs[t].out.oom)
+            all.oom = 1;
+        for (long i = 0; i < jobs[t].out.n; ++i)
+            kv_push(&all, jobs[t].out.v[i]);
+        free(jobs[t].out.v);
+    }
+    free(jobs);
+    free(th);
+    return kv_finish(&all, out, cap);
+}
+
+/* All (l,d)-motifs of seqs (n x m, row-major ASCII), seeds x over all of S_1.
+ * Returns the number of motifs (sorted unique keys in out, at most cap written)
+ * or a negative error. */
+long oracle_solve(const uint8_t *seqs, int n, int m, int l, int d, int threads,
+                  uint64_t *out, long cap)
+{
+    return run_solver(seqs, n, m, l, d, 0, 0, (long)m - l + 1, threads, out, cap);
+}
+
+/* The motifs lying in B(x, d) for the seeds x = s_1[j..j+l-1], j in
+ * [seed_lo, seed_hi): a bounded slice of oracle_solve's work. */
+long oracle_solve_seeds(const uint8_t *seqs, int n, int m, int l, int d, long seed_lo,
+                        long seed_hi, int threads, uint64_t *out, long cap)
+{
+    return run_solver(seqs, n, m, l, d, 0, seed_lo, seed_hi, threads, out, cap);
+}
+
+/* The same motif set through pairs (x in S_1, r in S_2, d_H(x,r) <= 2d). */
+long oracle_solve_pairs(const uint8_t *seqs, int n, int m, int l, int d, int threads,
+                        uint64_t *out, long cap)
+{
+    return run_solver(seqs, n, m, l, d, 1, 0, (long)m - l + 1, threads, out, cap);
+}
+
+/* Pattern-driven exhaustive search ("Exact PMS Algorithms", pattern driven
+ * approach): test all 4^l strings. Only for tiny l. */
+long oracle_bruteforce(const uint8_t *seqs, int n, int m, int l, int d, uint64_t *out, long cap)
+{
+    if (!valid_input(seqs, n, m, l, d) || l > 12)
+        return ORACLE_EINVAL;
+    keyvec kv = {0};
+    uint8_t cand[32];
+    uint64_t total = (uint64_t)1 << (2 * l);
+    for (uint64_t key = 0; key < total; ++key) {
+        oracle_decode(key, l, cand);
+        if (oracle_is_motif(cand, l, d, seqs, n, m))
+            kv_push(&kv, key);
+    }
+    return kv_finish(&kv, out, cap);
+}
