@@ -1,0 +1,172 @@
+/*
+ * pms.h -- C ABI of the GB300 library for exact planted (l,d)-motif search.
+ *
+ * The problem (paper: "Formal Definitions of qPMS", Definitions 1-5 and the
+ * qPMS definition with quorum q = n, i.e. the PMS problem): given n DNA
+ * sequences s_1..s_n of length m and integers l, d, report every l-mer M over
+ * {A,C,G,T} such that each s_i has an l-mer (a window s_i[j..j+l-1]) within
+ * Hamming distance d of M.
+ *
+ * All entry points return 0 (PMS_OK) or a negative PMS_E* code; none throws
+ * or aborts. A context is used by one call at a time (calls on one context
+ * are serialised by an internal mutex); distinct contexts are independent.
+ *
+ * Sequences are passed as row-major n x m arrays of the ASCII bytes 'A', 'C',
+ * 'G', 'T' (any other byte is PMS_EINVAL). Motifs are returned as 64-bit
+ * codes, 2 bits per base (A=0, C=1, G=2, T=3, the order of the paper's
+ * compression example), position 0 in the most significant used bits, so
+ * ascending codes are lexicographic order; pms_decode turns one back into
+ * text. Every motif set is returned sorted ascending and without duplicates.
+ *
+ * Limits of this build: 1 <= l <= 32 (one 32-bit word per bit-plane),
+ * 0 <= d < l, 1 <= n <= 64, l <= m <= 65536.
+ */
+#ifndef PMS_H
+#define PMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PMS_OK 0
+#define PMS_EINVAL (-1)    /* bad argument or a byte that is not A/C/G/T */
+#define PMS_ENOMEM (-2)    /* device memory budget or allocation exhausted */
+#define PMS_ECUDA (-3)     /* a CUDA call failed; pms_last_error has the text */
+#define PMS_ETIMEDOUT (-4) /* pms_wait: the ticket did not complete in time */
+#define PMS_ETOOMANY (-5)  /* more motifs (with duplicates) than the result
+                              capacity; count still holds the raw count */
+#define PMS_EBUSY (-6)     /* the served queue is full */
+#define PMS_ENOTFOUND (-7) /* unknown or already released ticket */
+
+#define PMS_LMAX 32
+#define PMS_NMAX 64
+
+typedef struct pms_ctx pms_ctx;
+
+/* One problem instance. seqs: host memory, row-major n x m ASCII. */
+typedef struct {
+    const uint8_t *seqs;
+    int n, m, l, d;
+} pms_instance;
+
+/* The answer for one instance. motifs points into memory owned by the
+ * context (pms_solve, pms_solve_batch: valid until the next solve call on
+ * the context or pms_destroy) or by the ticket (pms_wait: valid until
+ * pms_release of that ticket or pms_destroy). */
+typedef struct {
+    int status;             /* PMS_OK or a negative code for this instance */
+    const uint64_t *motifs; /* sorted unique motif codes */
+    size_t count;           /* number of motifs (raw count on PMS_ETOOMANY) */
+} pms_result;
+
+/* Tunables. Zero in any field selects the default (or the tuned value). */
+typedef struct {
+    int ctas_per_sm;       /* resident CTAs of the verification kernel per SM */
+    int chunk_work;        /* target work of one queue item, in candidate units */
+    int grab;              /* subsets a warp takes from a chunk at a time */
+    size_t max_motifs;     /* raw motif capacity per instance (rounded to 2^k) */
+    int count_work;        /* 1: also count comparisons (slower; for profiling) */
+    int serve_wave_items;  /* served form: queue items per wave launch */
+    int serve_max_inflight;/* served form: requests resident on the device */
+} pms_options;
+
+/* Work counters of the last solve (pms_solve / pms_solve_device /
+ * pms_solve_batch). The comparison counters are filled only when
+ * pms_options.count_work was set for that solve. */
+typedef struct {
+    uint64_t candidates;        /* size of the searched space: sum over seeds of |B(x,d)| */
+    uint64_t subsets;           /* position subsets visited (tree nodes at which substitutions start) */
+    uint64_t subsets_pruned;    /* subsets dismissed by the feasible-occurrence bound */
+    uint64_t candidates_tested; /* candidates compared explicitly against occurrences */
+    uint64_t cmp_rows;          /* l-mer comparisons building feasible-occurrence rows */
+    uint64_t cmp_reduce;        /* comparisons applying the subset bound to rows */
+    uint64_t cmp_verify;        /* candidate-versus-occurrence comparisons */
+    uint64_t seeds_infeasible;  /* seeds with an empty row (no motif possible) */
+    double ms_total;            /* wall time of the call, host clock */
+    double ms_kernel;           /* device time from the first to the last kernel */
+    double ms_verify;           /* device time of the verification kernel alone */
+} pms_stats;
+
+/* Creates a context on CUDA device `device`. mem_budget_bytes caps the device
+ * memory the context may hold (0 = no cap beyond the device's). The context
+ * owns a CUDA stream until pms_set_stream replaces it. */
+int pms_create(pms_ctx **out, int device, size_t mem_budget_bytes);
+
+/* Issue all further work on `cuda_stream` (a cudaStream_t, e.g. a PyTorch
+ * stream's handle); NULL returns to the context's own stream. */
+int pms_set_stream(pms_ctx *h, void *cuda_stream);
+
+/* Route the context's device allocations through alloc/free (e.g. a caching
+ * allocator). alloc(bytes, user) returns a device pointer or NULL;
+ * free_(ptr, user) releases it. Must be called before the first solve. */
+int pms_set_allocator(pms_ctx *h, void *(*alloc)(size_t bytes, void *user),
+                      void (*free_)(void *ptr, void *user), void *user);
+
+int pms_set_options(pms_ctx *h, const pms_options *opt);
+int pms_get_options(const pms_ctx *h, pms_options *opt);
+
+/* Solves one instance from host memory (Definitions 1-5 with q = n; the
+ * candidate set is the union of B(x, d) over the l-mers x of s_1,
+ * Observation 3.1). seqs: host, read only during the call. On success
+ * *motifs points to *count sorted unique codes owned by h (valid until the
+ * next solve on h or pms_destroy). Blocks until the result is on the host. */
+int pms_solve(pms_ctx *h, const uint8_t *seqs, int n, int m, int l, int d,
+              const uint64_t **motifs, size_t *count);
+
+/* Device-resident form of pms_solve: d_seqs is a device pointer to n*m
+ * ASCII bytes; the sorted unique codes are written to d_motifs (device,
+ * room for `capacity` codes) and d_status (device, 4 x uint32) receives
+ * {raw count, unique count, flags, 0}; flags bit 0 = invalid byte in the
+ * input, bit 1 = raw motifs exceeded the context's max_motifs. Enqueued on
+ * the context's stream; returns without waiting. Inputs are read and outputs
+ * written only by kernels on that stream. */
+int pms_solve_device(pms_ctx *h, const uint8_t *d_seqs, int n, int m, int l, int d,
+                     uint64_t *d_motifs, size_t capacity, uint32_t *d_status);
+
+/* Solves k independent instances in one pass: one upload, one packing
+ * launch, one persistent verification launch whose CTAs take (instance,
+ * seed, chunk) items from a device work queue, one segmented sort/unique
+ * launch, one download. out[i] receives instance i's result (memory owned
+ * by h as for pms_solve). Returns PMS_OK if the batch ran; per-instance
+ * errors are in out[i].status. */
+int pms_solve_batch(pms_ctx *h, const pms_instance *inst, int k, pms_result *out);
+
+/* Served form (continuous batching). pms_submit copies the instance and
+ * returns a ticket at once; a scheduler thread admits requests while the
+ * device-memory budget allows, and every verification wave launched takes
+ * queue items from all admitted requests, so work of requests arriving
+ * while others run overlaps on the device. pms_wait blocks up to timeout_ms
+ * (negative: no limit) for the ticket's result; PMS_ETIMEDOUT leaves the
+ * ticket valid. pms_release frees a completed ticket's result. */
+int pms_submit(pms_ctx *h, const pms_instance *inst, uint64_t *ticket);
+int pms_wait(pms_ctx *h, uint64_t ticket, int timeout_ms, pms_result *out);
+int pms_release(pms_ctx *h, uint64_t ticket);
+
+/* Work counters and timing of the last solve (waits for that solve's
+ * kernels if they are still running). */
+int pms_get_stats(const pms_ctx *h, pms_stats *out);
+
+/* Writes the l letters of `code` and a terminating NUL to out (l + 1 bytes). */
+int pms_decode(uint64_t code, int l, char *out);
+
+/* Text of the last error on h (empty string if none); valid until the next
+ * call on h. */
+const char *pms_last_error(const pms_ctx *h);
+
+/* Measures the issue rate of one integer instruction class on the context's
+ * device with a dedicated probe kernel: kind 0 = POPC, 1 = LOP3, 2 = IADD3,
+ * 3 = IMNMX (min). *per_clk_per_sm receives results per SM per SM clock
+ * (thread-level operations), from `clock64` deltas inside the kernel. */
+int pms_probe_int_rate(pms_ctx *h, int kind, double *per_clk_per_sm);
+
+/* Releases the context, its device memory, stream and scheduler thread. */
+void pms_destroy(pms_ctx *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMS_H */

@@ -1,0 +1,96 @@
+// pms_internal.h -- device data layout shared by the kernels (pms_kernels.cu)
+// and the host runtime (pms_runtime.cu). Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pms {
+
+constexpr int kLMax = 32;      // one 32-bit word per bit-plane
+constexpr int kNMax = 64;      // sequences per instance
+constexpr int kWarps = 8;      // warps per CTA of the verification kernel
+constexpr int kThreads = kWarps * 32;
+constexpr int kRbCap = 256;    // entries of a subset-reduced occurrence row kept in shared memory
+constexpr int kListCap = 512;  // surviving candidates a warp buffers before checking further rows
+
+// Flags reported per instance.
+constexpr uint32_t kFlagInvalidByte = 1u;
+constexpr uint32_t kFlagOverflow = 2u;
+
+// One instance as the kernels see it. Offsets index the arenas below.
+struct InstDev {
+    int n, m, l, d;
+    int W;                 // windows per sequence: m - l + 1
+    int cps;               // queue chunks per seed
+    int grab;              // subsets a warp claims at a time
+    int ctab;              // offset (ints) of this instance's table in the chunk arena:
+                           //   levoff[0..d+1] then cps pairs (g0, g1)
+    long long seq_off;     // byte offset of the n x m input bytes in the sequence arena
+    long long plane_off;   // offset (uint2) of the n x W window planes
+    long long raw_off;     // offset (uint64) of the raw motif buffer
+    uint32_t raw_cap;      // capacity of the raw motif buffer (power of two)
+    int pad;
+};
+
+// A contiguous range of queue items: chunks [chunk_lo, chunk_hi) of instance
+// `inst`; work_lo is the global item index of chunk_lo.
+struct Segment {
+    long long work_lo;
+    int inst;
+    int chunk_lo, chunk_hi;
+    int pad;
+};
+
+// Per-instance status written by the sort/unique kernel.
+struct StatusDev {
+    uint32_t raw_count;    // motifs emitted, duplicates included
+    uint32_t unique_count; // motifs after sort/unique (written to the dense output)
+    uint32_t flags;
+    uint32_t dense_off;    // first code of this instance in the dense output
+};
+
+// Work counters (count mode), indices into a uint64 array.
+enum Counter {
+    kCntSubsets = 0,
+    kCntPruned,
+    kCntTested,
+    kCntCmpRows,
+    kCntCmpReduce,
+    kCntCmpVerify,
+    kCntSeedsInfeasible,
+    kCntNum
+};
+
+struct MainParams {
+    const InstDev *inst;
+    const Segment *seg;
+    int nseg;
+    long long total;              // queue items in this launch
+    unsigned long long *head;     // queue head (zeroed before the launch)
+    const uint2 *planes;
+    const int *ctab;
+    uint64_t *raw;                // raw motif codes
+    uint32_t *raw_count;          // per instance
+    uint32_t *flags;              // per instance
+    uint32_t *scratch;            // per CTA: 3 * rows_cap words (D, H, L)
+    int rows_cap;                 // max (n - 1) * W over the instances
+    unsigned long long *counters; // kCntNum entries (count mode)
+    int *done;                    // per segment: finished items (served form), may be null
+};
+
+// Launch wrappers (pms_kernels.cu).
+cudaError_t launch_pack(const InstDev *inst, int ninst, const long long *win_prefix, long long total_windows,
+                        const uint8_t *seqs, uint2 *planes, uint32_t *flags, int blocks, cudaStream_t st);
+cudaError_t launch_main(const MainParams &p, int blocks, bool count_mode, cudaStream_t st);
+cudaError_t main_occupancy(int *blocks_per_sm, bool count_mode);
+size_t main_smem_bytes();
+cudaError_t launch_sort_unique(const InstDev *inst, const int *inst_list, int nlist, uint64_t *raw,
+                               const uint32_t *raw_count, const uint32_t *flags, StatusDev *status,
+                               uint64_t *dense, uint32_t dense_cap, uint32_t *dense_total,
+                               cudaStream_t st);
+cudaError_t init_tables();
+cudaError_t launch_probe(int kind, int iters, int blocks, unsigned long long *cycles, unsigned long long *sink,
+                         cudaStream_t st);
+
+}  // namespace pms

@@ -1,0 +1,746 @@
+// pms_kernels.cu -- sm_103a kernels of the exact planted (l,d)-motif search.
+//
+// Method (the paper's chapter "Our Approach" and the algorithms it builds on):
+//   * every l-mer is held as two 32-bit bit-planes (bit 1 and bit 0 of the
+//     A0 C1 G2 T3 codes, position k in bit k); the Hamming distance of two
+//     l-mers is popc((a.hi ^ b.hi) | (a.lo ^ b.lo)) (Sec. "String Compression");
+//   * candidates are the strings of B(x, d) for the l-mers x of s_1
+//     (Observation 3.1 with q = n), explored as the tree T_d(x) of qPMSPrune:
+//     a node is the set P of changed positions, its leaves the 3^|P| choices
+//     of new letters;
+//   * for each seed x and sequence s_i (i >= 2) the feasible occurrences are
+//     the windows w with d_H(x, w) <= 2d (PMS8's pair-distance preprocessing;
+//     any motif within d of x can only be within d of such a window); rows are
+//     checked smallest first (PMS8: "sort rows by size");
+//   * a node P keeps only the occurrences with popc(D_w ^ P) <= d, where D_w
+//     is the mismatch mask of x and w: on P the candidate differs from x, so
+//     it mismatches w wherever w agrees with x, and off P it mismatches w
+//     wherever x does. A node with an empty reduced row has no motif among
+//     its 3^|P| leaves (the branch-and-bound of qPMSPrune, applied per node);
+//   * each surviving leaf is verified against the reduced rows with packed
+//     XOR/OR/popc, warp ballots compact the survivors between rows, and the
+//     motifs are appended with one atomic per warp, then sorted and
+//     de-duplicated per instance.
+#include "pms_internal.h"
+
+namespace pms {
+
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+__constant__ uint32_t c_binom[kLMax + 1][kLMax + 1];  // C(a, b), 0 when b > a
+__constant__ unsigned long long c_pow3[kLMax + 1];
+
+struct __align__(16) WarpSmem {
+    uint2 rb0[kRbCap + 4];   // row 0 reduced by the current subset
+    uint2 rb1[kRbCap + 4];   // scratch reduced row for rows 1..
+    uint2 list[kListCap];    // candidates that survived row 0
+};
+
+struct __align__(16) CtaSmem {
+    int row_len[kNMax];      // indexed by sequence
+    int row_order[kNMax];    // sequences 1..n-1, smallest row first
+    unsigned long long g;
+    int inst, seed, chunk;
+    int cached_inst, cached_seed;
+    int feasible;
+    int next;                // next subset index of the chunk to claim
+    int pad;
+};
+
+// Colex unranking of the rank-th k-subset of {0..l-1} (combinatorial number
+// system): bit c of the result is set for each chosen position c.
+__device__ __forceinline__ uint32_t unrank_subset(uint32_t rank, int k, int l)
+{
+    uint32_t P = 0;
+    int c = l - 1;
+    for (int j = k; j >= 1; --j) {
+        while (c_binom[c][j] > rank)
+            --c;
+        P |= 1u << c;
+        rank -= c_binom[c][j];
+        --c;
+    }
+    return P;
+}
+
+// Next k-subset in colex order (the next larger integer with the same number of set bits).
+__device__ __forceinline__ uint32_t next_subset(uint32_t P)
+{
+    const uint32_t u = P & (0u - P);
+    const uint32_t v = P + u;
+    return v | (((v ^ P) >> 2) >> (__ffs(P) - 1));
+}
+
+__device__ __forceinline__ uint64_t to_key(uint32_t h, uint32_t lo, int l)
+{
+    uint64_t key = 0;
+    for (int k = 0; k < l; ++k)
+        key = (key << 2) | (uint64_t)((((h >> k) & 1u) << 1) | ((lo >> k) & 1u));
+    return key;
+}
+
+// Keeps the occurrences of one row whose mismatch mask D satisfies
+// popc(D ^ P) <= d; writes up to kRbCap of them (planes) to rb, pads rb to a
+// multiple of 4 entries, and returns how many qualify.
+__device__ __forceinline__ int reduce_row(const uint32_t *__restrict__ D, const uint32_t *__restrict__ H,
+                                          const uint32_t *__restrict__ L, int len, uint32_t P, int d,
+                                          uint2 *rb, int lane, uint32_t lt)
+{
+    int k = 0;
+    for (int e0 = 0; e0 < len; e0 += 32) {
+        const int e = e0 + lane;
+        bool keep = false;
+        if (e < len)
+            keep = __popc(D[e] ^ P) <= d;
+        const uint32_t bal = __ballot_sync(kFull, keep);
+        if (keep) {
+            const int pos = k + __popc(bal & lt);
+            if (pos < kRbCap)
+                rb[pos] = make_uint2(H[e], L[e]);
+        }
+        k += __popc(bal);
+    }
+    __syncwarp();
+    if (k > 0 && k <= kRbCap && lane < 4)
+        rb[k + lane] = rb[k - 1];
+    __syncwarp();
+    return k;
+}
+
+// Is some entry of a reduced row (shared memory, padded to 4) within d of (ch, cl)?
+__device__ __forceinline__ bool check_smem(const uint2 *rb, int k, uint32_t ch, uint32_t cl, int d)
+{
+    int mn = 64;
+    for (int e = 0; e < k; e += 4) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(rb + e);
+        const uint4 b = *reinterpret_cast<const uint4 *>(rb + e + 2);
+        mn = min(mn, __popc((ch ^ a.x) | (cl ^ a.y)));
+        mn = min(mn, __popc((ch ^ a.z) | (cl ^ a.w)));
+        mn = min(mn, __popc((ch ^ b.x) | (cl ^ b.y)));
+        mn = min(mn, __popc((ch ^ b.z) | (cl ^ b.w)));
+    }
+    return mn <= d;
+}
+
+// Same test against a full (unreduced) row in global memory; used when the
+// reduced row does not fit in shared memory.
+__device__ __forceinline__ bool check_glob(const uint32_t *__restrict__ H, const uint32_t *__restrict__ L, int len,
+                                           uint32_t ch, uint32_t cl, int d)
+{
+    int mn = 64;
+    for (int e = 0; e < len; ++e)
+        mn = min(mn, __popc((ch ^ H[e]) | (cl ^ L[e])));
+    return mn <= d;
+}
+
+struct WarpCtx {
+    const MainParams *p;
+    InstDev in;
+    int I;
+    int lane;
+    uint32_t lt;
+    const uint32_t *rowD, *rowH, *rowL;
+    const CtaSmem *cs;
+    WarpSmem *ws;
+    unsigned long long *cnt;   // per-thread counters (count mode)
+};
+
+template <bool kCount>
+__device__ __forceinline__ void emit(const WarpCtx &c, const uint2 *list, int N)
+{
+    const MainParams &p = *c.p;
+    for (int b = 0; b < N; b += 32) {
+        const int idx = b + c.lane;
+        const bool has = idx < N;
+        uint64_t key = 0;
+        if (has) {
+            const uint2 v = list[idx];
+            key = to_key(v.x, v.y, c.in.l);
+        }
+        const uint32_t bal = __ballot_sync(kFull, has);
+        uint32_t base = 0;
+        if (c.lane == 0)
+            base = atomicAdd(&p.raw_count[c.I], (uint32_t)__popc(bal));
+        base = __shfl_sync(kFull, base, 0);
+        const uint32_t pos = base + __popc(bal & c.lt);
+        if (has) {
+            if (pos < c.in.raw_cap)
+                p.raw[c.in.raw_off + pos] = key;
+            else
+                atomicOr(&p.flags[c.I], kFlagOverflow);
+        }
+    }
+    __syncwarp();
+}
+
+// Checks the buffered candidates against rows 1.. (row 0 already passed),
+// compacting survivors in place; emits those that pass every row.
+template <bool kCount>
+__device__ __forceinline__ void finish_list(const WarpCtx &c, uint32_t P, int N)
+{
+    const InstDev &in = c.in;
+    const int nrows = in.n - 1;
+    uint2 *list = c.ws->list;
+    __syncwarp();
+    for (int r = 1; r < nrows && N > 0; ++r) {
+        const int ri = c.cs->row_order[r];
+        const int len = c.cs->row_len[ri];
+        const size_t off = (size_t)(ri - 1) * in.W;
+        const int k = reduce_row(c.rowD + off, c.rowH + off, c.rowL + off, len, P, in.d, c.ws->rb1, c.lane, c.lt);
+        if (kCount && c.lane == 0)
+            c.cnt[kCntCmpReduce] += len;
+        if (k == 0) {
+            N = 0;
+            break;
+        }
+        const bool sm = k <= kRbCap;
+        int newN = 0;
+        for (int b = 0; b < N; b += 32) {
+            const int idx = b + c.lane;
+            const bool alive = idx < N;
+            uint2 v = make_uint2(0u, 0u);
+            if (alive)
+                v = list[idx];
+            bool hit = false;
+            if (alive) {
+                hit = sm ? check_smem(c.ws->rb1, k, v.x, v.y, in.d)
+                         : check_glob(c.rowH + off, c.rowL + off, len, v.x, v.y, in.d);
+                if (kCount)
+                    c.cnt[kCntCmpVerify] += sm ? k : len;
+            }
+            __syncwarp();
+            const uint32_t bal = __ballot_sync(kFull, hit);
+            if (hit)
+                list[newN + __popc(bal & c.lt)] = v;
+            newN += __popc(bal);
+        }
+        __syncwarp();
+        N = newN;
+    }
+    if (N > 0)
+        emit<kCount>(c, list, N);
+}
+
+// One node of T_d(x): the subset P of changed positions (|P| = lev). Lanes
+// own the letter choices on the lowest min(lev, 3) positions of P (27 lanes
+// at most); every lane then walks the choices on the remaining positions
+// with a base-3 odometer kept as two masks (Dh, Dl) over those positions:
+// state (0,1) -> (1,0) -> (1,1) -> carry, i.e. XOR deltas 1, 2, 3.
+template <bool kCount>
+__device__ __forceinline__ void process_subset(const WarpCtx &c, uint32_t P, int lev, uint32_t xh, uint32_t xl)
+{
+    const InstDev &in = c.in;
+    const int d = in.d;
+    const int nrows = in.n - 1;
+    uint32_t t = P;
+    const uint32_t b0 = t & (0u - t);
+    t ^= b0;
+    const uint32_t b1 = t & (0u - t);
+    t ^= b1;
+    const uint32_t b2 = t & (0u - t);
+    t ^= b2;
+    const uint32_t Phi = t;
+    const int nlo = lev < 3 ? lev : 3;
+    const int nlanes = nlo == 0 ? 1 : (nlo == 1 ? 3 : (nlo == 2 ? 9 : 27));
+    const bool active = c.lane < nlanes;
+    const int dg0 = c.lane % 3, dg1 = (c.lane / 3) % 3, dg2 = (c.lane / 9) % 3;
+    const uint32_t DhLo = (dg0 >= 1 ? b0 : 0u) | (dg1 >= 1 ? b1 : 0u) | (dg2 >= 1 ? b2 : 0u);
+    const uint32_t DlLo = (dg0 != 1 ? b0 : 0u) | (dg1 != 1 ? b1 : 0u) | (dg2 != 1 ? b2 : 0u);
+    const uint32_t ch0 = xh ^ DhLo, cl0 = xl ^ DlLo;
+    const unsigned long long iters = c_pow3[lev - nlo];
+
+    if (kCount && c.lane == 0)
+        c.cnt[kCntSubsets] += 1;
+
+    int k0 = 0, len0 = 0;
+    size_t off0 = 0;
+    if (nrows > 0) {
+        const int r0 = c.cs->row_order[0];
+        len0 = c.cs->row_len[r0];
+        off0 = (size_t)(r0 - 1) * in.W;
+        k0 = reduce_row(c.rowD + off0, c.rowH + off0, c.rowL + off0, len0, P, d, c.ws->rb0, c.lane, c.lt);
+        if (kCount && c.lane == 0)
+            c.cnt[kCntCmpReduce] += len0;
+        if (k0 == 0) {
+            if (kCount && c.lane == 0)
+                c.cnt[kCntPruned] += 1;
+            return;
+        }
+    }
+    const bool sm0 = k0 <= kRbCap;
+    uint2 *list = c.ws->list;
+    uint32_t Dh = 0u, Dl = Phi;
+    int listN = 0;
+    for (unsigned long long it = 0; it < iters; ++it) {
+        const uint32_t ch = ch0 ^ Dh, cl = cl0 ^ Dl;
+        bool hit = false;
+        if (active) {
+            if (nrows == 0)
+                hit = true;
+            else
+                hit = sm0 ? check_smem(c.ws->rb0, k0, ch, cl, d)
+                          : check_glob(c.rowH + off0, c.rowL + off0, len0, ch, cl, d);
+            if (kCount) {
+                c.cnt[kCntTested] += 1;
+                c.cnt[kCntCmpVerify] += sm0 ? k0 : len0;
+            }
+        }
+        const uint32_t bal = __ballot_sync(kFull, hit);
+        if (bal) {
+            if (hit)
+                list[listN + __popc(bal & c.lt)] = make_uint2(ch, cl);
+            listN += __popc(bal);
+            if (listN > kListCap - 32) {
+                finish_list<kCount>(c, P, listN);
+                listN = 0;
+            }
+        }
+        const uint32_t both = Dh & Dl;
+        const uint32_t open = Phi & ~both;
+        const uint32_t q = open & (0u - open);
+        const uint32_t below = Phi & (q - 1u);
+        Dh = (Dh & ~below) | q;
+        Dl = (Dl | below) ^ q;
+    }
+    if (listN > 0)
+        finish_list<kCount>(c, P, listN);
+}
+
+// Builds the feasible-occurrence rows of seed x for sequences 1..n-1 into
+// this CTA's scratch, records their sizes and the smallest-first order.
+__device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &in, int seed, CtaSmem &cs,
+                                           uint32_t *rowD, uint32_t *rowH, uint32_t *rowL, int warp, int lane,
+                                           uint32_t lt, unsigned long long *cnt, bool count_mode)
+{
+    const uint2 *pl = p.planes + in.plane_off;
+    const uint2 x = pl[seed];
+    const int W = in.W, n = in.n, lim = 2 * in.d;
+    for (int i = 1 + warp; i < n; i += kWarps) {
+        const uint2 *s = pl + (size_t)i * W;
+        uint32_t *Dr = rowD + (size_t)(i - 1) * W;
+        uint32_t *Hr = rowH + (size_t)(i - 1) * W;
+        uint32_t *Lr = rowL + (size_t)(i - 1) * W;
+        int k = 0;
+        for (int w0 = 0; w0 < W; w0 += 32) {
+            const int w = w0 + lane;
+            bool keep = false;
+            uint32_t dm = 0;
+            uint2 e = make_uint2(0u, 0u);
+            if (w < W) {
+                e = s[w];
+                dm = (x.x ^ e.x) | (x.y ^ e.y);
+                keep = __popc(dm) <= lim;
+            }
+            const uint32_t bal = __ballot_sync(kFull, keep);
+            if (keep) {
+                const int pos = k + __popc(bal & lt);
+                Dr[pos] = dm;
+                Hr[pos] = e.x;
+                Lr[pos] = e.y;
+            }
+            k += __popc(bal);
+        }
+        if (lane == 0) {
+            cs.row_len[i] = k;
+            if (count_mode && cnt)
+                cnt[kCntCmpRows] += W;
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        bool empty = false;
+        for (int i = 1 + lane; i < n; i += 32) {
+            const int li = cs.row_len[i];
+            empty |= li == 0;
+            int rank = 0;
+            for (int j = 1; j < n; ++j) {
+                const int lj = cs.row_len[j];
+                rank += (lj < li) || (lj == li && j < i);
+            }
+            cs.row_order[rank] = i;
+        }
+        const bool any_empty = __any_sync(kFull, empty);
+        if (lane == 0)
+            cs.feasible = !any_empty;
+    }
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpSmem *wsm = reinterpret_cast<WarpSmem *>(smem_raw);
+    CtaSmem &cs = *reinterpret_cast<CtaSmem *>(smem_raw + kWarps * sizeof(WarpSmem));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t *rowD = p.scratch + (size_t)blockIdx.x * 3 * (size_t)p.rows_cap;
+    uint32_t *rowH = rowD + p.rows_cap;
+    uint32_t *rowL = rowH + p.rows_cap;
+    unsigned long long cnt[kCount ? kCntNum : 1];
+#pragma unroll
+    for (int i = 0; i < (kCount ? kCntNum : 1); ++i)
+        cnt[i] = 0;
+
+    if (threadIdx.x == 0) {
+        cs.cached_inst = -1;
+        cs.cached_seed = -1;
+        cs.feasible = 0;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned long long g = atomicAdd(p.head, 1ull);
+            cs.g = g;
+            if (g < (unsigned long long)p.total) {
+                int lo = 0, hi = p.nseg - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (p.seg[mid].work_lo <= (long long)g)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                const Segment s = p.seg[lo];
+                const int cidx = s.chunk_lo + (int)((long long)g - s.work_lo);
+                const int cps = p.inst[s.inst].cps;
+                cs.inst = s.inst;
+                cs.seed = cidx / cps;
+                cs.chunk = cidx % cps;
+            }
+        }
+        __syncthreads();
+        if (cs.g >= (unsigned long long)p.total)
+            break;
+        const int I = cs.inst, seed = cs.seed, chunk = cs.chunk;
+        const InstDev in = p.inst[I];
+        const bool rebuild = (I != cs.cached_inst) || (seed != cs.cached_seed);
+        if (rebuild) {
+            build_rows(p, in, seed, cs, rowD, rowH, rowL, warp, lane, lt, kCount ? cnt : nullptr, kCount);
+            if (threadIdx.x == 0) {
+                cs.cached_inst = I;
+                cs.cached_seed = seed;
+            }
+        }
+        const int *tab = p.ctab + in.ctab;
+        const int g0 = tab[in.d + 2 + 2 * chunk];
+        const int g1 = tab[in.d + 2 + 2 * chunk + 1];
+        if (threadIdx.x == 0)
+            cs.next = g0;
+        __syncthreads();
+        if constexpr (kCount) {
+            if (threadIdx.x == 0 && chunk == 0 && !cs.feasible)
+                cnt[kCntSeedsInfeasible] += 1;
+        }
+        if (cs.feasible) {
+            const uint2 x = p.planes[in.plane_off + seed];
+            WarpCtx c{&p, in, I, lane, lt, rowD, rowH, rowL, &cs, &wsm[warp], kCount ? cnt : nullptr};
+            for (;;) {
+                int start = 0;
+                if (lane == 0)
+                    start = atomicAdd(&cs.next, in.grab);
+                start = __shfl_sync(kFull, start, 0);
+                if (start >= g1)
+                    break;
+                const int end = min(start + in.grab, g1);
+                int idx = start;
+                while (idx < end) {
+                    int lev = 0;
+                    while (tab[lev + 1] <= idx)
+                        ++lev;
+                    const int stop = min(end, tab[lev + 1]);
+                    uint32_t P = unrank_subset((uint32_t)(idx - tab[lev]), lev, in.l);
+                    for (int k = idx; k < stop; ++k) {
+                        process_subset<kCount>(c, P, lev, x.x, x.y);
+                        if (k + 1 < stop)
+                            P = next_subset(P);
+                    }
+                    idx = stop;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if constexpr (kCount) {
+#pragma unroll
+        for (int i = 0; i < kCntNum; ++i) {
+            unsigned long long v = cnt[i];
+            for (int o = 16; o > 0; o >>= 1)
+                v += __shfl_xor_sync(kFull, v, o);
+            if (lane == 0 && v)
+                atomicAdd(&p.counters[i], v);
+        }
+    }
+}
+
+// Window planes for every (instance, sequence, window); flags bytes that are not A/C/G/T.
+__global__ void pack_kernel(const InstDev *__restrict__ inst, int ninst, const long long *__restrict__ win_prefix,
+                            long long total, const uint8_t *__restrict__ seqs, uint2 *__restrict__ planes,
+                            uint32_t *__restrict__ flags)
+{
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = ninst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (win_prefix[mid] <= q)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const InstDev in = inst[lo];
+        const long long local = q - win_prefix[lo];
+        const int i = (int)(local / in.W), w = (int)(local % in.W);
+        const uint8_t *s = seqs + in.seq_off + (size_t)i * in.m + w;
+        uint32_t h = 0, lo_bits = 0;
+        bool bad = false;
+        for (int k = 0; k < in.l; ++k) {
+            const uint32_t ch = s[k];
+            bad |= !(ch == 'A' || ch == 'C' || ch == 'G' || ch == 'T');
+            const uint32_t code = ((ch >> 1) ^ (ch >> 2)) & 3u;  // A0 C1 G2 T3
+            h |= (code >> 1) << k;
+            lo_bits |= (code & 1u) << k;
+        }
+        planes[in.plane_off + local] = make_uint2(h, lo_bits);
+        if (bad)
+            atomicOr(&flags[lo], kFlagInvalidByte);
+    }
+}
+
+constexpr int kSortThreads = 1024;
+constexpr uint32_t kSortSmemKeys = 8192;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_tot, uint32_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    uint32_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o)
+            incl += y;
+    }
+    if (lane == 31)
+        warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = lane < nw ? warp_tot[lane] : 0u;
+        uint32_t ti = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, ti, o);
+            if (lane >= o)
+                ti += y;
+        }
+        if (lane < nw)
+            warp_tot[lane] = ti - t;
+        if (lane == 31)
+            *total = ti;
+    }
+    __syncthreads();
+    const uint32_t r = warp_tot[warp] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+// One CTA per instance: bitonic sort of the raw codes (shared memory when
+// they fit, else in place in global memory), then duplicates removed and the
+// unique codes appended to the dense output.
+__global__ void __launch_bounds__(kSortThreads)
+    sort_unique_kernel(const InstDev *__restrict__ inst, const int *__restrict__ inst_list, uint64_t *raw,
+                       const uint32_t *__restrict__ raw_count, const uint32_t *__restrict__ flags,
+                       StatusDev *__restrict__ status, uint64_t *__restrict__ dense, uint32_t dense_cap,
+                       uint32_t *dense_total)
+{
+    extern __shared__ __align__(16) uint64_t sk[];
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t s_total, s_base, s_run;
+    const int I = inst_list ? inst_list[blockIdx.x] : (int)blockIdx.x;
+    const InstDev in = inst[I];
+    const uint32_t rc = raw_count[I];
+    const uint32_t n = rc < in.raw_cap ? rc : in.raw_cap;
+    uint64_t *a = raw + in.raw_off;
+    uint32_t P2 = 1;
+    while (P2 < n)
+        P2 <<= 1;
+    const bool in_smem = P2 <= kSortSmemKeys;
+    uint64_t *buf = in_smem ? sk : a;
+    for (uint32_t i = threadIdx.x; i < P2; i += blockDim.x)
+        buf[i] = i < n ? a[i] : ~0ull;
+    __syncthreads();
+    for (uint32_t k = 2; k <= P2; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < P2; i += blockDim.x) {
+                const uint32_t ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t x = buf[i], y = buf[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) {
+                        buf[i] = y;
+                        buf[ixj] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    uint32_t local = 0;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+        local += (i == 0 || buf[i] != buf[i - 1]) ? 1u : 0u;
+    (void)block_exclusive_scan(local, warp_tot, &s_total);
+    if (threadIdx.x == 0) {
+        const uint32_t base = atomicAdd(dense_total, s_total);
+        s_base = base;
+        s_run = 0;
+        uint32_t f = flags[I];
+        if (rc > in.raw_cap || base + s_total > dense_cap)
+            f |= kFlagOverflow;
+        status[I] = StatusDev{rc, s_total, f, base};
+    }
+    __syncthreads();
+    for (uint32_t t0 = 0; t0 < n; t0 += blockDim.x) {
+        const uint32_t i = t0 + threadIdx.x;
+        const bool keep = i < n && (i == 0 || buf[i] != buf[i - 1]);
+        const uint32_t ex = block_exclusive_scan(keep ? 1u : 0u, warp_tot, &s_total);
+        const uint32_t pos = s_base + s_run + ex;
+        if (keep && pos < dense_cap)
+            dense[pos] = buf[i];
+        __syncthreads();
+        if (threadIdx.x == 0)
+            s_run += s_total;
+        __syncthreads();
+    }
+}
+
+// Integer pipe probe: each thread runs 8 independent chains of one
+// instruction class; thread 0 of each CTA records the SM clock cycles the
+// loop took between two CTA barriers.
+template <int kKind>
+__global__ void __launch_bounds__(1024) probe_kernel(int iters, unsigned long long *cycles, unsigned long long *sink)
+{
+    uint32_t a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+        a[u] = threadIdx.x * 2654435761u + u * 40503u + blockIdx.x;
+    const uint32_t b = blockIdx.x | 0x01010101u, c2 = threadIdx.x | 0x10000001u;
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (kKind == 0) {
+                    a[u] = __popc(a[u]) + a[u];           // POPC + IADD chain
+                } else if (kKind == 1) {
+                    a[u] = (a[u] ^ b) | (a[u] & c2);      // LOP3 chain
+                } else if (kKind == 2) {
+                    a[u] = a[u] + b + c2;                 // IADD3 chain
+                } else {
+                    // one l-mer comparison as in the verification loop
+                    a[u] = min(a[u], (uint32_t)__popc((b ^ a[(u + 1) & 7]) | (c2 ^ a[(u + 3) & 7])) + (uint32_t)i);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    uint32_t s = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+        s ^= a[u];
+    if (s == 0x12345678u)
+        atomicAdd(sink, 1ull);
+    if (threadIdx.x == 0)
+        cycles[blockIdx.x] = (unsigned long long)(t1 - t0);
+}
+
+}  // namespace
+
+cudaError_t init_tables()
+{
+    uint32_t binom[kLMax + 1][kLMax + 1] = {};
+    for (int a = 0; a <= kLMax; ++a) {
+        binom[a][0] = 1;
+        for (int b = 1; b <= a; ++b)
+            binom[a][b] = binom[a - 1][b - 1] + (b <= a - 1 ? binom[a - 1][b] : 0u);
+    }
+    unsigned long long pow3[kLMax + 1];
+    pow3[0] = 1;
+    for (int i = 1; i <= kLMax; ++i)
+        pow3[i] = pow3[i - 1] * 3ull;
+    cudaError_t e = cudaMemcpyToSymbol(c_binom, binom, sizeof(binom));
+    if (e != cudaSuccess)
+        return e;
+    return cudaMemcpyToSymbol(c_pow3, pow3, sizeof(pow3));
+}
+
+size_t main_smem_bytes()
+{
+    return kWarps * sizeof(WarpSmem) + sizeof(CtaSmem);
+}
+
+cudaError_t main_occupancy(int *blocks_per_sm, bool count_mode)
+{
+    const size_t smem = main_smem_bytes();
+    cudaError_t e;
+    if (count_mode) {
+        e = cudaFuncSetAttribute(main_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel<true>, kThreads, smem);
+    }
+    e = cudaFuncSetAttribute(main_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel<false>, kThreads, smem);
+}
+
+cudaError_t launch_main(const MainParams &p, int blocks, bool count_mode, cudaStream_t st)
+{
+    const size_t smem = main_smem_bytes();
+    if (count_mode)
+        main_kernel<true><<<blocks, kThreads, smem, st>>>(p);
+    else
+        main_kernel<false><<<blocks, kThreads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const InstDev *inst, int ninst, const long long *win_prefix, long long total_windows,
+                        const uint8_t *seqs, uint2 *planes, uint32_t *flags, int blocks, cudaStream_t st)
+{
+    pack_kernel<<<blocks, 256, 0, st>>>(inst, ninst, win_prefix, total_windows, seqs, planes, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_unique(const InstDev *inst, const int *inst_list, int nlist, uint64_t *raw,
+                               const uint32_t *raw_count, const uint32_t *flags, StatusDev *status,
+                               uint64_t *dense, uint32_t dense_cap, uint32_t *dense_total, cudaStream_t st)
+{
+    const size_t smem = kSortSmemKeys * sizeof(uint64_t);
+    static thread_local int attr_set_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_set_dev != dev) {
+        cudaError_t e = cudaFuncSetAttribute(sort_unique_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        attr_set_dev = dev;
+    }
+    sort_unique_kernel<<<nlist, kSortThreads, smem, st>>>(inst, inst_list, raw, raw_count, flags, status, dense,
+                                                          dense_cap, dense_total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probe(int kind, int iters, int blocks, unsigned long long *cycles, unsigned long long *sink,
+                         cudaStream_t st)
+{
+    switch (kind) {
+    case 0: probe_kernel<0><<<blocks, 1024, 0, st>>>(iters, cycles, sink); break;
+    case 1: probe_kernel<1><<<blocks, 1024, 0, st>>>(iters, cycles, sink); break;
+    case 2: probe_kernel<2><<<blocks, 1024, 0, st>>>(iters, cycles, sink); break;
+    default: probe_kernel<3><<<blocks, 1024, 0, st>>>(iters, cycles, sink); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pms

@@ -1,0 +1,874 @@
+// pms_runtime.cu -- host runtime behind the C ABI of include/pms.h:
+// contexts, device-memory budget and arenas, plan building (queue chunks),
+// the plain / device-resident / batched solves and the served scheduler.
+#include "pms_internal.h"
+#include "../../include/pms.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+using namespace pms;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kDefaultMaxMotifs = size_t(1) << 20;      // single-instance solves
+constexpr size_t kDefaultBatchMaxMotifs = size_t(1) << 16; // per instance of a batch
+constexpr int kDefaultChunkWork = 1 << 16;
+constexpr uint32_t kInlineKeys = 512;   // codes downloaded together with the status block
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+uint32_t pow2_at_least(size_t v)
+{
+    uint32_t p = 1;
+    while (p < v && p < (1u << 31))
+        p <<= 1;
+    return p;
+}
+
+double now_ms()
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+uint64_t binom(int a, int b)
+{
+    if (b < 0 || b > a)
+        return 0;
+    uint64_t r = 1;
+    for (int i = 1; i <= b; ++i)
+        r = r * (uint64_t)(a - b + i) / (uint64_t)i;
+    return r;
+}
+
+uint64_t ball_size(int l, int d)
+{
+    uint64_t s = 0, p3 = 1;
+    for (int i = 0; i <= d; ++i, p3 *= 3)
+        s += binom(l, i) * p3;
+    return s;
+}
+
+// The queue chunks of one seed for (l, d): levoff[0..d+1] (first subset index
+// of each level in the seed's subset sequence), then (g0, g1) ranges cut so
+// that each holds about `work` candidate units (3^|P| + a fixed cost per subset).
+struct ChunkTable {
+    std::vector<int> tab;
+    int cps = 0;
+};
+
+ChunkTable make_chunks(int l, int d, int work)
+{
+    ChunkTable ct;
+    std::vector<int> lev(d + 2, 0);
+    for (int i = 0; i <= d; ++i)
+        lev[i + 1] = lev[i] + (int)binom(l, i);
+    std::vector<int> cuts;
+    double acc = 0;
+    int start = 0, g = 0;
+    for (int i = 0; i <= d; ++i) {
+        const double w = std::pow(3.0, i) + 24.0;
+        long long remaining = (long long)binom(l, i);
+        while (remaining > 0) {
+            long long room = (long long)std::ceil(std::max(1.0, (work - acc) / w));
+            const long long take = std::min(room, remaining);
+            acc += take * w;
+            remaining -= take;
+            g += (int)take;
+            if (acc >= work) {
+                cuts.push_back(start);
+                cuts.push_back(g);
+                start = g;
+                acc = 0;
+            }
+        }
+    }
+    if (start < g) {
+        cuts.push_back(start);
+        cuts.push_back(g);
+    }
+    ct.tab = lev;
+    ct.tab.insert(ct.tab.end(), cuts.begin(), cuts.end());
+    ct.cps = (int)cuts.size() / 2;
+    return ct;
+}
+
+int default_grab(int d)
+{
+    uint64_t p3 = 1;
+    for (int i = 0; i < std::min(d, 8); ++i)
+        p3 *= 3;
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(32, 256 / p3));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------- context
+
+struct Served;
+
+struct pms_ctx {
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    void *(*ualloc)(size_t, void *) = nullptr;
+    void (*ufree)(void *, void *) = nullptr;
+    void *uuser = nullptr;
+    size_t budget = 0;     // 0: unlimited
+    size_t used = 0;
+    std::recursive_mutex mu;
+    std::string err;
+    pms_options opt{};
+    int num_sms = 0;
+    int occ[2] = {0, 0};   // CTAs per SM of the verification kernel (plain, count mode)
+    pms_stats stats{};
+    std::map<std::tuple<int, int, int>, ChunkTable> ctab_cache;
+
+    struct DBuf {
+        void *p = nullptr;
+        size_t cap = 0;
+    };
+    DBuf d_seqs, d_planes, d_raw, d_meta, d_ctr, d_scratch, d_result;
+    void *h_result = nullptr;   // pinned
+    size_t h_result_cap = 0;
+    void *h_meta = nullptr;     // pinned staging for descriptors and inputs
+    size_t h_meta_cap = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm0 = nullptr, evm1 = nullptr;
+    bool stats_pending = false;   // device times / counters of the last solve not read yet
+    bool stats_count = false;
+    size_t stats_k = 0;
+
+    std::vector<pms_result> batch_out;  // storage for pms_solve_batch results
+    Served *served = nullptr;
+
+    int fail(int code, const char *fmt, ...)
+    {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        err = buf;
+        return code;
+    }
+    int cuda_fail(cudaError_t e, const char *what)
+    {
+        return fail(e == cudaErrorMemoryAllocation ? PMS_ENOMEM : PMS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    }
+
+    void *dev_alloc(size_t bytes)
+    {
+        if (budget && used + bytes > budget)
+            return nullptr;
+        void *p = nullptr;
+        if (ualloc) {
+            p = ualloc(bytes, uuser);
+        } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        if (p)
+            used += bytes;
+        return p;
+    }
+    void dev_free(void *p, size_t bytes)
+    {
+        if (!p)
+            return;
+        if (ufree)
+            ufree(p, uuser);
+        else
+            cudaFree(p);
+        used -= bytes;
+    }
+    // Grow-only device buffer. Returns PMS_OK or PMS_ENOMEM.
+    int ensure(DBuf &b, size_t bytes)
+    {
+        bytes = round_up(std::max<size_t>(bytes, 1), kAlign);
+        if (b.cap >= bytes)
+            return PMS_OK;
+        if (b.p) {
+            cudaStreamSynchronize(stream);
+            dev_free(b.p, b.cap);
+            b.p = nullptr;
+            b.cap = 0;
+        }
+        const size_t want = std::max(bytes, (size_t)(bytes * 5 / 4));
+        void *p = dev_alloc(want);
+        if (!p) {
+            p = dev_alloc(bytes);
+            if (!p)
+                return fail(PMS_ENOMEM, "device allocation of %zu bytes refused (budget %zu, in use %zu)", bytes,
+                            budget, used);
+            b.cap = bytes;
+        } else {
+            b.cap = want;
+        }
+        b.p = p;
+        return PMS_OK;
+    }
+    int ensure_host(void *&p, size_t &cap, size_t bytes)
+    {
+        if (cap >= bytes)
+            return PMS_OK;
+        if (p) {
+            cudaStreamSynchronize(stream);
+            cudaFreeHost(p);
+            p = nullptr;
+            cap = 0;
+        }
+        bytes = round_up(std::max(bytes, cap * 2), 4096);
+        cudaError_t e = cudaHostAlloc(&p, bytes, cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return cuda_fail(e, "cudaHostAlloc");
+        }
+        cap = bytes;
+        return PMS_OK;
+    }
+
+    const ChunkTable &chunks(int l, int d)
+    {
+        const int work = opt.chunk_work > 0 ? opt.chunk_work : kDefaultChunkWork;
+        auto key = std::make_tuple(l, d, work);
+        auto it = ctab_cache.find(key);
+        if (it == ctab_cache.end())
+            it = ctab_cache.emplace(key, make_chunks(l, d, work)).first;
+        return it->second;
+    }
+};
+
+// Checks one instance's parameters. Returns PMS_OK or PMS_EINVAL (with text).
+static int check_params(pms_ctx *h, int n, int m, int l, int d)
+{
+    if (n < 1 || n > PMS_NMAX)
+        return h->fail(PMS_EINVAL, "n = %d outside [1, %d]", n, PMS_NMAX);
+    if (l < 1 || l > PMS_LMAX)
+        return h->fail(PMS_EINVAL, "l = %d outside [1, %d]", l, PMS_LMAX);
+    if (m < l || m > 65536)
+        return h->fail(PMS_EINVAL, "m = %d outside [l, 65536]", m);
+    if (d < 0 || d >= l)
+        return h->fail(PMS_EINVAL, "d = %d outside [0, l)", d);
+    uint64_t subsets = 0;
+    for (int i = 0; i <= d; ++i)
+        subsets += binom(l, i);
+    if (subsets > (uint64_t)INT32_MAX)
+        return h->fail(PMS_EINVAL, "(l, d) = (%d, %d): subset space too large", l, d);
+    return PMS_OK;
+}
+
+static int check_bytes(pms_ctx *h, const uint8_t *s, size_t len)
+{
+    for (size_t i = 0; i < len; ++i) {
+        const uint8_t c = s[i];
+        if (c != 'A' && c != 'C' && c != 'G' && c != 'T')
+            return h->fail(PMS_EINVAL, "byte %zu (0x%02x) is not one of A, C, G, T", i, c);
+    }
+    return PMS_OK;
+}
+
+// ------------------------------------------------------------------------- plan of one launch
+
+namespace {
+
+struct InstSpec {
+    int n, m, l, d;
+    const uint8_t *host_seqs;   // may be null (device-resident input)
+};
+
+// Host image of everything the kernels need for a set of instances.
+struct Plan {
+    std::vector<InstDev> inst;
+    std::vector<Segment> seg;
+    std::vector<long long> win_prefix;
+    std::vector<int> ctab;
+    long long total_items = 0;
+    long long total_windows = 0;
+    size_t seq_bytes = 0, planes = 0, raw = 0;
+    int rows_cap = 1;
+    uint64_t candidates = 0;
+};
+
+// Byte layout of the descriptor block (device d_meta, pinned h_meta).
+struct MetaLayout {
+    size_t inst, seg, win, ctab, total;
+    MetaLayout(const Plan &p)
+    {
+        size_t o = 0;
+        inst = o;
+        o = round_up(o + p.inst.size() * sizeof(InstDev), 16);
+        seg = o;
+        o = round_up(o + p.seg.size() * sizeof(Segment), 16);
+        win = o;
+        o = round_up(o + p.win_prefix.size() * sizeof(long long), 16);
+        ctab = o;
+        o = round_up(o + p.ctab.size() * sizeof(int), 16);
+        total = o;
+    }
+};
+
+// Counters block (d_ctr): head, work counters, dense_total, then per instance raw_count and flags.
+struct CtrLayout {
+    size_t head, work, dense_total, raw_count, flags, total;
+    CtrLayout(size_t k)
+    {
+        head = 0;
+        work = 8;
+        dense_total = work + kCntNum * 8;
+        raw_count = round_up(dense_total + 4, 16);
+        flags = round_up(raw_count + 4 * k, 16);
+        total = round_up(flags + 4 * k, 256);
+    }
+};
+
+// Result block (d_result): StatusDev per instance, then the dense codes.
+struct ResLayout {
+    size_t status, dense, total;
+    uint32_t dense_cap;
+    ResLayout(size_t k, size_t dense_keys)
+    {
+        status = 0;
+        dense = round_up(k * sizeof(StatusDev), 16);
+        dense_cap = (uint32_t)dense_keys;
+        total = dense + dense_keys * 8;
+    }
+};
+
+}  // namespace
+
+static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
+{
+    Plan P;
+    const size_t maxm = h->opt.max_motifs ? h->opt.max_motifs
+                                          : (specs.size() == 1 ? kDefaultMaxMotifs : kDefaultBatchMaxMotifs);
+    long long work = 0;
+    for (size_t k = 0; k < specs.size(); ++k) {
+        const InstSpec &s = specs[k];
+        InstDev in{};
+        in.n = s.n;
+        in.m = s.m;
+        in.l = s.l;
+        in.d = s.d;
+        in.W = s.m - s.l + 1;
+        const ChunkTable &ct = h->chunks(s.l, s.d);
+        in.cps = ct.cps;
+        in.grab = h->opt.grab > 0 ? h->opt.grab : default_grab(s.d);
+        in.ctab = (int)P.ctab.size();
+        P.ctab.insert(P.ctab.end(), ct.tab.begin(), ct.tab.end());
+        in.seq_off = (long long)P.seq_bytes;
+        P.seq_bytes += round_up((size_t)s.n * s.m, 16);
+        in.plane_off = (long long)P.planes;
+        P.planes += (size_t)s.n * in.W;
+        in.raw_off = (long long)P.raw;
+        in.raw_cap = pow2_at_least(maxm);
+        P.raw += in.raw_cap;
+        P.win_prefix.push_back(P.total_windows);
+        P.total_windows += (long long)s.n * in.W;
+        P.rows_cap = std::max(P.rows_cap, (s.n - 1) * in.W);
+        const int chunks = in.W * in.cps;
+        P.seg.push_back(Segment{work, (int)k, 0, chunks, 0});
+        work += chunks;
+        P.candidates += (uint64_t)in.W * ball_size(s.l, s.d);
+        P.inst.push_back(in);
+    }
+    P.total_items = work;
+    return P;
+}
+
+// Enqueues the whole pipeline of a plan on h->stream. d_seq_src: device
+// address of the input bytes (internal arena or user memory). Descriptors are
+// staged in h->h_meta and uploaded. Output: status/dense in the result block.
+static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, StatusDev *status_out,
+                        uint64_t *dense_out, uint32_t dense_cap, bool count_mode)
+{
+    const size_t k = P.inst.size();
+    MetaLayout ml(P);
+    CtrLayout cl(k);
+    int rc;
+    if ((rc = h->ensure(h->d_meta, ml.total)) || (rc = h->ensure(h->d_ctr, cl.total)) ||
+        (rc = h->ensure(h->d_planes, P.planes * sizeof(uint2))) || (rc = h->ensure(h->d_raw, P.raw * 8)))
+        return rc;
+    int occ = h->occ[count_mode ? 1 : 0];
+    if (h->opt.ctas_per_sm > 0)
+        occ = std::min(occ, h->opt.ctas_per_sm);
+    occ = std::max(occ, 1);
+    const long long blocks_ll = std::min<long long>((long long)h->num_sms * occ, std::max<long long>(P.total_items, 1));
+    const int blocks = (int)blocks_ll;
+    if ((rc = h->ensure(h->d_scratch, (size_t)blocks * 3 * (size_t)P.rows_cap * 4)))
+        return rc;
+    if ((rc = h->ensure_host(h->h_meta, h->h_meta_cap, ml.total)))
+        return rc;
+    // descriptors
+    char *hm = (char *)h->h_meta;
+    std::memcpy(hm + ml.inst, P.inst.data(), P.inst.size() * sizeof(InstDev));
+    std::memcpy(hm + ml.seg, P.seg.data(), P.seg.size() * sizeof(Segment));
+    std::memcpy(hm + ml.win, P.win_prefix.data(), P.win_prefix.size() * sizeof(long long));
+    std::memcpy(hm + ml.ctab, P.ctab.data(), P.ctab.size() * sizeof(int));
+    cudaStream_t st = h->stream;
+    char *dm = (char *)h->d_meta.p;
+    char *dc = (char *)h->d_ctr.p;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(dm, hm, ml.total, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return h->cuda_fail(e, "upload descriptors");
+    if ((e = cudaMemsetAsync(dc, 0, cl.total, st)) != cudaSuccess)
+        return h->cuda_fail(e, "clear counters");
+    const InstDev *d_inst = (const InstDev *)(dm + ml.inst);
+    uint32_t *d_flags = (uint32_t *)(dc + cl.flags);
+    uint32_t *d_rawcnt = (uint32_t *)(dc + cl.raw_count);
+    cudaEventRecord(h->ev0, st);
+    const int pack_blocks = (int)std::min<long long>((P.total_windows + 255) / 256, (long long)h->num_sms * 8);
+    if ((e = launch_pack(d_inst, (int)k, (const long long *)(dm + ml.win), P.total_windows, d_seq_src,
+                         (uint2 *)h->d_planes.p, d_flags, std::max(pack_blocks, 1), st)) != cudaSuccess)
+        return h->cuda_fail(e, "pack kernel");
+    MainParams mp{};
+    mp.inst = d_inst;
+    mp.seg = (const Segment *)(dm + ml.seg);
+    mp.nseg = (int)P.seg.size();
+    mp.total = P.total_items;
+    mp.head = (unsigned long long *)(dc + cl.head);
+    mp.planes = (const uint2 *)h->d_planes.p;
+    mp.ctab = (const int *)(dm + ml.ctab);
+    mp.raw = (uint64_t *)h->d_raw.p;
+    mp.raw_count = d_rawcnt;
+    mp.flags = d_flags;
+    mp.scratch = (uint32_t *)h->d_scratch.p;
+    mp.rows_cap = P.rows_cap;
+    mp.counters = (unsigned long long *)(dc + cl.work);
+    cudaEventRecord(h->evm0, st);
+    if (P.total_items > 0 && (e = launch_main(mp, blocks, count_mode, st)) != cudaSuccess)
+        return h->cuda_fail(e, "verification kernel");
+    cudaEventRecord(h->evm1, st);
+    if ((e = launch_sort_unique(d_inst, nullptr, (int)k, (uint64_t *)h->d_raw.p, d_rawcnt, d_flags, status_out,
+                                dense_out, dense_cap, (uint32_t *)(dc + cl.dense_total), st)) != cudaSuccess)
+        return h->cuda_fail(e, "sort/unique kernel");
+    cudaEventRecord(h->ev1, st);
+    return PMS_OK;
+}
+
+// Records what the host knows of the last solve; device times and counters
+// are read by collect_stats once its events have completed.
+static void begin_stats(pms_ctx *h, const Plan &P, bool count_mode, double t0)
+{
+    pms_stats s{};
+    s.candidates = P.candidates;
+    s.ms_total = now_ms() - t0;
+    h->stats = s;
+    h->stats_pending = true;
+    h->stats_count = count_mode;
+    h->stats_k = P.inst.size();
+}
+
+static void collect_stats(pms_ctx *h)
+{
+    if (!h->stats_pending)
+        return;
+    h->stats_pending = false;
+    if (cudaEventSynchronize(h->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    pms_stats &s = h->stats;
+    if (h->stats_count) {
+        unsigned long long c[kCntNum] = {};
+        CtrLayout cl(h->stats_k);
+        cudaMemcpy(c, (char *)h->d_ctr.p + cl.work, sizeof c, cudaMemcpyDeviceToHost);
+        s.subsets = c[kCntSubsets];
+        s.subsets_pruned = c[kCntPruned];
+        s.candidates_tested = c[kCntTested];
+        s.cmp_rows = c[kCntCmpRows];
+        s.cmp_reduce = c[kCntCmpReduce];
+        s.cmp_verify = c[kCntCmpVerify];
+        s.seeds_infeasible = c[kCntSeedsInfeasible];
+    }
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess)
+        s.ms_kernel = ms;
+    if (cudaEventElapsedTime(&ms, h->evm0, h->evm1) == cudaSuccess)
+        s.ms_verify = ms;
+    cudaGetLastError();
+}
+
+static int status_code(const StatusDev &s)
+{
+    if (s.flags & kFlagInvalidByte)
+        return PMS_EINVAL;
+    if (s.flags & kFlagOverflow)
+        return PMS_ETOOMANY;
+    return PMS_OK;
+}
+
+// Runs a plan whose inputs come from host memory and downloads all results
+// into h->h_result. On return (PMS_OK) statuses and codes are on the host.
+static int run_host_plan(pms_ctx *h, const Plan &P, const std::vector<InstSpec> &specs, double t0)
+{
+    const size_t k = P.inst.size();
+    const bool count_mode = h->opt.count_work != 0;
+    int rc;
+    if ((rc = h->ensure(h->d_seqs, P.seq_bytes)))
+        return rc;
+    size_t dense_keys = 0;
+    for (const InstDev &in : P.inst)
+        dense_keys += in.raw_cap;
+    ResLayout rl(k, dense_keys);
+    if ((rc = h->ensure(h->d_result, rl.total)))
+        return rc;
+    // stage inputs (pinned) and upload in one copy
+    const size_t inline_bytes = rl.dense + (size_t)kInlineKeys * 8;
+    if ((rc = h->ensure_host(h->h_result, h->h_result_cap, std::max(inline_bytes, P.seq_bytes))))
+        return rc;
+    char *stage = (char *)h->h_result;
+    for (size_t i = 0; i < k; ++i)
+        std::memcpy(stage + P.inst[i].seq_off, specs[i].host_seqs, (size_t)specs[i].n * specs[i].m);
+    cudaStream_t st = h->stream;
+    cudaError_t e = cudaMemcpyAsync(h->d_seqs.p, stage, P.seq_bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess)
+        return h->cuda_fail(e, "upload sequences");
+    char *dr = (char *)h->d_result.p;
+    if ((rc = enqueue_plan(h, P, (const uint8_t *)h->d_seqs.p, (StatusDev *)(dr + rl.status),
+                           (uint64_t *)(dr + rl.dense), rl.dense_cap, count_mode)))
+        return rc;
+    // statuses and the first codes in one download
+    const size_t first = std::min(inline_bytes, rl.total);
+    if ((e = cudaMemcpyAsync(h->h_result, dr, first, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return h->cuda_fail(e, "download results");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return h->cuda_fail(e, "solve");
+    const StatusDev *sd = (const StatusDev *)h->h_result;
+    uint64_t total = 0;
+    for (size_t i = 0; i < k; ++i)
+        total = std::max<uint64_t>(total, (uint64_t)sd[i].dense_off + sd[i].unique_count);
+    if (total > kInlineKeys) {
+        const size_t need = rl.dense + total * 8;
+        if (need > h->h_result_cap) {
+            std::vector<char> keep((const char *)h->h_result, (const char *)h->h_result + rl.dense);
+            void *np = nullptr;
+            if ((e = cudaHostAlloc(&np, round_up(need, 4096), cudaHostAllocDefault)) != cudaSuccess)
+                return h->cuda_fail(e, "cudaHostAlloc");
+            cudaFreeHost(h->h_result);
+            h->h_result = np;
+            h->h_result_cap = round_up(need, 4096);
+            std::memcpy(h->h_result, keep.data(), keep.size());
+        }
+        if ((e = cudaMemcpyAsync((char *)h->h_result + rl.dense, dr + rl.dense, total * 8, cudaMemcpyDeviceToHost,
+                                 st)) != cudaSuccess)
+            return h->cuda_fail(e, "download codes");
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return h->cuda_fail(e, "download codes");
+    }
+    begin_stats(h, P, count_mode, t0);
+    collect_stats(h);
+    return PMS_OK;
+}
+
+// ----------------------------------------------------------------------------- served form
+
+struct Served {};
+static void served_stop(pms_ctx *h) { (void)h; }
+
+// -------------------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+int pms_create(pms_ctx **out, int device, size_t mem_budget_bytes)
+{
+    if (!out)
+        return PMS_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return PMS_ECUDA;
+    }
+    auto *h = new pms_ctx();
+    h->device = device;
+    h->budget = mem_budget_bytes;
+    cudaError_t e;
+    if ((e = cudaSetDevice(device)) != cudaSuccess || (e = init_tables()) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess ||
+        (e = main_occupancy(&h->occ[0], false)) != cudaSuccess || (e = main_occupancy(&h->occ[1], true)) != cudaSuccess ||
+        (e = cudaEventCreate(&h->ev0)) != cudaSuccess || (e = cudaEventCreate(&h->ev1)) != cudaSuccess ||
+        (e = cudaEventCreate(&h->evm0)) != cudaSuccess || (e = cudaEventCreate(&h->evm1)) != cudaSuccess) {
+        cudaGetLastError();
+        pms_destroy(h);
+        return PMS_ECUDA;
+    }
+    h->stream = h->own_stream;
+    *out = h;
+    return PMS_OK;
+}
+
+int pms_set_stream(pms_ctx *h, void *cuda_stream)
+{
+    if (!h)
+        return PMS_EINVAL;
+    std::lock_guard<std::recursive_mutex> g(h->mu);
+    h->stream = cuda_stream ? (cudaStream_t)cuda_stream : h->own_stream;
+    return PMS_OK;
+}
+
+int pms_set_allocator(pms_ctx *h, void *(*alloc)(size_t, void *), void (*free_)(void *, void *), void *user)
+{
+    if (!h || (!alloc) != (!free_))
+        return PMS_EINVAL;
+    std::lock_guard<std::recursive_mutex> g(h->mu);
+    if (h->used)
+        return h->fail(PMS_EBUSY, "allocator must be set before the first solve");
+    h->ualloc = alloc;
+    h->ufree = free_;
+    h->uuser = user;
+    return PMS_OK;
+}
+
+int pms_set_options(pms_ctx *h, const pms_options *opt)
+{
+    if (!h || !opt)
+        return PMS_EINVAL;
+    if (opt->ctas_per_sm < 0 || opt->chunk_work < 0 || opt->grab < 0 || opt->serve_wave_items < 0 ||
+        opt->serve_max_inflight < 0 || opt->serve_max_inflight > 1024)
+        return h->fail(PMS_EINVAL, "negative option");
+    std::lock_guard<std::recursive_mutex> g(h->mu);
+    h->opt = *opt;
+    return PMS_OK;
+}
+
+int pms_get_options(const pms_ctx *h, pms_options *opt)
+{
+    if (!h || !opt)
+        return PMS_EINVAL;
+    *opt = h->opt;
+    return PMS_OK;
+}
+
+int pms_solve(pms_ctx *h, const uint8_t *seqs, int n, int m, int l, int d, const uint64_t **motifs, size_t *count)
+{
+    if (!h)
+        return PMS_EINVAL;
+    std::lock_guard<std::recursive_mutex> g(h->mu);
+    const double t0 = now_ms();
+    h->err.clear();
+    if (!seqs || !motifs || !count)
+        return h->fail(PMS_EINVAL, "null argument");
+    *motifs = nullptr;
+    *count = 0;
+    int rc;
+    if ((rc = check_params(h, n, m, l, d)) || (rc = check_bytes(h, seqs, (size_t)n * m)))
+        return rc;
+    cudaSetDevice(h->device);
+    std::vector<InstSpec> specs{InstSpec{n, m, l, d, seqs}};
+    Plan P = make_plan(h, specs);
+    if ((rc = run_host_plan(h, P, specs, t0)))
+        return rc;
+    const StatusDev *sd = (const StatusDev *)h->h_result;
+    ResLayout rl(1, 0);
+    *motifs = (const uint64_t *)((const char *)h->h_result + rl.dense) + sd[0].dense_off;
+    *count = sd[0].unique_count;
+    rc = status_code(sd[0]);
+    if (rc == PMS_ETOOMANY) {
+        *count = sd[0].raw_count;
+        return h->fail(rc, "%u motifs (with duplicates) exceed the capacity %u; raise max_motifs", sd[0].raw_count,
+                       P.inst[0].raw_cap);
+    }
+    if (rc)
+        return h->fail(rc, "invalid input byte");
+    return PMS_OK;
+}
+
+int pms_solve_device(pms_ctx *h, const uint8_t *d_seqs, int n, int m, int l, int d, uint64_t *d_motifs,
+                     size_t capacity, uint32_t *d_status)
+{
+    if (!h)
+        return PMS_EINVAL;
+    std::lock_guard<std::recursive_mutex> g(h->mu);
+    const double t0 = now_ms();
+    h->err.clear();
+    if (!d_seqs || !d_motifs || !d_status || capacity == 0)
+        return h->fail(PMS_EINVAL, "null argument or zero capacity");
+    int rc;
+    if ((rc = check_params(h, n, m, l, d)))
+        return rc;
+    cudaSetDevice(h->device);
+    std::vector<InstSpec> specs{InstSpec{n, m, l, d, nullptr}};
+    Plan P = make_plan(h, specs);
+    const uint32_t cap = (uint32_t)std::min<size_t>(capacity, 0xffffffffu);
+    if ((rc = enqueue_plan(h, P, d_seqs, (StatusDev *)d_status, d_motifs, cap, h->opt.count_work != 0)))
+        return rc;
+    begin_stats(h, P, h->opt.count_work != 0, t0);
+    return PMS_OK;
+}
+
+int pms_solve_batch(pms_ctx *h, const pms_instance *inst, int k, pms_result *out)
+{
+    if (!h)
+        return PMS_EINVAL;
+    std::lock_guard<std::recursive_mutex> g(h->mu);
+    const double t0 = now_ms();
+    h->err.clear();
+    if (!inst || !out || k < 1)
+        return h->fail(PMS_EINVAL, "null argument or k < 1");
+    std::vector<InstSpec> specs;
+    std::vector<int> which;   // index into inst of each valid instance
+    for (int i = 0; i < k; ++i) {
+        out[i] = pms_result{PMS_OK, nullptr, 0};
+        const pms_instance &q = inst[i];
+        int rc = q.seqs ? check_params(h, q.n, q.m, q.l, q.d) : h->fail(PMS_EINVAL, "null sequences");
+        if (!rc)
+            rc = check_bytes(h, q.seqs, (size_t)q.n * q.m);
+        if (rc) {
+            out[i].status = rc;
+            continue;
+        }
+        specs.push_back(InstSpec{q.n, q.m, q.l, q.d, q.seqs});
+        which.push_back(i);
+    }
+    h->err.clear();
+    if (specs.empty())
+        return PMS_OK;
+    cudaSetDevice(h->device);
+    Plan P = make_plan(h, specs);
+    int rc;
+    if ((rc = run_host_plan(h, P, specs, t0)))
+        return rc;
+    const StatusDev *sd = (const StatusDev *)h->h_result;
+    ResLayout rl(specs.size(), 0);
+    const uint64_t *dense = (const uint64_t *)((const char *)h->h_result + rl.dense);
+    for (size_t j = 0; j < specs.size(); ++j) {
+        pms_result &r = out[which[j]];
+        r.status = status_code(sd[j]);
+        r.motifs = dense + sd[j].dense_off;
+        r.count = r.status == PMS_ETOOMANY ? sd[j].raw_count : sd[j].unique_count;
+    }
+    return PMS_OK;
+}
+
+int pms_submit(pms_ctx *h, const pms_instance *inst, uint64_t *ticket)
+{
+    (void)inst;
+    (void)ticket;
+    if (!h)
+        return PMS_EINVAL;
+    return h->fail(PMS_EINVAL, "served form not available in this build");
+}
+
+int pms_wait(pms_ctx *h, uint64_t ticket, int timeout_ms, pms_result *out)
+{
+    (void)ticket;
+    (void)timeout_ms;
+    (void)out;
+    if (!h)
+        return PMS_EINVAL;
+    return PMS_ENOTFOUND;
+}
+
+int pms_release(pms_ctx *h, uint64_t ticket)
+{
+    (void)ticket;
+    if (!h)
+        return PMS_EINVAL;
+    return PMS_ENOTFOUND;
+}
+
+int pms_get_stats(const pms_ctx *h, pms_stats *out)
+{
+    if (!h || !out)
+        return PMS_EINVAL;
+    pms_ctx *hm = const_cast<pms_ctx *>(h);
+    std::lock_guard<std::recursive_mutex> g(hm->mu);
+    cudaSetDevice(hm->device);
+    collect_stats(hm);
+    *out = h->stats;
+    return PMS_OK;
+}
+
+int pms_decode(uint64_t code, int l, char *out)
+{
+    if (!out || l < 1 || l > PMS_LMAX)
+        return PMS_EINVAL;
+    static const char letters[4] = {'A', 'C', 'G', 'T'};
+    for (int k = l - 1; k >= 0; --k) {
+        out[k] = letters[code & 3u];
+        code >>= 2;
+    }
+    out[l] = '\0';
+    return PMS_OK;
+}
+
+const char *pms_last_error(const pms_ctx *h)
+{
+    return h ? h->err.c_str() : "null context";
+}
+
+int pms_probe_int_rate(pms_ctx *h, int kind, double *per_clk_per_sm)
+{
+    if (!h || !per_clk_per_sm || kind < 0 || kind > 3)
+        return PMS_EINVAL;
+    std::lock_guard<std::recursive_mutex> g(h->mu);
+    cudaSetDevice(h->device);
+    const int blocks = h->num_sms;
+    const int iters = 4096;
+    unsigned long long *d = nullptr;
+    if (cudaMalloc(&d, (blocks + 1) * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return h->fail(PMS_ENOMEM, "probe buffer");
+    }
+    cudaMemsetAsync(d, 0, (blocks + 1) * sizeof(unsigned long long), h->stream);
+    cudaError_t e = launch_probe(kind, iters, blocks, d + 1, d, h->stream);
+    std::vector<unsigned long long> cyc(blocks);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cyc.data(), d + 1, blocks * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess)
+        return h->cuda_fail(e, "probe");
+    std::sort(cyc.begin(), cyc.end());
+    const double c = (double)cyc[cyc.size() / 2];
+    const double ops = 1024.0 * iters * 4 * 8;   // threads x iterations x unroll x chains
+    *per_clk_per_sm = ops / std::max(c, 1.0);
+    return PMS_OK;
+}
+
+void pms_destroy(pms_ctx *h)
+{
+    if (!h)
+        return;
+    cudaSetDevice(h->device);
+    served_stop(h);
+    if (h->stream)
+        cudaStreamSynchronize(h->stream);
+    pms_ctx::DBuf *bufs[] = {&h->d_seqs, &h->d_planes, &h->d_raw, &h->d_meta, &h->d_ctr, &h->d_scratch, &h->d_result};
+    for (auto *b : bufs)
+        h->dev_free(b->p, b->cap);
+    if (h->h_result)
+        cudaFreeHost(h->h_result);
+    if (h->h_meta)
+        cudaFreeHost(h->h_meta);
+    if (h->ev0)
+        cudaEventDestroy(h->ev0);
+    if (h->ev1)
+        cudaEventDestroy(h->ev1);
+    if (h->evm0)
+        cudaEventDestroy(h->evm0);
+    if (h->evm1)
+        cudaEventDestroy(h->evm1);
+    if (h->own_stream)
+        cudaStreamDestroy(h->own_stream);
+    delete h;
+}
+
+}  // extern "C"
