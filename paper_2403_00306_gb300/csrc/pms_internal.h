@@ -13,6 +13,7 @@ constexpr int kWarps = 8;      // warps per CTA of the verification kernel
 constexpr int kThreads = kWarps * 32;
 constexpr int kRbCap = 256;    // entries of a subset-reduced occurrence row kept in shared memory
 constexpr int kListCap = 512;  // surviving candidates a warp buffers before checking further rows
+constexpr int kRowSmemCap = 4096;  // feasible occurrences of one seed held in shared memory
 
 // Flags reported per instance.
 constexpr uint32_t kFlagInvalidByte = 1u;
@@ -22,13 +23,16 @@ constexpr uint32_t kFlagOverflow = 2u;
 struct InstDev {
     int n, m, l, d;
     int W;                 // windows per sequence: m - l + 1
+    int NW;                // 32-bit words of one compatibility mask row: ceil(W / 32)
     int cps;               // queue chunks per seed
     int grab;              // subsets a warp claims at a time
     int ctab;              // offset (ints) of this instance's table in the chunk arena:
                            //   levoff[0..d+1] then cps pairs (g0, g1)
+    int prune_rows;        // rows checked for a feasible occurrence before leaves are tested
     long long seq_off;     // byte offset of the n x m input bytes in the sequence arena
     long long plane_off;   // offset (uint2) of the n x W window planes
-    long long raw_off;     // offset (uint64) of the raw motif buffer
+    long long raw_off;     // offset (uint64) of the raw motif buffer (and of its sort twin)
+    long long compat_off;  // offset (uint32) of the W x (n-1) x NW compatibility masks
     uint32_t raw_cap;      // capacity of the raw motif buffer (power of two)
     int pad;
 };
@@ -69,11 +73,12 @@ struct MainParams {
     long long total;              // queue items in this launch
     unsigned long long *head;     // queue head (zeroed before the launch)
     const uint2 *planes;
+    const uint32_t *compat;       // seed x row compatibility masks (d_H <= 2d)
     const int *ctab;
     uint64_t *raw;                // raw motif codes
     uint32_t *raw_count;          // per instance
     uint32_t *flags;              // per instance
-    uint32_t *scratch;            // per CTA: 3 * rows_cap words (D, H, L)
+    uint2 *scratch;               // per CTA: rows_cap entries, used when a seed's rows exceed shared memory
     int rows_cap;                 // max (n - 1) * W over the instances
     unsigned long long *counters; // kCntNum entries (count mode)
     int *done;                    // per segment: finished items (served form), may be null
@@ -82,10 +87,12 @@ struct MainParams {
 // Launch wrappers (pms_kernels.cu).
 cudaError_t launch_pack(const InstDev *inst, int ninst, const long long *win_prefix, long long total_windows,
                         const uint8_t *seqs, uint2 *planes, uint32_t *flags, int blocks, cudaStream_t st);
+cudaError_t launch_compat(const InstDev *inst, int ninst, const long long *row_prefix, long long total_rows,
+                          const uint2 *planes, uint32_t *compat, int blocks, cudaStream_t st);
 cudaError_t launch_main(const MainParams &p, int blocks, bool count_mode, cudaStream_t st);
 cudaError_t main_occupancy(int *blocks_per_sm, bool count_mode);
 size_t main_smem_bytes();
-cudaError_t launch_sort_unique(const InstDev *inst, const int *inst_list, int nlist, uint64_t *raw,
+cudaError_t launch_sort_unique(const InstDev *inst, const int *inst_list, int nlist, uint64_t *raw, uint64_t *tmp,
                                const uint32_t *raw_count, const uint32_t *flags, StatusDev *status,
                                uint64_t *dense, uint32_t dense_cap, uint32_t *dense_total,
                                cudaStream_t st);

@@ -23,6 +23,8 @@
 //     de-duplicated per instance.
 #include "pms_internal.h"
 
+#include <algorithm>
+
 namespace pms {
 
 namespace {
@@ -40,13 +42,16 @@ struct __align__(16) WarpSmem {
 
 struct __align__(16) CtaSmem {
     int row_len[kNMax];      // indexed by sequence
+    int row_off[kNMax];      // indexed by sequence: first entry of its row
     int row_order[kNMax];    // sequences 1..n-1, smallest row first
     unsigned long long g;
     int inst, seed, chunk;
     int cached_inst, cached_seed;
     int feasible;
+    int rows_in_smem;
+    int total_rows;
     int next;                // next subset index of the chunk to claim
-    int pad;
+    int pad[3];
 };
 
 // Colex unranking of the rank-th k-subset of {0..l-1} (combinatorial number
@@ -81,24 +86,27 @@ __device__ __forceinline__ uint64_t to_key(uint32_t h, uint32_t lo, int l)
     return key;
 }
 
-// Keeps the occurrences of one row whose mismatch mask D satisfies
-// popc(D ^ P) <= d; writes up to kRbCap of them (planes) to rb, pads rb to a
-// multiple of 4 entries, and returns how many qualify.
-__device__ __forceinline__ int reduce_row(const uint32_t *__restrict__ D, const uint32_t *__restrict__ H,
-                                          const uint32_t *__restrict__ L, int len, uint32_t P, int d,
+// Keeps the occurrences w of one row (planes in `row`, shared or global
+// memory) with popc(D_w ^ P) <= d, where D_w = (xh ^ w.hi) | (xl ^ w.lo);
+// writes up to kRbCap of them to rb, pads rb to a multiple of 4 entries, and
+// returns how many qualify.
+__device__ __forceinline__ int reduce_row(const uint2 *row, int len, uint32_t xh, uint32_t xl, uint32_t P, int d,
                                           uint2 *rb, int lane, uint32_t lt)
 {
     int k = 0;
     for (int e0 = 0; e0 < len; e0 += 32) {
         const int e = e0 + lane;
         bool keep = false;
-        if (e < len)
-            keep = __popc(D[e] ^ P) <= d;
+        uint2 w = make_uint2(0u, 0u);
+        if (e < len) {
+            w = row[e];
+            keep = __popc(((xh ^ w.x) | (xl ^ w.y)) ^ P) <= d;
+        }
         const uint32_t bal = __ballot_sync(kFull, keep);
         if (keep) {
             const int pos = k + __popc(bal & lt);
             if (pos < kRbCap)
-                rb[pos] = make_uint2(H[e], L[e]);
+                rb[pos] = w;
         }
         k += __popc(bal);
     }
@@ -107,6 +115,23 @@ __device__ __forceinline__ int reduce_row(const uint32_t *__restrict__ D, const 
         rb[k + lane] = rb[k - 1];
     __syncwarp();
     return k;
+}
+
+// Does the row hold at least one occurrence with popc(D_w ^ P) <= d?
+__device__ __forceinline__ bool row_feasible(const uint2 *row, int len, uint32_t xh, uint32_t xl, uint32_t P, int d,
+                                             int lane)
+{
+    for (int e0 = 0; e0 < len; e0 += 32) {
+        const int e = e0 + lane;
+        bool q = false;
+        if (e < len) {
+            const uint2 w = row[e];
+            q = __popc(((xh ^ w.x) | (xl ^ w.y)) ^ P) <= d;
+        }
+        if (__any_sync(kFull, q))
+            return true;
+    }
+    return false;
 }
 
 // Is some entry of a reduced row (shared memory, padded to 4) within d of (ch, cl)?
@@ -124,14 +149,15 @@ __device__ __forceinline__ bool check_smem(const uint2 *rb, int k, uint32_t ch, 
     return mn <= d;
 }
 
-// Same test against a full (unreduced) row in global memory; used when the
-// reduced row does not fit in shared memory.
-__device__ __forceinline__ bool check_glob(const uint32_t *__restrict__ H, const uint32_t *__restrict__ L, int len,
-                                           uint32_t ch, uint32_t cl, int d)
+// Same test against a full (unreduced) row; used when the reduced row does
+// not fit in the warp's buffer.
+__device__ __forceinline__ bool check_row(const uint2 *row, int len, uint32_t ch, uint32_t cl, int d)
 {
     int mn = 64;
-    for (int e = 0; e < len; ++e)
-        mn = min(mn, __popc((ch ^ H[e]) | (cl ^ L[e])));
+    for (int e = 0; e < len; ++e) {
+        const uint2 w = row[e];
+        mn = min(mn, __popc((ch ^ w.x) | (cl ^ w.y)));
+    }
     return mn <= d;
 }
 
@@ -141,7 +167,8 @@ struct WarpCtx {
     int I;
     int lane;
     uint32_t lt;
-    const uint32_t *rowD, *rowH, *rowL;
+    uint32_t xh, xl;           // the seed l-mer
+    const uint2 *rows;         // feasible occurrences of the seed (shared or global memory)
     const CtaSmem *cs;
     WarpSmem *ws;
     unsigned long long *cnt;   // per-thread counters (count mode)
@@ -187,8 +214,8 @@ __device__ __forceinline__ void finish_list(const WarpCtx &c, uint32_t P, int N)
     for (int r = 1; r < nrows && N > 0; ++r) {
         const int ri = c.cs->row_order[r];
         const int len = c.cs->row_len[ri];
-        const size_t off = (size_t)(ri - 1) * in.W;
-        const int k = reduce_row(c.rowD + off, c.rowH + off, c.rowL + off, len, P, in.d, c.ws->rb1, c.lane, c.lt);
+        const uint2 *row = c.rows + c.cs->row_off[ri];
+        const int k = reduce_row(row, len, c.xh, c.xl, P, in.d, c.ws->rb1, c.lane, c.lt);
         if (kCount && c.lane == 0)
             c.cnt[kCntCmpReduce] += len;
         if (k == 0) {
@@ -205,8 +232,7 @@ __device__ __forceinline__ void finish_list(const WarpCtx &c, uint32_t P, int N)
                 v = list[idx];
             bool hit = false;
             if (alive) {
-                hit = sm ? check_smem(c.ws->rb1, k, v.x, v.y, in.d)
-                         : check_glob(c.rowH + off, c.rowL + off, len, v.x, v.y, in.d);
+                hit = sm ? check_smem(c.ws->rb1, k, v.x, v.y, in.d) : check_row(row, len, v.x, v.y, in.d);
                 if (kCount)
                     c.cnt[kCntCmpVerify] += sm ? k : len;
             }
@@ -223,17 +249,48 @@ __device__ __forceinline__ void finish_list(const WarpCtx &c, uint32_t P, int N)
         emit<kCount>(c, list, N);
 }
 
-// One node of T_d(x): the subset P of changed positions (|P| = lev). Lanes
-// own the letter choices on the lowest min(lev, 3) positions of P (27 lanes
-// at most); every lane then walks the choices on the remaining positions
-// with a base-3 odometer kept as two masks (Dh, Dl) over those positions:
-// state (0,1) -> (1,0) -> (1,1) -> carry, i.e. XOR deltas 1, 2, 3.
+// One node of T_d(x): the subset P of changed positions (|P| = lev).
+// First every one of the first prune_rows rows (smallest first) must keep an
+// occurrence under the node's bound, else the node's 3^lev leaves are
+// dismissed together. Then lanes own the letter choices on the lowest
+// min(lev, 3) positions of P (27 lanes at most) and every lane walks the
+// choices on the remaining positions with a base-3 odometer kept as two masks
+// (Dh, Dl) over those positions: state (0,1) -> (1,0) -> (1,1) -> carry, i.e.
+// XOR deltas 1, 2, 3 of the 2-bit codes.
 template <bool kCount>
-__device__ __forceinline__ void process_subset(const WarpCtx &c, uint32_t P, int lev, uint32_t xh, uint32_t xl)
+__device__ __forceinline__ void process_subset(const WarpCtx &c, uint32_t P, int lev)
 {
     const InstDev &in = c.in;
     const int d = in.d;
     const int nrows = in.n - 1;
+    if (kCount && c.lane == 0)
+        c.cnt[kCntSubsets] += 1;
+
+    int k0 = 0, len0 = 0;
+    const uint2 *row0 = c.rows;
+    if (nrows > 0) {
+        const int r0 = c.cs->row_order[0];
+        len0 = c.cs->row_len[r0];
+        row0 = c.rows + c.cs->row_off[r0];
+        k0 = reduce_row(row0, len0, c.xh, c.xl, P, d, c.ws->rb0, c.lane, c.lt);
+        if (kCount && c.lane == 0)
+            c.cnt[kCntCmpReduce] += len0;
+        bool pruned = k0 == 0;
+        const int npr = min(in.prune_rows, nrows);
+        for (int r = 1; r < npr && !pruned; ++r) {
+            const int ri = c.cs->row_order[r];
+            const int len = c.cs->row_len[ri];
+            pruned = !row_feasible(c.rows + c.cs->row_off[ri], len, c.xh, c.xl, P, d, c.lane);
+            if (kCount && c.lane == 0)
+                c.cnt[kCntCmpReduce] += len;
+        }
+        if (pruned) {
+            if (kCount && c.lane == 0)
+                c.cnt[kCntPruned] += 1;
+            return;
+        }
+    }
+
     uint32_t t = P;
     const uint32_t b0 = t & (0u - t);
     t ^= b0;
@@ -248,27 +305,9 @@ __device__ __forceinline__ void process_subset(const WarpCtx &c, uint32_t P, int
     const int dg0 = c.lane % 3, dg1 = (c.lane / 3) % 3, dg2 = (c.lane / 9) % 3;
     const uint32_t DhLo = (dg0 >= 1 ? b0 : 0u) | (dg1 >= 1 ? b1 : 0u) | (dg2 >= 1 ? b2 : 0u);
     const uint32_t DlLo = (dg0 != 1 ? b0 : 0u) | (dg1 != 1 ? b1 : 0u) | (dg2 != 1 ? b2 : 0u);
-    const uint32_t ch0 = xh ^ DhLo, cl0 = xl ^ DlLo;
+    const uint32_t ch0 = c.xh ^ DhLo, cl0 = c.xl ^ DlLo;
     const unsigned long long iters = c_pow3[lev - nlo];
 
-    if (kCount && c.lane == 0)
-        c.cnt[kCntSubsets] += 1;
-
-    int k0 = 0, len0 = 0;
-    size_t off0 = 0;
-    if (nrows > 0) {
-        const int r0 = c.cs->row_order[0];
-        len0 = c.cs->row_len[r0];
-        off0 = (size_t)(r0 - 1) * in.W;
-        k0 = reduce_row(c.rowD + off0, c.rowH + off0, c.rowL + off0, len0, P, d, c.ws->rb0, c.lane, c.lt);
-        if (kCount && c.lane == 0)
-            c.cnt[kCntCmpReduce] += len0;
-        if (k0 == 0) {
-            if (kCount && c.lane == 0)
-                c.cnt[kCntPruned] += 1;
-            return;
-        }
-    }
     const bool sm0 = k0 <= kRbCap;
     uint2 *list = c.ws->list;
     uint32_t Dh = 0u, Dl = Phi;
@@ -280,8 +319,7 @@ __device__ __forceinline__ void process_subset(const WarpCtx &c, uint32_t P, int
             if (nrows == 0)
                 hit = true;
             else
-                hit = sm0 ? check_smem(c.ws->rb0, k0, ch, cl, d)
-                          : check_glob(c.rowH + off0, c.rowL + off0, len0, ch, cl, d);
+                hit = sm0 ? check_smem(c.ws->rb0, k0, ch, cl, d) : check_row(row0, len0, ch, cl, d);
             if (kCount) {
                 c.cnt[kCntTested] += 1;
                 c.cnt[kCntCmpVerify] += sm0 ? k0 : len0;
@@ -308,45 +346,25 @@ __device__ __forceinline__ void process_subset(const WarpCtx &c, uint32_t P, int
         finish_list<kCount>(c, P, listN);
 }
 
-// Builds the feasible-occurrence rows of seed x for sequences 1..n-1 into
-// this CTA's scratch, records their sizes and the smallest-first order.
+// Gathers the feasible occurrences of seed `seed` (windows within 2d, from
+// the compatibility masks) into `rows` (shared memory when they fit, else
+// this CTA's global scratch), records each row's size and offset and the
+// smallest-first order, and whether every row is non-empty.
 __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &in, int seed, CtaSmem &cs,
-                                           uint32_t *rowD, uint32_t *rowH, uint32_t *rowL, int warp, int lane,
-                                           uint32_t lt, unsigned long long *cnt, bool count_mode)
+                                           uint2 *smem_rows, uint2 *glob_rows, int warp, int lane,
+                                           unsigned long long *cnt)
 {
-    const uint2 *pl = p.planes + in.plane_off;
-    const uint2 x = pl[seed];
-    const int W = in.W, n = in.n, lim = 2 * in.d;
+    const int n = in.n, NW = in.NW, W = in.W;
+    const uint32_t *mask = p.compat + in.compat_off + (size_t)seed * (n - 1) * NW;
     for (int i = 1 + warp; i < n; i += kWarps) {
-        const uint2 *s = pl + (size_t)i * W;
-        uint32_t *Dr = rowD + (size_t)(i - 1) * W;
-        uint32_t *Hr = rowH + (size_t)(i - 1) * W;
-        uint32_t *Lr = rowL + (size_t)(i - 1) * W;
-        int k = 0;
-        for (int w0 = 0; w0 < W; w0 += 32) {
-            const int w = w0 + lane;
-            bool keep = false;
-            uint32_t dm = 0;
-            uint2 e = make_uint2(0u, 0u);
-            if (w < W) {
-                e = s[w];
-                dm = (x.x ^ e.x) | (x.y ^ e.y);
-                keep = __popc(dm) <= lim;
-            }
-            const uint32_t bal = __ballot_sync(kFull, keep);
-            if (keep) {
-                const int pos = k + __popc(bal & lt);
-                Dr[pos] = dm;
-                Hr[pos] = e.x;
-                Lr[pos] = e.y;
-            }
-            k += __popc(bal);
-        }
-        if (lane == 0) {
-            cs.row_len[i] = k;
-            if (count_mode && cnt)
-                cnt[kCntCmpRows] += W;
-        }
+        const uint32_t *mr = mask + (size_t)(i - 1) * NW;
+        int c = 0;
+        for (int k = lane; k < NW; k += 32)
+            c += __popc(mr[k]);
+        for (int o = 16; o > 0; o >>= 1)
+            c += __shfl_xor_sync(kFull, c, o);
+        if (lane == 0)
+            cs.row_len[i] = c;
     }
     __syncthreads();
     if (warp == 0) {
@@ -362,22 +380,63 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
             cs.row_order[rank] = i;
         }
         const bool any_empty = __any_sync(kFull, empty);
-        if (lane == 0)
+        __syncwarp();
+        if (lane == 0) {
+            int off = 0;
+            for (int r = 0; r < n - 1; ++r) {
+                const int i = cs.row_order[r];
+                cs.row_off[i] = off;
+                off += cs.row_len[i];
+            }
+            cs.total_rows = off;
             cs.feasible = !any_empty;
+            cs.rows_in_smem = off <= kRowSmemCap;
+            if (cnt)
+                cnt[kCntCmpRows] += (unsigned long long)(n - 1) * W;
+        }
     }
+    __syncthreads();
+    if (!cs.feasible)
+        return;
+    uint2 *rows = cs.rows_in_smem ? smem_rows : glob_rows;
+    const uint2 *pl = p.planes + in.plane_off;
+    for (int i = 1 + warp; i < n; i += kWarps) {
+        const uint32_t *mr = mask + (size_t)(i - 1) * NW;
+        const uint2 *s = pl + (size_t)i * W;
+        uint2 *dst = rows + cs.row_off[i];
+        int base = 0;
+        for (int k0 = 0; k0 < NW; k0 += 32) {
+            const int k = k0 + lane;
+            uint32_t bits = k < NW ? mr[k] : 0u;
+            const int c = __popc(bits);
+            int incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o)
+                    incl += y;
+            }
+            int pos = base + incl - c;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                dst[pos++] = s[32 * k + b];
+            }
+            base += __shfl_sync(kFull, incl, 31);
+        }
+    }
+    __syncthreads();
 }
 
 template <bool kCount>
-__global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
+__global__ void __launch_bounds__(kThreads, 2) main_kernel(MainParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *wsm = reinterpret_cast<WarpSmem *>(smem_raw);
-    CtaSmem &cs = *reinterpret_cast<CtaSmem *>(smem_raw + kWarps * sizeof(WarpSmem));
+    uint2 *smem_rows = reinterpret_cast<uint2 *>(smem_raw + kWarps * sizeof(WarpSmem));
+    CtaSmem &cs = *reinterpret_cast<CtaSmem *>(smem_raw + kWarps * sizeof(WarpSmem) + kRowSmemCap * sizeof(uint2));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    uint32_t *rowD = p.scratch + (size_t)blockIdx.x * 3 * (size_t)p.rows_cap;
-    uint32_t *rowH = rowD + p.rows_cap;
-    uint32_t *rowL = rowH + p.rows_cap;
+    uint2 *glob_rows = p.scratch + (size_t)blockIdx.x * (size_t)p.rows_cap;
     unsigned long long cnt[kCount ? kCntNum : 1];
 #pragma unroll
     for (int i = 0; i < (kCount ? kCntNum : 1); ++i)
@@ -416,7 +475,7 @@ __global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
         const InstDev in = p.inst[I];
         const bool rebuild = (I != cs.cached_inst) || (seed != cs.cached_seed);
         if (rebuild) {
-            build_rows(p, in, seed, cs, rowD, rowH, rowL, warp, lane, lt, kCount ? cnt : nullptr, kCount);
+            build_rows(p, in, seed, cs, smem_rows, glob_rows, warp, lane, kCount ? cnt : nullptr);
             if (threadIdx.x == 0) {
                 cs.cached_inst = I;
                 cs.cached_seed = seed;
@@ -434,7 +493,8 @@ __global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
         }
         if (cs.feasible) {
             const uint2 x = p.planes[in.plane_off + seed];
-            WarpCtx c{&p, in, I, lane, lt, rowD, rowH, rowL, &cs, &wsm[warp], kCount ? cnt : nullptr};
+            WarpCtx c{&p, in, I, lane, lt, x.x, x.y, cs.rows_in_smem ? smem_rows : glob_rows, &cs, &wsm[warp],
+                      kCount ? cnt : nullptr};
             for (;;) {
                 int start = 0;
                 if (lane == 0)
@@ -451,7 +511,7 @@ __global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
                     const int stop = min(end, tab[lev + 1]);
                     uint32_t P = unrank_subset((uint32_t)(idx - tab[lev]), lev, in.l);
                     for (int k = idx; k < stop; ++k) {
-                        process_subset<kCount>(c, P, lev, x.x, x.y);
+                        process_subset<kCount>(c, P, lev);
                         if (k + 1 < stop)
                             P = next_subset(P);
                     }
@@ -469,6 +529,45 @@ __global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
                 v += __shfl_xor_sync(kFull, v, o);
             if (lane == 0 && v)
                 atomicAdd(&p.counters[i], v);
+        }
+    }
+}
+
+// Compatibility masks (the pair-distance table of PMS8): for every seed
+// x = s_1[j..j+l-1] and every sequence i >= 2, bit w of row (j, i) is set iff
+// d_H(x, s_i[w..w+l-1]) <= 2d. One warp per (instance, seed, row).
+__global__ void compat_kernel(const InstDev *__restrict__ inst, int ninst, const long long *__restrict__ row_prefix,
+                              long long total_rows, const uint2 *__restrict__ planes, uint32_t *__restrict__ compat)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long q = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < total_rows; q += warps) {
+        int lo = 0, hi = ninst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (row_prefix[mid] <= q)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const InstDev in = inst[lo];
+        const long long local = q - row_prefix[lo];
+        const int j = (int)(local / (in.n - 1)), i = 1 + (int)(local % (in.n - 1));
+        const uint2 *pl = planes + in.plane_off;
+        const uint2 x = pl[j];
+        const uint2 *s = pl + (size_t)i * in.W;
+        uint32_t *out = compat + in.compat_off + (size_t)local * in.NW;
+        const int lim = 2 * in.d;
+        for (int w0 = 0; w0 < in.W; w0 += 32) {
+            const int w = w0 + lane;
+            bool keep = false;
+            if (w < in.W) {
+                const uint2 e = s[w];
+                keep = __popc((x.x ^ e.x) | (x.y ^ e.y)) <= lim;
+            }
+            const uint32_t bal = __ballot_sync(kFull, keep);
+            if (lane == 0)
+                out[w0 >> 5] = bal;
         }
     }
 }
@@ -508,7 +607,7 @@ __global__ void pack_kernel(const InstDev *__restrict__ inst, int ninst, const l
 }
 
 constexpr int kSortThreads = 1024;
-constexpr uint32_t kSortSmemKeys = 8192;
+constexpr uint32_t kSortSmemKeys = 8192;   // bitonic sort in shared memory up to this many codes
 
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_tot, uint32_t *total)
 {
@@ -542,12 +641,76 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *w
     return r;
 }
 
-// One CTA per instance: bitonic sort of the raw codes (shared memory when
-// they fit, else in place in global memory), then duplicates removed and the
-// unique codes appended to the dense output.
+// Stable LSD radix sort (8-bit digits) of n codes of `bits` significant bits
+// by one CTA; ping-pongs between a and t and returns the buffer holding the
+// sorted codes. smem: 2 x 32 x 256 counters plus 256 bin bases.
+__device__ uint64_t *block_radix_sort(uint64_t *a, uint64_t *t, uint32_t n, int bits, uint32_t *smem)
+{
+    uint32_t *cnt = smem;                 // [32][256] per-warp digit counts of a tile
+    uint32_t *off = smem + 32 * 256;      // [32][256] per-warp digit offsets of a tile
+    uint32_t *bin = smem + 2 * 32 * 256;  // [256] running bin starts
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint64_t *src = a, *dst = t;
+    for (int shift = 0; shift < bits; shift += 8) {
+        for (int i = threadIdx.x; i < 2 * 32 * 256 + 256; i += blockDim.x)
+            smem[i] = 0;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+            atomicAdd(&bin[(uint32_t)(src[i] >> shift) & 255u], 1u);
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t run = 0;
+            for (int b0 = 0; b0 < 256; b0 += 32) {
+                const uint32_t v = bin[b0 + lane];
+                uint32_t incl = v;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o)
+                        incl += y;
+                }
+                bin[b0 + lane] = run + incl - v;
+                run += __shfl_sync(kFull, incl, 31);
+            }
+        }
+        __syncthreads();
+        for (uint32_t t0 = 0; t0 < n; t0 += blockDim.x) {
+            const uint32_t i = t0 + threadIdx.x;
+            const bool valid = i < n;
+            const uint64_t key = valid ? src[i] : 0ull;
+            const uint32_t dig = valid ? ((uint32_t)(key >> shift) & 255u) : 256u;
+            const uint32_t peers = __match_any_sync(kFull, dig);
+            const uint32_t rank = __popc(peers & lt);
+            if (valid && rank == 0)
+                cnt[warp * 256 + dig] = __popc(peers);
+            __syncthreads();
+            if (threadIdx.x < 256) {
+                uint32_t run = bin[threadIdx.x];
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                    off[w * 256 + threadIdx.x] = run;
+                    run += cnt[w * 256 + threadIdx.x];
+                    cnt[w * 256 + threadIdx.x] = 0;
+                }
+                bin[threadIdx.x] = run;
+            }
+            __syncthreads();
+            if (valid)
+                dst[off[warp * 256 + dig] + rank] = key;
+            __syncthreads();
+        }
+        uint64_t *x = src;
+        src = dst;
+        dst = x;
+    }
+    return src;
+}
+
+// One CTA per instance: the raw codes sorted (bitonic in shared memory when
+// they fit, else radix sort through the instance's twin buffer), duplicates
+// removed, unique codes appended to the dense output.
 __global__ void __launch_bounds__(kSortThreads)
     sort_unique_kernel(const InstDev *__restrict__ inst, const int *__restrict__ inst_list, uint64_t *raw,
-                       const uint32_t *__restrict__ raw_count, const uint32_t *__restrict__ flags,
+                       uint64_t *tmp, const uint32_t *__restrict__ raw_count, const uint32_t *__restrict__ flags,
                        StatusDev *__restrict__ status, uint64_t *__restrict__ dense, uint32_t dense_cap,
                        uint32_t *dense_total)
 {
@@ -562,26 +725,31 @@ __global__ void __launch_bounds__(kSortThreads)
     uint32_t P2 = 1;
     while (P2 < n)
         P2 <<= 1;
-    const bool in_smem = P2 <= kSortSmemKeys;
-    uint64_t *buf = in_smem ? sk : a;
-    for (uint32_t i = threadIdx.x; i < P2; i += blockDim.x)
-        buf[i] = i < n ? a[i] : ~0ull;
-    __syncthreads();
-    for (uint32_t k = 2; k <= P2; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < P2; i += blockDim.x) {
-                const uint32_t ixj = i ^ j;
-                if (ixj > i) {
-                    const uint64_t x = buf[i], y = buf[ixj];
-                    const bool up = (i & k) == 0;
-                    if ((x > y) == up) {
-                        buf[i] = y;
-                        buf[ixj] = x;
+    const uint64_t *buf;
+    if (P2 <= kSortSmemKeys) {
+        for (uint32_t i = threadIdx.x; i < P2; i += blockDim.x)
+            sk[i] = i < n ? a[i] : ~0ull;
+        __syncthreads();
+        for (uint32_t k = 2; k <= P2; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t i = threadIdx.x; i < P2; i += blockDim.x) {
+                    const uint32_t ixj = i ^ j;
+                    if (ixj > i) {
+                        const uint64_t x = sk[i], y = sk[ixj];
+                        const bool up = (i & k) == 0;
+                        if ((x > y) == up) {
+                            sk[i] = y;
+                            sk[ixj] = x;
+                        }
                     }
                 }
+                __syncthreads();
             }
-            __syncthreads();
         }
+        buf = sk;
+    } else {
+        buf = block_radix_sort(a, tmp + in.raw_off, n, 2 * in.l, reinterpret_cast<uint32_t *>(sk));
+        __syncthreads();
     }
     uint32_t local = 0;
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
@@ -676,7 +844,7 @@ cudaError_t init_tables()
 
 size_t main_smem_bytes()
 {
-    return kWarps * sizeof(WarpSmem) + sizeof(CtaSmem);
+    return kWarps * sizeof(WarpSmem) + kRowSmemCap * sizeof(uint2) + sizeof(CtaSmem);
 }
 
 cudaError_t main_occupancy(int *blocks_per_sm, bool count_mode)
@@ -705,6 +873,13 @@ cudaError_t launch_main(const MainParams &p, int blocks, bool count_mode, cudaSt
     return cudaGetLastError();
 }
 
+cudaError_t launch_compat(const InstDev *inst, int ninst, const long long *row_prefix, long long total_rows,
+                          const uint2 *planes, uint32_t *compat, int blocks, cudaStream_t st)
+{
+    compat_kernel<<<blocks, 256, 0, st>>>(inst, ninst, row_prefix, total_rows, planes, compat);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack(const InstDev *inst, int ninst, const long long *win_prefix, long long total_windows,
                         const uint8_t *seqs, uint2 *planes, uint32_t *flags, int blocks, cudaStream_t st)
 {
@@ -712,11 +887,11 @@ cudaError_t launch_pack(const InstDev *inst, int ninst, const long long *win_pre
     return cudaGetLastError();
 }
 
-cudaError_t launch_sort_unique(const InstDev *inst, const int *inst_list, int nlist, uint64_t *raw,
+cudaError_t launch_sort_unique(const InstDev *inst, const int *inst_list, int nlist, uint64_t *raw, uint64_t *tmp,
                                const uint32_t *raw_count, const uint32_t *flags, StatusDev *status,
                                uint64_t *dense, uint32_t dense_cap, uint32_t *dense_total, cudaStream_t st)
 {
-    const size_t smem = kSortSmemKeys * sizeof(uint64_t);
+    const size_t smem = std::max<size_t>(kSortSmemKeys * sizeof(uint64_t), (2 * 32 * 256 + 256) * sizeof(uint32_t));
     static thread_local int attr_set_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -726,7 +901,7 @@ cudaError_t launch_sort_unique(const InstDev *inst, const int *inst_list, int nl
             return e;
         attr_set_dev = dev;
     }
-    sort_unique_kernel<<<nlist, kSortThreads, smem, st>>>(inst, inst_list, raw, raw_count, flags, status, dense,
+    sort_unique_kernel<<<nlist, kSortThreads, smem, st>>>(inst, inst_list, raw, tmp, raw_count, flags, status, dense,
                                                           dense_cap, dense_total);
     return cudaGetLastError();
 }

@@ -26,8 +26,6 @@ using namespace pms;
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr size_t kDefaultMaxMotifs = size_t(1) << 20;      // single-instance solves
-constexpr size_t kDefaultBatchMaxMotifs = size_t(1) << 16; // per instance of a batch
 constexpr int kDefaultChunkWork = 1 << 16;
 constexpr uint32_t kInlineKeys = 512;   // codes downloaded together with the status block
 
@@ -143,7 +141,7 @@ struct pms_ctx {
         void *p = nullptr;
         size_t cap = 0;
     };
-    DBuf d_seqs, d_planes, d_raw, d_meta, d_ctr, d_scratch, d_result;
+    DBuf d_seqs, d_planes, d_raw, d_tmp, d_compat, d_meta, d_ctr, d_scratch, d_result;
     void *h_result = nullptr;   // pinned
     size_t h_result_cap = 0;
     void *h_meta = nullptr;     // pinned staging for descriptors and inputs
@@ -153,7 +151,7 @@ struct pms_ctx {
     bool stats_count = false;
     size_t stats_k = 0;
 
-    std::vector<pms_result> batch_out;  // storage for pms_solve_batch results
+    std::vector<std::vector<uint64_t>> owned;   // result codes returned by the last solve call
     Served *served = nullptr;
 
     int fail(int code, const char *fmt, ...)
@@ -289,6 +287,7 @@ namespace {
 struct InstSpec {
     int n, m, l, d;
     const uint8_t *host_seqs;   // may be null (device-resident input)
+    uint32_t raw_cap = 0;       // 0: from max_motifs or the estimate
 };
 
 // Host image of everything the kernels need for a set of instances.
@@ -296,17 +295,19 @@ struct Plan {
     std::vector<InstDev> inst;
     std::vector<Segment> seg;
     std::vector<long long> win_prefix;
+    std::vector<long long> row_prefix;   // compatibility rows: sum of W * (n - 1)
     std::vector<int> ctab;
     long long total_items = 0;
     long long total_windows = 0;
-    size_t seq_bytes = 0, planes = 0, raw = 0;
+    long long total_rows = 0;
+    size_t seq_bytes = 0, planes = 0, raw = 0, compat = 0;
     int rows_cap = 1;
     uint64_t candidates = 0;
 };
 
 // Byte layout of the descriptor block (device d_meta, pinned h_meta).
 struct MetaLayout {
-    size_t inst, seg, win, ctab, total;
+    size_t inst, seg, win, rowp, ctab, total;
     MetaLayout(const Plan &p)
     {
         size_t o = 0;
@@ -316,6 +317,8 @@ struct MetaLayout {
         o = round_up(o + p.seg.size() * sizeof(Segment), 16);
         win = o;
         o = round_up(o + p.win_prefix.size() * sizeof(long long), 16);
+        rowp = o;
+        o = round_up(o + p.row_prefix.size() * sizeof(long long), 16);
         ctab = o;
         o = round_up(o + p.ctab.size() * sizeof(int), 16);
         total = o;
@@ -351,11 +354,38 @@ struct ResLayout {
 
 }  // namespace
 
+// Expected raw motif count (duplicates included) of an FM-like instance under
+// independence: W |B(x,d)| q^(n-1), q = P(a random sequence has a window
+// within d of a fixed l-mer). Sizes the raw buffer; overflow triggers a retry.
+static double expected_raw(int n, int m, int l, int d)
+{
+    const int W = m - l + 1;
+    const double nb = (double)ball_size(l, d);
+    const double p = std::min(1.0, nb / std::pow(4.0, l));
+    const double q = 1.0 - std::pow(1.0 - p, W);
+    return W * nb * std::pow(q, n - 1);
+}
+
+static uint32_t default_cap(const pms_ctx *h, const InstSpec &s, bool single)
+{
+    if (s.raw_cap)
+        return s.raw_cap;
+    if (h->opt.max_motifs)
+        return pow2_at_least(h->opt.max_motifs);
+    const double est = 4.0 * expected_raw(s.n, s.m, s.l, s.d) + 256.0;
+    const size_t lo = single ? (size_t)1 << 16 : (size_t)1 << 12;
+    return pow2_at_least(std::min<double>(std::max<double>(est, lo), (double)(1u << 24)));
+}
+
+static int default_prune_rows(int n, int d)
+{
+    (void)d;
+    return n - 1;
+}
+
 static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
 {
     Plan P;
-    const size_t maxm = h->opt.max_motifs ? h->opt.max_motifs
-                                          : (specs.size() == 1 ? kDefaultMaxMotifs : kDefaultBatchMaxMotifs);
     long long work = 0;
     for (size_t k = 0; k < specs.size(); ++k) {
         const InstSpec &s = specs[k];
@@ -365,9 +395,11 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
         in.l = s.l;
         in.d = s.d;
         in.W = s.m - s.l + 1;
+        in.NW = (in.W + 31) / 32;
         const ChunkTable &ct = h->chunks(s.l, s.d);
         in.cps = ct.cps;
         in.grab = h->opt.grab > 0 ? h->opt.grab : default_grab(s.d);
+        in.prune_rows = default_prune_rows(s.n, s.d);
         in.ctab = (int)P.ctab.size();
         P.ctab.insert(P.ctab.end(), ct.tab.begin(), ct.tab.end());
         in.seq_off = (long long)P.seq_bytes;
@@ -375,10 +407,14 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
         in.plane_off = (long long)P.planes;
         P.planes += (size_t)s.n * in.W;
         in.raw_off = (long long)P.raw;
-        in.raw_cap = pow2_at_least(maxm);
+        in.raw_cap = default_cap(h, s, specs.size() == 1);
         P.raw += in.raw_cap;
+        in.compat_off = (long long)P.compat;
+        P.compat += (size_t)in.W * (s.n - 1) * in.NW;
         P.win_prefix.push_back(P.total_windows);
         P.total_windows += (long long)s.n * in.W;
+        P.row_prefix.push_back(P.total_rows);
+        P.total_rows += (long long)in.W * (s.n - 1);
         P.rows_cap = std::max(P.rows_cap, (s.n - 1) * in.W);
         const int chunks = in.W * in.cps;
         P.seg.push_back(Segment{work, (int)k, 0, chunks, 0});
@@ -401,7 +437,8 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     CtrLayout cl(k);
     int rc;
     if ((rc = h->ensure(h->d_meta, ml.total)) || (rc = h->ensure(h->d_ctr, cl.total)) ||
-        (rc = h->ensure(h->d_planes, P.planes * sizeof(uint2))) || (rc = h->ensure(h->d_raw, P.raw * 8)))
+        (rc = h->ensure(h->d_planes, P.planes * sizeof(uint2))) || (rc = h->ensure(h->d_raw, P.raw * 8)) ||
+        (rc = h->ensure(h->d_tmp, P.raw * 8)) || (rc = h->ensure(h->d_compat, P.compat * 4)))
         return rc;
     int occ = h->occ[count_mode ? 1 : 0];
     if (h->opt.ctas_per_sm > 0)
@@ -409,7 +446,7 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     occ = std::max(occ, 1);
     const long long blocks_ll = std::min<long long>((long long)h->num_sms * occ, std::max<long long>(P.total_items, 1));
     const int blocks = (int)blocks_ll;
-    if ((rc = h->ensure(h->d_scratch, (size_t)blocks * 3 * (size_t)P.rows_cap * 4)))
+    if ((rc = h->ensure(h->d_scratch, (size_t)blocks * (size_t)P.rows_cap * sizeof(uint2))))
         return rc;
     if ((rc = h->ensure_host(h->h_meta, h->h_meta_cap, ml.total)))
         return rc;
@@ -418,6 +455,7 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     std::memcpy(hm + ml.inst, P.inst.data(), P.inst.size() * sizeof(InstDev));
     std::memcpy(hm + ml.seg, P.seg.data(), P.seg.size() * sizeof(Segment));
     std::memcpy(hm + ml.win, P.win_prefix.data(), P.win_prefix.size() * sizeof(long long));
+    std::memcpy(hm + ml.rowp, P.row_prefix.data(), P.row_prefix.size() * sizeof(long long));
     std::memcpy(hm + ml.ctab, P.ctab.data(), P.ctab.size() * sizeof(int));
     cudaStream_t st = h->stream;
     char *dm = (char *)h->d_meta.p;
@@ -435,6 +473,13 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     if ((e = launch_pack(d_inst, (int)k, (const long long *)(dm + ml.win), P.total_windows, d_seq_src,
                          (uint2 *)h->d_planes.p, d_flags, std::max(pack_blocks, 1), st)) != cudaSuccess)
         return h->cuda_fail(e, "pack kernel");
+    if (P.total_rows > 0) {
+        const int cw_blocks = (int)std::min<long long>((P.total_rows + 7) / 8, (long long)h->num_sms * 16);
+        if ((e = launch_compat(d_inst, (int)k, (const long long *)(dm + ml.rowp), P.total_rows,
+                               (const uint2 *)h->d_planes.p, (uint32_t *)h->d_compat.p, std::max(cw_blocks, 1), st)) !=
+            cudaSuccess)
+            return h->cuda_fail(e, "compatibility kernel");
+    }
     MainParams mp{};
     mp.inst = d_inst;
     mp.seg = (const Segment *)(dm + ml.seg);
@@ -442,18 +487,20 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     mp.total = P.total_items;
     mp.head = (unsigned long long *)(dc + cl.head);
     mp.planes = (const uint2 *)h->d_planes.p;
+    mp.compat = (const uint32_t *)h->d_compat.p;
     mp.ctab = (const int *)(dm + ml.ctab);
     mp.raw = (uint64_t *)h->d_raw.p;
     mp.raw_count = d_rawcnt;
     mp.flags = d_flags;
-    mp.scratch = (uint32_t *)h->d_scratch.p;
+    mp.scratch = (uint2 *)h->d_scratch.p;
     mp.rows_cap = P.rows_cap;
     mp.counters = (unsigned long long *)(dc + cl.work);
     cudaEventRecord(h->evm0, st);
     if (P.total_items > 0 && (e = launch_main(mp, blocks, count_mode, st)) != cudaSuccess)
         return h->cuda_fail(e, "verification kernel");
     cudaEventRecord(h->evm1, st);
-    if ((e = launch_sort_unique(d_inst, nullptr, (int)k, (uint64_t *)h->d_raw.p, d_rawcnt, d_flags, status_out,
+    if ((e = launch_sort_unique(d_inst, nullptr, (int)k, (uint64_t *)h->d_raw.p, (uint64_t *)h->d_tmp.p, d_rawcnt,
+                                d_flags, status_out,
                                 dense_out, dense_cap, (uint32_t *)(dc + cl.dense_total), st)) != cudaSuccess)
         return h->cuda_fail(e, "sort/unique kernel");
     cudaEventRecord(h->ev1, st);
@@ -575,6 +622,55 @@ static int run_host_plan(pms_ctx *h, const Plan &P, const std::vector<InstSpec> 
     return PMS_OK;
 }
 
+struct InstOut {
+    int status = PMS_OK;
+    uint32_t raw_count = 0;
+    std::vector<uint64_t> codes;
+};
+
+// Solves instances from host memory; instances whose raw motif buffer
+// overflowed are solved again with a larger buffer (unless the caller fixed
+// max_motifs), so the returned sets are complete.
+static int solve_specs(pms_ctx *h, std::vector<InstSpec> specs, std::vector<InstOut> &out, double t0)
+{
+    out.assign(specs.size(), InstOut{});
+    std::vector<int> todo(specs.size());
+    for (size_t i = 0; i < specs.size(); ++i)
+        todo[i] = (int)i;
+    uint64_t candidates = 0;
+    while (!todo.empty()) {
+        std::vector<InstSpec> sub;
+        for (int i : todo)
+            sub.push_back(specs[i]);
+        Plan P = make_plan(h, sub);
+        candidates += P.candidates;
+        int rc = run_host_plan(h, P, sub, t0);
+        if (rc)
+            return rc;
+        const StatusDev *sd = (const StatusDev *)h->h_result;
+        ResLayout rl(sub.size(), 0);
+        const uint64_t *dense = (const uint64_t *)((const char *)h->h_result + rl.dense);
+        std::vector<int> again;
+        for (size_t j = 0; j < sub.size(); ++j) {
+            const int idx = todo[j];
+            const uint32_t cap = P.inst[j].raw_cap;
+            const bool overflow = sd[j].raw_count > cap;
+            if (overflow && !(sd[j].flags & kFlagInvalidByte) && !h->opt.max_motifs && cap < (1u << 26)) {
+                specs[idx].raw_cap = pow2_at_least(std::max<size_t>((size_t)cap * 8, (size_t)sd[j].raw_count * 2));
+                again.push_back(idx);
+                continue;
+            }
+            InstOut &o = out[idx];
+            o.status = status_code(sd[j]);
+            o.raw_count = sd[j].raw_count;
+            o.codes.assign(dense + sd[j].dense_off, dense + sd[j].dense_off + sd[j].unique_count);
+        }
+        todo.swap(again);
+    }
+    h->stats.candidates = candidates;
+    return PMS_OK;
+}
+
 // ----------------------------------------------------------------------------- served form
 
 struct Served {};
@@ -671,18 +767,17 @@ int pms_solve(pms_ctx *h, const uint8_t *seqs, int n, int m, int l, int d, const
         return rc;
     cudaSetDevice(h->device);
     std::vector<InstSpec> specs{InstSpec{n, m, l, d, seqs}};
-    Plan P = make_plan(h, specs);
-    if ((rc = run_host_plan(h, P, specs, t0)))
+    std::vector<InstOut> res;
+    if ((rc = solve_specs(h, specs, res, t0)))
         return rc;
-    const StatusDev *sd = (const StatusDev *)h->h_result;
-    ResLayout rl(1, 0);
-    *motifs = (const uint64_t *)((const char *)h->h_result + rl.dense) + sd[0].dense_off;
-    *count = sd[0].unique_count;
-    rc = status_code(sd[0]);
+    h->owned.resize(1);
+    h->owned[0].swap(res[0].codes);
+    *motifs = h->owned[0].data();
+    *count = h->owned[0].size();
+    rc = res[0].status;
     if (rc == PMS_ETOOMANY) {
-        *count = sd[0].raw_count;
-        return h->fail(rc, "%u motifs (with duplicates) exceed the capacity %u; raise max_motifs", sd[0].raw_count,
-                       P.inst[0].raw_cap);
+        *count = res[0].raw_count;
+        return h->fail(rc, "%u motifs (with duplicates) exceed the capacity; raise max_motifs", res[0].raw_count);
     }
     if (rc)
         return h->fail(rc, "invalid input byte");
@@ -740,18 +835,17 @@ int pms_solve_batch(pms_ctx *h, const pms_instance *inst, int k, pms_result *out
     if (specs.empty())
         return PMS_OK;
     cudaSetDevice(h->device);
-    Plan P = make_plan(h, specs);
+    std::vector<InstOut> res;
     int rc;
-    if ((rc = run_host_plan(h, P, specs, t0)))
+    if ((rc = solve_specs(h, specs, res, t0)))
         return rc;
-    const StatusDev *sd = (const StatusDev *)h->h_result;
-    ResLayout rl(specs.size(), 0);
-    const uint64_t *dense = (const uint64_t *)((const char *)h->h_result + rl.dense);
+    h->owned.assign(specs.size(), {});
     for (size_t j = 0; j < specs.size(); ++j) {
         pms_result &r = out[which[j]];
-        r.status = status_code(sd[j]);
-        r.motifs = dense + sd[j].dense_off;
-        r.count = r.status == PMS_ETOOMANY ? sd[j].raw_count : sd[j].unique_count;
+        h->owned[j].swap(res[j].codes);
+        r.status = res[j].status;
+        r.motifs = h->owned[j].data();
+        r.count = r.status == PMS_ETOOMANY ? res[j].raw_count : h->owned[j].size();
     }
     return PMS_OK;
 }
@@ -851,7 +945,7 @@ void pms_destroy(pms_ctx *h)
     served_stop(h);
     if (h->stream)
         cudaStreamSynchronize(h->stream);
-    pms_ctx::DBuf *bufs[] = {&h->d_seqs, &h->d_planes, &h->d_raw, &h->d_meta, &h->d_ctr, &h->d_scratch, &h->d_result};
+    pms_ctx::DBuf *bufs[] = {&h->d_seqs, &h->d_planes, &h->d_raw, &h->d_tmp, &h->d_compat, &h->d_meta, &h->d_ctr, &h->d_scratch, &h->d_result};
     for (auto *b : bufs)
         h->dev_free(b->p, b->cap);
     if (h->h_result)
