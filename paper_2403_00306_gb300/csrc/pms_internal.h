@@ -12,8 +12,9 @@ constexpr int kNMax = 64;      // sequences per instance
 constexpr int kWarps = 8;      // warps per CTA of the verification kernel
 constexpr int kThreads = kWarps * 32;
 constexpr int kRbCap = 256;    // entries of a subset-reduced occurrence row kept in shared memory
-constexpr int kListCap = 512;  // surviving candidates a warp buffers before checking further rows
-constexpr int kRowSmemCap = 4096;  // feasible occurrences of one seed held in shared memory
+constexpr int kListCap = 256;  // surviving candidates a warp buffers before checking further rows
+constexpr int kSubBatch = 64;  // tree nodes (position subsets) a warp filters together
+constexpr int kRowSmemCap = 4096;  // feasible occurrences of one seed held in shared memory (padded)
 
 // Flags reported per instance.
 constexpr uint32_t kFlagInvalidByte = 1u;
@@ -78,8 +79,9 @@ struct MainParams {
     uint64_t *raw;                // raw motif codes
     uint32_t *raw_count;          // per instance
     uint32_t *flags;              // per instance
-    uint2 *scratch;               // per CTA: rows_cap entries, used when a seed's rows exceed shared memory
-    int rows_cap;                 // max (n - 1) * W over the instances
+    uint32_t *scratch;            // per CTA: 3 * rows_cap words (masks, then planes), used when a
+                                  // seed's rows exceed shared memory
+    int rows_cap;                 // max (n - 1) * (W + 3) over the instances
     unsigned long long *counters; // kCntNum entries (count mode)
     int *done;                    // per segment: finished items (served form), may be null
 };

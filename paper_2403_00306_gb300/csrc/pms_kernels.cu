@@ -35,14 +35,15 @@ __constant__ uint32_t c_binom[kLMax + 1][kLMax + 1];  // C(a, b), 0 when b > a
 __constant__ unsigned long long c_pow3[kLMax + 1];
 
 struct __align__(16) WarpSmem {
-    uint2 rb0[kRbCap + 4];   // row 0 reduced by the current subset
-    uint2 rb1[kRbCap + 4];   // scratch reduced row for rows 1..
-    uint2 list[kListCap];    // candidates that survived row 0
+    uint2 rb0[kRbCap + 4];      // row 0 reduced by the current subset
+    uint2 rb1[kRbCap + 4];      // scratch reduced row for rows 1..
+    uint2 list[kListCap];       // candidates that survived row 0
+    uint32_t subs[kSubBatch];   // position subsets being filtered
 };
 
 struct __align__(16) CtaSmem {
     int row_len[kNMax];      // indexed by sequence
-    int row_off[kNMax];      // indexed by sequence: first entry of its row
+    int row_off[kNMax];      // indexed by sequence: first entry of its row (multiple of 4)
     int row_order[kNMax];    // sequences 1..n-1, smallest row first
     unsigned long long g;
     int inst, seed, chunk;
@@ -70,14 +71,6 @@ __device__ __forceinline__ uint32_t unrank_subset(uint32_t rank, int k, int l)
     return P;
 }
 
-// Next k-subset in colex order (the next larger integer with the same number of set bits).
-__device__ __forceinline__ uint32_t next_subset(uint32_t P)
-{
-    const uint32_t u = P & (0u - P);
-    const uint32_t v = P + u;
-    return v | (((v ^ P) >> 2) >> (__ffs(P) - 1));
-}
-
 __device__ __forceinline__ uint64_t to_key(uint32_t h, uint32_t lo, int l)
 {
     uint64_t key = 0;
@@ -86,27 +79,31 @@ __device__ __forceinline__ uint64_t to_key(uint32_t h, uint32_t lo, int l)
     return key;
 }
 
-// Keeps the occurrences w of one row (planes in `row`, shared or global
-// memory) with popc(D_w ^ P) <= d, where D_w = (xh ^ w.hi) | (xl ^ w.lo);
-// writes up to kRbCap of them to rb, pads rb to a multiple of 4 entries, and
+// A seed's feasible occurrences: per entry the mismatch mask D of the seed
+// and the window, and the window's planes; rows are padded to a multiple of 4
+// entries with copies of their last entry.
+struct Rows {
+    const uint32_t *D;
+    const uint2 *HL;
+};
+
+// Keeps the occurrences w of one row with popc(D_w ^ P) <= d; writes up to
+// kRbCap of their planes to rb, pads rb to a multiple of 4 entries, and
 // returns how many qualify.
-__device__ __forceinline__ int reduce_row(const uint2 *row, int len, uint32_t xh, uint32_t xl, uint32_t P, int d,
-                                          uint2 *rb, int lane, uint32_t lt)
+__device__ __forceinline__ int reduce_row(const uint32_t *D, const uint2 *HL, int len, uint32_t P, int d, uint2 *rb,
+                                          int lane, uint32_t lt)
 {
     int k = 0;
     for (int e0 = 0; e0 < len; e0 += 32) {
         const int e = e0 + lane;
         bool keep = false;
-        uint2 w = make_uint2(0u, 0u);
-        if (e < len) {
-            w = row[e];
-            keep = __popc(((xh ^ w.x) | (xl ^ w.y)) ^ P) <= d;
-        }
+        if (e < len)
+            keep = __popc(D[e] ^ P) <= d;
         const uint32_t bal = __ballot_sync(kFull, keep);
         if (keep) {
             const int pos = k + __popc(bal & lt);
             if (pos < kRbCap)
-                rb[pos] = w;
+                rb[pos] = HL[e];
         }
         k += __popc(bal);
     }
@@ -115,23 +112,6 @@ __device__ __forceinline__ int reduce_row(const uint2 *row, int len, uint32_t xh
         rb[k + lane] = rb[k - 1];
     __syncwarp();
     return k;
-}
-
-// Does the row hold at least one occurrence with popc(D_w ^ P) <= d?
-__device__ __forceinline__ bool row_feasible(const uint2 *row, int len, uint32_t xh, uint32_t xl, uint32_t P, int d,
-                                             int lane)
-{
-    for (int e0 = 0; e0 < len; e0 += 32) {
-        const int e = e0 + lane;
-        bool q = false;
-        if (e < len) {
-            const uint2 w = row[e];
-            q = __popc(((xh ^ w.x) | (xl ^ w.y)) ^ P) <= d;
-        }
-        if (__any_sync(kFull, q))
-            return true;
-    }
-    return false;
 }
 
 // Is some entry of a reduced row (shared memory, padded to 4) within d of (ch, cl)?
@@ -151,11 +131,11 @@ __device__ __forceinline__ bool check_smem(const uint2 *rb, int k, uint32_t ch, 
 
 // Same test against a full (unreduced) row; used when the reduced row does
 // not fit in the warp's buffer.
-__device__ __forceinline__ bool check_row(const uint2 *row, int len, uint32_t ch, uint32_t cl, int d)
+__device__ __forceinline__ bool check_row(const uint2 *HL, int len, uint32_t ch, uint32_t cl, int d)
 {
     int mn = 64;
     for (int e = 0; e < len; ++e) {
-        const uint2 w = row[e];
+        const uint2 w = HL[e];
         mn = min(mn, __popc((ch ^ w.x) | (cl ^ w.y)));
     }
     return mn <= d;
@@ -168,7 +148,7 @@ struct WarpCtx {
     int lane;
     uint32_t lt;
     uint32_t xh, xl;           // the seed l-mer
-    const uint2 *rows;         // feasible occurrences of the seed (shared or global memory)
+    Rows rows;                 // feasible occurrences of the seed (shared or global memory)
     const CtaSmem *cs;
     WarpSmem *ws;
     unsigned long long *cnt;   // per-thread counters (count mode)
@@ -214,8 +194,8 @@ __device__ __forceinline__ void finish_list(const WarpCtx &c, uint32_t P, int N)
     for (int r = 1; r < nrows && N > 0; ++r) {
         const int ri = c.cs->row_order[r];
         const int len = c.cs->row_len[ri];
-        const uint2 *row = c.rows + c.cs->row_off[ri];
-        const int k = reduce_row(row, len, c.xh, c.xl, P, in.d, c.ws->rb1, c.lane, c.lt);
+        const int off = c.cs->row_off[ri];
+        const int k = reduce_row(c.rows.D + off, c.rows.HL + off, len, P, in.d, c.ws->rb1, c.lane, c.lt);
         if (kCount && c.lane == 0)
             c.cnt[kCntCmpReduce] += len;
         if (k == 0) {
@@ -232,7 +212,7 @@ __device__ __forceinline__ void finish_list(const WarpCtx &c, uint32_t P, int N)
                 v = list[idx];
             bool hit = false;
             if (alive) {
-                hit = sm ? check_smem(c.ws->rb1, k, v.x, v.y, in.d) : check_row(row, len, v.x, v.y, in.d);
+                hit = sm ? check_smem(c.ws->rb1, k, v.x, v.y, in.d) : check_row(c.rows.HL + off, len, v.x, v.y, in.d);
                 if (kCount)
                     c.cnt[kCntCmpVerify] += sm ? k : len;
             }
@@ -249,46 +229,31 @@ __device__ __forceinline__ void finish_list(const WarpCtx &c, uint32_t P, int N)
         emit<kCount>(c, list, N);
 }
 
-// One node of T_d(x): the subset P of changed positions (|P| = lev).
-// First every one of the first prune_rows rows (smallest first) must keep an
-// occurrence under the node's bound, else the node's 3^lev leaves are
-// dismissed together. Then lanes own the letter choices on the lowest
-// min(lev, 3) positions of P (27 lanes at most) and every lane walks the
-// choices on the remaining positions with a base-3 odometer kept as two masks
-// (Dh, Dl) over those positions: state (0,1) -> (1,0) -> (1,1) -> carry, i.e.
-// XOR deltas 1, 2, 3 of the 2-bit codes.
+// The leaves of one tree node P (|P| = lev) that survived the row filter.
+// Lanes own the letter choices on the lowest min(lev, 3) positions of P (27
+// lanes at most); every lane walks the choices on the remaining positions
+// with a base-3 odometer kept as two masks (Dh, Dl) over those positions:
+// state (0,1) -> (1,0) -> (1,1) -> carry, i.e. XOR deltas 1, 2, 3 of the
+// 2-bit codes. Each leaf is tested against row 0 reduced by P; the hits go
+// to the warp's list and on to the other rows.
 template <bool kCount>
-__device__ __forceinline__ void process_subset(const WarpCtx &c, uint32_t P, int lev)
+__device__ __forceinline__ void expand_subset(const WarpCtx &c, uint32_t P)
 {
     const InstDev &in = c.in;
     const int d = in.d;
     const int nrows = in.n - 1;
-    if (kCount && c.lane == 0)
-        c.cnt[kCntSubsets] += 1;
+    const int lev = __popc(P);
 
-    int k0 = 0, len0 = 0;
-    const uint2 *row0 = c.rows;
+    int k0 = 0, len0 = 0, off0 = 0;
     if (nrows > 0) {
         const int r0 = c.cs->row_order[0];
         len0 = c.cs->row_len[r0];
-        row0 = c.rows + c.cs->row_off[r0];
-        k0 = reduce_row(row0, len0, c.xh, c.xl, P, d, c.ws->rb0, c.lane, c.lt);
+        off0 = c.cs->row_off[r0];
+        k0 = reduce_row(c.rows.D + off0, c.rows.HL + off0, len0, P, d, c.ws->rb0, c.lane, c.lt);
         if (kCount && c.lane == 0)
             c.cnt[kCntCmpReduce] += len0;
-        bool pruned = k0 == 0;
-        const int npr = min(in.prune_rows, nrows);
-        for (int r = 1; r < npr && !pruned; ++r) {
-            const int ri = c.cs->row_order[r];
-            const int len = c.cs->row_len[ri];
-            pruned = !row_feasible(c.rows + c.cs->row_off[ri], len, c.xh, c.xl, P, d, c.lane);
-            if (kCount && c.lane == 0)
-                c.cnt[kCntCmpReduce] += len;
-        }
-        if (pruned) {
-            if (kCount && c.lane == 0)
-                c.cnt[kCntPruned] += 1;
+        if (k0 == 0)
             return;
-        }
     }
 
     uint32_t t = P;
@@ -319,7 +284,7 @@ __device__ __forceinline__ void process_subset(const WarpCtx &c, uint32_t P, int
             if (nrows == 0)
                 hit = true;
             else
-                hit = sm0 ? check_smem(c.ws->rb0, k0, ch, cl, d) : check_row(row0, len0, ch, cl, d);
+                hit = sm0 ? check_smem(c.ws->rb0, k0, ch, cl, d) : check_row(c.rows.HL + off0, len0, ch, cl, d);
             if (kCount) {
                 c.cnt[kCntTested] += 1;
                 c.cnt[kCntCmpVerify] += sm0 ? k0 : len0;
@@ -346,13 +311,63 @@ __device__ __forceinline__ void process_subset(const WarpCtx &c, uint32_t P, int
         finish_list<kCount>(c, P, listN);
 }
 
+// Breadth-first filter of the subsets in ws->subs[0..N): for the first
+// prune_rows rows in size order, a subset P stays only if the row holds an
+// occurrence with popc(D_w ^ P) <= d (the bound every leaf of P must meet).
+// Lanes own subsets, row entries are read by all lanes at once; survivors are
+// compacted after each row. Returns the number of survivors.
+template <bool kCount>
+__device__ __forceinline__ int filter_subsets(const WarpCtx &c, int N)
+{
+    const InstDev &in = c.in;
+    const int d = in.d;
+    const int nrows = min(in.prune_rows, in.n - 1);
+    uint32_t *subs = c.ws->subs;
+    for (int r = 0; r < nrows && N > 0; ++r) {
+        const int ri = c.cs->row_order[r];
+        const int len = c.cs->row_len[ri];
+        const uint4 *D4 = reinterpret_cast<const uint4 *>(c.rows.D + c.cs->row_off[ri]);
+        const int len4 = (len + 3) >> 2;
+        int newN = 0;
+        for (int b = 0; b < N; b += 32) {
+            const int idx = b + c.lane;
+            const bool alive = idx < N;
+            const uint32_t P = alive ? subs[idx] : 0u;
+            int mn = 64;
+            int e4 = 0;
+            for (; e4 < len4; ++e4) {
+                const uint4 v = D4[e4];
+                mn = min(mn, __popc(v.x ^ P));
+                mn = min(mn, __popc(v.y ^ P));
+                mn = min(mn, __popc(v.z ^ P));
+                mn = min(mn, __popc(v.w ^ P));
+                if ((e4 & 3) == 3 && __all_sync(kFull, !alive || mn <= d)) {
+                    ++e4;
+                    break;
+                }
+            }
+            if (kCount && alive)
+                c.cnt[kCntCmpReduce] += 4 * e4;
+            const bool pass = alive && mn <= d;
+            __syncwarp();
+            const uint32_t bal = __ballot_sync(kFull, pass);
+            if (pass)
+                subs[newN + __popc(bal & c.lt)] = P;
+            newN += __popc(bal);
+        }
+        __syncwarp();
+        N = newN;
+    }
+    return N;
+}
+
 // Gathers the feasible occurrences of seed `seed` (windows within 2d, from
-// the compatibility masks) into `rows` (shared memory when they fit, else
-// this CTA's global scratch), records each row's size and offset and the
+// the compatibility masks) into shared memory when they fit, else into this
+// CTA's global scratch; records each row's size, offset and the
 // smallest-first order, and whether every row is non-empty.
 __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &in, int seed, CtaSmem &cs,
-                                           uint2 *smem_rows, uint2 *glob_rows, int warp, int lane,
-                                           unsigned long long *cnt)
+                                           uint32_t *smem_D, uint2 *smem_HL, uint32_t *glob_D, uint2 *glob_HL,
+                                           int warp, int lane, unsigned long long *cnt)
 {
     const int n = in.n, NW = in.NW, W = in.W;
     const uint32_t *mask = p.compat + in.compat_off + (size_t)seed * (n - 1) * NW;
@@ -386,7 +401,7 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
             for (int r = 0; r < n - 1; ++r) {
                 const int i = cs.row_order[r];
                 cs.row_off[i] = off;
-                off += cs.row_len[i];
+                off += (cs.row_len[i] + 3) & ~3;
             }
             cs.total_rows = off;
             cs.feasible = !any_empty;
@@ -398,12 +413,14 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
     __syncthreads();
     if (!cs.feasible)
         return;
-    uint2 *rows = cs.rows_in_smem ? smem_rows : glob_rows;
+    uint32_t *Dd = cs.rows_in_smem ? smem_D : glob_D;
+    uint2 *Hd = cs.rows_in_smem ? smem_HL : glob_HL;
     const uint2 *pl = p.planes + in.plane_off;
+    const uint2 x = pl[seed];
     for (int i = 1 + warp; i < n; i += kWarps) {
         const uint32_t *mr = mask + (size_t)(i - 1) * NW;
         const uint2 *s = pl + (size_t)i * W;
-        uint2 *dst = rows + cs.row_off[i];
+        const int off = cs.row_off[i], len = cs.row_len[i];
         int base = 0;
         for (int k0 = 0; k0 < NW; k0 += 32) {
             const int k = k0 + lane;
@@ -415,13 +432,22 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
                 if (lane >= o)
                     incl += y;
             }
-            int pos = base + incl - c;
+            int pos = off + base + incl - c;
             while (bits) {
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1;
-                dst[pos++] = s[32 * k + b];
+                const uint2 w = s[32 * k + b];
+                Hd[pos] = w;
+                Dd[pos] = (x.x ^ w.x) | (x.y ^ w.y);
+                ++pos;
             }
             base += __shfl_sync(kFull, incl, 31);
+        }
+        __syncwarp();
+        const int padded = (len + 3) & ~3;
+        if (lane < padded - len) {
+            Hd[off + len + lane] = Hd[off + len - 1];
+            Dd[off + len + lane] = Dd[off + len - 1];
         }
     }
     __syncthreads();
@@ -432,11 +458,14 @@ __global__ void __launch_bounds__(kThreads, 2) main_kernel(MainParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *wsm = reinterpret_cast<WarpSmem *>(smem_raw);
-    uint2 *smem_rows = reinterpret_cast<uint2 *>(smem_raw + kWarps * sizeof(WarpSmem));
-    CtaSmem &cs = *reinterpret_cast<CtaSmem *>(smem_raw + kWarps * sizeof(WarpSmem) + kRowSmemCap * sizeof(uint2));
+    uint32_t *smem_D = reinterpret_cast<uint32_t *>(smem_raw + kWarps * sizeof(WarpSmem));
+    uint2 *smem_HL = reinterpret_cast<uint2 *>(smem_raw + kWarps * sizeof(WarpSmem) + kRowSmemCap * sizeof(uint32_t));
+    CtaSmem &cs = *reinterpret_cast<CtaSmem *>(smem_raw + kWarps * sizeof(WarpSmem) +
+                                               kRowSmemCap * (sizeof(uint32_t) + sizeof(uint2)));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    uint2 *glob_rows = p.scratch + (size_t)blockIdx.x * (size_t)p.rows_cap;
+    uint32_t *glob_D = p.scratch + (size_t)blockIdx.x * 3 * (size_t)p.rows_cap;
+    uint2 *glob_HL = reinterpret_cast<uint2 *>(glob_D + p.rows_cap);
     unsigned long long cnt[kCount ? kCntNum : 1];
 #pragma unroll
     for (int i = 0; i < (kCount ? kCntNum : 1); ++i)
@@ -475,7 +504,7 @@ __global__ void __launch_bounds__(kThreads, 2) main_kernel(MainParams p)
         const InstDev in = p.inst[I];
         const bool rebuild = (I != cs.cached_inst) || (seed != cs.cached_seed);
         if (rebuild) {
-            build_rows(p, in, seed, cs, smem_rows, glob_rows, warp, lane, kCount ? cnt : nullptr);
+            build_rows(p, in, seed, cs, smem_D, smem_HL, glob_D, glob_HL, warp, lane, kCount ? cnt : nullptr);
             if (threadIdx.x == 0) {
                 cs.cached_inst = I;
                 cs.cached_seed = seed;
@@ -493,30 +522,37 @@ __global__ void __launch_bounds__(kThreads, 2) main_kernel(MainParams p)
         }
         if (cs.feasible) {
             const uint2 x = p.planes[in.plane_off + seed];
-            WarpCtx c{&p, in, I, lane, lt, x.x, x.y, cs.rows_in_smem ? smem_rows : glob_rows, &cs, &wsm[warp],
-                      kCount ? cnt : nullptr};
+            Rows rows{cs.rows_in_smem ? smem_D : glob_D, cs.rows_in_smem ? smem_HL : glob_HL};
+            WarpCtx c{&p, in, I, lane, lt, x.x, x.y, rows, &cs, &wsm[warp], kCount ? cnt : nullptr};
+            uint32_t *subs = wsm[warp].subs;
             for (;;) {
                 int start = 0;
                 if (lane == 0)
-                    start = atomicAdd(&cs.next, in.grab);
+                    start = atomicAdd(&cs.next, kSubBatch);
                 start = __shfl_sync(kFull, start, 0);
                 if (start >= g1)
                     break;
-                const int end = min(start + in.grab, g1);
-                int idx = start;
-                while (idx < end) {
+                const int N = min(kSubBatch, g1 - start);
+                for (int j = lane; j < N; j += 32) {
+                    const int g = start + j;
                     int lev = 0;
-                    while (tab[lev + 1] <= idx)
+                    while (tab[lev + 1] <= g)
                         ++lev;
-                    const int stop = min(end, tab[lev + 1]);
-                    uint32_t P = unrank_subset((uint32_t)(idx - tab[lev]), lev, in.l);
-                    for (int k = idx; k < stop; ++k) {
-                        process_subset<kCount>(c, P, lev);
-                        if (k + 1 < stop)
-                            P = next_subset(P);
-                    }
-                    idx = stop;
+                    subs[j] = unrank_subset((uint32_t)(g - tab[lev]), lev, in.l);
                 }
+                __syncwarp();
+                if constexpr (kCount) {
+                    if (lane == 0)
+                        cnt[kCntSubsets] += N;
+                }
+                const int S = filter_subsets<kCount>(c, N);
+                if constexpr (kCount) {
+                    if (lane == 0)
+                        cnt[kCntPruned] += N - S;
+                }
+                for (int sidx = 0; sidx < S; ++sidx)
+                    expand_subset<kCount>(c, subs[sidx]);
+                __syncwarp();
             }
         }
         __syncthreads();
@@ -844,7 +880,7 @@ cudaError_t init_tables()
 
 size_t main_smem_bytes()
 {
-    return kWarps * sizeof(WarpSmem) + kRowSmemCap * sizeof(uint2) + sizeof(CtaSmem);
+    return kWarps * sizeof(WarpSmem) + kRowSmemCap * (sizeof(uint32_t) + sizeof(uint2)) + sizeof(CtaSmem);
 }
 
 cudaError_t main_occupancy(int *blocks_per_sm, bool count_mode)

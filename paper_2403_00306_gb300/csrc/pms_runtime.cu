@@ -415,7 +415,7 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
         P.total_windows += (long long)s.n * in.W;
         P.row_prefix.push_back(P.total_rows);
         P.total_rows += (long long)in.W * (s.n - 1);
-        P.rows_cap = std::max(P.rows_cap, (s.n - 1) * in.W);
+        P.rows_cap = std::max(P.rows_cap, (s.n - 1) * (in.W + 3));
         const int chunks = in.W * in.cps;
         P.seg.push_back(Segment{work, (int)k, 0, chunks, 0});
         work += chunks;
@@ -446,7 +446,7 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     occ = std::max(occ, 1);
     const long long blocks_ll = std::min<long long>((long long)h->num_sms * occ, std::max<long long>(P.total_items, 1));
     const int blocks = (int)blocks_ll;
-    if ((rc = h->ensure(h->d_scratch, (size_t)blocks * (size_t)P.rows_cap * sizeof(uint2))))
+    if ((rc = h->ensure(h->d_scratch, (size_t)blocks * 3 * (size_t)P.rows_cap * sizeof(uint32_t))))
         return rc;
     if ((rc = h->ensure_host(h->h_meta, h->h_meta_cap, ml.total)))
         return rc;
@@ -492,7 +492,7 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     mp.raw = (uint64_t *)h->d_raw.p;
     mp.raw_count = d_rawcnt;
     mp.flags = d_flags;
-    mp.scratch = (uint2 *)h->d_scratch.p;
+    mp.scratch = (uint32_t *)h->d_scratch.p;
     mp.rows_cap = P.rows_cap;
     mp.counters = (unsigned long long *)(dc + cl.work);
     cudaEventRecord(h->evm0, st);
