@@ -40,6 +40,8 @@ extern "C" {
                               capacity; count still holds the raw count */
 #define PMS_EBUSY (-6)     /* the served queue is full */
 #define PMS_ENOTFOUND (-7) /* unknown or already released ticket */
+#define PMS_ESCRATCH (-8)  /* instance too large for the fixed scratch of
+                              pms_solve_device_noalloc */
 
 #define PMS_LMAX 32
 #define PMS_NMAX 64
@@ -164,6 +166,43 @@ int pms_probe_int_rate(pms_ctx *h, int kind, double *per_clk_per_sm);
 
 /* Releases the context, its device memory, stream and scheduler thread. */
 void pms_destroy(pms_ctx *h);
+
+/* Allocation-free form of pms_solve_device, for callers that may not
+ * allocate device memory once they are running: applications whose device
+ * memory is planned up front and handed out only by their own allocator,
+ * and hosts in which cudaMalloc/cudaFree are off limits because they can
+ * block, synchronize the device or fail under memory pressure at a time the
+ * caller cannot control. The paper has no counterpart; this is plumbing.
+ *
+ * It needs no context. Every intermediate buffer (window planes,
+ * compatibility masks, raw motif codes and their sort buffer, counters,
+ * descriptors, per-CTA row scratch) is carved from one fixed array of
+ * 16 MiB that the library's device code reserves on each GPU it is loaded
+ * on and holds until the process exits; nothing is allocated per call.
+ * The caller passes, as for pms_solve_device, device pointers to the n*m
+ * ASCII input bytes, to room for `capacity` motif codes (d_motifs), and to
+ * 4 x uint32 of status {raw count, unique count, flags, 0}; the work is
+ * enqueued on `cuda_stream` (NULL: the legacy default stream) of the
+ * current device and the call returns without waiting.
+ *
+ * Limits: besides the pms_solve_device limits, the instance's buffers plus
+ * the row scratch of at least one CTA must fit in the 16 MiB (n = 20,
+ * m = 600 needs about 2 MiB plus 0.13 MiB per CTA, and gets about 100
+ * CTAs); larger instances return PMS_ESCRATCH before any work is queued.
+ * At most 65536 raw motif codes (duplicates included) are kept: more set
+ * status flag bit 1, as with max_motifs.
+ *
+ * Set-up: the first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) and loads the kernels' constant tables
+ * with that device current; make that first call before any stream capture
+ * is begun. All calls share the one array and it keeps whatever the last
+ * call left there (the counters a call relies on are cleared at its start),
+ * so calls whose work overlaps on the GPU -- on different streams, or from
+ * different threads without ordering -- race and corrupt each other's
+ * results; order them on one stream. Returns PMS_OK, PMS_EINVAL,
+ * PMS_ESCRATCH or PMS_ECUDA. */
+int pms_solve_device_noalloc(const uint8_t *d_seqs, int n, int m, int l, int d, uint64_t *d_motifs,
+                             size_t capacity, uint32_t *d_status, void *cuda_stream);
 
 #ifdef __cplusplus
 }

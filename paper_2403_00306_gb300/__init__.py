@@ -17,14 +17,16 @@ import numpy as np
 from . import build as _build
 
 PMS_OK, PMS_EINVAL, PMS_ENOMEM, PMS_ECUDA, PMS_ETIMEDOUT, PMS_ETOOMANY, PMS_EBUSY, PMS_ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7
+PMS_ESCRATCH = -8
 ERROR_NAMES = {0: "PMS_OK", -1: "PMS_EINVAL", -2: "PMS_ENOMEM", -3: "PMS_ECUDA", -4: "PMS_ETIMEDOUT",
-               -5: "PMS_ETOOMANY", -6: "PMS_EBUSY", -7: "PMS_ENOTFOUND"}
+               -5: "PMS_ETOOMANY", -6: "PMS_EBUSY", -7: "PMS_ENOTFOUND", -8: "PMS_ESCRATCH"}
 LMAX, NMAX = 32, 64
 
 #: names the C ABI exports (include/pms.h)
 ABI_FUNCTIONS = ["pms_create", "pms_set_stream", "pms_set_allocator", "pms_set_options", "pms_get_options",
                  "pms_solve", "pms_solve_device", "pms_solve_batch", "pms_submit", "pms_wait", "pms_release",
-                 "pms_get_stats", "pms_decode", "pms_last_error", "pms_probe_int_rate", "pms_destroy"]
+                 "pms_get_stats", "pms_decode", "pms_last_error", "pms_probe_int_rate", "pms_destroy",
+                 "pms_solve_device_noalloc"]
 
 
 class PMSError(RuntimeError):
@@ -99,6 +101,7 @@ def load(build_if_missing: bool = True):
             "pms_last_error": (ctypes.c_char_p, [vp]),
             "pms_probe_int_rate": (ci, [vp, ci, ctypes.POINTER(ctypes.c_double)]),
             "pms_destroy": (None, [vp]),
+            "pms_solve_device_noalloc": (ci, [vp, ci, ci, ci, ci, vp, sz, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -183,6 +186,19 @@ def pms_probe_int_rate(ctx: "Context", kind: int) -> float:
 
 def pms_set_allocator(ctx: "Context", alloc, free) -> None:
     ctx.set_allocator(alloc, free)
+
+
+def pms_solve_device_noalloc(d_seqs, n: int, m: int, l: int, d: int, d_motifs, capacity: int, d_status,
+                             stream=None) -> None:
+    """Allocation-free device solve (no context): every buffer comes from the library's fixed
+    per-GPU scratch array. Arguments as for Context.solve_device, plus the stream to enqueue on.
+    Calls that overlap on the GPU share that array and race; order them on one stream."""
+    p = lambda t: ctypes.c_void_p(int(t.data_ptr()) if hasattr(t, "data_ptr") else int(t))  # noqa: E731
+    handle = getattr(stream, "cuda_stream", stream)
+    rc = load().pms_solve_device_noalloc(p(d_seqs), int(n), int(m), int(l), int(d), p(d_motifs), int(capacity),
+                                         p(d_status), ctypes.c_void_p(int(handle or 0)))
+    if rc:
+        raise PMSError(rc, "pms_solve_device_noalloc")
 
 
 # ---------------------------------------------------------------- context object

@@ -966,3 +966,235 @@ void pms_destroy(pms_ctx *h)
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ allocation-free entry point
+//
+// pms_solve_device_noalloc runs the same pipeline as pms_solve_device for
+// callers that are not allowed to allocate device memory: every buffer it
+// needs comes from one fixed array in this file, reserved on each GPU when the
+// library's device code is loaded there and kept until the process exits.
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;   // the fixed array: 16 MiB per GPU
+constexpr uint32_t kNoAllocRawCap = 1u << 16;               // raw motif codes (duplicates included)
+constexpr int kNoAllocMaxDevices = 64;
+constexpr int kNoAllocMetaInts = 16384;                      // descriptor block: 64 KiB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+struct NoAllocDevice {
+    bool ready = false;
+    unsigned char *base = nullptr;   // device address of g_noalloc_scratch on this GPU
+    int num_sms = 0;
+    int occ = 1;
+};
+
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+
+// Once per device, with that device current: the array's device address,
+// the kernels' constant tables and launch attributes.
+int noalloc_setup(int dev, NoAllocDevice **out)
+{
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return PMS_EINVAL;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    NoAllocDevice &nd = g_noalloc_dev[dev];
+    if (!nd.ready) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || ptr == nullptr) {
+            cudaGetLastError();
+            return PMS_ECUDA;
+        }
+        if ((e = init_tables()) != cudaSuccess || (e = main_occupancy(&nd.occ, false)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&nd.num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) {
+            cudaGetLastError();
+            return PMS_ECUDA;
+        }
+        nd.base = (unsigned char *)ptr;
+        nd.occ = std::max(nd.occ, 1);
+        nd.ready = true;
+    }
+    *out = &nd;
+    return PMS_OK;
+}
+
+// The chunk table of one seed for (l, d), written into a caller array
+// (no heap): levoff[0..d+1] then (g0, g1) pairs. Returns the number of ints
+// written, or -1 if `cap` is too small. Same cuts as make_chunks.
+int chunk_table_into(int l, int d, int work, int *out, int cap, int *cps)
+{
+    if (d + 2 > cap)
+        return -1;
+    out[0] = 0;
+    for (int i = 0; i <= d; ++i)
+        out[i + 1] = out[i] + (int)binom(l, i);
+    int n = d + 2, pairs = 0;
+    double acc = 0;
+    int start = 0, g = 0;
+    for (int i = 0; i <= d; ++i) {
+        const double w = std::pow(3.0, i) + 24.0;
+        long long remaining = (long long)binom(l, i);
+        while (remaining > 0) {
+            const long long room = (long long)std::ceil(std::max(1.0, (work - acc) / w));
+            const long long take = std::min(room, remaining);
+            acc += take * w;
+            remaining -= take;
+            g += (int)take;
+            if (acc >= work) {
+                if (n + 2 > cap)
+                    return -1;
+                out[n++] = start;
+                out[n++] = g;
+                ++pairs;
+                start = g;
+                acc = 0;
+            }
+        }
+    }
+    if (start < g) {
+        if (n + 2 > cap)
+            return -1;
+        out[n++] = start;
+        out[n++] = g;
+        ++pairs;
+    }
+    *cps = pairs;
+    return n;
+}
+
+}  // namespace
+
+extern "C" int pms_solve_device_noalloc(const uint8_t *d_seqs, int n, int m, int l, int d, uint64_t *d_motifs,
+                                        size_t capacity, uint32_t *d_status, void *cuda_stream)
+{
+    if (!d_seqs || !d_motifs || !d_status || capacity == 0)
+        return PMS_EINVAL;
+    if (n < 1 || n > PMS_NMAX || l < 1 || l > PMS_LMAX || m < l || m > 65536 || d < 0 || d >= l)
+        return PMS_EINVAL;
+    uint64_t subsets = 0;
+    for (int i = 0; i <= d; ++i)
+        subsets += binom(l, i);
+    if (subsets > (uint64_t)INT32_MAX)
+        return PMS_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return PMS_ECUDA;
+    }
+    NoAllocDevice *nd = nullptr;
+    int rc = noalloc_setup(dev, &nd);
+    if (rc)
+        return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+
+    // descriptors, built on the stack
+    struct Meta {
+        InstDev inst;
+        Segment seg;
+        long long win_prefix;
+        long long row_prefix;
+        int ctab[kNoAllocMetaInts];
+    };
+    static_assert(sizeof(Meta) <= 80 * 1024, "descriptor block");
+    Meta meta;
+    std::memset(&meta, 0, offsetof(Meta, ctab));
+    int cps = 0;
+    const int nct = chunk_table_into(l, d, kDefaultChunkWork, meta.ctab, kNoAllocMetaInts, &cps);
+    if (nct < 0)
+        return PMS_ESCRATCH;
+    InstDev &in = meta.inst;
+    in.n = n;
+    in.m = m;
+    in.l = l;
+    in.d = d;
+    in.W = m - l + 1;
+    in.NW = (in.W + 31) / 32;
+    in.cps = cps;
+    in.grab = default_grab(d);
+    in.prune_rows = default_prune_rows(n, d);
+    in.ctab = 0;
+    in.seq_off = 0;
+    in.plane_off = 0;
+    in.raw_off = 0;
+    in.compat_off = 0;
+    in.raw_cap = kNoAllocRawCap;
+    const long long items = (long long)in.W * cps;
+    meta.seg = Segment{0, 0, 0, (int)items, 0};
+    meta.win_prefix = 0;
+    meta.row_prefix = 0;
+    const size_t meta_bytes = offsetof(Meta, ctab) + (size_t)nct * sizeof(int);
+
+    // carve the fixed array
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = round_up(off + bytes, kAlign);
+        return o;
+    };
+    const size_t o_meta = take(meta_bytes);
+    CtrLayout cl(1);
+    const size_t o_ctr = take(cl.total);
+    const size_t o_planes = take((size_t)n * in.W * sizeof(uint2));
+    const size_t o_compat = take((size_t)in.W * (n - 1) * in.NW * sizeof(uint32_t));
+    const size_t o_raw = take((size_t)kNoAllocRawCap * 8);
+    const size_t o_tmp = take((size_t)kNoAllocRawCap * 8);
+    const long long rows_cap = (long long)(n - 1) * (in.W + 3) > 0 ? (long long)(n - 1) * (in.W + 3) : 1;
+    const size_t per_cta = (size_t)3 * rows_cap * sizeof(uint32_t);
+    if (off > kNoAllocScratchBytes || kNoAllocScratchBytes - off < per_cta)
+        return PMS_ESCRATCH;
+    const long long fit = (long long)((kNoAllocScratchBytes - off) / per_cta);
+    const int blocks = (int)std::max<long long>(
+        1, std::min<long long>(std::min<long long>((long long)nd->num_sms * nd->occ, items), fit));
+    const size_t o_rows = take((size_t)blocks * per_cta);
+    unsigned char *base = nd->base;
+
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(base + o_meta, &meta, meta_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(base + o_ctr, 0, cl.total, st)) != cudaSuccess) {
+        cudaGetLastError();
+        return PMS_ECUDA;
+    }
+    const InstDev *d_inst = (const InstDev *)(base + o_meta + offsetof(Meta, inst));
+    unsigned char *dc = base + o_ctr;
+    uint32_t *d_flags = (uint32_t *)(dc + cl.flags);
+    uint32_t *d_rawcnt = (uint32_t *)(dc + cl.raw_count);
+    const long long windows = (long long)n * in.W;
+    const int pack_blocks = (int)std::max<long long>(1, std::min<long long>((windows + 255) / 256, (long long)nd->num_sms * 8));
+    if ((e = launch_pack(d_inst, 1, (const long long *)(base + o_meta + offsetof(Meta, win_prefix)), windows, d_seqs,
+                         (uint2 *)(base + o_planes), d_flags, pack_blocks, st)) != cudaSuccess)
+        return PMS_ECUDA;
+    const long long rows = (long long)in.W * (n - 1);
+    if (rows > 0) {
+        const int cw_blocks = (int)std::max<long long>(1, std::min<long long>((rows + 7) / 8, (long long)nd->num_sms * 16));
+        if ((e = launch_compat(d_inst, 1, (const long long *)(base + o_meta + offsetof(Meta, row_prefix)), rows,
+                               (const uint2 *)(base + o_planes), (uint32_t *)(base + o_compat), cw_blocks, st)) !=
+            cudaSuccess)
+            return PMS_ECUDA;
+    }
+    MainParams mp{};
+    mp.inst = d_inst;
+    mp.seg = (const Segment *)(base + o_meta + offsetof(Meta, seg));
+    mp.nseg = 1;
+    mp.total = items;
+    mp.head = (unsigned long long *)(dc + cl.head);
+    mp.planes = (const uint2 *)(base + o_planes);
+    mp.compat = (const uint32_t *)(base + o_compat);
+    mp.ctab = (const int *)(base + o_meta + offsetof(Meta, ctab));
+    mp.raw = (uint64_t *)(base + o_raw);
+    mp.raw_count = d_rawcnt;
+    mp.flags = d_flags;
+    mp.scratch = (uint32_t *)(base + o_rows);
+    mp.rows_cap = (int)rows_cap;
+    mp.counters = (unsigned long long *)(dc + cl.work);
+    if ((e = launch_main(mp, blocks, false, st)) != cudaSuccess)
+        return PMS_ECUDA;
+    const uint32_t cap = (uint32_t)std::min<size_t>(capacity, 0xffffffffu);
+    if ((e = launch_sort_unique(d_inst, nullptr, 1, (uint64_t *)(base + o_raw), (uint64_t *)(base + o_tmp), d_rawcnt,
+                                d_flags, (StatusDev *)d_status, d_motifs, cap, (uint32_t *)(dc + cl.dense_total),
+                                st)) != cudaSuccess)
+        return PMS_ECUDA;
+    return PMS_OK;
+}
