@@ -13,7 +13,7 @@ constexpr int kWarps = 8;      // warps per CTA of the verification kernel
 constexpr int kThreads = kWarps * 32;
 constexpr int kRbCap = 256;    // entries of a subset-reduced occurrence row kept in shared memory
 constexpr int kListCap = 256;  // surviving candidates a warp buffers before checking further rows
-constexpr int kSubBatch = 64;  // tree nodes (position subsets) a warp filters together
+constexpr int kSubBatch = 32;  // tree nodes (position subsets) a warp filters together
 constexpr int kRowSmemCap = 4096;  // feasible occurrences of one seed held in shared memory (padded)
 
 // Flags reported per instance.

@@ -42,6 +42,7 @@ struct __align__(16) WarpSmem {
 };
 
 struct __align__(16) CtaSmem {
+    uint32_t binom[kLMax + 1][kLMax + 1];
     int row_len[kNMax];      // indexed by sequence
     int row_off[kNMax];      // indexed by sequence: first entry of its row (multiple of 4)
     int row_order[kNMax];    // sequences 1..n-1, smallest row first
@@ -56,16 +57,17 @@ struct __align__(16) CtaSmem {
 };
 
 // Colex unranking of the rank-th k-subset of {0..l-1} (combinatorial number
-// system): bit c of the result is set for each chosen position c.
-__device__ __forceinline__ uint32_t unrank_subset(uint32_t rank, int k, int l)
+// system): bit c of the result is set for each chosen position c. `binom` is
+// the C(a, b) table (a copy in shared memory, as lanes index it differently).
+__device__ __forceinline__ uint32_t unrank_subset(uint32_t rank, int k, int l, const uint32_t (*binom)[kLMax + 1])
 {
     uint32_t P = 0;
     int c = l - 1;
     for (int j = k; j >= 1; --j) {
-        while (c_binom[c][j] > rank)
+        while (binom[c][j] > rank)
             --c;
         P |= 1u << c;
-        rank -= c_binom[c][j];
+        rank -= binom[c][j];
         --c;
     }
     return P;
@@ -117,16 +119,16 @@ __device__ __forceinline__ int reduce_row(const uint32_t *D, const uint2 *HL, in
 // Is some entry of a reduced row (shared memory, padded to 4) within d of (ch, cl)?
 __device__ __forceinline__ bool check_smem(const uint2 *rb, int k, uint32_t ch, uint32_t cl, int d)
 {
-    int mn = 64;
+    int m0 = 64, m1 = 64;
     for (int e = 0; e < k; e += 4) {
         const uint4 a = *reinterpret_cast<const uint4 *>(rb + e);
         const uint4 b = *reinterpret_cast<const uint4 *>(rb + e + 2);
-        mn = min(mn, __popc((ch ^ a.x) | (cl ^ a.y)));
-        mn = min(mn, __popc((ch ^ a.z) | (cl ^ a.w)));
-        mn = min(mn, __popc((ch ^ b.x) | (cl ^ b.y)));
-        mn = min(mn, __popc((ch ^ b.z) | (cl ^ b.w)));
+        m0 = min(m0, __popc((ch ^ a.x) | (cl ^ a.y)));
+        m1 = min(m1, __popc((ch ^ a.z) | (cl ^ a.w)));
+        m0 = min(m0, __popc((ch ^ b.x) | (cl ^ b.y)));
+        m1 = min(m1, __popc((ch ^ b.z) | (cl ^ b.w)));
     }
-    return mn <= d;
+    return min(m0, m1) <= d;
 }
 
 // Same test against a full (unreduced) row; used when the reduced row does
@@ -333,19 +335,20 @@ __device__ __forceinline__ int filter_subsets(const WarpCtx &c, int N)
             const int idx = b + c.lane;
             const bool alive = idx < N;
             const uint32_t P = alive ? subs[idx] : 0u;
-            int mn = 64;
+            int m0 = 64, m1 = 64;
             int e4 = 0;
             for (; e4 < len4; ++e4) {
                 const uint4 v = D4[e4];
-                mn = min(mn, __popc(v.x ^ P));
-                mn = min(mn, __popc(v.y ^ P));
-                mn = min(mn, __popc(v.z ^ P));
-                mn = min(mn, __popc(v.w ^ P));
-                if ((e4 & 3) == 3 && __all_sync(kFull, !alive || mn <= d)) {
+                m0 = min(m0, __popc(v.x ^ P));
+                m1 = min(m1, __popc(v.y ^ P));
+                m0 = min(m0, __popc(v.z ^ P));
+                m1 = min(m1, __popc(v.w ^ P));
+                if ((e4 & 3) == 3 && __all_sync(kFull, !alive || min(m0, m1) <= d)) {
                     ++e4;
                     break;
                 }
             }
+            const int mn = min(m0, m1);
             if (kCount && alive)
                 c.cnt[kCntCmpReduce] += 4 * e4;
             const bool pass = alive && mn <= d;
@@ -476,6 +479,8 @@ __global__ void __launch_bounds__(kThreads, 2) main_kernel(MainParams p)
         cs.cached_seed = -1;
         cs.feasible = 0;
     }
+    for (int i = threadIdx.x; i < (kLMax + 1) * (kLMax + 1); i += blockDim.x)
+        (&cs.binom[0][0])[i] = (&c_binom[0][0])[i];
     for (;;) {
         if (threadIdx.x == 0) {
             const unsigned long long g = atomicAdd(p.head, 1ull);
@@ -538,7 +543,7 @@ __global__ void __launch_bounds__(kThreads, 2) main_kernel(MainParams p)
                     int lev = 0;
                     while (tab[lev + 1] <= g)
                         ++lev;
-                    subs[j] = unrank_subset((uint32_t)(g - tab[lev]), lev, in.l);
+                    subs[j] = unrank_subset((uint32_t)(g - tab[lev]), lev, in.l, cs.binom);
                 }
                 __syncwarp();
                 if constexpr (kCount) {

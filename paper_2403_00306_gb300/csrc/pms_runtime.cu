@@ -26,7 +26,7 @@ using namespace pms;
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kDefaultChunkWork = 1 << 16;
+constexpr int kDefaultChunkWork = 1 << 20;
 constexpr uint32_t kInlineKeys = 512;   // codes downloaded together with the status block
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
