@@ -11,10 +11,10 @@ constexpr int kLMax = 32;      // one 32-bit word per bit-plane
 constexpr int kNMax = 64;      // sequences per instance
 constexpr int kWarps = 8;      // warps per CTA of the verification kernel
 constexpr int kThreads = kWarps * 32;
-constexpr int kRbCap = 256;    // entries of a subset-reduced occurrence row kept in shared memory
+constexpr int kRbCap = 128;    // entries of a subset-reduced occurrence row kept in shared memory
 constexpr int kListCap = 256;  // surviving candidates a warp buffers before checking further rows
-constexpr int kSubBatch = 32;  // tree nodes (position subsets) a warp filters together
-constexpr int kRowSmemCap = 4096;  // feasible occurrences of one seed held in shared memory (padded)
+constexpr int kSubBatch = 128; // tree nodes (position subsets) a warp filters together
+constexpr int kRowSmemCap = 2560;  // feasible occurrences of one seed held in shared memory (padded)
 
 // Flags reported per instance.
 constexpr uint32_t kFlagInvalidByte = 1u;

@@ -279,35 +279,69 @@ __device__ __forceinline__ void expand_subset(const WarpCtx &c, uint32_t P)
     uint2 *list = c.ws->list;
     uint32_t Dh = 0u, Dl = Phi;
     int listN = 0;
-    for (unsigned long long it = 0; it < iters; ++it) {
-        const uint32_t ch = ch0 ^ Dh, cl = cl0 ^ Dl;
-        bool hit = false;
-        if (active) {
-            if (nrows == 0)
-                hit = true;
-            else
-                hit = sm0 ? check_smem(c.ws->rb0, k0, ch, cl, d) : check_row(c.rows.HL + off0, len0, ch, cl, d);
-            if (kCount) {
-                c.cnt[kCntTested] += 1;
-                c.cnt[kCntCmpVerify] += sm0 ? k0 : len0;
-            }
-        }
-        const uint32_t bal = __ballot_sync(kFull, hit);
-        if (bal) {
-            if (hit)
-                list[listN + __popc(bal & c.lt)] = make_uint2(ch, cl);
-            listN += __popc(bal);
-            if (listN > kListCap - 32) {
-                finish_list<kCount>(c, P, listN);
-                listN = 0;
-            }
-        }
+    // two leaves per lane per step: the odometer state after one increment is
+    // computed alongside, so the two distance tests are independent
+    for (unsigned long long it = 0; it < iters; it += 2) {
+        const bool two = it + 1 < iters;
         const uint32_t both = Dh & Dl;
         const uint32_t open = Phi & ~both;
         const uint32_t q = open & (0u - open);
         const uint32_t below = Phi & (q - 1u);
-        Dh = (Dh & ~below) | q;
-        Dl = (Dl | below) ^ q;
+        const uint32_t Dh2 = (Dh & ~below) | q;
+        const uint32_t Dl2 = (Dl | below) ^ q;
+        const uint32_t ch_a = ch0 ^ Dh, cl_a = cl0 ^ Dl;
+        const uint32_t ch_b = ch0 ^ Dh2, cl_b = cl0 ^ Dl2;
+        bool hit_a = false, hit_b = false;
+        if (active) {
+            if (nrows == 0) {
+                hit_a = true;
+                hit_b = two;
+            } else if (sm0) {
+                int a0 = 64, a1 = 64, b0m = 64, b1m = 64;
+                for (int e = 0; e < k0; e += 4) {
+                    const uint4 u = *reinterpret_cast<const uint4 *>(c.ws->rb0 + e);
+                    const uint4 v = *reinterpret_cast<const uint4 *>(c.ws->rb0 + e + 2);
+                    a0 = min(a0, __popc((ch_a ^ u.x) | (cl_a ^ u.y)));
+                    b0m = min(b0m, __popc((ch_b ^ u.x) | (cl_b ^ u.y)));
+                    a1 = min(a1, __popc((ch_a ^ u.z) | (cl_a ^ u.w)));
+                    b1m = min(b1m, __popc((ch_b ^ u.z) | (cl_b ^ u.w)));
+                    a0 = min(a0, __popc((ch_a ^ v.x) | (cl_a ^ v.y)));
+                    b0m = min(b0m, __popc((ch_b ^ v.x) | (cl_b ^ v.y)));
+                    a1 = min(a1, __popc((ch_a ^ v.z) | (cl_a ^ v.w)));
+                    b1m = min(b1m, __popc((ch_b ^ v.z) | (cl_b ^ v.w)));
+                }
+                hit_a = min(a0, a1) <= d;
+                hit_b = two && min(b0m, b1m) <= d;
+            } else {
+                hit_a = check_row(c.rows.HL + off0, len0, ch_a, cl_a, d);
+                hit_b = two && check_row(c.rows.HL + off0, len0, ch_b, cl_b, d);
+            }
+            if (kCount) {
+                c.cnt[kCntTested] += two ? 2 : 1;
+                c.cnt[kCntCmpVerify] += (unsigned long long)(two ? 2 : 1) * (sm0 ? k0 : len0);
+            }
+        }
+        const uint32_t bal_a = __ballot_sync(kFull, hit_a);
+        const uint32_t bal_b = __ballot_sync(kFull, hit_b);
+        if (bal_a | bal_b) {
+            if (hit_a)
+                list[listN + __popc(bal_a & c.lt)] = make_uint2(ch_a, cl_a);
+            listN += __popc(bal_a);
+            if (hit_b)
+                list[listN + __popc(bal_b & c.lt)] = make_uint2(ch_b, cl_b);
+            listN += __popc(bal_b);
+            if (listN > kListCap - 64) {
+                finish_list<kCount>(c, P, listN);
+                listN = 0;
+            }
+        }
+        // advance the odometer by two
+        const uint32_t both2 = Dh2 & Dl2;
+        const uint32_t open2 = Phi & ~both2;
+        const uint32_t q2 = open2 & (0u - open2);
+        const uint32_t below2 = Phi & (q2 - 1u);
+        Dh = (Dh2 & ~below2) | q2;
+        Dl = (Dl2 | below2) ^ q2;
     }
     if (listN > 0)
         finish_list<kCount>(c, P, listN);
@@ -457,7 +491,7 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
 }
 
 template <bool kCount>
-__global__ void __launch_bounds__(kThreads, 2) main_kernel(MainParams p)
+__global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *wsm = reinterpret_cast<WarpSmem *>(smem_raw);
@@ -530,14 +564,18 @@ __global__ void __launch_bounds__(kThreads, 2) main_kernel(MainParams p)
             Rows rows{cs.rows_in_smem ? smem_D : glob_D, cs.rows_in_smem ? smem_HL : glob_HL};
             WarpCtx c{&p, in, I, lane, lt, x.x, x.y, rows, &cs, &wsm[warp], kCount ? cnt : nullptr};
             uint32_t *subs = wsm[warp].subs;
+            // batch size: up to kSubBatch subsets, but small chunks are split so
+            // that every warp of the CTA gets work
+            const int per_warp = (g1 - g0 + 2 * kWarps - 1) / (2 * kWarps);
+            const int batch = min(kSubBatch, max(32, (per_warp + 31) & ~31));
             for (;;) {
                 int start = 0;
                 if (lane == 0)
-                    start = atomicAdd(&cs.next, kSubBatch);
+                    start = atomicAdd(&cs.next, batch);
                 start = __shfl_sync(kFull, start, 0);
                 if (start >= g1)
                     break;
-                const int N = min(kSubBatch, g1 - start);
+                const int N = min(batch, g1 - start);
                 for (int j = lane; j < N; j += 32) {
                     const int g = start + j;
                     int lev = 0;
