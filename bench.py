@@ -366,12 +366,95 @@ def bench_batch(args, ws, rank, local, dist) -> dict:
             "gpu_launches": 3 * args.steps, "clocks": clk.summary()}
 
 
+def bench_serve(args, ws, rank, local, dist) -> dict:
+    """Poisson request stream through the served form (continuous batching)."""
+    import threading
+    from concurrent.futures import ThreadPoolExecutor
+
+    import torch
+    import paper_2403_00306_gb300 as pms
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    count, rate = args.serve_requests, args.serve_rate
+    reqs = list(pi.serve_requests(count=count, rate_per_s=rate, master_seed=7 + rank))
+    ctx = pms.Context(local)
+    # warm-up: a few requests, not timed
+    for _, inst in reqs[: max(3, args.warmup)]:
+        ctx.wait(ctx.submit(inst.seqs, inst.l, inst.d))
+    lat = [None] * count
+    done_t = [None] * count
+    ok = [True] * count
+    pool = ThreadPoolExecutor(max_workers=128)
+    lock = threading.Lock()
+
+    def waiter(i, t, arrival):
+        try:
+            ctx.wait(t)
+        except Exception:  # noqa: BLE001
+            ok[i] = False
+        now = time.perf_counter()
+        with lock:
+            done_t[i] = now
+            lat[i] = now - arrival
+        ctx.release(t)
+
+    barrier(dist)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        futs = []
+        for i, (ta, inst) in enumerate(reqs):
+            target = t0 + ta
+            delay = target - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            arrival = max(target, time.perf_counter()) if delay <= 0 else target
+            t = ctx.submit(inst.seqs, inst.l, inst.d)
+            futs.append(pool.submit(waiter, i, t, arrival))
+        for f in futs:
+            f.result()
+        t_end = max(done_t)
+    pool.shutdown()
+    st = ctx.stats()
+    # saturation: all requests of a slice submitted at once
+    sat_n = min(count, 2000)
+    ts = time.perf_counter()
+    tickets = [ctx.submit(inst.seqs, inst.l, inst.d) for _, inst in reqs[:sat_n]]
+    for t in tickets:
+        ctx.wait(t)
+        ctx.release(t)
+    sat = sat_n / (time.perf_counter() - ts)
+    ctx.close()
+    span = t_end - t0
+    solves = sum_over_ranks(dist, count)
+    span_max = max_over_ranks(dist, span)
+    lat_ms = sorted(1000.0 * x for x in lat)
+    cand = sum((inst.m - inst.l + 1) * n_ball(inst.l, inst.d) for _, inst in reqs)
+    return {"metric": METRIC, "value": solves / span_max, "unit": "solves/s", "n_gpus": ws, "steps": count,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * span_max / count, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"served: {count} Poisson requests at {rate}/s, (l,d) in {{(13,4),(15,4),(17,5)}}, "
+                                   "n=20, m in [200,1200]",
+                       "timing": "host clock from each arrival to pms_wait's return"},
+            "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[int(len(lat_ms) * 0.99) - 1],
+                           "max": lat_ms[-1]},
+            "offered_per_s": rate, "saturation_solves_per_s": sat,
+            "candidate_checks_per_s": cand / span, "all_ok": all(ok),
+            "serve": {"waves": st["serve_waves"], "overlapped_waves": st["serve_overlapped_waves"],
+                      "max_requests_per_wave": st["serve_max_requests_per_wave"]},
+            "e2e": {"value": solves / span_max, "unit": "solves/s",
+                    "h2d_bytes_per_step": int(statistics.mean(i.n * i.m for _, i in reqs)),
+                    "d2h_bytes_per_step": 16 + 512 * 8},
+            "gpu_launches": 3 * count + int(st["serve_waves"]), "clocks": clk.summary()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="plain15_4", choices=sorted(WORKLOADS) + ["batch"])
+    ap.add_argument("--workload", default="plain15_4", choices=sorted(WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -384,6 +467,8 @@ def main():
         return
     if args.workload == "batch":
         line = bench_batch(args, ws, rank, local, dist)
+    elif args.workload == "serve":
+        line = bench_serve(args, ws, rank, local, dist)
     else:
         l, d = WORKLOADS[args.workload]
         line = bench_plain(args, ws, rank, local, dist, l, d)

@@ -90,6 +90,9 @@ typedef struct {
     double ms_total;            /* wall time of the call, host clock */
     double ms_kernel;           /* device time from the first to the last kernel */
     double ms_verify;           /* device time of the verification kernel alone */
+    uint64_t serve_waves;       /* served form, cumulative: verification waves launched */
+    uint64_t serve_overlapped_waves;     /* waves holding chunks of more than one request */
+    uint64_t serve_max_requests_per_wave;
 } pms_stats;
 
 /* Creates a context on CUDA device `device`. mem_budget_bytes caps the device
@@ -136,13 +139,18 @@ int pms_solve_device(pms_ctx *h, const uint8_t *d_seqs, int n, int m, int l, int
  * errors are in out[i].status. */
 int pms_solve_batch(pms_ctx *h, const pms_instance *inst, int k, pms_result *out);
 
-/* Served form (continuous batching). pms_submit copies the instance and
- * returns a ticket at once; a scheduler thread admits requests while the
- * device-memory budget allows, and every verification wave launched takes
- * queue items from all admitted requests, so work of requests arriving
- * while others run overlaps on the device. pms_wait blocks up to timeout_ms
- * (negative: no limit) for the ticket's result; PMS_ETIMEDOUT leaves the
- * ticket valid. pms_release frees a completed ticket's result. */
+/* Served form (continuous batching). pms_submit validates and copies the
+ * instance and returns a ticket at once; the first submit on a context
+ * starts its scheduler thread, its own CUDA stream and a request pool (a
+ * device block of up to 1 GiB, at most half of what the budget leaves).
+ * The scheduler admits requests in arrival order while a slot
+ * (serve_max_inflight, default 64) and pool room are free, and launches
+ * verification waves whose work queue holds chunks of every admitted request
+ * (oldest first, about serve_wave_items x 65536 candidate units per wave):
+ * a request that arrives while others run joins the next wave, so their work
+ * overlaps on the device. pms_wait blocks up to timeout_ms (negative: no
+ * limit) for the ticket's result; PMS_ETIMEDOUT leaves the ticket valid.
+ * pms_release frees a completed ticket (PMS_EBUSY while it is running). */
 int pms_submit(pms_ctx *h, const pms_instance *inst, uint64_t *ticket);
 int pms_wait(pms_ctx *h, uint64_t ticket, int timeout_ms, pms_result *out);
 int pms_release(pms_ctx *h, uint64_t ticket);

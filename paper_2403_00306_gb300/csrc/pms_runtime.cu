@@ -673,8 +673,517 @@ static int solve_specs(pms_ctx *h, std::vector<InstSpec> specs, std::vector<Inst
 
 // ----------------------------------------------------------------------------- served form
 
-struct Served {};
-static void served_stop(pms_ctx *h) { (void)h; }
+// Served form: continuous batching. A scheduler thread admits submitted
+// requests while the request pool (a budgeted device block sub-allocated
+// first-fit) has room, uploads and packs each on admission, and launches
+// verification "waves": one persistent launch of the verification kernel
+// whose queue is the union of chunk ranges of every admitted request, oldest
+// first, up to a work budget. A request that arrives while waves run joins
+// the next wave, so its work overlaps the remaining work of the others. When
+// a wave holds a request's last chunks, that request's sort/unique and
+// download are enqueued right after the wave; an event per request reports
+// completion. No kernel waits on another: all ordering is stream order.
+
+struct Request {
+    uint64_t ticket = 0;
+    std::vector<uint8_t> seqs;
+    int n = 0, m = 0, l = 0, d = 0, W = 0;
+    int state = 0;                 // 0 pending, 1 admitted, 2 finishing, 3 done
+    int slot = -1;
+    size_t arena_off = 0, arena_bytes = 0;
+    uint32_t raw_cap = 0;
+    size_t dense_rel = 0, status_rel = 0;   // offsets in the arena
+    long long chunks_total = 0, chunks_next = 0;
+    double units_per_chunk = 1.0;
+    cudaEvent_t done_ev = nullptr;
+    int status = PMS_OK;
+    std::vector<uint64_t> codes;
+    size_t count = 0;
+};
+
+struct PoolAlloc {
+    std::map<size_t, size_t> free_;   // offset -> length
+    void reset(size_t s)
+    {
+        free_.clear();
+        if (s)
+            free_[0] = s;
+    }
+    bool alloc(size_t bytes, size_t &off)
+    {
+        bytes = round_up(bytes, kAlign);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                off = it->first;
+                const size_t rest = it->second - bytes;
+                free_.erase(it);
+                if (rest)
+                    free_[off + bytes] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes)
+    {
+        bytes = round_up(bytes, kAlign);
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+// A request's arena in the pool (offsets relative to the arena start).
+struct ReqLayout {
+    size_t seqs, planes, compat, raw, tmp, dense, status, ctab, total;
+    ReqLayout(int n, int m, int W, uint32_t raw_cap, size_t ctab_ints)
+    {
+        size_t o = 0;
+        auto take = [&](size_t b) {
+            const size_t r = o;
+            o = round_up(o + b, kAlign);
+            return r;
+        };
+        seqs = take((size_t)n * m);
+        planes = take((size_t)n * W * sizeof(uint2));
+        compat = take((size_t)W * (n - 1) * ((W + 31) / 32) * sizeof(uint32_t));
+        raw = take((size_t)raw_cap * 8);
+        tmp = take((size_t)raw_cap * 8);   // directly after raw: the sort's twin buffer
+        dense = take((size_t)raw_cap * 8);
+        status = take(sizeof(StatusDev) + kInlineKeys * 8);
+        ctab = take(ctab_ints * sizeof(int));
+        total = o;
+    }
+};
+
+struct Served {
+    pms_ctx *h = nullptr;
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    std::deque<Request *> pending;
+    std::vector<Request *> active;                 // admitted, not done (admission order)
+    std::unordered_map<uint64_t, std::unique_ptr<Request>> all;
+    cudaStream_t st = nullptr;
+    int slots = 0;
+    std::vector<int> free_slots;
+    char *pool = nullptr;
+    size_t pool_bytes = 0;
+    PoolAlloc palloc;
+    InstDev *d_inst = nullptr;       // [slots]
+    uint32_t *d_cnt = nullptr;       // raw_count[slots], flags[slots], dense_total[slots], zero[4], ids[slots]
+    InstDev *h_inst = nullptr;       // pinned [slots]
+    char *h_stage = nullptr;         // pinned [slots]: status block + inline codes of a finishing request
+    static constexpr size_t kStage = sizeof(StatusDev) + kInlineKeys * 8;
+    int *h_ctab = nullptr;           // pinned [slots][kCtabMax]
+    static constexpr int kCtabMax = 8192;
+    static constexpr int kRing = 4;
+    char *d_ring = nullptr;          // per wave: head + segments
+    char *h_ring = nullptr;          // pinned
+    size_t ring_stride = 0;
+    cudaEvent_t ring_ev[kRing] = {};
+    int ring_pos = 0;
+    uint32_t *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    long long rows_cap = 0;
+    int blocks = 0;
+    std::vector<cudaEvent_t> wave_ev;   // in-flight waves
+    std::string fatal;
+    long long waves = 0, max_reqs_per_wave = 0, overlapped_waves = 0;
+};
+
+// d_cnt words: raw_count[slots], flags[slots], dense_total[slots], then an
+// 8-word zero block (8-byte aligned; the prefix array of one-instance
+// launches), then the slot ids 0..slots-1 (instance lists of the sorts).
+static size_t srv_zero_word(int slots) { return round_up(3 * (size_t)slots, 2); }
+static size_t srv_cnt_words(int slots) { return srv_zero_word(slots) + 8 + (size_t)slots; }
+static uint32_t *srv_rawcnt(Served *S) { return S->d_cnt; }
+static uint32_t *srv_flags(Served *S) { return S->d_cnt + S->slots; }
+static uint32_t *srv_dense_total(Served *S) { return S->d_cnt + 2 * S->slots; }
+static long long *srv_zero(Served *S) { return (long long *)(S->d_cnt + srv_zero_word(S->slots)); }
+static int *srv_ids(Served *S) { return (int *)(S->d_cnt + srv_zero_word(S->slots) + 8); }
+
+static void served_loop(Served *S);
+
+static int served_start(pms_ctx *h)
+{
+    if (h->served)
+        return PMS_OK;
+    auto S = std::make_unique<Served>();
+    S->h = h;
+    S->slots = h->opt.serve_max_inflight > 0 ? h->opt.serve_max_inflight : 64;
+    size_t pool = (size_t)1 << 30;
+    if (h->budget) {
+        const size_t left = h->budget > h->used ? h->budget - h->used : 0;
+        pool = std::min(pool, left / 2);
+    }
+    if (pool < ((size_t)1 << 20))
+        return h->fail(PMS_ENOMEM, "served form: the memory budget leaves no room for a request pool");
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking)) != cudaSuccess)
+        return h->cuda_fail(e, "served stream");
+    const size_t cnt_words = srv_cnt_words(S->slots);
+    S->pool = (char *)h->dev_alloc(pool);
+    S->d_inst = (InstDev *)h->dev_alloc(S->slots * sizeof(InstDev));
+    S->d_cnt = (uint32_t *)h->dev_alloc(cnt_words * 4);
+    S->ring_stride = round_up(8 + (size_t)S->slots * sizeof(Segment), 256);
+    S->d_ring = (char *)h->dev_alloc(S->ring_stride * Served::kRing);
+    bool ok = S->pool && S->d_inst && S->d_cnt && S->d_ring;
+    if (ok)
+        ok = cudaHostAlloc((void **)&S->h_inst, S->slots * sizeof(InstDev), cudaHostAllocDefault) == cudaSuccess &&
+             cudaHostAlloc((void **)&S->h_ctab, (size_t)S->slots * Served::kCtabMax * sizeof(int),
+                           cudaHostAllocDefault) == cudaSuccess &&
+             cudaHostAlloc((void **)&S->h_ring, S->ring_stride * Served::kRing, cudaHostAllocDefault) == cudaSuccess &&
+             cudaHostAlloc((void **)&S->h_stage, S->slots * Served::kStage, cudaHostAllocDefault) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        h->dev_free(S->pool, pool);
+        h->dev_free(S->d_inst, S->slots * sizeof(InstDev));
+        h->dev_free(S->d_cnt, cnt_words * 4);
+        h->dev_free(S->d_ring, S->ring_stride * Served::kRing);
+        if (S->h_inst)
+            cudaFreeHost(S->h_inst);
+        if (S->h_ctab)
+            cudaFreeHost(S->h_ctab);
+        if (S->h_ring)
+            cudaFreeHost(S->h_ring);
+        if (S->h_stage)
+            cudaFreeHost(S->h_stage);
+        cudaStreamDestroy(S->st);
+        return h->fail(PMS_ENOMEM, "served form: device or pinned memory for the request pool is not available");
+    }
+    S->pool_bytes = pool;
+    S->palloc.reset(pool);
+    std::vector<uint32_t> init(cnt_words, 0);
+    int *ids = (int *)(init.data() + srv_zero_word(S->slots) + 8);
+    for (int i = 0; i < S->slots; ++i)
+        ids[i] = i;
+    cudaMemcpy(S->d_cnt, init.data(), cnt_words * 4, cudaMemcpyHostToDevice);
+    for (auto &ev : S->ring_ev)
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    for (int i = S->slots - 1; i >= 0; --i)
+        S->free_slots.push_back(i);
+    int occ = std::max(1, h->occ[0]);
+    if (h->opt.ctas_per_sm > 0)
+        occ = std::min(occ, h->opt.ctas_per_sm);
+    S->blocks = h->num_sms * occ;
+    h->served = S.release();
+    h->served->th = std::thread(served_loop, h->served);
+    return PMS_OK;
+}
+
+static void served_stop(pms_ctx *h)
+{
+    Served *S = h->served;
+    if (!S)
+        return;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    S->th.join();
+    cudaStreamSynchronize(S->st);
+    for (auto &kv : S->all)
+        if (kv.second->done_ev)
+            cudaEventDestroy(kv.second->done_ev);
+    for (auto &ev : S->ring_ev)
+        cudaEventDestroy(ev);
+    for (auto ev : S->wave_ev)
+        cudaEventDestroy(ev);
+    const size_t cnt_words = srv_cnt_words(S->slots);
+    h->dev_free(S->pool, S->pool_bytes);
+    h->dev_free(S->d_inst, S->slots * sizeof(InstDev));
+    h->dev_free(S->d_cnt, cnt_words * 4);
+    h->dev_free(S->d_ring, S->ring_stride * Served::kRing);
+    if (S->d_scratch)
+        h->dev_free(S->d_scratch, S->scratch_bytes);
+    cudaFreeHost(S->h_inst);
+    cudaFreeHost(S->h_ctab);
+    cudaFreeHost(S->h_ring);
+    cudaFreeHost(S->h_stage);
+    cudaStreamDestroy(S->st);
+    delete S;
+    h->served = nullptr;
+}
+
+// Admission: a slot and an arena must be free. Uploads the request, packs
+// its windows and builds its compatibility masks (stream order).
+static bool served_admit(Served *S, Request *r)
+{
+    pms_ctx *h = S->h;
+    if (S->free_slots.empty())
+        return false;
+    std::lock_guard<std::recursive_mutex> hg(h->mu);
+    const ChunkTable &ct = h->chunks(r->l, r->d);
+    if ((int)ct.tab.size() > Served::kCtabMax) {
+        r->status = PMS_EINVAL;
+        return true;
+    }
+    InstSpec spec{r->n, r->m, r->l, r->d, nullptr};
+    r->raw_cap = default_cap(h, spec, true);
+    ReqLayout L(r->n, r->m, r->W, r->raw_cap, ct.tab.size());
+    if (L.total > S->pool_bytes) {
+        r->status = PMS_ENOMEM;   // can never fit
+        return true;
+    }
+    size_t off;
+    if (!S->palloc.alloc(L.total, off))
+        return false;
+    r->slot = S->free_slots.back();
+    S->free_slots.pop_back();
+    r->arena_off = off;
+    r->arena_bytes = L.total;
+    r->dense_rel = L.dense;
+    r->status_rel = L.status;
+    r->chunks_total = (long long)r->W * ct.cps;
+    r->chunks_next = 0;
+    double units = 0;
+    for (int i = 0; i <= r->d; ++i)
+        units += (double)binom(r->l, i) * (std::pow(3.0, i) + 24.0);
+    r->units_per_chunk = std::max(1.0, units / ct.cps);
+    InstDev &in = S->h_inst[r->slot];
+    in = InstDev{};
+    in.n = r->n;
+    in.m = r->m;
+    in.l = r->l;
+    in.d = r->d;
+    in.W = r->W;
+    in.NW = (r->W + 31) / 32;
+    in.cps = ct.cps;
+    in.grab = h->opt.grab > 0 ? h->opt.grab : default_grab(r->d);
+    in.prune_rows = default_prune_rows(r->n, r->d);
+    in.seq_off = (long long)(off + L.seqs);
+    in.plane_off = (long long)((off + L.planes) / sizeof(uint2));
+    in.raw_off = (long long)((off + L.raw) / 8);
+    in.compat_off = (long long)((off + L.compat) / 4);
+    in.ctab = (int)((off + L.ctab) / sizeof(int));
+    in.raw_cap = r->raw_cap;
+    int *hc = S->h_ctab + (size_t)r->slot * Served::kCtabMax;
+    std::memcpy(hc, ct.tab.data(), ct.tab.size() * sizeof(int));
+    cudaStream_t st = S->st;
+    cudaMemcpyAsync(S->pool + off + L.seqs, r->seqs.data(), r->seqs.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(S->pool + off + L.ctab, hc, ct.tab.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(S->d_inst + r->slot, &in, sizeof(InstDev), cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(srv_rawcnt(S) + r->slot, 0, 4, st);
+    cudaMemsetAsync(srv_flags(S) + r->slot, 0, 4, st);
+    cudaMemsetAsync(srv_dense_total(S) + r->slot, 0, 4, st);
+    const long long windows = (long long)r->n * r->W;
+    launch_pack(S->d_inst + r->slot, 1, srv_zero(S), windows, (const uint8_t *)S->pool, (uint2 *)S->pool,
+                srv_flags(S) + r->slot, (int)std::max<long long>(1, std::min<long long>((windows + 255) / 256, h->num_sms * 8)),
+                st);
+    const long long rows = (long long)r->W * (r->n - 1);
+    if (rows > 0)
+        launch_compat(S->d_inst + r->slot, 1, srv_zero(S), rows, (const uint2 *)S->pool, (uint32_t *)S->pool,
+                      (int)std::max<long long>(1, std::min<long long>((rows + 7) / 8, (long long)h->num_sms * 16)), st);
+    r->state = 1;
+    return true;
+}
+
+static void served_fail_all(Served *S, const std::string &why)
+{
+    S->fatal = why;
+    for (Request *r : S->active) {
+        r->status = PMS_ECUDA;
+        r->state = 3;
+    }
+    for (Request *r : S->pending) {
+        r->status = PMS_ECUDA;
+        r->state = 3;
+    }
+    S->active.clear();
+    S->pending.clear();
+    S->cv_done.notify_all();
+}
+
+static void served_finish(Served *S, Request *r)
+{
+    const char *stage = S->h_stage + (size_t)r->slot * Served::kStage;
+    const StatusDev sd = *(const StatusDev *)stage;
+    const uint64_t *inl = (const uint64_t *)(stage + sizeof(StatusDev));
+    r->status = status_code(sd);
+    const uint32_t u = std::min<uint32_t>(sd.unique_count, r->raw_cap);
+    if (u <= kInlineKeys) {
+        r->codes.assign(inl, inl + u);
+    } else {
+        r->codes.resize(u);
+        cudaMemcpy(r->codes.data(), S->pool + r->arena_off + r->dense_rel, (size_t)u * 8, cudaMemcpyDeviceToHost);
+    }
+    r->count = r->status == PMS_ETOOMANY ? sd.raw_count : r->codes.size();
+    S->palloc.release(r->arena_off, r->arena_bytes);
+    S->free_slots.push_back(r->slot);
+    r->slot = -1;
+    r->state = 3;
+}
+
+static void served_loop(Served *S)
+{
+    pms_ctx *h = S->h;
+    cudaSetDevice(h->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    const double wave_units = h->opt.serve_wave_items > 0 ? (double)h->opt.serve_wave_items * 65536.0 : 8e8;
+    while (!S->stop) {
+        bool progressed = false;
+        // 1. admit in arrival order while a slot and pool room are free
+        while (!S->pending.empty()) {
+            Request *r = S->pending.front();
+            if (!served_admit(S, r))
+                break;
+            S->pending.pop_front();
+            if (r->state == 0) {   // rejected at admission
+                r->state = 3;
+                S->cv_done.notify_all();
+            } else {
+                S->active.push_back(r);
+            }
+            progressed = true;
+        }
+        // 2. a wave over all admitted requests with chunks left (at most 2 in flight)
+        while (!S->wave_ev.empty() && cudaEventQuery(S->wave_ev.front()) == cudaSuccess) {
+            cudaEventDestroy(S->wave_ev.front());
+            S->wave_ev.erase(S->wave_ev.begin());
+        }
+        std::vector<Segment> segs;
+        std::vector<Request *> finishing;
+        if (S->wave_ev.size() < 2) {
+            long long items = 0;
+            double units = 0;
+            long long need_rows = 0;
+            for (Request *r : S->active) {
+                if (r->state != 1 || r->chunks_next >= r->chunks_total)
+                    continue;
+                if (units >= wave_units || (int)segs.size() >= S->slots)
+                    break;
+                long long take = (long long)std::ceil((wave_units - units) / r->units_per_chunk);
+                take = std::max<long long>(1, std::min(take, r->chunks_total - r->chunks_next));
+                segs.push_back(Segment{items, r->slot, (int)r->chunks_next, (int)(r->chunks_next + take), 0});
+                r->chunks_next += take;
+                items += take;
+                units += take * r->units_per_chunk;
+                need_rows = std::max<long long>(need_rows, (long long)(r->n - 1) * (r->W + 3));
+                if (r->chunks_next >= r->chunks_total)
+                    finishing.push_back(r);
+            }
+            if (!segs.empty()) {
+                cudaError_t e = cudaSuccess;
+                if (need_rows > S->rows_cap) {
+                    std::lock_guard<std::recursive_mutex> hg(h->mu);
+                    cudaStreamSynchronize(S->st);
+                    if (S->d_scratch)
+                        h->dev_free(S->d_scratch, S->scratch_bytes);
+                    S->d_scratch = nullptr;
+                    S->rows_cap = need_rows;
+                    // row scratch for every CTA of a wave; under a tight budget the
+                    // waves get fewer CTAs rather than failing
+                    while (S->blocks > 0) {
+                        S->scratch_bytes = (size_t)S->blocks * 3 * (size_t)S->rows_cap * 4;
+                        S->d_scratch = (uint32_t *)h->dev_alloc(S->scratch_bytes);
+                        if (S->d_scratch)
+                            break;
+                        S->blocks /= 2;
+                    }
+                    if (!S->d_scratch) {
+                        served_fail_all(S, "served form: no memory for the row scratch");
+                        break;
+                    }
+                }
+                const int rp = S->ring_pos;
+                S->ring_pos = (S->ring_pos + 1) % Served::kRing;
+                cudaEventSynchronize(S->ring_ev[rp]);
+                char *hr = S->h_ring + rp * S->ring_stride;
+                char *dr = S->d_ring + rp * S->ring_stride;
+                const unsigned long long zero = 0;
+                std::memcpy(hr, &zero, 8);
+                std::memcpy(hr + 8, segs.data(), segs.size() * sizeof(Segment));
+                e = cudaMemcpyAsync(dr, hr, 8 + segs.size() * sizeof(Segment), cudaMemcpyHostToDevice, S->st);
+                MainParams mp{};
+                mp.inst = S->d_inst;
+                mp.seg = (const Segment *)(dr + 8);
+                mp.nseg = (int)segs.size();
+                mp.total = items;
+                mp.head = (unsigned long long *)dr;
+                mp.planes = (const uint2 *)S->pool;
+                mp.compat = (const uint32_t *)S->pool;
+                mp.ctab = (const int *)S->pool;
+                mp.raw = (uint64_t *)S->pool;
+                mp.raw_count = srv_rawcnt(S);
+                mp.flags = srv_flags(S);
+                mp.scratch = S->d_scratch;
+                mp.rows_cap = (int)S->rows_cap;
+                mp.counters = nullptr;
+                if (e == cudaSuccess)
+                    e = launch_main(mp, (int)std::min<long long>(S->blocks, items), false, S->st);
+                cudaEventRecord(S->ring_ev[rp], S->st);
+                for (Request *r : finishing) {
+                    char *base = S->pool + r->arena_off;
+                    char *stage = S->h_stage + (size_t)r->slot * Served::kStage;
+                    if (e == cudaSuccess)
+                        e = launch_sort_unique(S->d_inst, srv_ids(S) + r->slot, 1, (uint64_t *)S->pool,
+                                               (uint64_t *)S->pool + r->raw_cap, srv_rawcnt(S), srv_flags(S),
+                                               (StatusDev *)(base + r->status_rel) - r->slot,
+                                               (uint64_t *)(base + r->dense_rel), r->raw_cap,
+                                               srv_dense_total(S) + r->slot, S->st);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(stage, base + r->status_rel, sizeof(StatusDev), cudaMemcpyDeviceToHost,
+                                            S->st);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(stage + sizeof(StatusDev), base + r->dense_rel, kInlineKeys * 8,
+                                            cudaMemcpyDeviceToHost, S->st);
+                    cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
+                    cudaEventRecord(r->done_ev, S->st);
+                    r->state = 2;
+                }
+                cudaEvent_t wev;
+                cudaEventCreateWithFlags(&wev, cudaEventDisableTiming);
+                cudaEventRecord(wev, S->st);
+                S->wave_ev.push_back(wev);
+                S->waves += 1;
+                S->max_reqs_per_wave = std::max<long long>(S->max_reqs_per_wave, (long long)segs.size());
+                if (segs.size() > 1)
+                    S->overlapped_waves += 1;
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    served_fail_all(S, std::string("served wave: ") + cudaGetErrorString(e));
+                    break;
+                }
+                progressed = true;
+            }
+        }
+        // 3. completions
+        for (size_t i = 0; i < S->active.size();) {
+            Request *r = S->active[i];
+            if (r->state == 2 && cudaEventQuery(r->done_ev) == cudaSuccess) {
+                cudaEventDestroy(r->done_ev);
+                r->done_ev = nullptr;
+                served_finish(S, r);
+                S->active.erase(S->active.begin() + i);
+                S->cv_done.notify_all();
+                progressed = true;
+            } else {
+                ++i;
+            }
+        }
+        if (!progressed) {
+            if (S->active.empty() && S->pending.empty())
+                S->cv_work.wait(lk);
+            else
+                S->cv_work.wait_for(lk, std::chrono::microseconds(200));
+        }
+    }
+}
+
 
 // -------------------------------------------------------------------------------- C ABI
 
@@ -852,29 +1361,81 @@ int pms_solve_batch(pms_ctx *h, const pms_instance *inst, int k, pms_result *out
 
 int pms_submit(pms_ctx *h, const pms_instance *inst, uint64_t *ticket)
 {
-    (void)inst;
-    (void)ticket;
     if (!h)
         return PMS_EINVAL;
-    return h->fail(PMS_EINVAL, "served form not available in this build");
+    if (!inst || !ticket || !inst->seqs)
+        return h->fail(PMS_EINVAL, "null argument");
+    {
+        std::lock_guard<std::recursive_mutex> g(h->mu);
+        int rc = check_params(h, inst->n, inst->m, inst->l, inst->d);
+        if (!rc)
+            rc = check_bytes(h, inst->seqs, (size_t)inst->n * inst->m);
+        if (!rc) {
+            cudaSetDevice(h->device);
+            rc = served_start(h);
+        }
+        if (rc)
+            return rc;
+    }
+    Served *S = h->served;
+    auto r = std::make_unique<Request>();
+    r->seqs.assign(inst->seqs, inst->seqs + (size_t)inst->n * inst->m);
+    r->n = inst->n;
+    r->m = inst->m;
+    r->l = inst->l;
+    r->d = inst->d;
+    r->W = inst->m - inst->l + 1;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        if (!S->fatal.empty())
+            return h->fail(PMS_ECUDA, "%s", S->fatal.c_str());
+        if (S->pending.size() >= 65536)
+            return h->fail(PMS_EBUSY, "served queue full");
+        r->ticket = S->next_ticket++;
+        *ticket = r->ticket;
+        S->pending.push_back(r.get());
+        S->all.emplace(r->ticket, std::move(r));
+    }
+    S->cv_work.notify_all();
+    return PMS_OK;
 }
 
 int pms_wait(pms_ctx *h, uint64_t ticket, int timeout_ms, pms_result *out)
 {
-    (void)ticket;
-    (void)timeout_ms;
-    (void)out;
-    if (!h)
+    if (!h || !out)
         return PMS_EINVAL;
-    return PMS_ENOTFOUND;
+    Served *S = h->served;
+    if (!S)
+        return PMS_ENOTFOUND;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end())
+        return PMS_ENOTFOUND;
+    Request *r = it->second.get();
+    auto done = [&] { return r->state == 3; };
+    if (timeout_ms < 0)
+        S->cv_done.wait(lk, done);
+    else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done))
+        return PMS_ETIMEDOUT;
+    *out = pms_result{r->status, r->codes.data(), r->status == PMS_ETOOMANY ? r->count : r->codes.size()};
+    return PMS_OK;
 }
 
 int pms_release(pms_ctx *h, uint64_t ticket)
 {
-    (void)ticket;
     if (!h)
         return PMS_EINVAL;
-    return PMS_ENOTFOUND;
+    Served *S = h->served;
+    if (!S)
+        return PMS_ENOTFOUND;
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end())
+        return PMS_ENOTFOUND;
+    if (it->second->state != 3)
+        return PMS_EBUSY;
+    S->all.erase(it);
+    return PMS_OK;
 }
 
 int pms_get_stats(const pms_ctx *h, pms_stats *out)
@@ -882,10 +1443,20 @@ int pms_get_stats(const pms_ctx *h, pms_stats *out)
     if (!h || !out)
         return PMS_EINVAL;
     pms_ctx *hm = const_cast<pms_ctx *>(h);
-    std::lock_guard<std::recursive_mutex> g(hm->mu);
-    cudaSetDevice(hm->device);
-    collect_stats(hm);
-    *out = h->stats;
+    {
+        std::lock_guard<std::recursive_mutex> g(hm->mu);
+        cudaSetDevice(hm->device);
+        collect_stats(hm);
+        *out = h->stats;
+    }
+    // lock order: the scheduler takes its own lock before the context's, so
+    // the context lock is never held while taking the scheduler's
+    if (Served *S = hm->served) {
+        std::lock_guard<std::mutex> sg(S->mu);
+        out->serve_waves = (uint64_t)S->waves;
+        out->serve_overlapped_waves = (uint64_t)S->overlapped_waves;
+        out->serve_max_requests_per_wave = (uint64_t)S->max_reqs_per_wave;
+    }
     return PMS_OK;
 }
 
