@@ -73,6 +73,9 @@ typedef struct {
     int count_work;        /* 1: also count comparisons (slower; for profiling) */
     int serve_wave_items;  /* served form: queue items per wave launch */
     int serve_max_inflight;/* served form: requests resident on the device */
+    int smem_rows;         /* at most this many feasible occurrences of a seed are
+                              kept in shared memory (0: as many as fit); larger
+                              row sets are read from global memory */
 } pms_options;
 
 /* Work counters of the last solve (pms_solve / pms_solve_device /

@@ -81,7 +81,8 @@ struct MainParams {
     uint32_t *flags;              // per instance
     uint32_t *scratch;            // per CTA: 3 * rows_cap words (masks, then planes), used when a
                                   // seed's rows exceed shared memory
-    int rows_cap;                 // max (n - 1) * (W + 3) over the instances
+    int rows_cap;                 // max (n - 1) * (W + 3) over the instances, rounded up to a multiple of 4
+    int smem_rows_cap;            // row entries a seed may keep in shared memory (<= kRowSmemCap)
     unsigned long long *counters; // kCntNum entries (count mode)
     int *done;                    // per segment: finished items (served form), may be null
 };

@@ -442,7 +442,7 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
             }
             cs.total_rows = off;
             cs.feasible = !any_empty;
-            cs.rows_in_smem = off <= kRowSmemCap;
+            cs.rows_in_smem = off <= p.smem_rows_cap;
             if (cnt)
                 cnt[kCntCmpRows] += (unsigned long long)(n - 1) * W;
         }
@@ -501,6 +501,8 @@ __global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
                                                kRowSmemCap * (sizeof(uint32_t) + sizeof(uint2)));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
+    // rows_cap is a multiple of 4 words, so each CTA's slice and its plane
+    // part start on 16-byte boundaries (the row loops use 16-byte loads)
     uint32_t *glob_D = p.scratch + (size_t)blockIdx.x * 3 * (size_t)p.rows_cap;
     uint2 *glob_HL = reinterpret_cast<uint2 *>(glob_D + p.rows_cap);
     unsigned long long cnt[kCount ? kCntNum : 1];

@@ -415,7 +415,7 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
         P.total_windows += (long long)s.n * in.W;
         P.row_prefix.push_back(P.total_rows);
         P.total_rows += (long long)in.W * (s.n - 1);
-        P.rows_cap = std::max(P.rows_cap, (s.n - 1) * (in.W + 3));
+        P.rows_cap = std::max(P.rows_cap, (int)round_up((size_t)(s.n - 1) * (in.W + 3), 4));
         const int chunks = in.W * in.cps;
         P.seg.push_back(Segment{work, (int)k, 0, chunks, 0});
         work += chunks;
@@ -494,6 +494,7 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     mp.flags = d_flags;
     mp.scratch = (uint32_t *)h->d_scratch.p;
     mp.rows_cap = P.rows_cap;
+    mp.smem_rows_cap = h->opt.smem_rows > 0 ? std::min(h->opt.smem_rows, kRowSmemCap) : kRowSmemCap;
     mp.counters = (unsigned long long *)(dc + cl.work);
     cudaEventRecord(h->evm0, st);
     if (P.total_items > 0 && (e = launch_main(mp, blocks, count_mode, st)) != cudaSuccess)
@@ -1072,7 +1073,7 @@ static void served_loop(Served *S)
                 r->chunks_next += take;
                 items += take;
                 units += take * r->units_per_chunk;
-                need_rows = std::max<long long>(need_rows, (long long)(r->n - 1) * (r->W + 3));
+                need_rows = std::max<long long>(need_rows, (long long)round_up((size_t)(r->n - 1) * (r->W + 3), 4));
                 if (r->chunks_next >= r->chunks_total)
                     finishing.push_back(r);
             }
@@ -1122,6 +1123,7 @@ static void served_loop(Served *S)
                 mp.flags = srv_flags(S);
                 mp.scratch = S->d_scratch;
                 mp.rows_cap = (int)S->rows_cap;
+                mp.smem_rows_cap = h->opt.smem_rows > 0 ? std::min(h->opt.smem_rows, kRowSmemCap) : kRowSmemCap;
                 mp.counters = nullptr;
                 if (e == cudaSuccess)
                     e = launch_main(mp, (int)std::min<long long>(S->blocks, items), false, S->st);
@@ -1162,9 +1164,16 @@ static void served_loop(Served *S)
             }
         }
         // 3. completions
+        bool device_error = false;
         for (size_t i = 0; i < S->active.size();) {
             Request *r = S->active[i];
-            if (r->state == 2 && cudaEventQuery(r->done_ev) == cudaSuccess) {
+            cudaError_t q = r->state == 2 ? cudaEventQuery(r->done_ev) : cudaErrorNotReady;
+            if (q != cudaSuccess && q != cudaErrorNotReady) {
+                device_error = true;
+                S->fatal = std::string("served request: ") + cudaGetErrorString(q);
+                break;
+            }
+            if (r->state == 2 && q == cudaSuccess) {
                 cudaEventDestroy(r->done_ev);
                 r->done_ev = nullptr;
                 served_finish(S, r);
@@ -1174,6 +1183,11 @@ static void served_loop(Served *S)
             } else {
                 ++i;
             }
+        }
+        if (device_error) {
+            cudaGetLastError();
+            served_fail_all(S, S->fatal);
+            continue;
         }
         if (!progressed) {
             if (S->active.empty() && S->pending.empty())
@@ -1244,7 +1258,7 @@ int pms_set_options(pms_ctx *h, const pms_options *opt)
 {
     if (!h || !opt)
         return PMS_EINVAL;
-    if (opt->ctas_per_sm < 0 || opt->chunk_work < 0 || opt->grab < 0 || opt->serve_wave_items < 0 ||
+    if (opt->ctas_per_sm < 0 || opt->chunk_work < 0 || opt->grab < 0 || opt->serve_wave_items < 0 || opt->smem_rows < 0 ||
         opt->serve_max_inflight < 0 || opt->serve_max_inflight > 1024)
         return h->fail(PMS_EINVAL, "negative option");
     std::lock_guard<std::recursive_mutex> g(h->mu);
@@ -1712,7 +1726,8 @@ extern "C" int pms_solve_device_noalloc(const uint8_t *d_seqs, int n, int m, int
     const size_t o_compat = take((size_t)in.W * (n - 1) * in.NW * sizeof(uint32_t));
     const size_t o_raw = take((size_t)kNoAllocRawCap * 8);
     const size_t o_tmp = take((size_t)kNoAllocRawCap * 8);
-    const long long rows_cap = (long long)(n - 1) * (in.W + 3) > 0 ? (long long)(n - 1) * (in.W + 3) : 1;
+    // a multiple of 4 words keeps every CTA's slice 16-byte aligned (vector loads)
+    const long long rows_cap = std::max<long long>(4, (long long)round_up((size_t)(n - 1) * (in.W + 3), 4));
     const size_t per_cta = (size_t)3 * rows_cap * sizeof(uint32_t);
     if (off > kNoAllocScratchBytes || kNoAllocScratchBytes - off < per_cta)
         return PMS_ESCRATCH;
@@ -1759,6 +1774,7 @@ extern "C" int pms_solve_device_noalloc(const uint8_t *d_seqs, int n, int m, int
     mp.flags = d_flags;
     mp.scratch = (uint32_t *)(base + o_rows);
     mp.rows_cap = (int)rows_cap;
+    mp.smem_rows_cap = kRowSmemCap;
     mp.counters = (unsigned long long *)(dc + cl.work);
     if ((e = launch_main(mp, blocks, false, st)) != cudaSuccess)
         return PMS_ECUDA;

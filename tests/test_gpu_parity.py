@@ -57,6 +57,18 @@ def test_small_instances_match_oracle(ctx, oracle_, case):
     assert np.array_equal(ctx.solve(seqs, l, d), oracle_.solve(seqs, l, d, cap=1 << 24))
 
 
+@pytest.mark.parametrize("case", [c for c in SMALL if c[0] > 1][:10] + [(9, 301, 9, 2, 31), (16, 201, 11, 3, 32)],
+                         ids=lambda c: "n{}_m{}_l{}_d{}".format(*c[:4]))
+def test_rows_in_global_scratch_match_oracle(oracle_, case):
+    # shared memory limited to 8 row entries: every seed's rows go to the per-CTA global scratch
+    n, m, l, d, seed = case
+    c = pms.Context(0)
+    c.set_options(smem_rows=8)
+    inst = pi.planted_instance(n, m, l, d, seed)
+    assert np.array_equal(c.solve(inst.seqs, l, d), oracle_.solve(inst.seqs, l, d, cap=1 << 24))
+    c.close()
+
+
 def test_plain_9_2_full_size_matches_oracle(ctx, oracle_):
     for seed in (1, 2, 3):
         inst = pi.plain_instance(9, 2, seed=seed)
