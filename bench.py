@@ -143,6 +143,11 @@ def barrier(dist):
         dist.barrier()
 
 
+def rank_seeds(rank: int, count: int, base: int = 1) -> list[int]:
+    """Instance seeds of one rank: ranks solve disjoint instances (weak scaling, no data exchange)."""
+    return [base + rank * 100000 + i for i in range(count)]
+
+
 def n_ball(l: int, d: int) -> int:
     return sum(math.comb(l, i) * 3 ** i for i in range(d + 1))
 
@@ -217,7 +222,7 @@ def bench_plain(args, ws, rank, local, dist, l, d) -> dict:
     torch.cuda.set_device(dev)
     n, m = 20, 600
     K, Wm = args.steps, args.warmup
-    seeds = [1 + rank * 100000 + i for i in range(K + Wm)]
+    seeds = rank_seeds(rank, K + Wm)
     insts = [pi.planted_instance(n, m, l, d, s) for s in seeds]
     d_in = [torch.from_numpy(i.seqs.copy()).to(dev) for i in insts]
     cap = 1 << 16
