@@ -76,7 +76,17 @@ typedef struct {
     int smem_rows;         /* at most this many feasible occurrences of a seed are
                               kept in shared memory (0: as many as fit); larger
                               row sets are read from global memory */
+    int autotune;          /* 1: tune each new instance class before solving it */
 } pms_options;
+
+/* A tuned schedule for one instance class (l, d, n rounded up to a power of
+ * two, m rounded up to a power of two). */
+typedef struct {
+    int chunk_work;   /* candidate units per queue item */
+    int prune_rows;   /* rows the tree-node filter applies before leaves are expanded */
+    int ctas_per_sm;  /* resident CTAs of the verification kernel */
+    double ms;        /* device time of the pipeline on the tuning instance */
+} pms_tuning;
 
 /* Work counters of the last solve (pms_solve / pms_solve_device /
  * pms_solve_batch). The comparison counters are filled only when
@@ -157,6 +167,20 @@ int pms_solve_batch(pms_ctx *h, const pms_instance *inst, int k, pms_result *out
 int pms_submit(pms_ctx *h, const pms_instance *inst, uint64_t *ticket);
 int pms_wait(pms_ctx *h, uint64_t ticket, int timeout_ms, pms_result *out);
 int pms_release(pms_ctx *h, uint64_t ticket);
+
+/* Autotuner (no counterpart in the paper; it picks the schedule of the
+ * verification kernel). pms_autotune times the device pipeline on a
+ * synthetic instance of the class (n, m, l, d) (uniform random bases) for a
+ * few settings, coordinate by coordinate: rows applied by the tree-node
+ * filter, work per queue item, CTAs per SM; the best is kept in the context
+ * for the class (l, d, n and m rounded up to powers of two) and used by every
+ * later solve of that class, and copied to *out when out is non-null.
+ * pms_save_tuning / pms_load_tuning write / read the context's table as text
+ * (one class per line). Options chunk_work / ctas_per_sm, when set,
+ * override the tuned values. */
+int pms_autotune(pms_ctx *h, int n, int m, int l, int d, pms_tuning *out);
+int pms_save_tuning(const pms_ctx *h, const char *path);
+int pms_load_tuning(pms_ctx *h, const char *path);
 
 /* Work counters and timing of the last solve (waits for that solve's
  * kernels if they are still running). */

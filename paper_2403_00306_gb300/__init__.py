@@ -26,7 +26,7 @@ LMAX, NMAX = 32, 64
 ABI_FUNCTIONS = ["pms_create", "pms_set_stream", "pms_set_allocator", "pms_set_options", "pms_get_options",
                  "pms_solve", "pms_solve_device", "pms_solve_batch", "pms_submit", "pms_wait", "pms_release",
                  "pms_get_stats", "pms_decode", "pms_last_error", "pms_probe_int_rate", "pms_destroy",
-                 "pms_solve_device_noalloc"]
+                 "pms_solve_device_noalloc", "pms_autotune", "pms_save_tuning", "pms_load_tuning"]
 
 
 class PMSError(RuntimeError):
@@ -47,7 +47,12 @@ class pms_result(ctypes.Structure):
 class pms_options(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int), ("chunk_work", ctypes.c_int), ("grab", ctypes.c_int),
                 ("max_motifs", ctypes.c_size_t), ("count_work", ctypes.c_int), ("serve_wave_items", ctypes.c_int),
-                ("serve_max_inflight", ctypes.c_int), ("smem_rows", ctypes.c_int)]
+                ("serve_max_inflight", ctypes.c_int), ("smem_rows", ctypes.c_int), ("autotune", ctypes.c_int)]
+
+
+class pms_tuning(ctypes.Structure):
+    _fields_ = [("chunk_work", ctypes.c_int), ("prune_rows", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("ms", ctypes.c_double)]
 
 
 class pms_stats(ctypes.Structure):
@@ -104,6 +109,9 @@ def load(build_if_missing: bool = True):
             "pms_probe_int_rate": (ci, [vp, ci, ctypes.POINTER(ctypes.c_double)]),
             "pms_destroy": (None, [vp]),
             "pms_solve_device_noalloc": (ci, [vp, ci, ci, ci, ci, vp, sz, vp, vp]),
+            "pms_autotune": (ci, [vp, ci, ci, ci, ci, ctypes.c_void_p]),
+            "pms_save_tuning": (ci, [vp, ctypes.c_char_p]),
+            "pms_load_tuning": (ci, [vp, ctypes.c_char_p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -188,6 +196,18 @@ def pms_probe_int_rate(ctx: "Context", kind: int) -> float:
 
 def pms_set_allocator(ctx: "Context", alloc, free) -> None:
     ctx.set_allocator(alloc, free)
+
+
+def pms_autotune(ctx: "Context", n: int, m: int, l: int, d: int) -> dict:
+    return ctx.autotune(n, m, l, d)
+
+
+def pms_save_tuning(ctx: "Context", path: str) -> None:
+    ctx.save_tuning(path)
+
+
+def pms_load_tuning(ctx: "Context", path: str) -> None:
+    ctx.load_tuning(path)
 
 
 def pms_solve_device_noalloc(d_seqs, n: int, m: int, l: int, d: int, d_motifs, capacity: int, d_status,
@@ -291,6 +311,18 @@ class Context:
         s = pms_stats()
         self._check(self._lib.pms_get_stats(self._h, ctypes.byref(s)), "pms_get_stats")
         return s.as_dict()
+
+    def autotune(self, n: int, m: int, l: int, d: int) -> dict:
+        t = pms_tuning()
+        self._check(self._lib.pms_autotune(self._h, int(n), int(m), int(l), int(d),
+                                           ctypes.cast(ctypes.byref(t), ctypes.c_void_p)), "pms_autotune")
+        return {name: getattr(t, name) for name, _ in pms_tuning._fields_}
+
+    def save_tuning(self, path: str) -> None:
+        self._check(self._lib.pms_save_tuning(self._h, str(path).encode()), "pms_save_tuning")
+
+    def load_tuning(self, path: str) -> None:
+        self._check(self._lib.pms_load_tuning(self._h, str(path).encode()), "pms_load_tuning")
 
     def probe_int_rate(self, kind: int) -> float:
         v = ctypes.c_double()

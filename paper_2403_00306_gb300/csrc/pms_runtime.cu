@@ -240,9 +240,43 @@ struct pms_ctx {
         return PMS_OK;
     }
 
-    const ChunkTable &chunks(int l, int d)
+    // Autotuned schedules per instance class (l, d, n bucket, m bucket).
+    struct Tuning {
+        int chunk_work = 0;
+        int prune_rows = 0;   // 0: all rows
+        int ctas_per_sm = 0;
+        double ms = 0;
+    };
+    std::map<std::tuple<int, int, int, int>, Tuning> tuned;
+    static int bucket(int v)
     {
-        const int work = opt.chunk_work > 0 ? opt.chunk_work : kDefaultChunkWork;
+        int b = 1;
+        while (b < v)
+            b <<= 1;
+        return b;
+    }
+    const Tuning *tuning(int n, int m, int l, int d) const
+    {
+        auto it = tuned.find(std::make_tuple(l, d, bucket(n), bucket(m)));
+        return it == tuned.end() ? nullptr : &it->second;
+    }
+    int chunk_work_for(int n, int m, int l, int d) const
+    {
+        if (opt.chunk_work > 0)
+            return opt.chunk_work;
+        const Tuning *t = tuning(n, m, l, d);
+        return t && t->chunk_work > 0 ? t->chunk_work : kDefaultChunkWork;
+    }
+    int prune_rows_for(int n, int m, int l, int d) const
+    {
+        const Tuning *t = tuning(n, m, l, d);
+        return t && t->prune_rows > 0 ? std::min(t->prune_rows, n - 1) : n - 1;
+    }
+
+    const ChunkTable &chunks(int l, int d, int work = 0)
+    {
+        if (work <= 0)
+            work = opt.chunk_work > 0 ? opt.chunk_work : kDefaultChunkWork;
         auto key = std::make_tuple(l, d, work);
         auto it = ctab_cache.find(key);
         if (it == ctab_cache.end())
@@ -396,10 +430,10 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
         in.d = s.d;
         in.W = s.m - s.l + 1;
         in.NW = (in.W + 31) / 32;
-        const ChunkTable &ct = h->chunks(s.l, s.d);
+        const ChunkTable &ct = h->chunks(s.l, s.d, h->chunk_work_for(s.n, s.m, s.l, s.d));
         in.cps = ct.cps;
         in.grab = h->opt.grab > 0 ? h->opt.grab : default_grab(s.d);
-        in.prune_rows = default_prune_rows(s.n, s.d);
+        in.prune_rows = h->prune_rows_for(s.n, s.m, s.l, s.d);
         in.ctab = (int)P.ctab.size();
         P.ctab.insert(P.ctab.end(), ct.tab.begin(), ct.tab.end());
         in.seq_off = (long long)P.seq_bytes;
@@ -441,8 +475,14 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
         (rc = h->ensure(h->d_tmp, P.raw * 8)) || (rc = h->ensure(h->d_compat, P.compat * 4)))
         return rc;
     int occ = h->occ[count_mode ? 1 : 0];
-    if (h->opt.ctas_per_sm > 0)
+    if (h->opt.ctas_per_sm > 0) {
         occ = std::min(occ, h->opt.ctas_per_sm);
+    } else if (!P.inst.empty()) {
+        const InstDev &i0 = P.inst[0];
+        const pms_ctx::Tuning *t = h->tuning(i0.n, i0.m, i0.l, i0.d);
+        if (t && t->ctas_per_sm > 0)
+            occ = std::min(occ, t->ctas_per_sm);
+    }
     occ = std::max(occ, 1);
     const long long blocks_ll = std::min<long long>((long long)h->num_sms * occ, std::max<long long>(P.total_items, 1));
     const int blocks = (int)blocks_ll;
@@ -632,8 +672,12 @@ struct InstOut {
 // Solves instances from host memory; instances whose raw motif buffer
 // overflowed are solved again with a larger buffer (unless the caller fixed
 // max_motifs), so the returned sets are complete.
+static int autotune_missing(pms_ctx *h, const std::vector<InstSpec> &specs);
+
 static int solve_specs(pms_ctx *h, std::vector<InstSpec> specs, std::vector<InstOut> &out, double t0)
 {
+    if (int rc = autotune_missing(h, specs))
+        return rc;
     out.assign(specs.size(), InstOut{});
     std::vector<int> todo(specs.size());
     for (size_t i = 0; i < specs.size(); ++i)
@@ -669,6 +713,102 @@ static int solve_specs(pms_ctx *h, std::vector<InstSpec> specs, std::vector<Inst
         todo.swap(again);
     }
     h->stats.candidates = candidates;
+    return PMS_OK;
+}
+
+// ----------------------------------------------------------------------------- autotuner
+
+// Tunes the schedule of one instance class by coordinate descent on a
+// synthetic instance of that class (uniform random bases), timing the
+// device pipeline with CUDA events: first how many rows the node filter
+// applies before leaves are expanded, then the work per queue item, then
+// the resident CTAs per SM. The best setting is stored for the class.
+static int autotune_class(pms_ctx *h, int n, int m, int l, int d, pms_ctx::Tuning &best)
+{
+    std::vector<uint8_t> seqs((size_t)n * m);
+    uint64_t x = 0x9E3779B97F4A7C15ull ^ ((uint64_t)n << 40) ^ ((uint64_t)m << 20) ^ ((uint64_t)l << 8) ^ (uint64_t)d;
+    static const uint8_t letters[4] = {'A', 'C', 'G', 'T'};
+    for (auto &c : seqs) {
+        x ^= x << 13;
+        x ^= x >> 7;
+        x ^= x << 17;
+        c = letters[(x >> 33) & 3u];
+    }
+    const auto key = std::make_tuple(l, d, pms_ctx::bucket(n), pms_ctx::bucket(m));
+    const pms_options saved = h->opt;
+    h->opt.chunk_work = 0;
+    h->opt.ctas_per_sm = 0;
+    h->opt.count_work = 0;
+    std::vector<InstSpec> specs{InstSpec{n, m, l, d, seqs.data()}};
+    auto run = [&](const pms_ctx::Tuning &t, double &ms) -> int {
+        h->tuned[key] = t;
+        double bestms = 1e30;
+        for (int rep = 0; rep < 2; ++rep) {
+            Plan P = make_plan(h, specs);
+            const int rc = run_host_plan(h, P, specs, now_ms());
+            if (rc)
+                return rc;
+            bestms = std::min(bestms, h->stats.ms_kernel);
+        }
+        ms = bestms;
+        return PMS_OK;
+    };
+    pms_ctx::Tuning cur;
+    cur.chunk_work = kDefaultChunkWork;
+    cur.prune_rows = n - 1;
+    cur.ctas_per_sm = std::max(1, h->occ[0]);
+    int rc = run(cur, cur.ms);
+    std::vector<int> prune_c = {n - 1, 8, 4, 2, 1};
+    std::vector<int> work_c = {1 << 18, 1 << 20, 1 << 22};
+    std::vector<int> cta_c;
+    for (int c = std::max(1, h->occ[0]); c >= 1 && (int)cta_c.size() < 2; --c)
+        cta_c.push_back(c);
+    for (int dim = 0; dim < 3 && rc == PMS_OK; ++dim) {
+        const std::vector<int> &vals = dim == 0 ? prune_c : (dim == 1 ? work_c : cta_c);
+        for (int v : vals) {
+            pms_ctx::Tuning t = cur;
+            if (dim == 0) {
+                if (v > n - 1 || v == cur.prune_rows)
+                    continue;
+                t.prune_rows = v;
+            } else if (dim == 1) {
+                if (v == cur.chunk_work)
+                    continue;
+                t.chunk_work = v;
+            } else {
+                if (v == cur.ctas_per_sm)
+                    continue;
+                t.ctas_per_sm = v;
+            }
+            if ((rc = run(t, t.ms)))
+                break;
+            if (t.ms < cur.ms)
+                cur = t;
+        }
+    }
+    h->opt = saved;
+    if (rc) {
+        h->tuned.erase(key);
+        return rc;
+    }
+    h->tuned[key] = cur;
+    best = cur;
+    return PMS_OK;
+}
+
+// Tunes every class of `specs` not tuned yet (pms_options.autotune).
+static int autotune_missing(pms_ctx *h, const std::vector<InstSpec> &specs)
+{
+    if (!h->opt.autotune)
+        return PMS_OK;
+    for (const InstSpec &s : specs) {
+        if (h->tuning(s.n, s.m, s.l, s.d))
+            continue;
+        pms_ctx::Tuning t;
+        const int rc = autotune_class(h, s.n, s.m, s.l, s.d, t);
+        if (rc)
+            return rc;
+    }
     return PMS_OK;
 }
 
@@ -928,7 +1068,7 @@ static bool served_admit(Served *S, Request *r)
     if (S->free_slots.empty())
         return false;
     std::lock_guard<std::recursive_mutex> hg(h->mu);
-    const ChunkTable &ct = h->chunks(r->l, r->d);
+    const ChunkTable &ct = h->chunks(r->l, r->d, h->chunk_work_for(r->n, r->m, r->l, r->d));
     if ((int)ct.tab.size() > Served::kCtabMax) {
         r->status = PMS_EINVAL;
         return true;
@@ -965,7 +1105,7 @@ static bool served_admit(Served *S, Request *r)
     in.NW = (r->W + 31) / 32;
     in.cps = ct.cps;
     in.grab = h->opt.grab > 0 ? h->opt.grab : default_grab(r->d);
-    in.prune_rows = default_prune_rows(r->n, r->d);
+    in.prune_rows = h->prune_rows_for(r->n, r->m, r->l, r->d);
     in.seq_off = (long long)(off + L.seqs);
     in.plane_off = (long long)((off + L.planes) / sizeof(uint2));
     in.raw_off = (long long)((off + L.raw) / 8);
@@ -1322,6 +1462,8 @@ int pms_solve_device(pms_ctx *h, const uint8_t *d_seqs, int n, int m, int l, int
         return rc;
     cudaSetDevice(h->device);
     std::vector<InstSpec> specs{InstSpec{n, m, l, d, nullptr}};
+    if ((rc = autotune_missing(h, specs)))
+        return rc;
     Plan P = make_plan(h, specs);
     const uint32_t cap = (uint32_t)std::min<size_t>(capacity, 0xffffffffu);
     if ((rc = enqueue_plan(h, P, d_seqs, (StatusDev *)d_status, d_motifs, cap, h->opt.count_work != 0)))
@@ -1450,6 +1592,73 @@ int pms_release(pms_ctx *h, uint64_t ticket)
         return PMS_EBUSY;
     S->all.erase(it);
     return PMS_OK;
+}
+
+int pms_autotune(pms_ctx *h, int n, int m, int l, int d, pms_tuning *out)
+{
+    if (!h)
+        return PMS_EINVAL;
+    std::lock_guard<std::recursive_mutex> g(h->mu);
+    h->err.clear();
+    int rc = check_params(h, n, m, l, d);
+    if (rc)
+        return rc;
+    cudaSetDevice(h->device);
+    pms_ctx::Tuning t;
+    if ((rc = autotune_class(h, n, m, l, d, t)))
+        return rc;
+    if (out)
+        *out = pms_tuning{t.chunk_work, t.prune_rows, t.ctas_per_sm, t.ms};
+    return PMS_OK;
+}
+
+int pms_save_tuning(const pms_ctx *h, const char *path)
+{
+    if (!h || !path)
+        return PMS_EINVAL;
+    pms_ctx *hm = const_cast<pms_ctx *>(h);
+    std::lock_guard<std::recursive_mutex> g(hm->mu);
+    FILE *f = std::fopen(path, "w");
+    if (!f)
+        return hm->fail(PMS_EINVAL, "cannot write %s", path);
+    std::fprintf(f, "# l d n_bucket m_bucket chunk_work prune_rows ctas_per_sm ms\n");
+    for (const auto &kv : h->tuned)
+        std::fprintf(f, "%d %d %d %d %d %d %d %.6f\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                     std::get<2>(kv.first), std::get<3>(kv.first), kv.second.chunk_work, kv.second.prune_rows,
+                     kv.second.ctas_per_sm, kv.second.ms);
+    std::fclose(f);
+    return PMS_OK;
+}
+
+int pms_load_tuning(pms_ctx *h, const char *path)
+{
+    if (!h || !path)
+        return PMS_EINVAL;
+    std::lock_guard<std::recursive_mutex> g(h->mu);
+    FILE *f = std::fopen(path, "r");
+    if (!f)
+        return h->fail(PMS_EINVAL, "cannot read %s", path);
+    char line[256];
+    int loaded = 0;
+    while (std::fgets(line, sizeof line, f)) {
+        if (line[0] == '#')
+            continue;
+        int l, d, nb, mb, cw, pr, cta;
+        double ms;
+        if (std::sscanf(line, "%d %d %d %d %d %d %d %lf", &l, &d, &nb, &mb, &cw, &pr, &cta, &ms) != 8)
+            continue;
+        if (l < 1 || l > PMS_LMAX || d < 0 || d >= l || cw < 0 || pr < 0 || cta < 0)
+            continue;
+        pms_ctx::Tuning t;
+        t.chunk_work = cw;
+        t.prune_rows = pr;
+        t.ctas_per_sm = cta;
+        t.ms = ms;
+        h->tuned[std::make_tuple(l, d, nb, mb)] = t;
+        ++loaded;
+    }
+    std::fclose(f);
+    return loaded > 0 ? PMS_OK : h->fail(PMS_EINVAL, "no tuning entries in %s", path);
 }
 
 int pms_get_stats(const pms_ctx *h, pms_stats *out)
