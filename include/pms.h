@@ -68,7 +68,9 @@ typedef struct {
 typedef struct {
     int ctas_per_sm;       /* resident CTAs of the verification kernel per SM */
     int chunk_work;        /* target work of one queue item, in candidate units */
-    int grab;              /* subsets a warp takes from a chunk at a time */
+    int grab;              /* tree-node batches: 0 = fixed (up to 128 nodes per warp
+                              claim); g > 0 = guided, shrinking to g nodes as a
+                              queue item runs out */
     size_t max_motifs;     /* raw motif capacity per instance (rounded to 2^k) */
     int count_work;        /* 1: also count comparisons (slower; for profiling) */
     int serve_wave_items;  /* served form: queue items per wave launch */
@@ -85,6 +87,7 @@ typedef struct {
     int chunk_work;   /* candidate units per queue item */
     int prune_rows;   /* rows the tree-node filter applies before leaves are expanded */
     int ctas_per_sm;  /* resident CTAs of the verification kernel */
+    int grab;         /* node batch policy (as pms_options.grab) */
     double ms;        /* device time of the pipeline on the tuning instance */
 } pms_tuning;
 
@@ -172,7 +175,8 @@ int pms_release(pms_ctx *h, uint64_t ticket);
  * verification kernel). pms_autotune times the device pipeline on a
  * synthetic instance of the class (n, m, l, d) (uniform random bases) for a
  * few settings, coordinate by coordinate: rows applied by the tree-node
- * filter, work per queue item, CTAs per SM; the best is kept in the context
+ * filter, work per queue item, CTAs per SM, node batch policy; the best is
+ * kept in the context
  * for the class (l, d, n and m rounded up to powers of two) and used by every
  * later solve of that class, and copied to *out when out is non-null.
  * pms_save_tuning / pms_load_tuning write / read the context's table as text

@@ -52,7 +52,7 @@ class pms_options(ctypes.Structure):
 
 class pms_tuning(ctypes.Structure):
     _fields_ = [("chunk_work", ctypes.c_int), ("prune_rows", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-                ("ms", ctypes.c_double)]
+                ("grab", ctypes.c_int), ("ms", ctypes.c_double)]
 
 
 class pms_stats(ctypes.Structure):

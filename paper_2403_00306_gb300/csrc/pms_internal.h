@@ -26,7 +26,7 @@ struct InstDev {
     int W;                 // windows per sequence: m - l + 1
     int NW;                // 32-bit words of one compatibility mask row: ceil(W / 32)
     int cps;               // queue chunks per seed
-    int grab;              // subsets a warp claims at a time
+    int grab;              // 0: fixed node batches; > 0: guided batches shrinking to this size
     int ctab;              // offset (ints) of this instance's table in the chunk arena:
                            //   levoff[0..d+1] then cps pairs (g0, g1)
     int prune_rows;        // rows checked for a feasible occurrence before leaves are tested
@@ -34,6 +34,7 @@ struct InstDev {
     long long plane_off;   // offset (uint2) of the n x W window planes
     long long raw_off;     // offset (uint64) of the raw motif buffer (and of its sort twin)
     long long compat_off;  // offset (uint32) of the W x (n-1) x NW compatibility masks
+    long long rlen_off;    // offset (int) of the W x (n-1) row sizes (set bits of each mask row)
     uint32_t raw_cap;      // capacity of the raw motif buffer (power of two)
     int pad;
 };
@@ -75,6 +76,7 @@ struct MainParams {
     unsigned long long *head;     // queue head (zeroed before the launch)
     const uint2 *planes;
     const uint32_t *compat;       // seed x row compatibility masks (d_H <= 2d)
+    const int *rowlen;            // seed x row sizes of those masks
     const int *ctab;
     uint64_t *raw;                // raw motif codes
     uint32_t *raw_count;          // per instance
@@ -91,7 +93,7 @@ struct MainParams {
 cudaError_t launch_pack(const InstDev *inst, int ninst, const long long *win_prefix, long long total_windows,
                         const uint8_t *seqs, uint2 *planes, uint32_t *flags, int blocks, cudaStream_t st);
 cudaError_t launch_compat(const InstDev *inst, int ninst, const long long *row_prefix, long long total_rows,
-                          const uint2 *planes, uint32_t *compat, int blocks, cudaStream_t st);
+                          const uint2 *planes, uint32_t *compat, int *rowlen, int blocks, cudaStream_t st);
 cudaError_t launch_main(const MainParams &p, int blocks, bool count_mode, cudaStream_t st);
 cudaError_t main_occupancy(int *blocks_per_sm, bool count_mode);
 size_t main_smem_bytes();

@@ -365,32 +365,41 @@ __device__ __forceinline__ int filter_subsets(const WarpCtx &c, int N)
         const uint4 *D4 = reinterpret_cast<const uint4 *>(c.rows.D + c.cs->row_off[ri]);
         const int len4 = (len + 3) >> 2;
         int newN = 0;
-        for (int b = 0; b < N; b += 32) {
-            const int idx = b + c.lane;
-            const bool alive = idx < N;
-            const uint32_t P = alive ? subs[idx] : 0u;
-            int m0 = 64, m1 = 64;
+        // two subsets per lane share every 16-byte load of row entries
+        for (int b = 0; b < N; b += 64) {
+            const int i0 = b + c.lane, i1 = b + 32 + c.lane;
+            const bool al0 = i0 < N, al1 = i1 < N;
+            const uint32_t P0 = al0 ? subs[i0] : 0u, P1 = al1 ? subs[i1] : 0u;
+            int m00 = 64, m01 = 64, m10 = 64, m11 = 64;
             int e4 = 0;
             for (; e4 < len4; ++e4) {
                 const uint4 v = D4[e4];
-                m0 = min(m0, __popc(v.x ^ P));
-                m1 = min(m1, __popc(v.y ^ P));
-                m0 = min(m0, __popc(v.z ^ P));
-                m1 = min(m1, __popc(v.w ^ P));
-                if ((e4 & 3) == 3 && __all_sync(kFull, !alive || min(m0, m1) <= d)) {
+                m00 = min(m00, __popc(v.x ^ P0));
+                m10 = min(m10, __popc(v.x ^ P1));
+                m01 = min(m01, __popc(v.y ^ P0));
+                m11 = min(m11, __popc(v.y ^ P1));
+                m00 = min(m00, __popc(v.z ^ P0));
+                m10 = min(m10, __popc(v.z ^ P1));
+                m01 = min(m01, __popc(v.w ^ P0));
+                m11 = min(m11, __popc(v.w ^ P1));
+                if ((e4 & 3) == 3 &&
+                    __all_sync(kFull, (!al0 || min(m00, m01) <= d) && (!al1 || min(m10, m11) <= d))) {
                     ++e4;
                     break;
                 }
             }
-            const int mn = min(m0, m1);
-            if (kCount && alive)
-                c.cnt[kCntCmpReduce] += 4 * e4;
-            const bool pass = alive && mn <= d;
+            if (kCount)
+                c.cnt[kCntCmpReduce] += 4ull * e4 * ((al0 ? 1 : 0) + (al1 ? 1 : 0));
+            const bool pass0 = al0 && min(m00, m01) <= d;
+            const bool pass1 = al1 && min(m10, m11) <= d;
             __syncwarp();
-            const uint32_t bal = __ballot_sync(kFull, pass);
-            if (pass)
-                subs[newN + __popc(bal & c.lt)] = P;
-            newN += __popc(bal);
+            const uint32_t bal0 = __ballot_sync(kFull, pass0);
+            const uint32_t bal1 = __ballot_sync(kFull, pass1);
+            if (pass0)
+                subs[newN + __popc(bal0 & c.lt)] = P0;
+            if (pass1)
+                subs[newN + __popc(bal0) + __popc(bal1 & c.lt)] = P1;
+            newN += __popc(bal0) + __popc(bal1);
         }
         __syncwarp();
         N = newN;
@@ -400,91 +409,94 @@ __device__ __forceinline__ int filter_subsets(const WarpCtx &c, int N)
 
 // Gathers the feasible occurrences of seed `seed` (windows within 2d, from
 // the compatibility masks) into shared memory when they fit, else into this
-// CTA's global scratch; records each row's size, offset and the
-// smallest-first order, and whether every row is non-empty.
+// CTA's global scratch. Every warp derives the smallest-first row order and
+// the row offsets from the precomputed row sizes (two rows per lane, n <= 64)
+// and fills its own rows; warp 0 also records them for the later phases.
 __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &in, int seed, CtaSmem &cs,
                                            uint32_t *smem_D, uint2 *smem_HL, uint32_t *glob_D, uint2 *glob_HL,
                                            int warp, int lane, unsigned long long *cnt)
 {
-    const int n = in.n, NW = in.NW, W = in.W;
-    const uint32_t *mask = p.compat + in.compat_off + (size_t)seed * (n - 1) * NW;
-    for (int i = 1 + warp; i < n; i += kWarps) {
-        const uint32_t *mr = mask + (size_t)(i - 1) * NW;
-        int c = 0;
-        for (int k = lane; k < NW; k += 32)
-            c += __popc(mr[k]);
-        for (int o = 16; o > 0; o >>= 1)
-            c += __shfl_xor_sync(kFull, c, o);
-        if (lane == 0)
-            cs.row_len[i] = c;
+    const int n = in.n, NW = in.NW, W = in.W, R = n - 1;
+    const int *rl = p.rowlen + in.rlen_off + (size_t)seed * R;
+    const int big = 0x7fffffff;
+    const int la = lane < R ? rl[lane] : big;            // size of row (sequence) lane + 1
+    const int lb = lane + 32 < R ? rl[lane + 32] : big;  // size of row lane + 33
+    int ra = 0, rb = 0;                                  // ranks in smallest-first order
+    for (int j = 0; j < R; ++j) {
+        const int lj = __shfl_sync(kFull, j < 32 ? la : lb, j & 31);
+        ra += (lj < la) || (lj == la && j < lane);
+        rb += (lj < lb) || (lj == lb && j < lane + 32);
     }
-    __syncthreads();
+    const int pa = lane < R ? (la + 3) & ~3 : 0, pb = lane + 32 < R ? (lb + 3) & ~3 : 0;
+    int oa = 0, ob = 0, total = 0;                       // offsets: padded sizes of the rows ranked before
+    for (int j = 0; j < R; ++j) {
+        const int rj = __shfl_sync(kFull, j < 32 ? ra : rb, j & 31);
+        const int pj = __shfl_sync(kFull, j < 32 ? pa : pb, j & 31);
+        oa += rj < ra ? pj : 0;
+        ob += rj < rb ? pj : 0;
+        total += pj;
+    }
+    const bool empty = __any_sync(kFull, (lane < R && la == 0) || (lane + 32 < R && lb == 0));
+    const bool in_smem = total <= p.smem_rows_cap;
     if (warp == 0) {
-        bool empty = false;
-        for (int i = 1 + lane; i < n; i += 32) {
-            const int li = cs.row_len[i];
-            empty |= li == 0;
-            int rank = 0;
-            for (int j = 1; j < n; ++j) {
-                const int lj = cs.row_len[j];
-                rank += (lj < li) || (lj == li && j < i);
-            }
-            cs.row_order[rank] = i;
+        if (lane < R) {
+            cs.row_len[lane + 1] = la;
+            cs.row_off[lane + 1] = oa;
+            cs.row_order[ra] = lane + 1;
         }
-        const bool any_empty = __any_sync(kFull, empty);
-        __syncwarp();
+        if (lane + 32 < R) {
+            cs.row_len[lane + 33] = lb;
+            cs.row_off[lane + 33] = ob;
+            cs.row_order[rb] = lane + 33;
+        }
         if (lane == 0) {
-            int off = 0;
-            for (int r = 0; r < n - 1; ++r) {
-                const int i = cs.row_order[r];
-                cs.row_off[i] = off;
-                off += (cs.row_len[i] + 3) & ~3;
-            }
-            cs.total_rows = off;
-            cs.feasible = !any_empty;
-            cs.rows_in_smem = off <= p.smem_rows_cap;
+            cs.total_rows = total;
+            cs.feasible = !empty;
+            cs.rows_in_smem = in_smem;
             if (cnt)
-                cnt[kCntCmpRows] += (unsigned long long)(n - 1) * W;
+                cnt[kCntCmpRows] += (unsigned long long)R * W;
         }
     }
-    __syncthreads();
-    if (!cs.feasible)
-        return;
-    uint32_t *Dd = cs.rows_in_smem ? smem_D : glob_D;
-    uint2 *Hd = cs.rows_in_smem ? smem_HL : glob_HL;
-    const uint2 *pl = p.planes + in.plane_off;
-    const uint2 x = pl[seed];
-    for (int i = 1 + warp; i < n; i += kWarps) {
-        const uint32_t *mr = mask + (size_t)(i - 1) * NW;
-        const uint2 *s = pl + (size_t)i * W;
-        const int off = cs.row_off[i], len = cs.row_len[i];
-        int base = 0;
-        for (int k0 = 0; k0 < NW; k0 += 32) {
-            const int k = k0 + lane;
-            uint32_t bits = k < NW ? mr[k] : 0u;
-            const int c = __popc(bits);
-            int incl = c;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o)
-                    incl += y;
+    if (!empty) {
+        uint32_t *Dd = in_smem ? smem_D : glob_D;
+        uint2 *Hd = in_smem ? smem_HL : glob_HL;
+        const uint2 *pl = p.planes + in.plane_off;
+        const uint2 x = pl[seed];
+        const uint32_t *mask = p.compat + in.compat_off + (size_t)seed * R * NW;
+        for (int i = 1 + warp; i < n; i += kWarps) {
+            const uint32_t *mr = mask + (size_t)(i - 1) * NW;
+            const uint2 *s = pl + (size_t)i * W;
+            const int src = (i - 1) & 31;
+            const int off = __shfl_sync(kFull, i - 1 < 32 ? oa : ob, src);
+            const int len = __shfl_sync(kFull, i - 1 < 32 ? la : lb, src);
+            int base = 0;
+            for (int k0 = 0; k0 < NW; k0 += 32) {
+                const int k = k0 + lane;
+                uint32_t bits = k < NW ? mr[k] : 0u;
+                const int c = __popc(bits);
+                int incl = c;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o)
+                        incl += y;
+                }
+                int pos = off + base + incl - c;
+                while (bits) {
+                    const int bt = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const uint2 w = s[32 * k + bt];
+                    Hd[pos] = w;
+                    Dd[pos] = (x.x ^ w.x) | (x.y ^ w.y);
+                    ++pos;
+                }
+                base += __shfl_sync(kFull, incl, 31);
             }
-            int pos = off + base + incl - c;
-            while (bits) {
-                const int b = __ffs(bits) - 1;
-                bits &= bits - 1;
-                const uint2 w = s[32 * k + b];
-                Hd[pos] = w;
-                Dd[pos] = (x.x ^ w.x) | (x.y ^ w.y);
-                ++pos;
+            __syncwarp();
+            const int padded = (len + 3) & ~3;
+            if (lane < padded - len) {
+                Hd[off + len + lane] = Hd[off + len - 1];
+                Dd[off + len + lane] = Dd[off + len - 1];
             }
-            base += __shfl_sync(kFull, incl, 31);
-        }
-        __syncwarp();
-        const int padded = (len + 3) & ~3;
-        if (lane < padded - len) {
-            Hd[off + len + lane] = Hd[off + len - 1];
-            Dd[off + len + lane] = Dd[off + len - 1];
         }
     }
     __syncthreads();
@@ -566,15 +578,25 @@ __global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
             Rows rows{cs.rows_in_smem ? smem_D : glob_D, cs.rows_in_smem ? smem_HL : glob_HL};
             WarpCtx c{&p, in, I, lane, lt, x.x, x.y, rows, &cs, &wsm[warp], kCount ? cnt : nullptr};
             uint32_t *subs = wsm[warp].subs;
-            // batch size: up to kSubBatch subsets, but small chunks are split so
-            // that every warp of the CTA gets work
+            // batch size: up to kSubBatch subsets (large batches keep the
+            // breadth-first filter's lanes full), but small chunks are split so
+            // that every warp of the CTA gets work. With in.grab > 0 batches
+            // shrink toward in.grab as the chunk runs out (guided
+            // self-scheduling), which evens out warps whose nodes expand to
+            // many leaves.
             const int per_warp = (g1 - g0 + 2 * kWarps - 1) / (2 * kWarps);
-            const int batch = min(kSubBatch, max(32, (per_warp + 31) & ~31));
+            const int fixed = min(kSubBatch, max(32, (per_warp + 31) & ~31));
             for (;;) {
-                int start = 0;
-                if (lane == 0)
+                int start = 0, batch = fixed;
+                if (lane == 0) {
+                    if (in.grab > 0) {
+                        const int left = g1 - *reinterpret_cast<volatile int *>(&cs.next);
+                        batch = min(fixed, max(in.grab, ((left + 2 * kWarps - 1) / (2 * kWarps) + 31) & ~31));
+                    }
                     start = atomicAdd(&cs.next, batch);
+                }
                 start = __shfl_sync(kFull, start, 0);
+                batch = __shfl_sync(kFull, batch, 0);
                 if (start >= g1)
                     break;
                 const int N = min(batch, g1 - start);
@@ -618,7 +640,8 @@ __global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
 // x = s_1[j..j+l-1] and every sequence i >= 2, bit w of row (j, i) is set iff
 // d_H(x, s_i[w..w+l-1]) <= 2d. One warp per (instance, seed, row).
 __global__ void compat_kernel(const InstDev *__restrict__ inst, int ninst, const long long *__restrict__ row_prefix,
-                              long long total_rows, const uint2 *__restrict__ planes, uint32_t *__restrict__ compat)
+                              long long total_rows, const uint2 *__restrict__ planes, uint32_t *__restrict__ compat,
+                              int *__restrict__ rowlen)
 {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
@@ -639,6 +662,7 @@ __global__ void compat_kernel(const InstDev *__restrict__ inst, int ninst, const
         const uint2 *s = pl + (size_t)i * in.W;
         uint32_t *out = compat + in.compat_off + (size_t)local * in.NW;
         const int lim = 2 * in.d;
+        int total = 0;
         for (int w0 = 0; w0 < in.W; w0 += 32) {
             const int w = w0 + lane;
             bool keep = false;
@@ -647,9 +671,12 @@ __global__ void compat_kernel(const InstDev *__restrict__ inst, int ninst, const
                 keep = __popc((x.x ^ e.x) | (x.y ^ e.y)) <= lim;
             }
             const uint32_t bal = __ballot_sync(kFull, keep);
+            total += __popc(bal);
             if (lane == 0)
                 out[w0 >> 5] = bal;
         }
+        if (lane == 0)
+            rowlen[in.rlen_off + local] = total;
     }
 }
 
@@ -955,9 +982,9 @@ cudaError_t launch_main(const MainParams &p, int blocks, bool count_mode, cudaSt
 }
 
 cudaError_t launch_compat(const InstDev *inst, int ninst, const long long *row_prefix, long long total_rows,
-                          const uint2 *planes, uint32_t *compat, int blocks, cudaStream_t st)
+                          const uint2 *planes, uint32_t *compat, int *rowlen, int blocks, cudaStream_t st)
 {
-    compat_kernel<<<blocks, 256, 0, st>>>(inst, ninst, row_prefix, total_rows, planes, compat);
+    compat_kernel<<<blocks, 256, 0, st>>>(inst, ninst, row_prefix, total_rows, planes, compat, rowlen);
     return cudaGetLastError();
 }
 

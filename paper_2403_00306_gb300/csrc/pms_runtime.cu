@@ -106,13 +106,6 @@ ChunkTable make_chunks(int l, int d, int work)
     return ct;
 }
 
-int default_grab(int d)
-{
-    uint64_t p3 = 1;
-    for (int i = 0; i < std::min(d, 8); ++i)
-        p3 *= 3;
-    return (int)std::max<uint64_t>(1, std::min<uint64_t>(32, 256 / p3));
-}
 
 }  // namespace
 
@@ -141,7 +134,7 @@ struct pms_ctx {
         void *p = nullptr;
         size_t cap = 0;
     };
-    DBuf d_seqs, d_planes, d_raw, d_tmp, d_compat, d_meta, d_ctr, d_scratch, d_result;
+    DBuf d_seqs, d_planes, d_raw, d_tmp, d_compat, d_rowlen, d_meta, d_ctr, d_scratch, d_result;
     void *h_result = nullptr;   // pinned
     size_t h_result_cap = 0;
     void *h_meta = nullptr;     // pinned staging for descriptors and inputs
@@ -245,6 +238,7 @@ struct pms_ctx {
         int chunk_work = 0;
         int prune_rows = 0;   // 0: all rows
         int ctas_per_sm = 0;
+        int grab = 0;         // node batch policy (InstDev.grab)
         double ms = 0;
     };
     std::map<std::tuple<int, int, int, int>, Tuning> tuned;
@@ -260,12 +254,20 @@ struct pms_ctx {
         auto it = tuned.find(std::make_tuple(l, d, bucket(n), bucket(m)));
         return it == tuned.end() ? nullptr : &it->second;
     }
+    // 0: no fixed value (the plan sizes chunks from its total work)
     int chunk_work_for(int n, int m, int l, int d) const
     {
         if (opt.chunk_work > 0)
             return opt.chunk_work;
         const Tuning *t = tuning(n, m, l, d);
-        return t && t->chunk_work > 0 ? t->chunk_work : kDefaultChunkWork;
+        return t && t->chunk_work > 0 ? t->chunk_work : 0;
+    }
+    int grab_for(int n, int m, int l, int d) const
+    {
+        if (opt.grab > 0)
+            return opt.grab;
+        const Tuning *t = tuning(n, m, l, d);
+        return t ? t->grab : 0;
     }
     int prune_rows_for(int n, int m, int l, int d) const
     {
@@ -334,7 +336,7 @@ struct Plan {
     long long total_items = 0;
     long long total_windows = 0;
     long long total_rows = 0;
-    size_t seq_bytes = 0, planes = 0, raw = 0, compat = 0;
+    size_t seq_bytes = 0, planes = 0, raw = 0, compat = 0, rowlen = 0;
     int rows_cap = 1;
     uint64_t candidates = 0;
 };
@@ -421,6 +423,7 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
 {
     Plan P;
     long long work = 0;
+    const int adaptive = kDefaultChunkWork;   // untuned classes: about 2^20 candidate units per queue item
     for (size_t k = 0; k < specs.size(); ++k) {
         const InstSpec &s = specs[k];
         InstDev in{};
@@ -430,9 +433,10 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
         in.d = s.d;
         in.W = s.m - s.l + 1;
         in.NW = (in.W + 31) / 32;
-        const ChunkTable &ct = h->chunks(s.l, s.d, h->chunk_work_for(s.n, s.m, s.l, s.d));
+        const int cw = h->chunk_work_for(s.n, s.m, s.l, s.d);
+        const ChunkTable &ct = h->chunks(s.l, s.d, cw > 0 ? cw : adaptive);
         in.cps = ct.cps;
-        in.grab = h->opt.grab > 0 ? h->opt.grab : default_grab(s.d);
+        in.grab = h->grab_for(s.n, s.m, s.l, s.d);
         in.prune_rows = h->prune_rows_for(s.n, s.m, s.l, s.d);
         in.ctab = (int)P.ctab.size();
         P.ctab.insert(P.ctab.end(), ct.tab.begin(), ct.tab.end());
@@ -445,6 +449,8 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
         P.raw += in.raw_cap;
         in.compat_off = (long long)P.compat;
         P.compat += (size_t)in.W * (s.n - 1) * in.NW;
+        in.rlen_off = (long long)P.rowlen;
+        P.rowlen += (size_t)in.W * (s.n - 1);
         P.win_prefix.push_back(P.total_windows);
         P.total_windows += (long long)s.n * in.W;
         P.row_prefix.push_back(P.total_rows);
@@ -472,7 +478,8 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     int rc;
     if ((rc = h->ensure(h->d_meta, ml.total)) || (rc = h->ensure(h->d_ctr, cl.total)) ||
         (rc = h->ensure(h->d_planes, P.planes * sizeof(uint2))) || (rc = h->ensure(h->d_raw, P.raw * 8)) ||
-        (rc = h->ensure(h->d_tmp, P.raw * 8)) || (rc = h->ensure(h->d_compat, P.compat * 4)))
+        (rc = h->ensure(h->d_tmp, P.raw * 8)) || (rc = h->ensure(h->d_compat, P.compat * 4)) ||
+        (rc = h->ensure(h->d_rowlen, P.rowlen * 4)))
         return rc;
     int occ = h->occ[count_mode ? 1 : 0];
     if (h->opt.ctas_per_sm > 0) {
@@ -516,7 +523,8 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     if (P.total_rows > 0) {
         const int cw_blocks = (int)std::min<long long>((P.total_rows + 7) / 8, (long long)h->num_sms * 16);
         if ((e = launch_compat(d_inst, (int)k, (const long long *)(dm + ml.rowp), P.total_rows,
-                               (const uint2 *)h->d_planes.p, (uint32_t *)h->d_compat.p, std::max(cw_blocks, 1), st)) !=
+                               (const uint2 *)h->d_planes.p, (uint32_t *)h->d_compat.p, (int *)h->d_rowlen.p,
+                               std::max(cw_blocks, 1), st)) !=
             cudaSuccess)
             return h->cuda_fail(e, "compatibility kernel");
     }
@@ -528,6 +536,7 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     mp.head = (unsigned long long *)(dc + cl.head);
     mp.planes = (const uint2 *)h->d_planes.p;
     mp.compat = (const uint32_t *)h->d_compat.p;
+    mp.rowlen = (const int *)h->d_rowlen.p;
     mp.ctab = (const int *)(dm + ml.ctab);
     mp.raw = (uint64_t *)h->d_raw.p;
     mp.raw_count = d_rawcnt;
@@ -759,12 +768,13 @@ static int autotune_class(pms_ctx *h, int n, int m, int l, int d, pms_ctx::Tunin
     cur.ctas_per_sm = std::max(1, h->occ[0]);
     int rc = run(cur, cur.ms);
     std::vector<int> prune_c = {n - 1, 8, 4, 2, 1};
-    std::vector<int> work_c = {1 << 18, 1 << 20, 1 << 22};
+    std::vector<int> work_c = {1 << 16, 1 << 18, 1 << 20, 1 << 22};
     std::vector<int> cta_c;
     for (int c = std::max(1, h->occ[0]); c >= 1 && (int)cta_c.size() < 2; --c)
         cta_c.push_back(c);
-    for (int dim = 0; dim < 3 && rc == PMS_OK; ++dim) {
-        const std::vector<int> &vals = dim == 0 ? prune_c : (dim == 1 ? work_c : cta_c);
+    std::vector<int> grab_c = {0, 32, 64};
+    for (int dim = 0; dim < 4 && rc == PMS_OK; ++dim) {
+        const std::vector<int> &vals = dim == 0 ? prune_c : (dim == 1 ? work_c : (dim == 2 ? cta_c : grab_c));
         for (int v : vals) {
             pms_ctx::Tuning t = cur;
             if (dim == 0) {
@@ -775,10 +785,14 @@ static int autotune_class(pms_ctx *h, int n, int m, int l, int d, pms_ctx::Tunin
                 if (v == cur.chunk_work)
                     continue;
                 t.chunk_work = v;
-            } else {
+            } else if (dim == 2) {
                 if (v == cur.ctas_per_sm)
                     continue;
                 t.ctas_per_sm = v;
+            } else {
+                if (v == cur.grab)
+                    continue;
+                t.grab = v;
             }
             if ((rc = run(t, t.ms)))
                 break;
@@ -886,7 +900,7 @@ struct PoolAlloc {
 
 // A request's arena in the pool (offsets relative to the arena start).
 struct ReqLayout {
-    size_t seqs, planes, compat, raw, tmp, dense, status, ctab, total;
+    size_t seqs, planes, compat, rowlen, raw, tmp, dense, status, ctab, total;
     ReqLayout(int n, int m, int W, uint32_t raw_cap, size_t ctab_ints)
     {
         size_t o = 0;
@@ -898,6 +912,7 @@ struct ReqLayout {
         seqs = take((size_t)n * m);
         planes = take((size_t)n * W * sizeof(uint2));
         compat = take((size_t)W * (n - 1) * ((W + 31) / 32) * sizeof(uint32_t));
+        rowlen = take((size_t)W * (n - 1) * sizeof(int));
         raw = take((size_t)raw_cap * 8);
         tmp = take((size_t)raw_cap * 8);   // directly after raw: the sort's twin buffer
         dense = take((size_t)raw_cap * 8);
@@ -1068,7 +1083,8 @@ static bool served_admit(Served *S, Request *r)
     if (S->free_slots.empty())
         return false;
     std::lock_guard<std::recursive_mutex> hg(h->mu);
-    const ChunkTable &ct = h->chunks(r->l, r->d, h->chunk_work_for(r->n, r->m, r->l, r->d));
+    const int cw = h->chunk_work_for(r->n, r->m, r->l, r->d);
+    const ChunkTable &ct = h->chunks(r->l, r->d, cw > 0 ? cw : kDefaultChunkWork);
     if ((int)ct.tab.size() > Served::kCtabMax) {
         r->status = PMS_EINVAL;
         return true;
@@ -1104,12 +1120,13 @@ static bool served_admit(Served *S, Request *r)
     in.W = r->W;
     in.NW = (r->W + 31) / 32;
     in.cps = ct.cps;
-    in.grab = h->opt.grab > 0 ? h->opt.grab : default_grab(r->d);
+    in.grab = h->grab_for(r->n, r->m, r->l, r->d);
     in.prune_rows = h->prune_rows_for(r->n, r->m, r->l, r->d);
     in.seq_off = (long long)(off + L.seqs);
     in.plane_off = (long long)((off + L.planes) / sizeof(uint2));
     in.raw_off = (long long)((off + L.raw) / 8);
     in.compat_off = (long long)((off + L.compat) / 4);
+    in.rlen_off = (long long)((off + L.rowlen) / 4);
     in.ctab = (int)((off + L.ctab) / sizeof(int));
     in.raw_cap = r->raw_cap;
     int *hc = S->h_ctab + (size_t)r->slot * Served::kCtabMax;
@@ -1128,6 +1145,7 @@ static bool served_admit(Served *S, Request *r)
     const long long rows = (long long)r->W * (r->n - 1);
     if (rows > 0)
         launch_compat(S->d_inst + r->slot, 1, srv_zero(S), rows, (const uint2 *)S->pool, (uint32_t *)S->pool,
+                      (int *)S->pool,
                       (int)std::max<long long>(1, std::min<long long>((rows + 7) / 8, (long long)h->num_sms * 16)), st);
     r->state = 1;
     return true;
@@ -1257,6 +1275,7 @@ static void served_loop(Served *S)
                 mp.head = (unsigned long long *)dr;
                 mp.planes = (const uint2 *)S->pool;
                 mp.compat = (const uint32_t *)S->pool;
+                mp.rowlen = (const int *)S->pool;
                 mp.ctab = (const int *)S->pool;
                 mp.raw = (uint64_t *)S->pool;
                 mp.raw_count = srv_rawcnt(S);
@@ -1608,7 +1627,7 @@ int pms_autotune(pms_ctx *h, int n, int m, int l, int d, pms_tuning *out)
     if ((rc = autotune_class(h, n, m, l, d, t)))
         return rc;
     if (out)
-        *out = pms_tuning{t.chunk_work, t.prune_rows, t.ctas_per_sm, t.ms};
+        *out = pms_tuning{t.chunk_work, t.prune_rows, t.ctas_per_sm, t.grab, t.ms};
     return PMS_OK;
 }
 
@@ -1621,11 +1640,11 @@ int pms_save_tuning(const pms_ctx *h, const char *path)
     FILE *f = std::fopen(path, "w");
     if (!f)
         return hm->fail(PMS_EINVAL, "cannot write %s", path);
-    std::fprintf(f, "# l d n_bucket m_bucket chunk_work prune_rows ctas_per_sm ms\n");
+    std::fprintf(f, "# l d n_bucket m_bucket chunk_work prune_rows ctas_per_sm grab ms\n");
     for (const auto &kv : h->tuned)
-        std::fprintf(f, "%d %d %d %d %d %d %d %.6f\n", std::get<0>(kv.first), std::get<1>(kv.first),
+        std::fprintf(f, "%d %d %d %d %d %d %d %d %.6f\n", std::get<0>(kv.first), std::get<1>(kv.first),
                      std::get<2>(kv.first), std::get<3>(kv.first), kv.second.chunk_work, kv.second.prune_rows,
-                     kv.second.ctas_per_sm, kv.second.ms);
+                     kv.second.ctas_per_sm, kv.second.grab, kv.second.ms);
     std::fclose(f);
     return PMS_OK;
 }
@@ -1643,16 +1662,17 @@ int pms_load_tuning(pms_ctx *h, const char *path)
     while (std::fgets(line, sizeof line, f)) {
         if (line[0] == '#')
             continue;
-        int l, d, nb, mb, cw, pr, cta;
+        int l, d, nb, mb, cw, pr, cta, gr;
         double ms;
-        if (std::sscanf(line, "%d %d %d %d %d %d %d %lf", &l, &d, &nb, &mb, &cw, &pr, &cta, &ms) != 8)
+        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %lf", &l, &d, &nb, &mb, &cw, &pr, &cta, &gr, &ms) != 9)
             continue;
-        if (l < 1 || l > PMS_LMAX || d < 0 || d >= l || cw < 0 || pr < 0 || cta < 0)
+        if (l < 1 || l > PMS_LMAX || d < 0 || d >= l || cw < 0 || pr < 0 || cta < 0 || gr < 0)
             continue;
         pms_ctx::Tuning t;
         t.chunk_work = cw;
         t.prune_rows = pr;
         t.ctas_per_sm = cta;
+        t.grab = gr;
         t.ms = ms;
         h->tuned[std::make_tuple(l, d, nb, mb)] = t;
         ++loaded;
@@ -1739,7 +1759,7 @@ void pms_destroy(pms_ctx *h)
     served_stop(h);
     if (h->stream)
         cudaStreamSynchronize(h->stream);
-    pms_ctx::DBuf *bufs[] = {&h->d_seqs, &h->d_planes, &h->d_raw, &h->d_tmp, &h->d_compat, &h->d_meta, &h->d_ctr, &h->d_scratch, &h->d_result};
+    pms_ctx::DBuf *bufs[] = {&h->d_seqs, &h->d_planes, &h->d_raw, &h->d_tmp, &h->d_compat, &h->d_rowlen, &h->d_meta, &h->d_ctr, &h->d_scratch, &h->d_result};
     for (auto *b : bufs)
         h->dev_free(b->p, b->cap);
     if (h->h_result)
@@ -1907,7 +1927,7 @@ extern "C" int pms_solve_device_noalloc(const uint8_t *d_seqs, int n, int m, int
     in.W = m - l + 1;
     in.NW = (in.W + 31) / 32;
     in.cps = cps;
-    in.grab = default_grab(d);
+    in.grab = 0;
     in.prune_rows = default_prune_rows(n, d);
     in.ctab = 0;
     in.seq_off = 0;
@@ -1933,6 +1953,7 @@ extern "C" int pms_solve_device_noalloc(const uint8_t *d_seqs, int n, int m, int
     const size_t o_ctr = take(cl.total);
     const size_t o_planes = take((size_t)n * in.W * sizeof(uint2));
     const size_t o_compat = take((size_t)in.W * (n - 1) * in.NW * sizeof(uint32_t));
+    const size_t o_rowlen = take((size_t)in.W * (n - 1) * sizeof(int));
     const size_t o_raw = take((size_t)kNoAllocRawCap * 8);
     const size_t o_tmp = take((size_t)kNoAllocRawCap * 8);
     // a multiple of 4 words keeps every CTA's slice 16-byte aligned (vector loads)
@@ -1965,7 +1986,8 @@ extern "C" int pms_solve_device_noalloc(const uint8_t *d_seqs, int n, int m, int
     if (rows > 0) {
         const int cw_blocks = (int)std::max<long long>(1, std::min<long long>((rows + 7) / 8, (long long)nd->num_sms * 16));
         if ((e = launch_compat(d_inst, 1, (const long long *)(base + o_meta + offsetof(Meta, row_prefix)), rows,
-                               (const uint2 *)(base + o_planes), (uint32_t *)(base + o_compat), cw_blocks, st)) !=
+                               (const uint2 *)(base + o_planes), (uint32_t *)(base + o_compat),
+                               (int *)(base + o_rowlen), cw_blocks, st)) !=
             cudaSuccess)
             return PMS_ECUDA;
     }
@@ -1977,6 +1999,7 @@ extern "C" int pms_solve_device_noalloc(const uint8_t *d_seqs, int n, int m, int
     mp.head = (unsigned long long *)(dc + cl.head);
     mp.planes = (const uint2 *)(base + o_planes);
     mp.compat = (const uint32_t *)(base + o_compat);
+    mp.rowlen = (const int *)(base + o_rowlen);
     mp.ctab = (const int *)(base + o_meta + offsetof(Meta, ctab));
     mp.raw = (uint64_t *)(base + o_raw);
     mp.raw_count = d_rawcnt;
