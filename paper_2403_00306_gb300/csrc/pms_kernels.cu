@@ -231,6 +231,105 @@ __device__ __forceinline__ void finish_list(const WarpCtx &c, uint32_t P, int N)
         emit<kCount>(c, list, N);
 }
 
+// The leaf walk of one node: every active lane tests the leaves of its
+// letter choices on the lowest positions of P, two per step (the odometer
+// state after one increment is computed alongside, so the two tests are
+// independent), against row 0 reduced by P; hits are appended to the warp's
+// list (which is checked against the other rows when it fills up). kReg > 0:
+// the reduced row (at most kReg entries, padded copies included) is held in
+// registers; kReg == 0: read from shared memory, or from the full row when the
+// reduction overflowed; kReg < 0: no rows (n = 1), every leaf is kept.
+template <bool kCount, int kReg>
+__device__ __forceinline__ int leaf_loop(const WarpCtx &c, uint32_t P, uint32_t Phi, uint32_t ch0, uint32_t cl0,
+                                         bool active, unsigned long long iters, int k0, int len0, int off0)
+{
+    const int d = c.in.d;
+    const bool sm0 = k0 <= kRbCap;
+    uint2 e[kReg > 0 ? kReg : 1];
+    if constexpr (kReg > 0) {
+#pragma unroll
+        for (int i = 0; i < kReg; ++i)
+            e[i] = c.ws->rb0[i < k0 ? i : k0 - 1];
+    }
+    uint2 *list = c.ws->list;
+    uint32_t Dh = 0u, Dl = Phi;
+    int listN = 0;
+    for (unsigned long long it = 0; it < iters; it += 2) {
+        const bool two = it + 1 < iters;
+        const uint32_t both = Dh & Dl;
+        const uint32_t open = Phi & ~both;
+        const uint32_t q = open & (0u - open);
+        const uint32_t below = Phi & (q - 1u);
+        const uint32_t Dh2 = (Dh & ~below) | q;
+        const uint32_t Dl2 = (Dl | below) ^ q;
+        const uint32_t ch_a = ch0 ^ Dh, cl_a = cl0 ^ Dl;
+        const uint32_t ch_b = ch0 ^ Dh2, cl_b = cl0 ^ Dl2;
+        bool hit_a = false, hit_b = false;
+        if (active) {
+            if constexpr (kReg < 0) {
+                hit_a = true;
+                hit_b = two;
+            } else if constexpr (kReg > 0) {
+                int a0 = 64, a1 = 64, b0m = 64, b1m = 64;
+#pragma unroll
+                for (int i = 0; i < kReg; i += 2) {
+                    a0 = min(a0, __popc((ch_a ^ e[i].x) | (cl_a ^ e[i].y)));
+                    b0m = min(b0m, __popc((ch_b ^ e[i].x) | (cl_b ^ e[i].y)));
+                    a1 = min(a1, __popc((ch_a ^ e[i + 1].x) | (cl_a ^ e[i + 1].y)));
+                    b1m = min(b1m, __popc((ch_b ^ e[i + 1].x) | (cl_b ^ e[i + 1].y)));
+                }
+                hit_a = min(a0, a1) <= d;
+                hit_b = two && min(b0m, b1m) <= d;
+            } else if (sm0) {
+                int a0 = 64, a1 = 64, b0m = 64, b1m = 64;
+                for (int i = 0; i < k0; i += 4) {
+                    const uint4 u = *reinterpret_cast<const uint4 *>(c.ws->rb0 + i);
+                    const uint4 v = *reinterpret_cast<const uint4 *>(c.ws->rb0 + i + 2);
+                    a0 = min(a0, __popc((ch_a ^ u.x) | (cl_a ^ u.y)));
+                    b0m = min(b0m, __popc((ch_b ^ u.x) | (cl_b ^ u.y)));
+                    a1 = min(a1, __popc((ch_a ^ u.z) | (cl_a ^ u.w)));
+                    b1m = min(b1m, __popc((ch_b ^ u.z) | (cl_b ^ u.w)));
+                    a0 = min(a0, __popc((ch_a ^ v.x) | (cl_a ^ v.y)));
+                    b0m = min(b0m, __popc((ch_b ^ v.x) | (cl_b ^ v.y)));
+                    a1 = min(a1, __popc((ch_a ^ v.z) | (cl_a ^ v.w)));
+                    b1m = min(b1m, __popc((ch_b ^ v.z) | (cl_b ^ v.w)));
+                }
+                hit_a = min(a0, a1) <= d;
+                hit_b = two && min(b0m, b1m) <= d;
+            } else {
+                hit_a = check_row(c.rows.HL + off0, len0, ch_a, cl_a, d);
+                hit_b = two && check_row(c.rows.HL + off0, len0, ch_b, cl_b, d);
+            }
+            if (kCount) {
+                c.cnt[kCntTested] += two ? 2 : 1;
+                c.cnt[kCntCmpVerify] += (unsigned long long)(two ? 2 : 1) * (kReg < 0 ? 0 : (sm0 ? k0 : len0));
+            }
+        }
+        const uint32_t bal_a = __ballot_sync(kFull, hit_a);
+        const uint32_t bal_b = __ballot_sync(kFull, hit_b);
+        if (bal_a | bal_b) {
+            if (hit_a)
+                list[listN + __popc(bal_a & c.lt)] = make_uint2(ch_a, cl_a);
+            listN += __popc(bal_a);
+            if (hit_b)
+                list[listN + __popc(bal_b & c.lt)] = make_uint2(ch_b, cl_b);
+            listN += __popc(bal_b);
+            if (listN > kListCap - 64) {
+                finish_list<kCount>(c, P, listN);
+                listN = 0;
+            }
+        }
+        // advance the odometer by two
+        const uint32_t both2 = Dh2 & Dl2;
+        const uint32_t open2 = Phi & ~both2;
+        const uint32_t q2 = open2 & (0u - open2);
+        const uint32_t below2 = Phi & (q2 - 1u);
+        Dh = (Dh2 & ~below2) | q2;
+        Dl = (Dl2 | below2) ^ q2;
+    }
+    return listN;
+}
+
 // The leaves of one tree node P (|P| = lev) that survived the row filter.
 // Lanes own the letter choices on the lowest min(lev, 3) positions of P (27
 // lanes at most); every lane walks the choices on the remaining positions
@@ -275,74 +374,15 @@ __device__ __forceinline__ void expand_subset(const WarpCtx &c, uint32_t P)
     const uint32_t ch0 = c.xh ^ DhLo, cl0 = c.xl ^ DlLo;
     const unsigned long long iters = c_pow3[lev - nlo];
 
-    const bool sm0 = k0 <= kRbCap;
-    uint2 *list = c.ws->list;
-    uint32_t Dh = 0u, Dl = Phi;
     int listN = 0;
-    // two leaves per lane per step: the odometer state after one increment is
-    // computed alongside, so the two distance tests are independent
-    for (unsigned long long it = 0; it < iters; it += 2) {
-        const bool two = it + 1 < iters;
-        const uint32_t both = Dh & Dl;
-        const uint32_t open = Phi & ~both;
-        const uint32_t q = open & (0u - open);
-        const uint32_t below = Phi & (q - 1u);
-        const uint32_t Dh2 = (Dh & ~below) | q;
-        const uint32_t Dl2 = (Dl | below) ^ q;
-        const uint32_t ch_a = ch0 ^ Dh, cl_a = cl0 ^ Dl;
-        const uint32_t ch_b = ch0 ^ Dh2, cl_b = cl0 ^ Dl2;
-        bool hit_a = false, hit_b = false;
-        if (active) {
-            if (nrows == 0) {
-                hit_a = true;
-                hit_b = two;
-            } else if (sm0) {
-                int a0 = 64, a1 = 64, b0m = 64, b1m = 64;
-                for (int e = 0; e < k0; e += 4) {
-                    const uint4 u = *reinterpret_cast<const uint4 *>(c.ws->rb0 + e);
-                    const uint4 v = *reinterpret_cast<const uint4 *>(c.ws->rb0 + e + 2);
-                    a0 = min(a0, __popc((ch_a ^ u.x) | (cl_a ^ u.y)));
-                    b0m = min(b0m, __popc((ch_b ^ u.x) | (cl_b ^ u.y)));
-                    a1 = min(a1, __popc((ch_a ^ u.z) | (cl_a ^ u.w)));
-                    b1m = min(b1m, __popc((ch_b ^ u.z) | (cl_b ^ u.w)));
-                    a0 = min(a0, __popc((ch_a ^ v.x) | (cl_a ^ v.y)));
-                    b0m = min(b0m, __popc((ch_b ^ v.x) | (cl_b ^ v.y)));
-                    a1 = min(a1, __popc((ch_a ^ v.z) | (cl_a ^ v.w)));
-                    b1m = min(b1m, __popc((ch_b ^ v.z) | (cl_b ^ v.w)));
-                }
-                hit_a = min(a0, a1) <= d;
-                hit_b = two && min(b0m, b1m) <= d;
-            } else {
-                hit_a = check_row(c.rows.HL + off0, len0, ch_a, cl_a, d);
-                hit_b = two && check_row(c.rows.HL + off0, len0, ch_b, cl_b, d);
-            }
-            if (kCount) {
-                c.cnt[kCntTested] += two ? 2 : 1;
-                c.cnt[kCntCmpVerify] += (unsigned long long)(two ? 2 : 1) * (sm0 ? k0 : len0);
-            }
-        }
-        const uint32_t bal_a = __ballot_sync(kFull, hit_a);
-        const uint32_t bal_b = __ballot_sync(kFull, hit_b);
-        if (bal_a | bal_b) {
-            if (hit_a)
-                list[listN + __popc(bal_a & c.lt)] = make_uint2(ch_a, cl_a);
-            listN += __popc(bal_a);
-            if (hit_b)
-                list[listN + __popc(bal_b & c.lt)] = make_uint2(ch_b, cl_b);
-            listN += __popc(bal_b);
-            if (listN > kListCap - 64) {
-                finish_list<kCount>(c, P, listN);
-                listN = 0;
-            }
-        }
-        // advance the odometer by two
-        const uint32_t both2 = Dh2 & Dl2;
-        const uint32_t open2 = Phi & ~both2;
-        const uint32_t q2 = open2 & (0u - open2);
-        const uint32_t below2 = Phi & (q2 - 1u);
-        Dh = (Dh2 & ~below2) | q2;
-        Dl = (Dl2 | below2) ^ q2;
-    }
+    if (nrows == 0)
+        listN = leaf_loop<kCount, -1>(c, P, Phi, ch0, cl0, active, iters, k0, len0, off0);
+    else if (k0 <= 4)
+        listN = leaf_loop<kCount, 4>(c, P, Phi, ch0, cl0, active, iters, k0, len0, off0);
+    else if (k0 <= 8)
+        listN = leaf_loop<kCount, 8>(c, P, Phi, ch0, cl0, active, iters, k0, len0, off0);
+    else
+        listN = leaf_loop<kCount, 0>(c, P, Phi, ch0, cl0, active, iters, k0, len0, off0);
     if (listN > 0)
         finish_list<kCount>(c, P, listN);
 }
