@@ -79,6 +79,13 @@ typedef struct {
                               kept in shared memory (0: as many as fit); larger
                               row sets are read from global memory */
     int autotune;          /* 1: tune each new instance class before solving it */
+    int seed_mode;         /* 0: every seed x of s_1 searches B(x, d) as a tree
+                              (Observation 3.1); 1: pair seeds (x in s_1, r in s_2,
+                              d_H(x, r) <= 2d) search B(x, d) & B(r, d)
+                              (Observation 3.3), except seeds with a pair
+                              closer than d + 1, which keep the tree form.
+                              Plain and batched solves; the served and
+                              allocation-free forms use 0. */
 } pms_options;
 
 /* A tuned schedule for one instance class (l, d, n rounded up to a power of

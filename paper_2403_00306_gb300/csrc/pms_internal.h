@@ -35,6 +35,9 @@ struct InstDev {
     long long raw_off;     // offset (uint64) of the raw motif buffer (and of its sort twin)
     long long compat_off;  // offset (uint32) of the W x (n-1) x NW compatibility masks
     long long rlen_off;    // offset (int) of the W x (n-1) row sizes (set bits of each mask row)
+    long long seed_off;    // offset of this instance's W seeds in the per-seed mode array
+    int cps_b;             // pair mode: queue items per seed (blocks of 64 windows of s_2)
+    int pad2;
     uint32_t raw_cap;      // capacity of the raw motif buffer (power of two)
     int pad;
 };
@@ -87,7 +90,12 @@ struct MainParams {
     int smem_rows_cap;            // row entries a seed may keep in shared memory (<= kRowSmemCap)
     unsigned long long *counters; // kCntNum entries (count mode)
     int *done;                    // per segment: finished items (served form), may be null
+    const uint8_t *mode;          // per seed: 0 = tree over B(x, d), 1 = pairs (x, r); null: all 0
 };
+
+// Seed modes of the pair form.
+constexpr uint8_t kModeTree = 0;
+constexpr uint8_t kModePair = 1;
 
 // Launch wrappers (pms_kernels.cu).
 cudaError_t launch_pack(const InstDev *inst, int ninst, const long long *win_prefix, long long total_windows,
@@ -95,6 +103,10 @@ cudaError_t launch_pack(const InstDev *inst, int ninst, const long long *win_pre
 cudaError_t launch_compat(const InstDev *inst, int ninst, const long long *row_prefix, long long total_rows,
                           const uint2 *planes, uint32_t *compat, int *rowlen, int blocks, cudaStream_t st);
 cudaError_t launch_main(const MainParams &p, int blocks, bool count_mode, cudaStream_t st);
+cudaError_t launch_pairs(const MainParams &p, int blocks, bool count_mode, cudaStream_t st);
+cudaError_t pairs_occupancy(int *blocks_per_sm, bool count_mode);
+cudaError_t launch_classify(const InstDev *inst, int ninst, const long long *seed_prefix, long long total_seeds,
+                            const uint2 *planes, const uint32_t *compat, uint8_t *mode, int blocks, cudaStream_t st);
 cudaError_t main_occupancy(int *blocks_per_sm, bool count_mode);
 size_t main_smem_bytes();
 cudaError_t launch_sort_unique(const InstDev *inst, const int *inst_list, int nlist, uint64_t *raw, uint64_t *tmp,

@@ -595,6 +595,10 @@ __global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
             break;
         const int I = cs.inst, seed = cs.seed, chunk = cs.chunk;
         const InstDev in = p.inst[I];
+        if (p.mode && p.mode[in.seed_off + seed] != kModeTree) {
+            __syncthreads();   // this seed is searched by the pair kernel
+            continue;
+        }
         const bool rebuild = (I != cs.cached_inst) || (seed != cs.cached_seed);
         if (rebuild) {
             build_rows(p, in, seed, cs, smem_D, smem_HL, glob_D, glob_HL, warp, lane, kCount ? cnt : nullptr);
@@ -673,6 +677,499 @@ __global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
             if (lane == 0 && v)
                 atomicAdd(&p.counters[i], v);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pair form (Observation 3.3 with q = n): a motif is within d of an l-mer x
+// of s_1 and of an l-mer r of s_2, so it lies in B(x, d) & B(r, d), and
+// d_H(x, r) <= 2d (the s_2 row of x's compatibility masks). Let D = d_H(x, r),
+// Delta the positions where x and r differ. A string c of the intersection
+// changes a of the l - D agreeing positions (3 letters each), gives t of the
+// differing positions a third letter (2 each), keeps x's letter on e_x of the
+// others and takes r's on the rest, with a + t + (D - t - e_x) <= d and
+// a + t + e_x <= d. Such c can only be within d of a window w if
+// popc(mism(x, w) & mism(r, w)) <= min(2d, 3d - D): c agrees with x or r
+// everywhere except on at most min(d, 2d - D) positions.
+
+// Pair bound for one row entry w (D_w = mism(x, w) is stored with the entry).
+__device__ __forceinline__ bool pair_ok(uint32_t Dw, uint2 w, uint2 r, int bound)
+{
+    return __popc(Dw & ((r.x ^ w.x) | (r.y ^ w.y))) <= bound;
+}
+
+__device__ __forceinline__ bool row_has_pair(const uint32_t *D, const uint2 *HL, int len, uint2 r, int bound, int lane)
+{
+    for (int e0 = 0; e0 < len; e0 += 32) {
+        const int e = e0 + lane;
+        const bool q = e < len && pair_ok(D[e], HL[e], r, bound);
+        if (__any_sync(kFull, q))
+            return true;
+    }
+    return false;
+}
+
+// Row entries meeting the pair bound, into rb (padded to 4); returns how many.
+__device__ __forceinline__ int reduce_row_pair(const uint32_t *D, const uint2 *HL, int len, uint2 r, int bound,
+                                               uint2 *rb, int lane, uint32_t lt)
+{
+    int k = 0;
+    for (int e0 = 0; e0 < len; e0 += 32) {
+        const int e = e0 + lane;
+        uint2 w = make_uint2(0u, 0u);
+        bool keep = false;
+        if (e < len) {
+            w = HL[e];
+            keep = pair_ok(D[e], w, r, bound);
+        }
+        const uint32_t bal = __ballot_sync(kFull, keep);
+        if (keep) {
+            const int pos = k + __popc(bal & lt);
+            if (pos < kRbCap)
+                rb[pos] = w;
+        }
+        k += __popc(bal);
+    }
+    __syncwarp();
+    if (k > 0 && k <= kRbCap && lane < 4)
+        rb[k + lane] = rb[k - 1];
+    __syncwarp();
+    return k;
+}
+
+struct PairCtx {
+    uint2 r;          // planes of the s_2 window
+    int bound;        // pair bound
+    int row0;         // sequence of the first verified row (smallest of s_3..s_n)
+};
+
+// Candidates of one pair that passed row 0: checked against the other rows
+// (s_3..s_n without row 0, each reduced by the pair bound), then emitted.
+template <bool kCount>
+__device__ __forceinline__ void finish_list_pair(const WarpCtx &c, const PairCtx &pc, int N)
+{
+    const InstDev &in = c.in;
+    const int nrows = in.n - 1;
+    uint2 *list = c.ws->list;
+    __syncwarp();
+    for (int rr = 0; rr < nrows && N > 0; ++rr) {
+        const int ri = c.cs->row_order[rr];
+        if (ri == 1 || ri == pc.row0)
+            continue;
+        const int len = c.cs->row_len[ri];
+        const int off = c.cs->row_off[ri];
+        const int k = reduce_row_pair(c.rows.D + off, c.rows.HL + off, len, pc.r, pc.bound, c.ws->rb1, c.lane, c.lt);
+        if (kCount && c.lane == 0)
+            c.cnt[kCntCmpReduce] += len;
+        if (k == 0) {
+            N = 0;
+            break;
+        }
+        const bool sm = k <= kRbCap;
+        int newN = 0;
+        for (int b = 0; b < N; b += 32) {
+            const int idx = b + c.lane;
+            const bool alive = idx < N;
+            uint2 v = make_uint2(0u, 0u);
+            if (alive)
+                v = list[idx];
+            bool hit = false;
+            if (alive) {
+                hit = sm ? check_smem(c.ws->rb1, k, v.x, v.y, in.d) : check_row(c.rows.HL + off, len, v.x, v.y, in.d);
+                if (kCount)
+                    c.cnt[kCntCmpVerify] += sm ? k : len;
+            }
+            __syncwarp();
+            const uint32_t bal = __ballot_sync(kFull, hit);
+            if (hit)
+                list[newN + __popc(bal & c.lt)] = v;
+            newN += __popc(bal);
+        }
+        __syncwarp();
+        N = newN;
+    }
+    if (N > 0)
+        emit<kCount>(c, list, N);
+}
+
+// Deposit table of the differing positions: lut[16 k + v] = the positions of
+// Delta numbered 4k..4k+3 selected by the 4 bits of v.
+__device__ __forceinline__ void build_deposit_lut(uint32_t Delta, uint32_t *lut, int lane)
+{
+    for (int e = lane; e < 128; e += 32) {
+        const int k = e >> 4, v = e & 15;
+        uint32_t m = Delta;
+        for (int s = 0; s < 4 * k; ++s)
+            m &= m - 1u;
+        uint32_t dep = 0;
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t low = m & (0u - m);
+            if ((v >> j) & 1)
+                dep |= low;
+            m ^= low;
+        }
+        lut[e] = dep;
+    }
+    __syncwarp();
+}
+
+// Maps a mask over the numbered differing positions to the positions themselves.
+__device__ __forceinline__ uint32_t deposit_delta(uint32_t c, const uint32_t *lut, int nibbles)
+{
+    uint32_t r = 0;
+    for (int k = 0; k < nibbles; ++k)
+        r |= lut[k * 16 + ((c >> (4 * k)) & 15u)];
+    return r;
+}
+
+// Inserts a 0 bit at every set position of Tc (ascending), i.e. maps a mask
+// over the differing positions outside T onto the numbering of all of them.
+__device__ __forceinline__ uint32_t skip_positions(uint32_t c, uint32_t Tc)
+{
+    while (Tc) {
+        const uint32_t low = Tc & (0u - Tc);
+        const uint32_t below = low - 1u;
+        c = ((c & ~below) << 1) | (c & below);
+        Tc ^= low;
+    }
+    return c;
+}
+
+// Next k-subset in colex order (next larger integer with the same popcount).
+__device__ __forceinline__ uint32_t next_combination(uint32_t v)
+{
+    const uint32_t u = v & (0u - v);
+    const uint32_t w = v + u;
+    return w | (((w ^ v) >> 2) >> (__ffs(v) - 1));
+}
+
+// All leaves of one pair: classes (a, t, e_x) in a warp-uniform loop; inside a
+// class the choices on agreeing positions, the third-letter set T and its
+// letters are warp-uniform too, and lanes own contiguous ranges of the e_x
+// subsets (unranked once, then stepped in colex order).
+template <bool kCount, int kReg>
+__device__ __forceinline__ void pair_leaves(const WarpCtx &c, const PairCtx &pc, uint32_t Delta, uint32_t Agree, int D,
+                                            int k0, int len0, int off0, const uint32_t (*binom)[kLMax + 1])
+{
+    const InstDev &in = c.in;
+    const int d = in.d, l = in.l;
+    const bool no_rows = in.n <= 2;
+    const uint32_t GH = c.xh ^ pc.r.x, GL = c.xl ^ pc.r.y;   // per position XOR code of x and r
+    uint32_t *lut = c.ws->subs;
+    build_deposit_lut(Delta, lut, c.lane);
+    const int nib = (D + 3) >> 2;
+    uint2 e[kReg > 0 ? kReg : 1];
+    if constexpr (kReg > 0) {
+#pragma unroll
+        for (int i = 0; i < kReg; ++i)
+            e[i] = c.ws->rb0[i < k0 ? i : k0 - 1];
+    }
+    const bool sm0 = k0 <= kRbCap;
+    uint2 *list = c.ws->list;
+    int listN = 0;
+    const int nAg = l - D;
+    for (int a = 0; a <= min(d, nAg); ++a) {
+        for (int t = 0; t <= min(D, d - a); ++t) {
+            for (int ex = 0; ex <= D - t; ++ex) {
+                const int er = D - t - ex;
+                if (a + t + er > d || a + t + ex > d)
+                    continue;
+                const uint32_t nA = binom[nAg][a], nT = binom[D][t], nE = binom[D - t][ex];
+                const uint32_t per = (nE + 31) / 32;              // e_x subsets per lane
+                const uint32_t lo = min(nE, c.lane * per), hi = min(nE, lo + per);
+                // first e_x subset of this lane (numbered over the D - t positions outside T)
+                const uint32_t e_first = lo < hi ? unrank_subset(lo, ex, D - t, binom) : 0u;
+                uint32_t Pa = a ? ((1u << a) - 1u) : 0u;           // compact a-subset of the agreeing positions
+                for (uint32_t iA = 0; iA < nA; ++iA) {
+                    // deposit Pa onto the agreeing positions
+                    uint32_t PaM = 0, m = Agree, q = Pa;
+                    while (q) {
+                        const uint32_t low = m & (0u - m);
+                        if (q & 1u)
+                            PaM |= low;
+                        m ^= low;
+                        q >>= 1;
+                    }
+                    // odometer over the letters of the a changed agreeing positions
+                    uint32_t DhA = 0u, DlA = PaM;
+                    const unsigned long long nsub = c_pow3[a];
+                    for (unsigned long long sub = 0; sub < nsub; ++sub) {
+                        uint32_t Tc = t ? ((1u << t) - 1u) : 0u;   // compact t-subset of the differing positions
+                        for (uint32_t iT = 0; iT < nT; ++iT) {
+                            const uint32_t TM = deposit_delta(Tc, lut, nib);
+                            const uint32_t R = Delta & ~TM;
+                            for (uint32_t wbits = 0; wbits < (1u << t); ++wbits) {
+                                // third letters on T: choice bits spread over T's positions
+                                uint32_t Wm = 0, mt = TM, wb = wbits;
+                                while (wb) {
+                                    const uint32_t low = mt & (0u - mt);
+                                    if (wb & 1u)
+                                        Wm |= low;
+                                    mt ^= low;
+                                    wb >>= 1;
+                                }
+                                const uint32_t dHT = (Wm | (GL & ~GH)) & TM;
+                                const uint32_t dLT = ((GH & ~GL) | (Wm ^ (GH & GL))) & TM;
+                                const uint32_t bh = c.xh ^ DhA ^ dHT ^ (GH & R);
+                                const uint32_t bl = c.xl ^ DlA ^ dLT ^ (GL & R);
+                                uint32_t ec = e_first;
+                                for (uint32_t i0 = 0; i0 < per; ++i0) {
+                                    const bool act = lo + i0 < hi;
+                                    const uint32_t Ex = act ? deposit_delta(skip_positions(ec, Tc), lut, nib) : 0u;
+                                    const uint32_t ch = bh ^ (GH & Ex), cl = bl ^ (GL & Ex);
+                                    bool hit = false;
+                                    if (act) {
+                                        if (no_rows) {
+                                            hit = true;
+                                        } else if constexpr (kReg > 0) {
+                                            int m0 = 64, m1 = 64;
+#pragma unroll
+                                            for (int i = 0; i < kReg; i += 2) {
+                                                m0 = min(m0, __popc((ch ^ e[i].x) | (cl ^ e[i].y)));
+                                                m1 = min(m1, __popc((ch ^ e[i + 1].x) | (cl ^ e[i + 1].y)));
+                                            }
+                                            hit = min(m0, m1) <= d;
+                                        } else {
+                                            hit = sm0 ? check_smem(c.ws->rb0, k0, ch, cl, d)
+                                                      : check_row(c.rows.HL + off0, len0, ch, cl, d);
+                                        }
+                                        if (kCount) {
+                                            c.cnt[kCntTested] += 1;
+                                            c.cnt[kCntCmpVerify] += no_rows ? 0 : (sm0 ? k0 : len0);
+                                        }
+                                        if (ex > 0 && lo + i0 + 1 < hi)
+                                            ec = next_combination(ec);
+                                    }
+                                    const uint32_t bal = __ballot_sync(kFull, hit);
+                                    if (bal) {
+                                        if (hit)
+                                            list[listN + __popc(bal & c.lt)] = make_uint2(ch, cl);
+                                        listN += __popc(bal);
+                                        if (listN > kListCap - 32) {
+                                            finish_list_pair<kCount>(c, pc, listN);
+                                            listN = 0;
+                                        }
+                                    }
+                                }
+                            }
+                            if (t > 0 && iT + 1 < nT)
+                                Tc = next_combination(Tc);
+                        }
+                        // odometer step over PaM (as in the tree form)
+                        const uint32_t both = DhA & DlA;
+                        const uint32_t open = PaM & ~both;
+                        const uint32_t qq = open & (0u - open);
+                        const uint32_t below = PaM & (qq - 1u);
+                        DhA = (DhA & ~below) | qq;
+                        DlA = (DlA | below) ^ qq;
+                    }
+                    if (a > 0 && iA + 1 < nA)
+                        Pa = next_combination(Pa);
+                }
+            }
+        }
+    }
+    if (listN > 0)
+        finish_list_pair<kCount>(c, pc, listN);
+}
+
+template <bool kCount>
+__device__ __forceinline__ void process_pair(const WarpCtx &c, uint2 r, const uint32_t (*binom)[kLMax + 1])
+{
+    const InstDev &in = c.in;
+    const int d = in.d, l = in.l;
+    const uint32_t lmask = l == 32 ? 0xffffffffu : ((1u << l) - 1u);
+    const uint32_t Delta = ((c.xh ^ r.x) | (c.xl ^ r.y)) & lmask;
+    const int D = __popc(Delta);
+    const uint32_t Agree = lmask & ~Delta;
+    PairCtx pc{r, min(2 * d, 3 * d - D), 0};
+    if (kCount && c.lane == 0)
+        c.cnt[kCntSubsets] += 1;
+    // every row s_3..s_n must hold an occurrence meeting the pair bound
+    const int nrows = in.n - 1;
+    int r0 = 0;
+    for (int rr = 0; rr < nrows; ++rr) {
+        const int ri = c.cs->row_order[rr];
+        if (ri == 1)
+            continue;
+        if (r0 == 0)
+            r0 = ri;
+        const int off = c.cs->row_off[ri];
+        const bool ok = row_has_pair(c.rows.D + off, c.rows.HL + off, c.cs->row_len[ri], r, pc.bound, c.lane);
+        if (kCount && c.lane == 0)
+            c.cnt[kCntCmpReduce] += c.cs->row_len[ri];
+        if (!ok) {
+            if (kCount && c.lane == 0)
+                c.cnt[kCntPruned] += 1;
+            return;
+        }
+    }
+    pc.row0 = r0;
+    int k0 = 0, len0 = 0, off0 = 0;
+    if (r0) {
+        len0 = c.cs->row_len[r0];
+        off0 = c.cs->row_off[r0];
+        k0 = reduce_row_pair(c.rows.D + off0, c.rows.HL + off0, len0, r, pc.bound, c.ws->rb0, c.lane, c.lt);
+        if (k0 == 0)
+            return;
+    }
+    if (!r0 || k0 > 8)
+        pair_leaves<kCount, 0>(c, pc, Delta, Agree, D, k0, len0, off0, binom);
+    else if (k0 <= 4)
+        pair_leaves<kCount, 4>(c, pc, Delta, Agree, D, k0, len0, off0, binom);
+    else
+        pair_leaves<kCount, 8>(c, pc, Delta, Agree, D, k0, len0, off0, binom);
+}
+
+// Pair-form kernel: queue items are (instance, seed x, block of 64 windows of
+// s_2); the CTA gathers x's feasible occurrences, its warps take the pairs
+// (x, r) of the block (r within 2d of x) one at a time. Seeds whose mode is
+// not kModePair are left to the tree kernel.
+template <bool kCount>
+__global__ void __launch_bounds__(kThreads, 2) pair_kernel(MainParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpSmem *wsm = reinterpret_cast<WarpSmem *>(smem_raw);
+    uint32_t *smem_D = reinterpret_cast<uint32_t *>(smem_raw + kWarps * sizeof(WarpSmem));
+    uint2 *smem_HL = reinterpret_cast<uint2 *>(smem_raw + kWarps * sizeof(WarpSmem) + kRowSmemCap * sizeof(uint32_t));
+    CtaSmem &cs = *reinterpret_cast<CtaSmem *>(smem_raw + kWarps * sizeof(WarpSmem) +
+                                               kRowSmemCap * (sizeof(uint32_t) + sizeof(uint2)));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t *glob_D = p.scratch + (size_t)blockIdx.x * 3 * (size_t)p.rows_cap;
+    uint2 *glob_HL = reinterpret_cast<uint2 *>(glob_D + p.rows_cap);
+    unsigned long long cnt[kCount ? kCntNum : 1];
+#pragma unroll
+    for (int i = 0; i < (kCount ? kCntNum : 1); ++i)
+        cnt[i] = 0;
+    if (threadIdx.x == 0) {
+        cs.cached_inst = -1;
+        cs.cached_seed = -1;
+        cs.feasible = 0;
+    }
+    for (int i = threadIdx.x; i < (kLMax + 1) * (kLMax + 1); i += blockDim.x)
+        (&cs.binom[0][0])[i] = (&c_binom[0][0])[i];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned long long g = atomicAdd(p.head, 1ull);
+            cs.g = g;
+            if (g < (unsigned long long)p.total) {
+                int lo = 0, hi = p.nseg - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (p.seg[mid].work_lo <= (long long)g)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                const Segment s = p.seg[lo];
+                const int cidx = s.chunk_lo + (int)((long long)g - s.work_lo);
+                const int cps = p.inst[s.inst].cps_b;
+                cs.inst = s.inst;
+                cs.seed = cidx / cps;
+                cs.chunk = cidx % cps;
+            }
+        }
+        __syncthreads();
+        if (cs.g >= (unsigned long long)p.total)
+            break;
+        const int I = cs.inst, seed = cs.seed, chunk = cs.chunk;
+        const InstDev in = p.inst[I];
+        if (!p.mode || p.mode[in.seed_off + seed] != kModePair) {
+            __syncthreads();
+            continue;
+        }
+        const bool rebuild = (I != cs.cached_inst) || (seed != cs.cached_seed);
+        if (rebuild) {
+            build_rows(p, in, seed, cs, smem_D, smem_HL, glob_D, glob_HL, warp, lane, kCount ? cnt : nullptr);
+            if (threadIdx.x == 0) {
+                cs.cached_inst = I;
+                cs.cached_seed = seed;
+            }
+        }
+        if (threadIdx.x == 0)
+            cs.next = 0;
+        __syncthreads();
+        if (cs.feasible) {
+            const uint2 *pl = p.planes + in.plane_off;
+            const uint2 x = pl[seed];
+            Rows rows{cs.rows_in_smem ? smem_D : glob_D, cs.rows_in_smem ? smem_HL : glob_HL};
+            WarpCtx c{&p, in, I, lane, lt, x.x, x.y, rows, &cs, &wsm[warp], kCount ? cnt : nullptr};
+            // the pairs of this block: set bits of x's s_2 mask words 2 chunk, 2 chunk + 1
+            const uint32_t *mrow = p.compat + in.compat_off + (size_t)seed * (in.n - 1) * in.NW;
+            const int w0 = 2 * chunk;
+            const uint32_t m0 = w0 < in.NW ? mrow[w0] : 0u;
+            const uint32_t m1 = w0 + 1 < in.NW ? mrow[w0 + 1] : 0u;
+            const int npairs = __popc(m0) + __popc(m1);
+            for (;;) {
+                int q = 0;
+                if (lane == 0)
+                    q = atomicAdd(&cs.next, 1);
+                q = __shfl_sync(kFull, q, 0);
+                if (q >= npairs)
+                    break;
+                // q-th set bit of (m0, m1)
+                int bit;
+                if (q < __popc(m0)) {
+                    bit = __fns(m0, 0, q + 1);
+                } else {
+                    bit = 32 + __fns(m1, 0, q - __popc(m0) + 1);
+                }
+                const int rw = 64 * chunk + bit;
+                process_pair<kCount>(c, pl[(size_t)in.W + rw], cs.binom);
+            }
+        }
+        __syncthreads();
+    }
+    if constexpr (kCount) {
+#pragma unroll
+        for (int i = 0; i < kCntNum; ++i) {
+            unsigned long long v = cnt[i];
+            for (int o = 16; o > 0; o >>= 1)
+                v += __shfl_xor_sync(kFull, v, o);
+            if (lane == 0 && v)
+                atomicAdd(&p.counters[i], v);
+        }
+    }
+}
+
+// Seed modes: a seed uses the pair form unless one of its pairs is closer
+// than d + 1 (then the intersection B(x, d) & B(r, d) is large and dominated
+// by changes on agreeing positions, which the tree form covers better).
+__global__ void classify_kernel(const InstDev *__restrict__ inst, int ninst, const long long *__restrict__ seed_prefix,
+                                long long total_seeds, const uint2 *__restrict__ planes,
+                                const uint32_t *__restrict__ compat, uint8_t *__restrict__ mode)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long q = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < total_seeds; q += warps) {
+        int lo = 0, hi = ninst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (seed_prefix[mid] <= q)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const InstDev in = inst[lo];
+        const int j = (int)(q - seed_prefix[lo]);
+        bool close = in.n < 2;
+        if (!close) {
+            const uint2 *pl = planes + in.plane_off;
+            const uint2 x = pl[j];
+            const uint32_t *mrow = compat + in.compat_off + (size_t)j * (in.n - 1) * in.NW;
+            for (int w0 = 0; w0 < in.W && !close; w0 += 32) {
+                const int w = w0 + lane;
+                bool c = false;
+                if (w < in.W && ((mrow[w >> 5] >> (w & 31)) & 1u)) {
+                    const uint2 r = pl[(size_t)in.W + w];
+                    c = __popc((x.x ^ r.x) | (x.y ^ r.y)) <= in.d;
+                }
+                close = __any_sync(kFull, c);
+            }
+        }
+        if (lane == 0)
+            mode[in.seed_off + j] = close ? kModeTree : kModePair;
     }
 }
 
@@ -1025,6 +1522,39 @@ cudaError_t launch_compat(const InstDev *inst, int ninst, const long long *row_p
                           const uint2 *planes, uint32_t *compat, int *rowlen, int blocks, cudaStream_t st)
 {
     compat_kernel<<<blocks, 256, 0, st>>>(inst, ninst, row_prefix, total_rows, planes, compat, rowlen);
+    return cudaGetLastError();
+}
+
+cudaError_t pairs_occupancy(int *blocks_per_sm, bool count_mode)
+{
+    const size_t smem = main_smem_bytes();
+    cudaError_t e;
+    if (count_mode) {
+        e = cudaFuncSetAttribute(pair_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pair_kernel<true>, kThreads, smem);
+    }
+    e = cudaFuncSetAttribute(pair_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pair_kernel<false>, kThreads, smem);
+}
+
+cudaError_t launch_pairs(const MainParams &p, int blocks, bool count_mode, cudaStream_t st)
+{
+    const size_t smem = main_smem_bytes();
+    if (count_mode)
+        pair_kernel<true><<<blocks, kThreads, smem, st>>>(p);
+    else
+        pair_kernel<false><<<blocks, kThreads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classify(const InstDev *inst, int ninst, const long long *seed_prefix, long long total_seeds,
+                            const uint2 *planes, const uint32_t *compat, uint8_t *mode, int blocks, cudaStream_t st)
+{
+    classify_kernel<<<blocks, 256, 0, st>>>(inst, ninst, seed_prefix, total_seeds, planes, compat, mode);
     return cudaGetLastError();
 }
 

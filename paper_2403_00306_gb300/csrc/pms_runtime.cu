@@ -127,6 +127,7 @@ struct pms_ctx {
     pms_options opt{};
     int num_sms = 0;
     int occ[2] = {0, 0};   // CTAs per SM of the verification kernel (plain, count mode)
+    int occ_pair[2] = {0, 0};  // same for the pair-form kernel
     pms_stats stats{};
     std::map<std::tuple<int, int, int>, ChunkTable> ctab_cache;
 
@@ -134,7 +135,7 @@ struct pms_ctx {
         void *p = nullptr;
         size_t cap = 0;
     };
-    DBuf d_seqs, d_planes, d_raw, d_tmp, d_compat, d_rowlen, d_meta, d_ctr, d_scratch, d_result;
+    DBuf d_seqs, d_planes, d_raw, d_tmp, d_compat, d_rowlen, d_mode, d_meta, d_ctr, d_scratch, d_result;
     void *h_result = nullptr;   // pinned
     size_t h_result_cap = 0;
     void *h_meta = nullptr;     // pinned staging for descriptors and inputs
@@ -332,6 +333,11 @@ struct Plan {
     std::vector<Segment> seg;
     std::vector<long long> win_prefix;
     std::vector<long long> row_prefix;   // compatibility rows: sum of W * (n - 1)
+    std::vector<long long> seed_prefix;  // seeds: sum of W
+    std::vector<Segment> seg_pair;       // pair-form queue (blocks of 64 windows of s_2 per seed)
+    long long total_pair_items = 0;
+    long long total_seeds = 0;
+    bool pair_mode = false;
     std::vector<int> ctab;
     long long total_items = 0;
     long long total_windows = 0;
@@ -343,7 +349,7 @@ struct Plan {
 
 // Byte layout of the descriptor block (device d_meta, pinned h_meta).
 struct MetaLayout {
-    size_t inst, seg, win, rowp, ctab, total;
+    size_t inst, seg, win, rowp, seedp, segp, ctab, total;
     MetaLayout(const Plan &p)
     {
         size_t o = 0;
@@ -355,6 +361,10 @@ struct MetaLayout {
         o = round_up(o + p.win_prefix.size() * sizeof(long long), 16);
         rowp = o;
         o = round_up(o + p.row_prefix.size() * sizeof(long long), 16);
+        seedp = o;
+        o = round_up(o + p.seed_prefix.size() * sizeof(long long), 16);
+        segp = o;
+        o = round_up(o + p.seg_pair.size() * sizeof(Segment), 16);
         ctab = o;
         o = round_up(o + p.ctab.size() * sizeof(int), 16);
         total = o;
@@ -363,11 +373,12 @@ struct MetaLayout {
 
 // Counters block (d_ctr): head, work counters, dense_total, then per instance raw_count and flags.
 struct CtrLayout {
-    size_t head, work, dense_total, raw_count, flags, total;
+    size_t head, head_pair, work, dense_total, raw_count, flags, total;
     CtrLayout(size_t k)
     {
         head = 0;
-        work = 8;
+        head_pair = 8;
+        work = 16;
         dense_total = work + kCntNum * 8;
         raw_count = round_up(dense_total + 4, 16);
         flags = round_up(raw_count + 4 * k, 16);
@@ -455,6 +466,12 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
         P.total_windows += (long long)s.n * in.W;
         P.row_prefix.push_back(P.total_rows);
         P.total_rows += (long long)in.W * (s.n - 1);
+        in.seed_off = P.total_seeds;
+        P.seed_prefix.push_back(P.total_seeds);
+        P.total_seeds += in.W;
+        in.cps_b = (in.W + 63) / 64;
+        P.seg_pair.push_back(Segment{P.total_pair_items, (int)k, 0, in.W * in.cps_b, 0});
+        P.total_pair_items += (long long)in.W * in.cps_b;
         P.rows_cap = std::max(P.rows_cap, (int)round_up((size_t)(s.n - 1) * (in.W + 3), 4));
         const int chunks = in.W * in.cps;
         P.seg.push_back(Segment{work, (int)k, 0, chunks, 0});
@@ -463,6 +480,7 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
         P.inst.push_back(in);
     }
     P.total_items = work;
+    P.pair_mode = h->opt.seed_mode == 1;
     return P;
 }
 
@@ -479,7 +497,7 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     if ((rc = h->ensure(h->d_meta, ml.total)) || (rc = h->ensure(h->d_ctr, cl.total)) ||
         (rc = h->ensure(h->d_planes, P.planes * sizeof(uint2))) || (rc = h->ensure(h->d_raw, P.raw * 8)) ||
         (rc = h->ensure(h->d_tmp, P.raw * 8)) || (rc = h->ensure(h->d_compat, P.compat * 4)) ||
-        (rc = h->ensure(h->d_rowlen, P.rowlen * 4)))
+        (rc = h->ensure(h->d_rowlen, P.rowlen * 4)) || (rc = h->ensure(h->d_mode, (size_t)P.total_seeds)))
         return rc;
     int occ = h->occ[count_mode ? 1 : 0];
     if (h->opt.ctas_per_sm > 0) {
@@ -503,6 +521,8 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     std::memcpy(hm + ml.seg, P.seg.data(), P.seg.size() * sizeof(Segment));
     std::memcpy(hm + ml.win, P.win_prefix.data(), P.win_prefix.size() * sizeof(long long));
     std::memcpy(hm + ml.rowp, P.row_prefix.data(), P.row_prefix.size() * sizeof(long long));
+    std::memcpy(hm + ml.seedp, P.seed_prefix.data(), P.seed_prefix.size() * sizeof(long long));
+    std::memcpy(hm + ml.segp, P.seg_pair.data(), P.seg_pair.size() * sizeof(Segment));
     std::memcpy(hm + ml.ctab, P.ctab.data(), P.ctab.size() * sizeof(int));
     cudaStream_t st = h->stream;
     char *dm = (char *)h->d_meta.p;
@@ -528,7 +548,15 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
             cudaSuccess)
             return h->cuda_fail(e, "compatibility kernel");
     }
+    if (P.pair_mode && P.total_seeds > 0) {
+        const int cb = (int)std::min<long long>((P.total_seeds + 7) / 8, (long long)h->num_sms * 16);
+        if ((e = launch_classify(d_inst, (int)k, (const long long *)(dm + ml.seedp), P.total_seeds,
+                                 (const uint2 *)h->d_planes.p, (const uint32_t *)h->d_compat.p, (uint8_t *)h->d_mode.p,
+                                 std::max(cb, 1), st)) != cudaSuccess)
+            return h->cuda_fail(e, "classify kernel");
+    }
     MainParams mp{};
+    mp.mode = P.pair_mode ? (const uint8_t *)h->d_mode.p : nullptr;
     mp.inst = d_inst;
     mp.seg = (const Segment *)(dm + ml.seg);
     mp.nseg = (int)P.seg.size();
@@ -548,6 +576,20 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     cudaEventRecord(h->evm0, st);
     if (P.total_items > 0 && (e = launch_main(mp, blocks, count_mode, st)) != cudaSuccess)
         return h->cuda_fail(e, "verification kernel");
+    if (P.pair_mode && P.total_pair_items > 0) {
+        MainParams pp = mp;
+        pp.seg = (const Segment *)(dm + ml.segp);
+        pp.nseg = (int)P.seg_pair.size();
+        pp.total = P.total_pair_items;
+        pp.head = (unsigned long long *)(dc + cl.head_pair);
+        int occp = std::max(1, h->occ_pair[count_mode ? 1 : 0]);
+        const int pblocks = (int)std::min<long long>((long long)h->num_sms * occp, P.total_pair_items);
+        if (pblocks > blocks && (rc = h->ensure(h->d_scratch, (size_t)pblocks * 3 * (size_t)P.rows_cap * 4)))
+            return rc;
+        pp.scratch = (uint32_t *)h->d_scratch.p;
+        if ((e = launch_pairs(pp, pblocks, count_mode, st)) != cudaSuccess)
+            return h->cuda_fail(e, "pair kernel");
+    }
     cudaEventRecord(h->evm1, st);
     if ((e = launch_sort_unique(d_inst, nullptr, (int)k, (uint64_t *)h->d_raw.p, (uint64_t *)h->d_tmp.p, d_rawcnt,
                                 d_flags, status_out,
@@ -1380,6 +1422,8 @@ int pms_create(pms_ctx **out, int device, size_t mem_budget_bytes)
         (e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess ||
         (e = main_occupancy(&h->occ[0], false)) != cudaSuccess || (e = main_occupancy(&h->occ[1], true)) != cudaSuccess ||
+        (e = pairs_occupancy(&h->occ_pair[0], false)) != cudaSuccess ||
+        (e = pairs_occupancy(&h->occ_pair[1], true)) != cudaSuccess ||
         (e = cudaEventCreate(&h->ev0)) != cudaSuccess || (e = cudaEventCreate(&h->ev1)) != cudaSuccess ||
         (e = cudaEventCreate(&h->evm0)) != cudaSuccess || (e = cudaEventCreate(&h->evm1)) != cudaSuccess) {
         cudaGetLastError();
@@ -1418,6 +1462,7 @@ int pms_set_options(pms_ctx *h, const pms_options *opt)
     if (!h || !opt)
         return PMS_EINVAL;
     if (opt->ctas_per_sm < 0 || opt->chunk_work < 0 || opt->grab < 0 || opt->serve_wave_items < 0 || opt->smem_rows < 0 ||
+        opt->seed_mode < 0 || opt->seed_mode > 1 ||
         opt->serve_max_inflight < 0 || opt->serve_max_inflight > 1024)
         return h->fail(PMS_EINVAL, "negative option");
     std::lock_guard<std::recursive_mutex> g(h->mu);
@@ -1759,7 +1804,7 @@ void pms_destroy(pms_ctx *h)
     served_stop(h);
     if (h->stream)
         cudaStreamSynchronize(h->stream);
-    pms_ctx::DBuf *bufs[] = {&h->d_seqs, &h->d_planes, &h->d_raw, &h->d_tmp, &h->d_compat, &h->d_rowlen, &h->d_meta, &h->d_ctr, &h->d_scratch, &h->d_result};
+    pms_ctx::DBuf *bufs[] = {&h->d_seqs, &h->d_planes, &h->d_raw, &h->d_tmp, &h->d_compat, &h->d_rowlen, &h->d_mode, &h->d_meta, &h->d_ctr, &h->d_scratch, &h->d_result};
     for (auto *b : bufs)
         h->dev_free(b->p, b->cap);
     if (h->h_result)
