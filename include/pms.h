@@ -68,8 +68,9 @@ typedef struct {
 typedef struct {
     int ctas_per_sm;       /* resident CTAs of the verification kernel per SM */
     int chunk_work;        /* target work of one queue item, in candidate units */
-    int grab;              /* tree-node batches: 0 = fixed (up to 128 nodes per warp
-                              claim); g > 0 = guided, shrinking to g nodes as a
+    int grab;              /* tree-node filter: 0 = breadth-first batches of up to
+                              128 nodes (default); 1 = per-lane row walk with
+                              refill; g > 1 = batches shrinking to g nodes as a
                               queue item runs out */
     size_t max_motifs;     /* raw motif capacity per instance (rounded to 2^k) */
     int count_work;        /* 1: also count comparisons (slower; for profiling) */

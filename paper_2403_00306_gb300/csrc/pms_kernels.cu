@@ -447,6 +447,121 @@ __device__ __forceinline__ int filter_subsets(const WarpCtx &c, int N)
     return N;
 }
 
+// Depth-first-free row walk of the tree nodes of a chunk: every lane holds
+// one node P and the position r of the next row (smallest rows first) it has
+// to pass; a step tests each lane's node against its own row (the bound
+// popc(D_w ^ P) <= d), a node failing a row is dismissed, a node passing the
+// last filtered row is queued for leaf expansion, and freed lanes take the
+// next nodes of the chunk at once, so lanes stay busy however unevenly nodes
+// are pruned. Queued nodes are expanded (expand_subset) when the queue
+// fills and at the end.
+template <bool kCount>
+__device__ __forceinline__ void walk_subsets(const WarpCtx &c, const int *tab, int g1, CtaSmem &cs)
+{
+    const InstDev &in = c.in;
+    const int d = in.d;
+    const int nrows = min(in.prune_rows, in.n - 1);
+    uint32_t *queue = c.ws->subs;
+    int qn = 0;
+    int pool_lo = 0, pool_hi = 0;      // subsets claimed by this warp, not yet started
+    bool exhausted = false;            // the chunk has no unclaimed subsets left
+    uint32_t P = 0;
+    int r = 0;
+    bool has = false;
+    for (;;) {
+        // refill free lanes from the warp's pool, claiming more when it runs dry
+        uint32_t freem = __ballot_sync(kFull, !has);
+        while (freem) {
+            if (pool_lo >= pool_hi) {
+                if (exhausted)
+                    break;
+                int start = 0;
+                if (c.lane == 0)
+                    start = atomicAdd(&cs.next, 64);
+                start = __shfl_sync(kFull, start, 0);
+                if (start >= g1) {
+                    exhausted = true;
+                    break;
+                }
+                pool_lo = start;
+                pool_hi = min(start + 64, g1);
+            }
+            const int take = min(__popc(freem), pool_hi - pool_lo);
+            const int rank = __popc(freem & c.lt);
+            if (!has && rank < take) {
+                const int g = pool_lo + rank;
+                int lev = 0;
+                while (tab[lev + 1] <= g)
+                    ++lev;
+                P = unrank_subset((uint32_t)(g - tab[lev]), lev, in.l, cs.binom);
+                r = 0;
+                has = true;
+            }
+            pool_lo += take;
+            if (kCount && c.lane == 0)
+                c.cnt[kCntSubsets] += take;
+            freem = __ballot_sync(kFull, !has);
+        }
+        if (!__any_sync(kFull, has))
+            break;
+        if (nrows > 0) {
+            // one row per lane
+            int ri = 0, len4 = 0;
+            const uint4 *D4 = reinterpret_cast<const uint4 *>(c.rows.D);
+            if (has) {
+                ri = c.cs->row_order[r];
+                len4 = (c.cs->row_len[ri] + 3) >> 2;
+                D4 = reinterpret_cast<const uint4 *>(c.rows.D + c.cs->row_off[ri]);
+            }
+            const int maxlen4 = __reduce_max_sync(kFull, (unsigned)len4);
+            int m0 = 64, m1 = 64;
+            int e4 = 0;
+            for (; e4 < maxlen4; ++e4) {
+                if (e4 < len4) {
+                    const uint4 v = D4[e4];
+                    m0 = min(m0, __popc(v.x ^ P));
+                    m1 = min(m1, __popc(v.y ^ P));
+                    m0 = min(m0, __popc(v.z ^ P));
+                    m1 = min(m1, __popc(v.w ^ P));
+                }
+                if ((e4 & 3) == 3 && __all_sync(kFull, !has || min(m0, m1) <= d)) {
+                    ++e4;
+                    break;
+                }
+            }
+            if (kCount && has)
+                c.cnt[kCntCmpReduce] += 4ull * min(e4, len4);
+            const bool pass = has && min(m0, m1) <= d;
+            if (has && !pass) {
+                has = false;
+                if (kCount)
+                    c.cnt[kCntPruned] += 1;
+            }
+            if (pass)
+                ++r;
+        }
+        // nodes that passed every filtered row go to the expansion queue
+        const bool done = has && r >= nrows;
+        const uint32_t bal = __ballot_sync(kFull, done);
+        if (done) {
+            queue[qn + __popc(bal & c.lt)] = P;
+            has = false;
+        }
+        qn += __popc(bal);
+        if (qn > kSubBatch - 32) {
+            __syncwarp();
+            for (int i = 0; i < qn; ++i)
+                expand_subset<kCount>(c, queue[i]);
+            __syncwarp();
+            qn = 0;
+        }
+    }
+    __syncwarp();
+    for (int i = 0; i < qn; ++i)
+        expand_subset<kCount>(c, queue[i]);
+    __syncwarp();
+}
+
 // Gathers the feasible occurrences of seed `seed` (windows within 2d, from
 // the compatibility masks) into shared memory when they fit, else into this
 // CTA's global scratch. Every warp derives the smallest-first row order and
@@ -621,49 +736,52 @@ __global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
             const uint2 x = p.planes[in.plane_off + seed];
             Rows rows{cs.rows_in_smem ? smem_D : glob_D, cs.rows_in_smem ? smem_HL : glob_HL};
             WarpCtx c{&p, in, I, lane, lt, x.x, x.y, rows, &cs, &wsm[warp], kCount ? cnt : nullptr};
-            uint32_t *subs = wsm[warp].subs;
-            // batch size: up to kSubBatch subsets (large batches keep the
-            // breadth-first filter's lanes full), but small chunks are split so
-            // that every warp of the CTA gets work. With in.grab > 0 batches
-            // shrink toward in.grab as the chunk runs out (guided
-            // self-scheduling), which evens out warps whose nodes expand to
-            // many leaves.
-            const int per_warp = (g1 - g0 + 2 * kWarps - 1) / (2 * kWarps);
-            const int fixed = min(kSubBatch, max(32, (per_warp + 31) & ~31));
-            for (;;) {
-                int start = 0, batch = fixed;
-                if (lane == 0) {
-                    if (in.grab > 0) {
-                        const int left = g1 - *reinterpret_cast<volatile int *>(&cs.next);
-                        batch = min(fixed, max(in.grab, ((left + 2 * kWarps - 1) / (2 * kWarps) + 31) & ~31));
+            if (in.grab == 1) {
+                walk_subsets<kCount>(c, tab, g1, cs);
+            } else {
+                uint32_t *subs = wsm[warp].subs;
+                // batch filter: batches of up to kSubBatch subsets (large batches
+                // keep the breadth-first filter's lanes full), small chunks split
+                // so that every warp gets work; with in.grab > 1 batches shrink
+                // toward in.grab as the chunk runs out (guided self-scheduling);
+                // in.grab == 1 selects the row walk above instead
+                const int per_warp = (g1 - g0 + 2 * kWarps - 1) / (2 * kWarps);
+                const int fixed = min(kSubBatch, max(32, (per_warp + 31) & ~31));
+                for (;;) {
+                    int start = 0, batch = fixed;
+                    if (lane == 0) {
+                        if (in.grab > 1) {
+                            const int left = g1 - *reinterpret_cast<volatile int *>(&cs.next);
+                            batch = min(fixed, max(in.grab, ((left + 2 * kWarps - 1) / (2 * kWarps) + 31) & ~31));
+                        }
+                        start = atomicAdd(&cs.next, batch);
                     }
-                    start = atomicAdd(&cs.next, batch);
+                    start = __shfl_sync(kFull, start, 0);
+                    batch = __shfl_sync(kFull, batch, 0);
+                    if (start >= g1)
+                        break;
+                    const int N = min(batch, g1 - start);
+                    for (int j = lane; j < N; j += 32) {
+                        const int g = start + j;
+                        int lev = 0;
+                        while (tab[lev + 1] <= g)
+                            ++lev;
+                        subs[j] = unrank_subset((uint32_t)(g - tab[lev]), lev, in.l, cs.binom);
+                    }
+                    __syncwarp();
+                    if constexpr (kCount) {
+                        if (lane == 0)
+                            cnt[kCntSubsets] += N;
+                    }
+                    const int S = filter_subsets<kCount>(c, N);
+                    if constexpr (kCount) {
+                        if (lane == 0)
+                            cnt[kCntPruned] += N - S;
+                    }
+                    for (int sidx = 0; sidx < S; ++sidx)
+                        expand_subset<kCount>(c, subs[sidx]);
+                    __syncwarp();
                 }
-                start = __shfl_sync(kFull, start, 0);
-                batch = __shfl_sync(kFull, batch, 0);
-                if (start >= g1)
-                    break;
-                const int N = min(batch, g1 - start);
-                for (int j = lane; j < N; j += 32) {
-                    const int g = start + j;
-                    int lev = 0;
-                    while (tab[lev + 1] <= g)
-                        ++lev;
-                    subs[j] = unrank_subset((uint32_t)(g - tab[lev]), lev, in.l, cs.binom);
-                }
-                __syncwarp();
-                if constexpr (kCount) {
-                    if (lane == 0)
-                        cnt[kCntSubsets] += N;
-                }
-                const int S = filter_subsets<kCount>(c, N);
-                if constexpr (kCount) {
-                    if (lane == 0)
-                        cnt[kCntPruned] += N - S;
-                }
-                for (int sidx = 0; sidx < S; ++sidx)
-                    expand_subset<kCount>(c, subs[sidx]);
-                __syncwarp();
             }
         }
         __syncthreads();

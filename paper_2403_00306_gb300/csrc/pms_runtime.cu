@@ -814,7 +814,7 @@ static int autotune_class(pms_ctx *h, int n, int m, int l, int d, pms_ctx::Tunin
     std::vector<int> cta_c;
     for (int c = std::max(1, h->occ[0]); c >= 1 && (int)cta_c.size() < 2; --c)
         cta_c.push_back(c);
-    std::vector<int> grab_c = {0, 32, 64};
+    std::vector<int> grab_c = {0, 1, 32, 64};
     for (int dim = 0; dim < 4 && rc == PMS_OK; ++dim) {
         const std::vector<int> &vals = dim == 0 ? prune_c : (dim == 1 ? work_c : (dim == 2 ? cta_c : grab_c));
         for (int v : vals) {
