@@ -64,6 +64,11 @@ def _declare(lib):
         "oracle_solve_seeds": (c_long, [u8p, c_int, c_int, c_int, c_int, c_long, c_long, c_int, u64p, c_long]),
         "oracle_solve_pairs": (c_long, [u8p, c_int, c_int, c_int, c_int, c_int, u64p, c_long]),
         "oracle_bruteforce": (c_long, [u8p, c_int, c_int, c_int, c_int, u64p, c_long]),
+        "oracle_is_qmotif": (c_int, [u8p, c_int, c_int, c_int, u8p, c_int, c_int]),
+        "oracle_solve_quorum": (c_long, [u8p, c_int, c_int, c_int, c_int, c_int, c_int, u64p, c_long]),
+        "oracle_solve_quorum_seeds": (c_long, [u8p, c_int, c_int, c_int, c_int, c_int, c_long, c_long, c_int, u64p,
+                                                c_long]),
+        "oracle_bruteforce_quorum": (c_long, [u8p, c_int, c_int, c_int, c_int, c_int, u64p, c_long]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -198,6 +203,28 @@ class Oracle:
 
     def bruteforce(self, seqs, l: int, d: int, cap: int = 1 << 22) -> np.ndarray:
         return self._solve(self.lib.oracle_bruteforce, seqs, l, d, cap=cap)
+
+    # --- quorum (qPMS) ---
+    def is_qmotif(self, M, seqs: np.ndarray, d: int, q: int) -> bool:
+        M = _bytes(M)
+        seqs = np.ascontiguousarray(seqs, dtype=np.uint8)
+        ma, pm = _u8(M)
+        n, m = seqs.shape
+        return bool(self.lib.oracle_is_qmotif(pm, len(M), d, q, seqs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                              n, m))
+
+    def solve_quorum(self, seqs, l: int, d: int, q: int, threads: int | None = None, cap: int = 1 << 22) -> np.ndarray:
+        """All (l,d,q)-motifs as sorted unique keys."""
+        return self._solve(self.lib.oracle_solve_quorum, seqs, l, d, q, threads or os.cpu_count() or 1, cap=cap)
+
+    def solve_quorum_seeds(self, seqs, l: int, d: int, q: int, seed_lo: int, seed_hi: int,
+                           threads: int | None = None, cap: int = 1 << 22) -> np.ndarray:
+        """(l,d,q)-motifs inside B(x, d) for seeds [seed_lo, seed_hi) numbered over s_1, s_2, ..."""
+        return self._solve(self.lib.oracle_solve_quorum_seeds, seqs, l, d, q, seed_lo, seed_hi,
+                           threads or os.cpu_count() or 1, cap=cap)
+
+    def bruteforce_quorum(self, seqs, l: int, d: int, q: int, cap: int = 1 << 22) -> np.ndarray:
+        return self._solve(self.lib.oracle_bruteforce_quorum, seqs, l, d, q, cap=cap)
 
     def decode_all(self, keys, l: int) -> list[str]:
         return [self.decode(int(k), l) for k in keys]

@@ -88,6 +88,17 @@ int oracle_is_motif(const uint8_t *M, int l, int d, const uint8_t *seqs, int n, 
     return 1;
 }
 
+/* Definition 5 for general q: M is an (l,d,q)-motif iff at least q of the n
+ * strings are within d of M. */
+int oracle_is_qmotif(const uint8_t *M, int l, int d, int q, const uint8_t *seqs, int n, int m)
+{
+    int hits = 0;
+    for (int i = 0; i < n; ++i)
+        if (string_has_occurrence(M, l, d, seqs + (size_t)i * m, m))
+            hits += 1;
+    return hits >= q;
+}
+
 /* ---- bit-plane compression (chapter "Our Approach", "String Compression") ----
  * An l-mer is stored as ceil(log2 |Sigma|) = 2 groups of ceil(l/32) 32-bit
  * words; bit g of the code of character k goes to bit (k mod 32) of word
@@ -218,6 +229,7 @@ static int valid_input(const uint8_t *seqs, int n, int m, int l, int d)
 
 typedef struct {
     const uint8_t *x;   /* root l-mer */
+    int q;              /* quorum used by the motif test (0: all n strings) */
     uint8_t *cur;       /* the node being visited (x with some changes) */
     int l, d;
     /* what to do with each node */
@@ -234,7 +246,9 @@ static void visit_node(walk_t *w)
     w->visited += 1;
     if (w->other && oracle_hamming(w->cur, w->other, w->l) > w->d)
         return;
-    if (w->mode == 1 || oracle_is_motif(w->cur, w->l, w->d, w->seqs, w->n, w->m))
+    if (w->mode == 1 ||
+        (w->q > 0 ? oracle_is_qmotif(w->cur, w->l, w->d, w->q, w->seqs, w->n, w->m)
+                  : oracle_is_motif(w->cur, w->l, w->d, w->seqs, w->n, w->m)))
         kv_push(w->out, oracle_key(w->cur, w->l));
 }
 
@@ -263,7 +277,7 @@ long oracle_neighbourhood(const uint8_t *x, int l, int d, uint64_t *out, long ca
     uint8_t cur[32];
     memcpy(cur, x, (size_t)l);
     keyvec kv = {0};
-    walk_t w = {x, cur, l, d, NULL, 0, 0, NULL, 1, &kv, 0};
+    walk_t w = {x, 0, cur, l, d, NULL, 0, 0, NULL, 1, &kv, 0};
     walk_tree(&w, 0, 0);
     return kv_finish(&kv, out, cap);
 }
@@ -277,7 +291,7 @@ long oracle_neighbourhood_visits(const uint8_t *x, int l, int d)
     uint8_t cur[32];
     memcpy(cur, x, (size_t)l);
     keyvec kv = {0};
-    walk_t w = {x, cur, l, d, NULL, 0, 0, NULL, 1, &kv, 0};
+    walk_t w = {x, 0, cur, l, d, NULL, 0, 0, NULL, 1, &kv, 0};
     walk_tree(&w, 0, 0);
     free(kv.v);
     return w.visited;
@@ -289,7 +303,7 @@ long oracle_pair_intersection_size(const uint8_t *x, const uint8_t *r, int l, in
     uint8_t cur[32];
     memcpy(cur, x, (size_t)l);
     keyvec kv = {0};
-    walk_t w = {x, cur, l, d, NULL, 0, 0, r, 1, &kv, 0};
+    walk_t w = {x, 0, cur, l, d, NULL, 0, 0, r, 1, &kv, 0};
     walk_tree(&w, 0, 0);
     long n = kv.n;
     free(kv.v);
@@ -301,6 +315,7 @@ long oracle_pair_intersection_size(const uint8_t *x, const uint8_t *r, int l, in
 typedef struct {
     const uint8_t *seqs;
     int n, m, l, d;
+    int q;              /* quorum (0: n, the PMS problem) */
     int variant;        /* 0: seeds x in S_1; 1: pairs (x in S_1, r in S_2) */
     int tid, nthreads;
     long seed_lo, seed_hi;   /* range of windows of s_1 used as seeds */
@@ -313,13 +328,15 @@ static void *solve_worker(void *arg)
     const uint8_t *s1 = j->seqs;
     const uint8_t *s2 = j->n > 1 ? j->seqs + j->m : NULL;
     uint8_t cur[32];
+    const long W = (long)j->m - j->l + 1;
     for (long x0 = j->seed_lo + j->tid; x0 < j->seed_hi; x0 += j->nthreads) {
-        const uint8_t *x = s1 + x0;
+        /* seed x0 numbers the l-mers of s_1, s_2, ... in order (W per string) */
+        const uint8_t *x = s1 + (x0 / W) * (long)j->m + (x0 % W);
         if (j->variant == 0 || s2 == NULL) {
             /* Observation 3.1 with q = n: every motif is within d of some
              * l-mer x of s_1, so the candidates are the union of B(x, d). */
             memcpy(cur, x, (size_t)j->l);
-            walk_t w = {x, cur, j->l, j->d, j->seqs, j->n, j->m, NULL, 0, &j->out, 0};
+            walk_t w = {x, j->q, cur, j->l, j->d, j->seqs, j->n, j->m, NULL, 0, &j->out, 0};
             walk_tree(&w, 0, 0);
         } else {
             /* Observation 3.3 with q = n: a motif is within d of an l-mer x
@@ -330,7 +347,7 @@ static void *solve_worker(void *arg)
                 if (oracle_hamming(x, r, j->l) > 2 * j->d)
                     continue;
                 memcpy(cur, x, (size_t)j->l);
-                walk_t w = {x, cur, j->l, j->d, j->seqs, j->n, j->m, r, 0, &j->out, 0};
+                walk_t w = {x, 0, cur, j->l, j->d, j->seqs, j->n, j->m, r, 0, &j->out, 0};
                 walk_tree(&w, 0, 0);
             }
         }
@@ -338,16 +355,18 @@ static void *solve_worker(void *arg)
     return NULL;
 }
 
-static long run_solver(const uint8_t *seqs, int n, int m, int l, int d, int variant,
+static long run_solver(const uint8_t *seqs, int n, int m, int l, int d, int q, int variant,
                        long seed_lo, long seed_hi, int threads, uint64_t *out, long cap)
 {
-    if (!valid_input(seqs, n, m, l, d))
+    if (!valid_input(seqs, n, m, l, d) || q < 0 || q > n)
         return ORACLE_EINVAL;
     long W = (long)m - l + 1;
+    /* Observation 3.1: seeds from the l-mers of s_1..s_{n-q+1} (only s_1 for q = n) */
+    const long nseeds = (q > 0 ? (long)(n - q + 1) : 1L) * W;
     if (seed_lo < 0)
         seed_lo = 0;
-    if (seed_hi > W)
-        seed_hi = W;
+    if (seed_hi > nseeds)
+        seed_hi = nseeds;
     if (threads < 1)
         threads = 1;
     if (threads > 256)
@@ -360,7 +379,7 @@ static long run_solver(const uint8_t *seqs, int n, int m, int l, int d, int vari
         return ORACLE_ENOMEM;
     }
     for (int t = 0; t < threads; ++t) {
-        jobs[t] = (job_t){seqs, n, m, l, d, variant, t, threads, seed_lo, seed_hi, {0}};
+        jobs[t] = (job_t){seqs, n, m, l, d, q, variant, t, threads, seed_lo, seed_hi, {0}};
         if (threads == 1 || pthread_create(&th[t], NULL, solve_worker, &jobs[t]) != 0) {
             solve_worker(&jobs[t]);
             th[t] = 0;
@@ -387,7 +406,7 @@ static long run_solver(const uint8_t *seqs, int n, int m, int l, int d, int vari
 long oracle_solve(const uint8_t *seqs, int n, int m, int l, int d, int threads,
                   uint64_t *out, long cap)
 {
-    return run_solver(seqs, n, m, l, d, 0, 0, (long)m - l + 1, threads, out, cap);
+    return run_solver(seqs, n, m, l, d, 0, 0, 0, (long)m - l + 1, threads, out, cap);
 }
 
 /* The motifs lying in B(x, d) for the seeds x = s_1[j..j+l-1], j in
@@ -395,14 +414,52 @@ long oracle_solve(const uint8_t *seqs, int n, int m, int l, int d, int threads,
 long oracle_solve_seeds(const uint8_t *seqs, int n, int m, int l, int d, long seed_lo,
                         long seed_hi, int threads, uint64_t *out, long cap)
 {
-    return run_solver(seqs, n, m, l, d, 0, seed_lo, seed_hi, threads, out, cap);
+    return run_solver(seqs, n, m, l, d, 0, 0, seed_lo, seed_hi, threads, out, cap);
 }
 
 /* The same motif set through pairs (x in S_1, r in S_2, d_H(x,r) <= 2d). */
 long oracle_solve_pairs(const uint8_t *seqs, int n, int m, int l, int d, int threads,
                         uint64_t *out, long cap)
 {
-    return run_solver(seqs, n, m, l, d, 1, 0, (long)m - l + 1, threads, out, cap);
+    return run_solver(seqs, n, m, l, d, 0, 1, 0, (long)m - l + 1, threads, out, cap);
+}
+
+/* qPMS (the qPMS definition, quorum q <= n): all (l,d,q)-motifs. Seeds are
+ * the l-mers of s_1..s_{n-q+1} (Observation 3.1: a string within d of at
+ * least q strings is within d of one of any n - q + 1 of them). */
+long oracle_solve_quorum(const uint8_t *seqs, int n, int m, int l, int d, int q, int threads, uint64_t *out,
+                         long cap)
+{
+    if (q < 1)
+        return ORACLE_EINVAL;
+    return run_solver(seqs, n, m, l, d, q, 0, 0, (long)(n - q + 1) * (m - l + 1), threads, out, cap);
+}
+
+/* The (l,d,q)-motifs lying in B(x, d) for seeds x numbered
+ * [seed_lo, seed_hi) over the l-mers of s_1, s_2, ... (W per string). */
+long oracle_solve_quorum_seeds(const uint8_t *seqs, int n, int m, int l, int d, int q, long seed_lo, long seed_hi,
+                               int threads, uint64_t *out, long cap)
+{
+    if (q < 1)
+        return ORACLE_EINVAL;
+    return run_solver(seqs, n, m, l, d, q, 0, seed_lo, seed_hi, threads, out, cap);
+}
+
+/* Pattern-driven exhaustive search with a quorum: all 4^l strings tested
+ * with oracle_is_qmotif. Only for tiny l. */
+long oracle_bruteforce_quorum(const uint8_t *seqs, int n, int m, int l, int d, int q, uint64_t *out, long cap)
+{
+    if (!valid_input(seqs, n, m, l, d) || l > 12 || q < 1 || q > n)
+        return ORACLE_EINVAL;
+    keyvec kv = {0};
+    uint8_t cand[32];
+    uint64_t total = (uint64_t)1 << (2 * l);
+    for (uint64_t key = 0; key < total; ++key) {
+        oracle_decode(key, l, cand);
+        if (oracle_is_qmotif(cand, l, d, q, seqs, n, m))
+            kv_push(&kv, key);
+    }
+    return kv_finish(&kv, out, cap);
 }
 
 /* Pattern-driven exhaustive search ("Exact PMS Algorithms", pattern driven

@@ -231,6 +231,33 @@ def check_invariants(o) -> None:
     assert parts == base
 
 
+def check_quorum(o) -> None:
+    # brute force with a quorum on tiny inputs, every q
+    for (n, m, l, d, seed) in [(5, 30, 6, 1, 501), (4, 25, 5, 2, 502), (6, 20, 6, 2, 503)]:
+        inst = pi.planted_instance(n, m, l, d, seed)
+        prev = None
+        for q in range(1, n + 1):
+            got = o.solve_quorum(inst.seqs, l, d, q, threads=2)
+            assert np.array_equal(got, o.bruteforce_quorum(inst.seqs, l, d, q)), (n, m, l, d, q)
+            assert py_key(inst.motif.decode()) in set(int(k) for k in got)
+            if prev is not None:
+                assert set(int(k) for k in got) <= prev          # fewer motifs as the quorum rises
+            prev = set(int(k) for k in got)
+        # q = n is the PMS problem
+        assert np.array_equal(o.solve_quorum(inst.seqs, l, d, n, threads=2), o.solve(inst.seqs, l, d, threads=2))
+    # q = 1: every string within d of some l-mer of some sequence (written out in Python)
+    seqs = pi.random_sequences(3, 9, 510)
+    l, d = 5, 1
+    want = set()
+    for row in seqs:
+        for x in lmers(bytes(row), l):
+            for t in itertools.product(ACGT, repeat=l):
+                s = "".join(t)
+                if py_hamming(x, s) <= d:
+                    want.add(py_key(s))
+    assert [int(k) for k in o.solve_quorum(seqs, l, d, 1, threads=1)] == sorted(want)
+
+
 ALL_PINS = [check_compression_example, check_distance_definitions, check_neighbourhood_counts,
             check_neighbourhood_members, check_pair_intersections, check_bruteforce_agreement,
-            check_planted_motif_found, check_special_cases, check_invariants]
+            check_planted_motif_found, check_special_cases, check_invariants, check_quorum]

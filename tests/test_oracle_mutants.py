@@ -35,6 +35,10 @@ MUTANTS = {
     "group_dropped": ("for (int g = 0; g < 2; ++g)\n            acc |=", "for (int g = 0; g < 1; ++g)\n            acc |="),
     # pair variant uses d instead of 2d for the pair filter
     "pair_filter_tight": ("> 2 * j->d)", "> j->d)"),
+    # quorum: seeds only from s_1 (Observation 3.1 needs s_1..s_{n-q+1})
+    "quorum_seeds_first_only": ("(q > 0 ? (long)(n - q + 1) : 1L) * W", "1L * W"),
+    # quorum test off by one
+    "quorum_threshold": ("return hits >= q;", "return hits > q;"),
     # Hamming distance counts matches instead of mismatches at the first position
     "hamming_first_position": ("for (int k = 0; k < l; ++k)\n        if (a[k] != b[k])",
                                "for (int k = 1; k < l; ++k)\n        if (a[k] != b[k])"),
