@@ -87,6 +87,13 @@ typedef struct {
                               closer than d + 1, which keep the tree form.
                               Plain and batched solves; the served and
                               allocation-free forms use 0. */
+    int quorum;            /* q of the qPMS problem (Definition 5): report the
+                              l-mers within d of at least q of the n sequences.
+                              0 or q >= n: q = n, the PMS problem. With q < n the
+                              seeds are the l-mers of s_1..s_{n-q+1}
+                              (Observation 3.1) and every candidate may miss up
+                              to n - q sequences. Plain and batched solves; the
+                              served and allocation-free forms solve q = n. */
 } pms_options;
 
 /* A tuned schedule for one instance class (l, d, n rounded up to a power of

@@ -92,11 +92,18 @@ int oracle_is_motif(const uint8_t *M, int l, int d, const uint8_t *seqs, int n, 
  * strings are within d of M. */
 int oracle_is_qmotif(const uint8_t *M, int l, int d, int q, const uint8_t *seqs, int n, int m)
 {
-    int hits = 0;
-    for (int i = 0; i < n; ++i)
+    int hits = 0, misses = 0;
+    for (int i = 0; i < n; ++i) {
         if (string_has_occurrence(M, l, d, seqs + (size_t)i * m, m))
             hits += 1;
-    return hits >= q;
+        else
+            misses += 1;
+        if (hits >= q)
+            return 1;          /* q strings found: it is a motif */
+        if (misses > n - q)
+            return 0;          /* fewer than q strings can remain */
+    }
+    return 0;
 }
 
 /* ---- bit-plane compression (chapter "Our Approach", "String Compression") ----

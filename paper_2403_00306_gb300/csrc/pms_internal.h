@@ -12,7 +12,7 @@ constexpr int kNMax = 64;      // sequences per instance
 constexpr int kWarps = 8;      // warps per CTA of the verification kernel
 constexpr int kThreads = kWarps * 32;
 constexpr int kRbCap = 128;    // entries of a subset-reduced occurrence row kept in shared memory
-constexpr int kListCap = 256;  // surviving candidates a warp buffers before checking further rows
+constexpr int kListCap = 192;  // surviving candidates a warp buffers before checking further rows
 constexpr int kSubBatch = 128; // tree nodes (position subsets) a warp filters together
 constexpr int kRowSmemCap = 2560;  // feasible occurrences of one seed held in shared memory (padded)
 
@@ -35,9 +35,11 @@ struct InstDev {
     long long raw_off;     // offset (uint64) of the raw motif buffer (and of its sort twin)
     long long compat_off;  // offset (uint32) of the W x (n-1) x NW compatibility masks
     long long rlen_off;    // offset (int) of the W x (n-1) row sizes (set bits of each mask row)
-    long long seed_off;    // offset of this instance's W seeds in the per-seed mode array
+    long long seed_off;    // offset of this instance's seeds in the per-seed mode array
     int cps_b;             // pair mode: queue items per seed (blocks of 64 windows of s_2)
-    int pad2;
+    int q;                 // quorum: a motif needs q of the n sequences (q = n: PMS)
+    int nseed;             // sequences whose l-mers are seeds: n - q + 1
+    int pad3;
     uint32_t raw_cap;      // capacity of the raw motif buffer (power of two)
     int pad;
 };

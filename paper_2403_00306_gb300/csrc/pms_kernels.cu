@@ -39,6 +39,8 @@ struct __align__(16) WarpSmem {
     uint2 rb1[kRbCap + 4];      // scratch reduced row for rows 1..
     uint2 list[kListCap];       // candidates that survived row 0
     uint32_t subs[kSubBatch];   // position subsets being filtered
+    uint8_t lmiss[kListCap];    // quorum form: rows each listed candidate has missed
+    uint8_t smiss[kSubBatch];   // quorum form: rows each subset has missed
 };
 
 struct __align__(16) CtaSmem {
@@ -562,6 +564,186 @@ __device__ __forceinline__ void walk_subsets(const WarpCtx &c, const int *tab, i
     __syncwarp();
 }
 
+// ---------------------------------------------------------------------------
+// Quorum form (qPMS, q < n): a motif needs q of the n sequences, i.e. the
+// seed's own sequence and q - 1 of the n - 1 rows; a candidate may miss up
+// to n - q rows. Nodes and leaves carry a count of missed rows instead of
+// being dropped at the first miss.
+
+// Appends the codes of the lanes with `has` set to the instance's raw motifs.
+__device__ __forceinline__ void emit_lanes(const WarpCtx &c, bool has, uint2 v)
+{
+    const MainParams &p = *c.p;
+    const uint32_t bal = __ballot_sync(kFull, has);
+    if (!bal)
+        return;
+    uint32_t base = 0;
+    if (c.lane == 0)
+        base = atomicAdd(&p.raw_count[c.I], (uint32_t)__popc(bal));
+    base = __shfl_sync(kFull, base, 0);
+    if (has) {
+        const uint32_t pos = base + __popc(bal & c.lt);
+        if (pos < c.in.raw_cap)
+            p.raw[c.in.raw_off + pos] = to_key(v.x, v.y, c.in.l);
+        else
+            atomicOr(&p.flags[c.I], kFlagOverflow);
+    }
+}
+
+// The listed leaves of node P against every row in order: a leaf is emitted
+// as soon as it hits q - 1 rows, dropped once it misses more than n - q.
+template <bool kCount>
+__device__ __forceinline__ void finish_list_q(const WarpCtx &c, uint32_t P, int N)
+{
+    const InstDev &in = c.in;
+    const int nrows = in.n - 1;
+    const int budget = in.n - in.q, need = in.q - 1;
+    uint2 *list = c.ws->list;
+    uint8_t *lm = c.ws->lmiss;
+    __syncwarp();
+    for (int r = 0; r < nrows && N > 0; ++r) {
+        const int ri = c.cs->row_order[r];
+        const int len = c.cs->row_len[ri];
+        const int off = c.cs->row_off[ri];
+        const int k = len > 0 ? reduce_row(c.rows.D + off, c.rows.HL + off, len, P, in.d, c.ws->rb1, c.lane, c.lt) : 0;
+        if (kCount && c.lane == 0)
+            c.cnt[kCntCmpReduce] += len;
+        const bool sm = k <= kRbCap;
+        int newN = 0;
+        for (int b = 0; b < N; b += 32) {
+            const int idx = b + c.lane;
+            const bool alive = idx < N;
+            uint2 v = make_uint2(0u, 0u);
+            int ms = 0;
+            if (alive) {
+                v = list[idx];
+                ms = lm[idx];
+            }
+            bool hit = false;
+            if (alive && k > 0) {
+                hit = sm ? check_smem(c.ws->rb1, k, v.x, v.y, in.d) : check_row(c.rows.HL + off, len, v.x, v.y, in.d);
+                if (kCount)
+                    c.cnt[kCntCmpVerify] += sm ? k : len;
+            }
+            if (alive && !hit)
+                ++ms;
+            const bool accept = alive && (r + 1 - ms) >= need;
+            const bool keep = alive && !accept && ms <= budget;
+            __syncwarp();
+            emit_lanes(c, accept, v);
+            const uint32_t bal = __ballot_sync(kFull, keep);
+            if (keep) {
+                const int pos = newN + __popc(bal & c.lt);
+                list[pos] = v;
+                lm[pos] = (uint8_t)ms;
+            }
+            newN += __popc(bal);
+        }
+        __syncwarp();
+        N = newN;
+    }
+    __syncwarp();
+}
+
+// Every leaf of a node that survived the quorum filter goes through the rows.
+template <bool kCount>
+__device__ __forceinline__ void expand_subset_q(const WarpCtx &c, uint32_t P)
+{
+    const int lev = __popc(P);
+    uint32_t t = P;
+    const uint32_t b0 = t & (0u - t);
+    t ^= b0;
+    const uint32_t b1 = t & (0u - t);
+    t ^= b1;
+    const uint32_t b2 = t & (0u - t);
+    t ^= b2;
+    const uint32_t Phi = t;
+    const int nlo = lev < 3 ? lev : 3;
+    const int nlanes = nlo == 0 ? 1 : (nlo == 1 ? 3 : (nlo == 2 ? 9 : 27));
+    const bool active = c.lane < nlanes;
+    const int dg0 = c.lane % 3, dg1 = (c.lane / 3) % 3, dg2 = (c.lane / 9) % 3;
+    const uint32_t DhLo = (dg0 >= 1 ? b0 : 0u) | (dg1 >= 1 ? b1 : 0u) | (dg2 >= 1 ? b2 : 0u);
+    const uint32_t DlLo = (dg0 != 1 ? b0 : 0u) | (dg1 != 1 ? b1 : 0u) | (dg2 != 1 ? b2 : 0u);
+    const uint32_t ch0 = c.xh ^ DhLo, cl0 = c.xl ^ DlLo;
+    const unsigned long long iters = c_pow3[lev - nlo];
+    uint2 *list = c.ws->list;
+    int listN = 0;
+    uint32_t Dh = 0u, Dl = Phi;
+    for (unsigned long long it = 0; it < iters; ++it) {
+        const uint32_t bal = __ballot_sync(kFull, active);
+        if (active) {
+            const int pos = listN + __popc(bal & c.lt);
+            list[pos] = make_uint2(ch0 ^ Dh, cl0 ^ Dl);
+            c.ws->lmiss[pos] = 0;
+            if (kCount)
+                c.cnt[kCntTested] += 1;
+        }
+        listN += __popc(bal);
+        if (listN > kListCap - 32) {
+            finish_list_q<kCount>(c, P, listN);
+            listN = 0;
+        }
+        const uint32_t both = Dh & Dl;
+        const uint32_t open = Phi & ~both;
+        const uint32_t q = open & (0u - open);
+        const uint32_t below = Phi & (q - 1u);
+        Dh = (Dh & ~below) | q;
+        Dl = (Dl | below) ^ q;
+    }
+    if (listN > 0)
+        finish_list_q<kCount>(c, P, listN);
+}
+
+// Node filter with a miss budget: a node is dismissed once more than n - q of
+// the filtered rows hold no occurrence meeting its bound.
+template <bool kCount>
+__device__ __forceinline__ int filter_subsets_q(const WarpCtx &c, int N)
+{
+    const InstDev &in = c.in;
+    const int d = in.d;
+    const int budget = in.n - in.q;
+    const int nrows = min(in.prune_rows, in.n - 1);
+    uint32_t *subs = c.ws->subs;
+    uint8_t *sm = c.ws->smiss;
+    for (int r = 0; r < nrows && N > 0; ++r) {
+        const int ri = c.cs->row_order[r];
+        const int len = c.cs->row_len[ri];
+        const uint4 *D4 = reinterpret_cast<const uint4 *>(c.rows.D + c.cs->row_off[ri]);
+        const int len4 = (len + 3) >> 2;
+        int newN = 0;
+        for (int b = 0; b < N; b += 32) {
+            const int idx = b + c.lane;
+            const bool alive = idx < N;
+            const uint32_t P = alive ? subs[idx] : 0u;
+            int ms = alive ? sm[idx] : 0;
+            int m0 = 64, m1 = 64;
+            for (int e4 = 0; e4 < len4; ++e4) {
+                const uint4 v = D4[e4];
+                m0 = min(m0, __popc(v.x ^ P));
+                m1 = min(m1, __popc(v.y ^ P));
+                m0 = min(m0, __popc(v.z ^ P));
+                m1 = min(m1, __popc(v.w ^ P));
+            }
+            if (kCount && alive)
+                c.cnt[kCntCmpReduce] += 4ull * len4;
+            if (alive && min(m0, m1) > d)
+                ++ms;
+            const bool keep = alive && ms <= budget;
+            __syncwarp();
+            const uint32_t bal = __ballot_sync(kFull, keep);
+            if (keep) {
+                const int pos = newN + __popc(bal & c.lt);
+                subs[pos] = P;
+                sm[pos] = (uint8_t)ms;
+            }
+            newN += __popc(bal);
+        }
+        __syncwarp();
+        N = newN;
+    }
+    return N;
+}
+
 // Gathers the feasible occurrences of seed `seed` (windows within 2d, from
 // the compatibility masks) into shared memory when they fit, else into this
 // CTA's global scratch. Every warp derives the smallest-first row order and
@@ -591,7 +773,9 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
         ob += rj < rb ? pj : 0;
         total += pj;
     }
-    const bool empty = __any_sync(kFull, (lane < R && la == 0) || (lane + 32 < R && lb == 0));
+    // a seed is hopeless when more rows are empty than the quorum may miss
+    const int nempty = __popc(__ballot_sync(kFull, lane < R && la == 0)) + __popc(__ballot_sync(kFull, lane + 32 < R && lb == 0));
+    const bool empty = nempty > in.n - in.q;
     const bool in_smem = total <= p.smem_rows_cap;
     if (warp == 0) {
         if (lane < R) {
@@ -618,9 +802,10 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
         const uint2 *pl = p.planes + in.plane_off;
         const uint2 x = pl[seed];
         const uint32_t *mask = p.compat + in.compat_off + (size_t)seed * R * NW;
+        const int si = seed / W;   // the seed's own sequence has no row
         for (int i = 1 + warp; i < n; i += kWarps) {
             const uint32_t *mr = mask + (size_t)(i - 1) * NW;
-            const uint2 *s = pl + (size_t)i * W;
+            const uint2 *s = pl + (size_t)(i - 1 < si ? i - 1 : i) * W;
             const int src = (i - 1) & 31;
             const int off = __shfl_sync(kFull, i - 1 < 32 ? oa : ob, src);
             const int len = __shfl_sync(kFull, i - 1 < 32 ? la : lb, src);
@@ -648,7 +833,7 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
             }
             __syncwarp();
             const int padded = (len + 3) & ~3;
-            if (lane < padded - len) {
+            if (len > 0 && lane < padded - len) {
                 Hd[off + len + lane] = Hd[off + len - 1];
                 Dd[off + len + lane] = Dd[off + len - 1];
             }
@@ -736,7 +921,40 @@ __global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
             const uint2 x = p.planes[in.plane_off + seed];
             Rows rows{cs.rows_in_smem ? smem_D : glob_D, cs.rows_in_smem ? smem_HL : glob_HL};
             WarpCtx c{&p, in, I, lane, lt, x.x, x.y, rows, &cs, &wsm[warp], kCount ? cnt : nullptr};
-            if (in.grab == 1) {
+            if (in.q < in.n) {
+                // quorum form: batches of nodes with miss budgets
+                uint32_t *subs = wsm[warp].subs;
+                for (;;) {
+                    int start = 0;
+                    if (lane == 0)
+                        start = atomicAdd(&cs.next, kSubBatch);
+                    start = __shfl_sync(kFull, start, 0);
+                    if (start >= g1)
+                        break;
+                    const int N = min(kSubBatch, g1 - start);
+                    for (int j = lane; j < N; j += 32) {
+                        const int g = start + j;
+                        int lev = 0;
+                        while (tab[lev + 1] <= g)
+                            ++lev;
+                        subs[j] = unrank_subset((uint32_t)(g - tab[lev]), lev, in.l, cs.binom);
+                        wsm[warp].smiss[j] = 0;
+                    }
+                    __syncwarp();
+                    if constexpr (kCount) {
+                        if (lane == 0)
+                            cnt[kCntSubsets] += N;
+                    }
+                    const int S = filter_subsets_q<kCount>(c, N);
+                    if constexpr (kCount) {
+                        if (lane == 0)
+                            cnt[kCntPruned] += N - S;
+                    }
+                    for (int sidx = 0; sidx < S; ++sidx)
+                        expand_subset_q<kCount>(c, subs[sidx]);
+                    __syncwarp();
+                }
+            } else if (in.grab == 1) {
                 walk_subsets<kCount>(c, tab, g1, cs);
             } else {
                 uint32_t *subs = wsm[warp].subs;
@@ -1311,7 +1529,11 @@ __global__ void compat_kernel(const InstDev *__restrict__ inst, int ninst, const
         }
         const InstDev in = inst[lo];
         const long long local = q - row_prefix[lo];
-        const int j = (int)(local / (in.n - 1)), i = 1 + (int)(local % (in.n - 1));
+        // seed j numbers the l-mers of the seed sequences (W each); row k of a
+        // seed of sequence si is sequence k (k < si) or k + 1 (k >= si)
+        const int j = (int)(local / (in.n - 1)), k = (int)(local % (in.n - 1));
+        const int si = j / in.W;
+        const int i = k < si ? k : k + 1;
         const uint2 *pl = planes + in.plane_off;
         const uint2 x = pl[j];
         const uint2 *s = pl + (size_t)i * in.W;

@@ -404,13 +404,20 @@ struct ResLayout {
 // Expected raw motif count (duplicates included) of an FM-like instance under
 // independence: W |B(x,d)| q^(n-1), q = P(a random sequence has a window
 // within d of a fixed l-mer). Sizes the raw buffer; overflow triggers a retry.
-static double expected_raw(int n, int m, int l, int d)
+static double expected_raw(int n, int m, int l, int d, int quorum = 0)
 {
     const int W = m - l + 1;
     const double nb = (double)ball_size(l, d);
     const double p = std::min(1.0, nb / std::pow(4.0, l));
     const double q = 1.0 - std::pow(1.0 - p, W);
-    return W * nb * std::pow(q, n - 1);
+    if (quorum <= 0 || quorum >= n)
+        return W * nb * std::pow(q, n - 1);
+    // quorum form: seeds from n - quorum + 1 sequences, a candidate needs
+    // quorum - 1 of the other n - 1 sequences: binomial tail
+    double tail = 0;
+    for (int i = quorum - 1; i <= n - 1; ++i)
+        tail += (double)binom(n - 1, i) * std::pow(q, i) * std::pow(1.0 - q, n - 1 - i);
+    return (double)(n - quorum + 1) * W * nb * tail;
 }
 
 static uint32_t default_cap(const pms_ctx *h, const InstSpec &s, bool single)
@@ -419,7 +426,7 @@ static uint32_t default_cap(const pms_ctx *h, const InstSpec &s, bool single)
         return s.raw_cap;
     if (h->opt.max_motifs)
         return pow2_at_least(h->opt.max_motifs);
-    const double est = 4.0 * expected_raw(s.n, s.m, s.l, s.d) + 256.0;
+    const double est = 4.0 * expected_raw(s.n, s.m, s.l, s.d, h->opt.quorum) + 256.0;
     const size_t lo = single ? (size_t)1 << 16 : (size_t)1 << 12;
     return pow2_at_least(std::min<double>(std::max<double>(est, lo), (double)(1u << 24)));
 }
@@ -435,6 +442,7 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
     Plan P;
     long long work = 0;
     const int adaptive = kDefaultChunkWork;   // untuned classes: about 2^20 candidate units per queue item
+    bool quorum_used = false;
     for (size_t k = 0; k < specs.size(); ++k) {
         const InstSpec &s = specs[k];
         InstDev in{};
@@ -444,6 +452,9 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
         in.d = s.d;
         in.W = s.m - s.l + 1;
         in.NW = (in.W + 31) / 32;
+        in.q = (h->opt.quorum > 0 && h->opt.quorum < s.n) ? h->opt.quorum : s.n;
+        in.nseed = s.n - in.q + 1;
+        const long long seeds = (long long)in.nseed * in.W;
         const int cw = h->chunk_work_for(s.n, s.m, s.l, s.d);
         const ChunkTable &ct = h->chunks(s.l, s.d, cw > 0 ? cw : adaptive);
         in.cps = ct.cps;
@@ -459,13 +470,13 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
         in.raw_cap = default_cap(h, s, specs.size() == 1);
         P.raw += in.raw_cap;
         in.compat_off = (long long)P.compat;
-        P.compat += (size_t)in.W * (s.n - 1) * in.NW;
+        P.compat += (size_t)seeds * (s.n - 1) * in.NW;
         in.rlen_off = (long long)P.rowlen;
-        P.rowlen += (size_t)in.W * (s.n - 1);
+        P.rowlen += (size_t)seeds * (s.n - 1);
         P.win_prefix.push_back(P.total_windows);
         P.total_windows += (long long)s.n * in.W;
         P.row_prefix.push_back(P.total_rows);
-        P.total_rows += (long long)in.W * (s.n - 1);
+        P.total_rows += seeds * (s.n - 1);
         in.seed_off = P.total_seeds;
         P.seed_prefix.push_back(P.total_seeds);
         P.total_seeds += in.W;
@@ -473,14 +484,16 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
         P.seg_pair.push_back(Segment{P.total_pair_items, (int)k, 0, in.W * in.cps_b, 0});
         P.total_pair_items += (long long)in.W * in.cps_b;
         P.rows_cap = std::max(P.rows_cap, (int)round_up((size_t)(s.n - 1) * (in.W + 3), 4));
-        const int chunks = in.W * in.cps;
+        const int chunks = (int)(seeds * in.cps);
         P.seg.push_back(Segment{work, (int)k, 0, chunks, 0});
         work += chunks;
-        P.candidates += (uint64_t)in.W * ball_size(s.l, s.d);
+        P.candidates += (uint64_t)seeds * ball_size(s.l, s.d);
+        if (in.q < in.n)
+            quorum_used = true;
         P.inst.push_back(in);
     }
     P.total_items = work;
-    P.pair_mode = h->opt.seed_mode == 1;
+    P.pair_mode = h->opt.seed_mode == 1 && !quorum_used;   // pair seeds are for q = n
     return P;
 }
 
@@ -1164,6 +1177,8 @@ static bool served_admit(Served *S, Request *r)
     in.cps = ct.cps;
     in.grab = h->grab_for(r->n, r->m, r->l, r->d);
     in.prune_rows = h->prune_rows_for(r->n, r->m, r->l, r->d);
+    in.q = r->n;
+    in.nseed = 1;
     in.seq_off = (long long)(off + L.seqs);
     in.plane_off = (long long)((off + L.planes) / sizeof(uint2));
     in.raw_off = (long long)((off + L.raw) / 8);
@@ -1462,7 +1477,7 @@ int pms_set_options(pms_ctx *h, const pms_options *opt)
     if (!h || !opt)
         return PMS_EINVAL;
     if (opt->ctas_per_sm < 0 || opt->chunk_work < 0 || opt->grab < 0 || opt->serve_wave_items < 0 || opt->smem_rows < 0 ||
-        opt->seed_mode < 0 || opt->seed_mode > 1 ||
+        opt->seed_mode < 0 || opt->seed_mode > 1 || opt->quorum < 0 ||
         opt->serve_max_inflight < 0 || opt->serve_max_inflight > 1024)
         return h->fail(PMS_EINVAL, "negative option");
     std::lock_guard<std::recursive_mutex> g(h->mu);
@@ -1974,6 +1989,8 @@ extern "C" int pms_solve_device_noalloc(const uint8_t *d_seqs, int n, int m, int
     in.cps = cps;
     in.grab = 0;
     in.prune_rows = default_prune_rows(n, d);
+    in.q = n;        // the PMS problem
+    in.nseed = 1;
     in.ctab = 0;
     in.seq_off = 0;
     in.plane_off = 0;

@@ -38,7 +38,7 @@ MUTANTS = {
     # quorum: seeds only from s_1 (Observation 3.1 needs s_1..s_{n-q+1})
     "quorum_seeds_first_only": ("(q > 0 ? (long)(n - q + 1) : 1L) * W", "1L * W"),
     # quorum test off by one
-    "quorum_threshold": ("return hits >= q;", "return hits > q;"),
+    "quorum_threshold": ("if (hits >= q)\n            return 1;", "if (hits > q)\n            return 1;"),
     # Hamming distance counts matches instead of mismatches at the first position
     "hamming_first_position": ("for (int k = 0; k < l; ++k)\n        if (a[k] != b[k])",
                                "for (int k = 1; k < l; ++k)\n        if (a[k] != b[k])"),
