@@ -271,6 +271,9 @@ __device__ __forceinline__ int leaf_loop(const WarpCtx &c, uint32_t P, uint32_t 
             if constexpr (kReg < 0) {
                 hit_a = true;
                 hit_b = two;
+            } else if constexpr (kReg == 1) {
+                hit_a = __popc((ch_a ^ e[0].x) | (cl_a ^ e[0].y)) <= d;
+                hit_b = two && __popc((ch_b ^ e[0].x) | (cl_b ^ e[0].y)) <= d;
             } else if constexpr (kReg > 0) {
                 int a0 = 64, a1 = 64, b0m = 64, b1m = 64;
 #pragma unroll
@@ -379,6 +382,10 @@ __device__ __forceinline__ void expand_subset(const WarpCtx &c, uint32_t P)
     int listN = 0;
     if (nrows == 0)
         listN = leaf_loop<kCount, -1>(c, P, Phi, ch0, cl0, active, iters, k0, len0, off0);
+    else if (k0 <= 1)
+        listN = leaf_loop<kCount, 1>(c, P, Phi, ch0, cl0, active, iters, k0, len0, off0);
+    else if (k0 <= 2)
+        listN = leaf_loop<kCount, 2>(c, P, Phi, ch0, cl0, active, iters, k0, len0, off0);
     else if (k0 <= 4)
         listN = leaf_loop<kCount, 4>(c, P, Phi, ch0, cl0, active, iters, k0, len0, off0);
     else if (k0 <= 8)
