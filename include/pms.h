@@ -94,6 +94,21 @@ typedef struct {
                               (Observation 3.1) and every candidate may miss up
                               to n - q sequences. Plain and batched solves; the
                               served and allocation-free forms solve q = n. */
+    int partial_rows;      /* one more level of the tree T_d(x) between a node P
+                              (its set of changed positions) and its leaves: the
+                              letters on the changed positions above the three
+                              lowest are fixed first, and such a partial
+                              candidate is kept only if each of the first
+                              partial_rows rows (smallest first) holds an
+                              occurrence that a leaf below it could still reach
+                              within d; only the kept partials' leaves are
+                              tested (the row shrinking of the paper's
+                              depth-first search, one level deep).
+                              0: tuned value, else the default (1 row for
+                              d = 5, 4 rows for d >= 6, when fewer than 0.15
+                              windows of a random sequence are expected within
+                              d of a candidate; none otherwise); -1: no partial
+                              level; k > 0: k rows. Tree form, q = n. */
 } pms_options;
 
 /* A tuned schedule for one instance class (l, d, n rounded up to a power of
@@ -103,6 +118,7 @@ typedef struct {
     int prune_rows;   /* rows the tree-node filter applies before leaves are expanded */
     int ctas_per_sm;  /* resident CTAs of the verification kernel */
     int grab;         /* node batch policy (as pms_options.grab) */
+    int partial_rows; /* rows tested at the partial-candidate level (-1: none) */
     double ms;        /* device time of the pipeline on the tuning instance */
 } pms_tuning;
 

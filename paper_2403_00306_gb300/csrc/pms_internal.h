@@ -39,7 +39,8 @@ struct InstDev {
     int cps_b;             // pair mode: queue items per seed (blocks of 64 windows of s_2)
     int q;                 // quorum: a motif needs q of the n sequences (q = n: PMS)
     int nseed;             // sequences whose l-mers are seeds: n - q + 1
-    int pad3;
+    int partial_rows;      // rows a partial candidate (letters fixed above the 3 lowest changed positions)
+                           //   is tested against before its leaves; 0: no partial level
     uint32_t raw_cap;      // capacity of the raw motif buffer (power of two)
     int pad;
 };

@@ -335,6 +335,159 @@ __device__ __forceinline__ int leaf_loop(const WarpCtx &c, uint32_t P, uint32_t 
     return listN;
 }
 
+// Lower bound on the distance from a window w to every leaf that agrees with
+// the partial candidate (ph, pl) outside the free positions Plow and differs
+// from the seed x on each of them: mismatches outside Plow, plus the free
+// positions where w agrees with x (the leaf must differ from x there).
+__device__ __forceinline__ int partial_bound(uint32_t ph, uint32_t pl, uint2 w, uint32_t xh, uint32_t xl,
+                                             uint32_t Plow)
+{
+    return __popc(((ph ^ w.x) | (pl ^ w.y)) & ~Plow) + __popc(Plow & ~((xh ^ w.x) | (xl ^ w.y)));
+}
+
+// One more tree level between a node P and its leaves. A partial candidate
+// fixes the letters on the positions Phi of P above its three lowest (Plow);
+// it survives a row only if some occurrence w of the row has
+// partial_bound <= d, since every leaf below it is at least that far from w.
+// Lanes own partials (32 per group, numbered like the odometer's states),
+// test them against row 0 reduced by P and then rows 1..partial_rows-1,
+// reduced in turn, stopping once no partial of the group is left; the warp
+// then tests the leaves of the surviving partials only (27 lanes own the
+// letters on Plow, two partials per step) against row 0, and the hits go on
+// to the other rows through the warp's list.
+template <bool kCount, int kReg>
+__device__ __forceinline__ int partial_walk(const WarpCtx &c, uint32_t P, uint32_t Phi, uint32_t Plow,
+                                            uint32_t DhLo, uint32_t DlLo, bool active, int h, int k0, int len0,
+                                            int off0)
+{
+    const int d = c.in.d;
+    const int R = min(c.in.partial_rows, c.in.n - 1);
+    const bool sm0 = k0 <= kRbCap;
+    uint2 e[kReg > 0 ? kReg : 1];
+    if constexpr (kReg > 0) {
+#pragma unroll
+        for (int i = 0; i < kReg; ++i)
+            e[i] = c.ws->rb0[i < k0 ? i : k0 - 1];
+    }
+    uint2 *list = c.ws->list;
+    const uint32_t npart = (uint32_t)c_pow3[h];   // h <= 20, so 3^h < 2^32
+    int listN = 0;
+    for (uint32_t g0 = 0; g0 < npart; g0 += 32) {
+        const uint32_t pidx = g0 + (uint32_t)c.lane;
+        bool live = pidx < npart;
+        // odometer state number pidx: base-3 digits over Phi, lowest position first
+        uint32_t Dh = 0u, Dl = 0u;
+        {
+            uint32_t r = pidx;
+            uint32_t t = Phi;
+            while (t) {
+                const uint32_t b = t & (0u - t);
+                t ^= b;
+                const uint32_t r3 = r / 3u;
+                const uint32_t dg = r - 3u * r3;
+                r = r3;
+                Dh |= dg >= 1u ? b : 0u;
+                Dl |= dg != 1u ? b : 0u;
+            }
+        }
+        const uint32_t ph = c.xh ^ Dh, pl = c.xl ^ Dl;
+        if (live) {
+            int mn = 64;
+            if constexpr (kReg > 0) {
+#pragma unroll
+                for (int i = 0; i < kReg; ++i)
+                    mn = min(mn, partial_bound(ph, pl, e[i], c.xh, c.xl, Plow));
+            } else if (sm0) {
+                for (int i = 0; i < k0; ++i)
+                    mn = min(mn, partial_bound(ph, pl, c.ws->rb0[i], c.xh, c.xl, Plow));
+            } else {
+                for (int i = 0; i < len0; ++i)
+                    mn = min(mn, partial_bound(ph, pl, c.rows.HL[off0 + i], c.xh, c.xl, Plow));
+            }
+            live = mn <= d;
+            if (kCount)
+                c.cnt[kCntCmpReduce] += sm0 ? k0 : len0;
+        }
+        for (int r = 1; r < R; ++r) {
+            if (!__any_sync(kFull, live))
+                break;
+            const int ri = c.cs->row_order[r];
+            const int len = c.cs->row_len[ri];
+            const int off = c.cs->row_off[ri];
+            const int k = reduce_row(c.rows.D + off, c.rows.HL + off, len, P, d, c.ws->rb1, c.lane, c.lt);
+            if (kCount && c.lane == 0)
+                c.cnt[kCntCmpReduce] += len;
+            if (live) {
+                int mn = 64;
+                if (k <= kRbCap) {
+                    for (int i = 0; i < k; ++i)
+                        mn = min(mn, partial_bound(ph, pl, c.ws->rb1[i], c.xh, c.xl, Plow));
+                } else {
+                    for (int i = 0; i < len; ++i)
+                        mn = min(mn, partial_bound(ph, pl, c.rows.HL[off + i], c.xh, c.xl, Plow));
+                }
+                live = mn <= d;
+                if (kCount)
+                    c.cnt[kCntCmpReduce] += k <= kRbCap ? k : len;
+            }
+        }
+        uint32_t mask = __ballot_sync(kFull, live);
+        while (mask) {
+            const int pa = __ffs(mask) - 1;
+            mask &= mask - 1u;
+            const bool two = mask != 0u;
+            const int pb = two ? __ffs(mask) - 1 : pa;
+            if (two)
+                mask &= mask - 1u;
+            const uint32_t ch_a = __shfl_sync(kFull, ph, pa) ^ DhLo, cl_a = __shfl_sync(kFull, pl, pa) ^ DlLo;
+            const uint32_t ch_b = __shfl_sync(kFull, ph, pb) ^ DhLo, cl_b = __shfl_sync(kFull, pl, pb) ^ DlLo;
+            bool hit_a = false, hit_b = false;
+            if (active) {
+                if constexpr (kReg == 1) {
+                    hit_a = __popc((ch_a ^ e[0].x) | (cl_a ^ e[0].y)) <= d;
+                    hit_b = two && __popc((ch_b ^ e[0].x) | (cl_b ^ e[0].y)) <= d;
+                } else if constexpr (kReg > 0) {
+                    int a0 = 64, a1 = 64, b0m = 64, b1m = 64;
+#pragma unroll
+                    for (int i = 0; i < kReg; i += 2) {
+                        a0 = min(a0, __popc((ch_a ^ e[i].x) | (cl_a ^ e[i].y)));
+                        b0m = min(b0m, __popc((ch_b ^ e[i].x) | (cl_b ^ e[i].y)));
+                        a1 = min(a1, __popc((ch_a ^ e[i + 1].x) | (cl_a ^ e[i + 1].y)));
+                        b1m = min(b1m, __popc((ch_b ^ e[i + 1].x) | (cl_b ^ e[i + 1].y)));
+                    }
+                    hit_a = min(a0, a1) <= d;
+                    hit_b = two && min(b0m, b1m) <= d;
+                } else if (sm0) {
+                    hit_a = check_smem(c.ws->rb0, k0, ch_a, cl_a, d);
+                    hit_b = two && check_smem(c.ws->rb0, k0, ch_b, cl_b, d);
+                } else {
+                    hit_a = check_row(c.rows.HL + off0, len0, ch_a, cl_a, d);
+                    hit_b = two && check_row(c.rows.HL + off0, len0, ch_b, cl_b, d);
+                }
+                if (kCount) {
+                    c.cnt[kCntTested] += two ? 2 : 1;
+                    c.cnt[kCntCmpVerify] += (unsigned long long)(two ? 2 : 1) * (sm0 ? k0 : len0);
+                }
+            }
+            const uint32_t bal_a = __ballot_sync(kFull, hit_a);
+            const uint32_t bal_b = __ballot_sync(kFull, hit_b);
+            if (bal_a | bal_b) {
+                if (hit_a)
+                    list[listN + __popc(bal_a & c.lt)] = make_uint2(ch_a, cl_a);
+                listN += __popc(bal_a);
+                if (hit_b)
+                    list[listN + __popc(bal_b & c.lt)] = make_uint2(ch_b, cl_b);
+                listN += __popc(bal_b);
+                if (listN > kListCap - 64) {
+                    finish_list<kCount>(c, P, listN);
+                    listN = 0;
+                }
+            }
+        }
+    }
+    return listN;
+}
+
 // The leaves of one tree node P (|P| = lev) that survived the row filter.
 // Lanes own the letter choices on the lowest min(lev, 3) positions of P (27
 // lanes at most); every lane walks the choices on the remaining positions
@@ -380,7 +533,20 @@ __device__ __forceinline__ void expand_subset(const WarpCtx &c, uint32_t P)
     const unsigned long long iters = c_pow3[lev - nlo];
 
     int listN = 0;
-    if (nrows == 0)
+    if (nrows > 0 && in.partial_rows > 0 && lev > nlo && lev - nlo <= 20) {
+        const uint32_t Plow = b0 | b1 | b2;
+        const int h = lev - nlo;
+        if (k0 <= 1)
+            listN = partial_walk<kCount, 1>(c, P, Phi, Plow, DhLo, DlLo, active, h, k0, len0, off0);
+        else if (k0 <= 2)
+            listN = partial_walk<kCount, 2>(c, P, Phi, Plow, DhLo, DlLo, active, h, k0, len0, off0);
+        else if (k0 <= 4)
+            listN = partial_walk<kCount, 4>(c, P, Phi, Plow, DhLo, DlLo, active, h, k0, len0, off0);
+        else if (k0 <= 8)
+            listN = partial_walk<kCount, 8>(c, P, Phi, Plow, DhLo, DlLo, active, h, k0, len0, off0);
+        else
+            listN = partial_walk<kCount, 0>(c, P, Phi, Plow, DhLo, DlLo, active, h, k0, len0, off0);
+    } else if (nrows == 0)
         listN = leaf_loop<kCount, -1>(c, P, Phi, ch0, cl0, active, iters, k0, len0, off0);
     else if (k0 <= 1)
         listN = leaf_loop<kCount, 1>(c, P, Phi, ch0, cl0, active, iters, k0, len0, off0);

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
@@ -30,6 +31,26 @@ constexpr int kDefaultChunkWork = 1 << 20;
 constexpr uint32_t kInlineKeys = 512;   // codes downloaded together with the status block
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Rows tested at the partial-candidate level when no tuned value exists
+// (-1: no partial level). The level pays when a random window is rarely within
+// d of a candidate (E = expected such windows per sequence of a uniform
+// i.i.d. instance, small for (17,5) and (19,6), about 0.5 for (13,4) and
+// (15,5), where it was measured slower) and the tree has nodes with more than
+// three changed positions (d >= 5).
+int default_partial_rows(int n, int m, int l, int d)
+{
+    (void)n;
+    if (d < 5)
+        return -1;
+    double p = 0, c = 1;   // P(Binomial(l, 3/4) <= d)
+    for (int i = 0; i <= d; ++i) {
+        p += c * std::pow(0.75, i) * std::pow(0.25, l - i);
+        c = c * (l - i) / (i + 1);
+    }
+    const double E = (m - l + 1) * p;
+    return E < 0.15 ? (d >= 6 ? 4 : 1) : -1;
+}
 
 uint32_t pow2_at_least(size_t v)
 {
@@ -240,6 +261,7 @@ struct pms_ctx {
         int prune_rows = 0;   // 0: all rows
         int ctas_per_sm = 0;
         int grab = 0;         // node batch policy (InstDev.grab)
+        int partial_rows = 0; // rows of the partial-candidate level: -1 none, 0 default, k > 0
         double ms = 0;
     };
     std::map<std::tuple<int, int, int, int>, Tuning> tuned;
@@ -269,6 +291,18 @@ struct pms_ctx {
             return opt.grab;
         const Tuning *t = tuning(n, m, l, d);
         return t ? t->grab : 0;
+    }
+    // rows the partial-candidate level tests (0: no partial level)
+    int partial_rows_for(int n, int m, int l, int d) const
+    {
+        int v = opt.partial_rows;
+        if (v == 0) {
+            const Tuning *t = tuning(n, m, l, d);
+            v = t ? t->partial_rows : 0;
+        }
+        if (v == 0)
+            v = default_partial_rows(n, m, l, d);
+        return v < 0 ? 0 : std::min(v, n - 1);
     }
     int prune_rows_for(int n, int m, int l, int d) const
     {
@@ -460,6 +494,7 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
         in.cps = ct.cps;
         in.grab = h->grab_for(s.n, s.m, s.l, s.d);
         in.prune_rows = h->prune_rows_for(s.n, s.m, s.l, s.d);
+        in.partial_rows = h->partial_rows_for(s.n, s.m, s.l, s.d);
         in.ctab = (int)P.ctab.size();
         P.ctab.insert(P.ctab.end(), ct.tab.begin(), ct.tab.end());
         in.seq_off = (long long)P.seq_bytes;
@@ -803,6 +838,8 @@ static int autotune_class(pms_ctx *h, int n, int m, int l, int d, pms_ctx::Tunin
     h->opt.chunk_work = 0;
     h->opt.ctas_per_sm = 0;
     h->opt.count_work = 0;
+    h->opt.grab = 0;
+    h->opt.partial_rows = 0;
     std::vector<InstSpec> specs{InstSpec{n, m, l, d, seqs.data()}};
     auto run = [&](const pms_ctx::Tuning &t, double &ms) -> int {
         h->tuned[key] = t;
@@ -821,6 +858,7 @@ static int autotune_class(pms_ctx *h, int n, int m, int l, int d, pms_ctx::Tunin
     cur.chunk_work = kDefaultChunkWork;
     cur.prune_rows = n - 1;
     cur.ctas_per_sm = std::max(1, h->occ[0]);
+    cur.partial_rows = default_partial_rows(n, m, l, d);
     int rc = run(cur, cur.ms);
     std::vector<int> prune_c = {n - 1, 8, 4, 2, 1};
     std::vector<int> work_c = {1 << 16, 1 << 18, 1 << 20, 1 << 22};
@@ -828,8 +866,10 @@ static int autotune_class(pms_ctx *h, int n, int m, int l, int d, pms_ctx::Tunin
     for (int c = std::max(1, h->occ[0]); c >= 1 && (int)cta_c.size() < 2; --c)
         cta_c.push_back(c);
     std::vector<int> grab_c = {0, 1, 32, 64};
-    for (int dim = 0; dim < 4 && rc == PMS_OK; ++dim) {
-        const std::vector<int> &vals = dim == 0 ? prune_c : (dim == 1 ? work_c : (dim == 2 ? cta_c : grab_c));
+    std::vector<int> partial_c = {-1, 1, 2, 4};
+    for (int dim = 0; dim < 5 && rc == PMS_OK; ++dim) {
+        const std::vector<int> &vals =
+            dim == 0 ? prune_c : (dim == 1 ? work_c : (dim == 2 ? cta_c : (dim == 3 ? grab_c : partial_c)));
         for (int v : vals) {
             pms_ctx::Tuning t = cur;
             if (dim == 0) {
@@ -844,10 +884,14 @@ static int autotune_class(pms_ctx *h, int n, int m, int l, int d, pms_ctx::Tunin
                 if (v == cur.ctas_per_sm)
                     continue;
                 t.ctas_per_sm = v;
-            } else {
+            } else if (dim == 3) {
                 if (v == cur.grab)
                     continue;
                 t.grab = v;
+            } else {
+                if (v == cur.partial_rows || v > n - 1)
+                    continue;
+                t.partial_rows = v;
             }
             if ((rc = run(t, t.ms)))
                 break;
@@ -1177,6 +1221,7 @@ static bool served_admit(Served *S, Request *r)
     in.cps = ct.cps;
     in.grab = h->grab_for(r->n, r->m, r->l, r->d);
     in.prune_rows = h->prune_rows_for(r->n, r->m, r->l, r->d);
+    in.partial_rows = h->partial_rows_for(r->n, r->m, r->l, r->d);
     in.q = r->n;
     in.nseed = 1;
     in.seq_off = (long long)(off + L.seqs);
@@ -1477,7 +1522,7 @@ int pms_set_options(pms_ctx *h, const pms_options *opt)
     if (!h || !opt)
         return PMS_EINVAL;
     if (opt->ctas_per_sm < 0 || opt->chunk_work < 0 || opt->grab < 0 || opt->serve_wave_items < 0 || opt->smem_rows < 0 ||
-        opt->seed_mode < 0 || opt->seed_mode > 1 || opt->quorum < 0 ||
+        opt->seed_mode < 0 || opt->seed_mode > 1 || opt->quorum < 0 || opt->partial_rows < -1 ||
         opt->serve_max_inflight < 0 || opt->serve_max_inflight > 1024)
         return h->fail(PMS_EINVAL, "negative option");
     std::lock_guard<std::recursive_mutex> g(h->mu);
@@ -1687,7 +1732,7 @@ int pms_autotune(pms_ctx *h, int n, int m, int l, int d, pms_tuning *out)
     if ((rc = autotune_class(h, n, m, l, d, t)))
         return rc;
     if (out)
-        *out = pms_tuning{t.chunk_work, t.prune_rows, t.ctas_per_sm, t.grab, t.ms};
+        *out = pms_tuning{t.chunk_work, t.prune_rows, t.ctas_per_sm, t.grab, t.partial_rows, t.ms};
     return PMS_OK;
 }
 
@@ -1700,11 +1745,11 @@ int pms_save_tuning(const pms_ctx *h, const char *path)
     FILE *f = std::fopen(path, "w");
     if (!f)
         return hm->fail(PMS_EINVAL, "cannot write %s", path);
-    std::fprintf(f, "# l d n_bucket m_bucket chunk_work prune_rows ctas_per_sm grab ms\n");
+    std::fprintf(f, "# l d n_bucket m_bucket chunk_work prune_rows ctas_per_sm grab partial_rows ms\n");
     for (const auto &kv : h->tuned)
-        std::fprintf(f, "%d %d %d %d %d %d %d %d %.6f\n", std::get<0>(kv.first), std::get<1>(kv.first),
+        std::fprintf(f, "%d %d %d %d %d %d %d %d %d %.6f\n", std::get<0>(kv.first), std::get<1>(kv.first),
                      std::get<2>(kv.first), std::get<3>(kv.first), kv.second.chunk_work, kv.second.prune_rows,
-                     kv.second.ctas_per_sm, kv.second.grab, kv.second.ms);
+                     kv.second.ctas_per_sm, kv.second.grab, kv.second.partial_rows, kv.second.ms);
     std::fclose(f);
     return PMS_OK;
 }
@@ -1722,17 +1767,18 @@ int pms_load_tuning(pms_ctx *h, const char *path)
     while (std::fgets(line, sizeof line, f)) {
         if (line[0] == '#')
             continue;
-        int l, d, nb, mb, cw, pr, cta, gr;
+        int l, d, nb, mb, cw, pr, cta, gr, pp;
         double ms;
-        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %lf", &l, &d, &nb, &mb, &cw, &pr, &cta, &gr, &ms) != 9)
+        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d %lf", &l, &d, &nb, &mb, &cw, &pr, &cta, &gr, &pp, &ms) != 10)
             continue;
-        if (l < 1 || l > PMS_LMAX || d < 0 || d >= l || cw < 0 || pr < 0 || cta < 0 || gr < 0)
+        if (l < 1 || l > PMS_LMAX || d < 0 || d >= l || cw < 0 || pr < 0 || cta < 0 || gr < 0 || pp < -1)
             continue;
         pms_ctx::Tuning t;
         t.chunk_work = cw;
         t.prune_rows = pr;
         t.ctas_per_sm = cta;
         t.grab = gr;
+        t.partial_rows = pp;
         t.ms = ms;
         h->tuned[std::make_tuple(l, d, nb, mb)] = t;
         ++loaded;
@@ -1989,6 +2035,10 @@ extern "C" int pms_solve_device_noalloc(const uint8_t *d_seqs, int n, int m, int
     in.cps = cps;
     in.grab = 0;
     in.prune_rows = default_prune_rows(n, d);
+    {
+        const int pr = default_partial_rows(n, m, l, d);
+        in.partial_rows = pr < 0 ? 0 : std::min(pr, n - 1);
+    }
     in.q = n;        // the PMS problem
     in.nseed = 1;
     in.ctab = 0;

@@ -69,6 +69,48 @@ def test_rows_in_global_scratch_match_oracle(oracle_, case):
     c.close()
 
 
+DEEP = [
+    # (n, m, l, d, seed) -- trees with nodes of 4 or more changed positions
+    (4, 45, 7, 4, 7),
+    (5, 40, 12, 5, 14),
+    (6, 40, 13, 5, 21),
+    (8, 60, 12, 4, 22),
+    (4, 30, 14, 6, 23),
+    (3, 25, 10, 6, 24),    # 2d > l with a deep tree
+]
+
+
+_DEEP_WANT = {}
+
+
+@pytest.mark.parametrize("partial_rows", [-1, 1, 2, 5])
+@pytest.mark.parametrize("case", DEEP, ids=lambda c: "n{}_m{}_l{}_d{}".format(*c[:4]))
+def test_partial_level_matches_oracle(oracle_, case, partial_rows):
+    # the partial-candidate level (letters fixed above the three lowest changed
+    # positions, tested against the first rows before the leaves) off and on
+    n, m, l, d, seed = case
+    inst = pi.planted_instance(n, m, l, d, seed)
+    seqs = pi.random_sequences(n, m, seed + 555)
+    if case not in _DEEP_WANT:
+        _DEEP_WANT[case] = (oracle_.solve(inst.seqs, l, d, cap=1 << 24), oracle_.solve(seqs, l, d, cap=1 << 24))
+    want_planted, want_random = _DEEP_WANT[case]
+    c = pms.Context(0)
+    c.set_options(partial_rows=partial_rows)
+    assert np.array_equal(c.solve(inst.seqs, l, d), want_planted)
+    assert np.array_equal(c.solve(seqs, l, d), want_random)
+    c.set_options(partial_rows=partial_rows, smem_rows=8)    # rows in global scratch
+    assert np.array_equal(c.solve(inst.seqs, l, d), want_planted)
+    c.close()
+
+
+@pytest.mark.parametrize("l,d,partial_rows", [(13, 4, 3), (15, 4, 1), (17, 5, -1), (17, 5, 4)])
+def test_partial_level_full_size_sampled_seeds(oracle_, l, d, partial_rows):
+    c = pms.Context(0)
+    c.set_options(partial_rows=partial_rows)
+    _sampled_parity(c, oracle_, l, d, 2, 4)
+    c.close()
+
+
 def test_plain_9_2_full_size_matches_oracle(ctx, oracle_):
     for seed in (1, 2, 3):
         inst = pi.plain_instance(9, 2, seed=seed)
