@@ -68,10 +68,14 @@ typedef struct {
 typedef struct {
     int ctas_per_sm;       /* resident CTAs of the verification kernel per SM */
     int chunk_work;        /* target work of one queue item, in candidate units */
-    int grab;              /* tree-node filter: 0 = breadth-first batches of up to
-                              128 nodes (default); 1 = per-lane row walk with
-                              refill; g > 1 = batches shrinking to g nodes as a
-                              queue item runs out */
+    int grab;              /* tree-node filter: 0 = the tuned value, else 1;
+                              1 = lane-asynchronous walk: every lane takes one
+                              node through the rows, leaves a row at the
+                              node's own first feasible occurrence and takes
+                              the next node at once (default); g > 1 =
+                              breadth-first batches of up to 128 nodes that
+                              shrink to g nodes as a queue item runs out
+                              (g >= 128: fixed batches of 128) */
     size_t max_motifs;     /* raw motif capacity per instance (rounded to 2^k) */
     int count_work;        /* 1: also count comparisons (slower; for profiling) */
     int serve_wave_items;  /* served form: queue items per wave launch */

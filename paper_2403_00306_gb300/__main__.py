@@ -1,6 +1,7 @@
 """Command line: solve one seeded synthetic planted-motif instance on the GPU.
 
     python -m paper_2403_00306_gb300 --l 15 --d 4 [--n 20 --m 600 --seed 1 --repeat 1 --count]
+                                     [--opt grab=1 --opt partial_rows=-1 ...]
 
 Prints the motifs found and the solve's counters/timings (JSON). Used, for
 instance, as the target of ncu captures of one solve.
@@ -26,11 +27,19 @@ def main() -> None:
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--count", action="store_true", help="also count comparisons (count-mode kernel)")
     ap.add_argument("--device", type=int, default=0)
+    ap.add_argument("--opt", action="append", default=[], metavar="NAME=VALUE",
+                    help="set a pms_options field (repeatable)")
     a = ap.parse_args()
+    opts = {}
+    for kv in a.opt:
+        k, v = kv.split("=", 1)
+        opts[k] = int(v)
     inst = pi.planted_instance(a.n, a.m, a.l, a.d, a.seed)
     with pms.Context(a.device) as ctx:
         if a.count:
-            ctx.set_options(count_work=1)
+            opts["count_work"] = 1
+        if opts:
+            ctx.set_options(**opts)
         for _ in range(a.repeat):
             codes = ctx.solve(inst.seqs, a.l, a.d)
         stats = ctx.stats()

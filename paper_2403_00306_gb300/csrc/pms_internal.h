@@ -26,7 +26,7 @@ struct InstDev {
     int W;                 // windows per sequence: m - l + 1
     int NW;                // 32-bit words of one compatibility mask row: ceil(W / 32)
     int cps;               // queue chunks per seed
-    int grab;              // 0: fixed node batches; 1: row walk with refill; > 1: guided batches shrinking to this size
+    int grab;              // 0: fixed node batches; 1: lane-asynchronous walk; > 1: guided batches shrinking to this size
     int ctab;              // offset (ints) of this instance's table in the chunk arena:
                            //   levoff[0..d+1] then cps pairs (g0, g1)
     int prune_rows;        // rows checked for a feasible occurrence before leaves are tested

@@ -39,8 +39,13 @@ struct __align__(16) WarpSmem {
     uint2 rb1[kRbCap + 4];      // scratch reduced row for rows 1..
     uint2 list[kListCap];       // candidates that survived row 0
     uint32_t subs[kSubBatch];   // position subsets being filtered
-    uint8_t lmiss[kListCap];    // quorum form: rows each listed candidate has missed
-    uint8_t smiss[kSubBatch];   // quorum form: rows each subset has missed
+    union {
+        struct {
+            uint8_t lmiss[kListCap];    // quorum form: rows each listed candidate has missed
+            uint8_t smiss[kSubBatch];   // quorum form: rows each subset has missed
+        } q;
+        uint32_t stash[68];             // node walk: its state parked while leaves are expanded
+    } u;
 };
 
 struct __align__(16) CtaSmem {
@@ -48,6 +53,8 @@ struct __align__(16) CtaSmem {
     int row_len[kNMax];      // indexed by sequence
     int row_off[kNMax];      // indexed by sequence: first entry of its row (multiple of 4)
     int row_order[kNMax];    // sequences 1..n-1, smallest row first
+    int rank_off4[kNMax];    // by rank in that order: first entry quad of the row
+    int rank_len4[kNMax];    // by rank in that order: entry quads of the row (padded size / 4)
     unsigned long long g;
     int inst, seed, chunk;
     int cached_inst, cached_seed;
@@ -622,119 +629,161 @@ __device__ __forceinline__ int filter_subsets(const WarpCtx &c, int N)
     return N;
 }
 
-// Depth-first-free row walk of the tree nodes of a chunk: every lane holds
-// one node P and the position r of the next row (smallest rows first) it has
-// to pass; a step tests each lane's node against its own row (the bound
-// popc(D_w ^ P) <= d), a node failing a row is dismissed, a node passing the
-// last filtered row is queued for leaf expansion, and freed lanes take the
-// next nodes of the chunk at once, so lanes stay busy however unevenly nodes
-// are pruned. Queued nodes are expanded (expand_subset) when the queue
-// fills and at the end.
+// Lane-asynchronous node filter of a chunk: every lane holds one tree node P
+// and its position in the rows (row rank r, entry quad e4); each step a lane
+// tests the next 8 entries of its own row with the bound popc(D_w ^ P) <= d.
+// A hit moves the lane's node to the next row, a row scanned to its end
+// dismisses the node, a node that passes the last filtered row goes to the
+// expansion queue, and a free lane takes the next node of the warp's pool at
+// once. So every node stops scanning a row at its own first hit (the
+// sequential early-exit rule) instead of waiting for the slowest node of a
+// batch. The pool holds nodes claimed 32 to 64 at a time and unranked by all
+// lanes together. subs[0..64) is the pool, subs[64..128) the queue.
+//
+// walk_run runs the walk until 32 or more nodes are queued or the chunk is
+// done, and returns the queue length; the caller expands the queued nodes
+// and calls it again. Between calls the walk's state is parked in the warp's
+// shared memory (stash[0..32): each lane's node; stash[32..64): its row rank,
+// quad and whether it holds a node; stash[64..67): pool position, pool size,
+// chunk exhausted), so that no register is held across the leaf expansion.
+__device__ __forceinline__ void walk_init(const WarpCtx &c)
+{
+    uint32_t *st = c.ws->u.stash;
+    st[c.lane] = 0u;
+    st[32 + c.lane] = 0u;
+    if (c.lane < 3)
+        st[64 + c.lane] = 0u;
+    __syncwarp();
+}
+
 template <bool kCount>
-__device__ __forceinline__ void walk_subsets(const WarpCtx &c, const int *tab, int g1, CtaSmem &cs)
+__device__ __forceinline__ int walk_run(const WarpCtx &c, const int *tab, int g0, int g1, CtaSmem &cs, bool &finished)
 {
     const InstDev &in = c.in;
     const int d = in.d;
     const int nrows = min(in.prune_rows, in.n - 1);
-    uint32_t *queue = c.ws->subs;
+    uint32_t *pool = c.ws->subs;
+    uint32_t *queue = c.ws->subs + 64;
+    uint32_t *st = c.ws->u.stash;
+    const uint4 *D4 = reinterpret_cast<const uint4 *>(c.rows.D);
+    const int claim = (g1 - g0 + 2 * kWarps - 1) / (2 * kWarps);
+    const volatile uint32_t *vst = st;
+    uint32_t P = vst[c.lane];
+    const uint32_t w0 = vst[32 + c.lane];
+    int r = (int)(w0 & 0xffu);
+    int e4 = (int)((w0 >> 8) & 0x7fffffu);
+    bool has = (w0 >> 31) != 0u;
+    int pool_pos = (int)vst[64], pool_n = (int)vst[65];
+    bool exhausted = vst[66] != 0u;
+    int off4 = 0, len4 = 0;
+    if (nrows > 0) {
+        const int rr = min(r, nrows - 1);
+        off4 = cs.rank_off4[rr];
+        len4 = cs.rank_len4[rr];
+    }
     int qn = 0;
-    int pool_lo = 0, pool_hi = 0;      // subsets claimed by this warp, not yet started
-    bool exhausted = false;            // the chunk has no unclaimed subsets left
-    uint32_t P = 0;
-    int r = 0;
-    bool has = false;
+    finished = false;
+    __syncwarp();
     for (;;) {
-        // refill free lanes from the warp's pool, claiming more when it runs dry
         uint32_t freem = __ballot_sync(kFull, !has);
-        while (freem) {
-            if (pool_lo >= pool_hi) {
-                if (exhausted)
-                    break;
+        if (freem) {
+            int avail = pool_n - pool_pos;
+            if (avail < __popc(freem) && !exhausted) {
+                // move the unstarted rest to the front and claim more; claims
+                // are sized so that every warp of the CTA gets a share of small chunks
+                uint32_t keep = 0u;
+                if (c.lane < avail)
+                    keep = pool[pool_pos + c.lane];
+                __syncwarp();
+                if (c.lane < avail)
+                    pool[c.lane] = keep;
+                const int want = min(64 - avail, max(32, claim));
                 int start = 0;
                 if (c.lane == 0)
-                    start = atomicAdd(&cs.next, 64);
+                    start = atomicAdd(&cs.next, want);
                 start = __shfl_sync(kFull, start, 0);
-                if (start >= g1) {
+                const int got = start < g1 ? min(want, g1 - start) : 0;
+                if (start + want >= g1)
                     exhausted = true;
-                    break;
+                for (int j = c.lane; j < got; j += 32) {
+                    const int g = start + j;
+                    int lev = 0;
+                    while (tab[lev + 1] <= g)
+                        ++lev;
+                    pool[avail + j] = unrank_subset((uint32_t)(g - tab[lev]), lev, in.l, cs.binom);
                 }
-                pool_lo = start;
-                pool_hi = min(start + 64, g1);
+                __syncwarp();
+                if (kCount && c.lane == 0)
+                    c.cnt[kCntSubsets] += got;
+                pool_pos = 0;
+                pool_n = avail + got;
+                avail = pool_n;
             }
-            const int take = min(__popc(freem), pool_hi - pool_lo);
+            const int take = min(__popc(freem), avail);
             const int rank = __popc(freem & c.lt);
             if (!has && rank < take) {
-                const int g = pool_lo + rank;
-                int lev = 0;
-                while (tab[lev + 1] <= g)
-                    ++lev;
-                P = unrank_subset((uint32_t)(g - tab[lev]), lev, in.l, cs.binom);
+                P = pool[pool_pos + rank];
                 r = 0;
+                e4 = 0;
                 has = true;
+                if (nrows > 0) {
+                    off4 = cs.rank_off4[0];
+                    len4 = cs.rank_len4[0];
+                }
             }
-            pool_lo += take;
-            if (kCount && c.lane == 0)
-                c.cnt[kCntSubsets] += take;
-            freem = __ballot_sync(kFull, !has);
+            pool_pos += take;
         }
-        if (!__any_sync(kFull, has))
+        if (!__any_sync(kFull, has)) {
+            finished = true;
             break;
-        if (nrows > 0) {
-            // one row per lane
-            int ri = 0, len4 = 0;
-            const uint4 *D4 = reinterpret_cast<const uint4 *>(c.rows.D);
-            if (has) {
-                ri = c.cs->row_order[r];
-                len4 = (c.cs->row_len[ri] + 3) >> 2;
-                D4 = reinterpret_cast<const uint4 *>(c.rows.D + c.cs->row_off[ri]);
-            }
-            const int maxlen4 = __reduce_max_sync(kFull, (unsigned)len4);
-            int m0 = 64, m1 = 64;
-            int e4 = 0;
-            for (; e4 < maxlen4; ++e4) {
-                if (e4 < len4) {
-                    const uint4 v = D4[e4];
-                    m0 = min(m0, __popc(v.x ^ P));
-                    m1 = min(m1, __popc(v.y ^ P));
-                    m0 = min(m0, __popc(v.z ^ P));
-                    m1 = min(m1, __popc(v.w ^ P));
-                }
-                if ((e4 & 3) == 3 && __all_sync(kFull, !has || min(m0, m1) <= d)) {
-                    ++e4;
-                    break;
-                }
-            }
+        }
+        // one step of every lane: the next 8 entries of its row, as selects
+        // rather than branches (a lane without a node reads the first quad of
+        // the rows and ignores the result)
+        bool done = false;
+        if (nrows == 0) {
+            done = has;
+        } else {
+            const int a4 = has ? off4 + e4 : 0;
+            const bool second = has && e4 + 1 < len4;
+            const uint4 v = D4[a4];
+            const uint4 u = D4[second ? a4 + 1 : a4];
+            const int mn = min(min(min(__popc(v.x ^ P), __popc(v.y ^ P)), min(__popc(v.z ^ P), __popc(v.w ^ P))),
+                               min(min(__popc(u.x ^ P), __popc(u.y ^ P)), min(__popc(u.z ^ P), __popc(u.w ^ P))));
             if (kCount && has)
-                c.cnt[kCntCmpReduce] += 4ull * min(e4, len4);
-            const bool pass = has && min(m0, m1) <= d;
-            if (has && !pass) {
-                has = false;
-                if (kCount)
-                    c.cnt[kCntPruned] += 1;
+                c.cnt[kCntCmpReduce] += second ? 8 : 4;
+            const bool hit = has && mn <= d;
+            e4 = hit ? 0 : e4 + 2;
+            r += hit ? 1 : 0;
+            done = hit && r == nrows;
+            if (hit && r < nrows) {
+                off4 = cs.rank_off4[r];
+                len4 = cs.rank_len4[r];
             }
-            if (pass)
-                ++r;
+            const bool dismiss = has && !hit && e4 >= len4;
+            if (kCount && dismiss)
+                c.cnt[kCntPruned] += 1;
+            has = has && !dismiss;
         }
         // nodes that passed every filtered row go to the expansion queue
-        const bool done = has && r >= nrows;
         const uint32_t bal = __ballot_sync(kFull, done);
         if (done) {
             queue[qn + __popc(bal & c.lt)] = P;
             has = false;
         }
         qn += __popc(bal);
-        if (qn > kSubBatch - 32) {
-            __syncwarp();
-            for (int i = 0; i < qn; ++i)
-                expand_subset<kCount>(c, queue[i]);
-            __syncwarp();
-            qn = 0;
-        }
+        if (qn >= 32)
+            break;
+    }
+    st[c.lane] = P;
+    st[32 + c.lane] = (uint32_t)r | ((uint32_t)e4 << 8) | (has ? 0x80000000u : 0u);
+    if (c.lane == 0) {
+        st[64] = (uint32_t)pool_pos;
+        st[65] = (uint32_t)pool_n;
+        st[66] = exhausted ? 1u : 0u;
     }
     __syncwarp();
-    for (int i = 0; i < qn; ++i)
-        expand_subset<kCount>(c, queue[i]);
-    __syncwarp();
+    return qn;
 }
 
 // ---------------------------------------------------------------------------
@@ -772,7 +821,7 @@ __device__ __forceinline__ void finish_list_q(const WarpCtx &c, uint32_t P, int 
     const int nrows = in.n - 1;
     const int budget = in.n - in.q, need = in.q - 1;
     uint2 *list = c.ws->list;
-    uint8_t *lm = c.ws->lmiss;
+    uint8_t *lm = c.ws->u.q.lmiss;
     __syncwarp();
     for (int r = 0; r < nrows && N > 0; ++r) {
         const int ri = c.cs->row_order[r];
@@ -847,7 +896,7 @@ __device__ __forceinline__ void expand_subset_q(const WarpCtx &c, uint32_t P)
         if (active) {
             const int pos = listN + __popc(bal & c.lt);
             list[pos] = make_uint2(ch0 ^ Dh, cl0 ^ Dl);
-            c.ws->lmiss[pos] = 0;
+            c.ws->u.q.lmiss[pos] = 0;
             if (kCount)
                 c.cnt[kCntTested] += 1;
         }
@@ -877,7 +926,7 @@ __device__ __forceinline__ int filter_subsets_q(const WarpCtx &c, int N)
     const int budget = in.n - in.q;
     const int nrows = min(in.prune_rows, in.n - 1);
     uint32_t *subs = c.ws->subs;
-    uint8_t *sm = c.ws->smiss;
+    uint8_t *sm = c.ws->u.q.smiss;
     for (int r = 0; r < nrows && N > 0; ++r) {
         const int ri = c.cs->row_order[r];
         const int len = c.cs->row_len[ri];
@@ -955,11 +1004,15 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
             cs.row_len[lane + 1] = la;
             cs.row_off[lane + 1] = oa;
             cs.row_order[ra] = lane + 1;
+            cs.rank_off4[ra] = oa >> 2;
+            cs.rank_len4[ra] = pa >> 2;
         }
         if (lane + 32 < R) {
             cs.row_len[lane + 33] = lb;
             cs.row_off[lane + 33] = ob;
             cs.row_order[rb] = lane + 33;
+            cs.rank_off4[rb] = ob >> 2;
+            cs.rank_len4[rb] = pb >> 2;
         }
         if (lane == 0) {
             cs.total_rows = total;
@@ -1111,7 +1164,7 @@ __global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
                         while (tab[lev + 1] <= g)
                             ++lev;
                         subs[j] = unrank_subset((uint32_t)(g - tab[lev]), lev, in.l, cs.binom);
-                        wsm[warp].smiss[j] = 0;
+                        wsm[warp].u.q.smiss[j] = 0;
                     }
                     __syncwarp();
                     if constexpr (kCount) {
@@ -1128,14 +1181,24 @@ __global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
                     __syncwarp();
                 }
             } else if (in.grab == 1) {
-                walk_subsets<kCount>(c, tab, g1, cs);
+                walk_init(c);
+                for (;;) {
+                    bool fin;
+                    const int qn = walk_run<kCount>(c, tab, g0, g1, cs, fin);
+                    const uint32_t *queue = wsm[warp].subs + 64;
+                    for (int i = 0; i < qn; ++i)
+                        expand_subset<kCount>(c, queue[i]);
+                    __syncwarp();
+                    if (fin)
+                        break;
+                }
             } else {
                 uint32_t *subs = wsm[warp].subs;
                 // batch filter: batches of up to kSubBatch subsets (large batches
                 // keep the breadth-first filter's lanes full), small chunks split
                 // so that every warp gets work; with in.grab > 1 batches shrink
                 // toward in.grab as the chunk runs out (guided self-scheduling);
-                // in.grab == 1 selects the row walk above instead
+                // in.grab == 1 selects the lane walk above instead
                 const int per_warp = (g1 - g0 + 2 * kWarps - 1) / (2 * kWarps);
                 const int fixed = min(kSubBatch, max(32, (per_warp + 31) & ~31));
                 for (;;) {

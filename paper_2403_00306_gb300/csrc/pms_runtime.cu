@@ -28,6 +28,7 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kDefaultChunkWork = 1 << 20;
+constexpr int kDefaultGrab = 1;         // node filter: the lane-asynchronous walk
 constexpr uint32_t kInlineKeys = 512;   // codes downloaded together with the status block
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -260,7 +261,7 @@ struct pms_ctx {
         int chunk_work = 0;
         int prune_rows = 0;   // 0: all rows
         int ctas_per_sm = 0;
-        int grab = 0;         // node batch policy (InstDev.grab)
+        int grab = 0;         // node filter (InstDev.grab; 0: the default)
         int partial_rows = 0; // rows of the partial-candidate level: -1 none, 0 default, k > 0
         double ms = 0;
     };
@@ -285,12 +286,14 @@ struct pms_ctx {
         const Tuning *t = tuning(n, m, l, d);
         return t && t->chunk_work > 0 ? t->chunk_work : 0;
     }
+    // node filter of the verification kernel (InstDev.grab): 1 = lane walk
+    // (default), g > 1 = breadth-first batches shrinking to g nodes
     int grab_for(int n, int m, int l, int d) const
     {
         if (opt.grab > 0)
             return opt.grab;
         const Tuning *t = tuning(n, m, l, d);
-        return t ? t->grab : 0;
+        return t && t->grab > 0 ? t->grab : kDefaultGrab;
     }
     // rows the partial-candidate level tests (0: no partial level)
     int partial_rows_for(int n, int m, int l, int d) const
@@ -859,13 +862,14 @@ static int autotune_class(pms_ctx *h, int n, int m, int l, int d, pms_ctx::Tunin
     cur.prune_rows = n - 1;
     cur.ctas_per_sm = std::max(1, h->occ[0]);
     cur.partial_rows = default_partial_rows(n, m, l, d);
+    cur.grab = kDefaultGrab;
     int rc = run(cur, cur.ms);
     std::vector<int> prune_c = {n - 1, 8, 4, 2, 1};
     std::vector<int> work_c = {1 << 16, 1 << 18, 1 << 20, 1 << 22};
     std::vector<int> cta_c;
     for (int c = std::max(1, h->occ[0]); c >= 1 && (int)cta_c.size() < 2; --c)
         cta_c.push_back(c);
-    std::vector<int> grab_c = {0, 1, 32, 64};
+    std::vector<int> grab_c = {1, 128, 32};
     std::vector<int> partial_c = {-1, 1, 2, 4};
     for (int dim = 0; dim < 5 && rc == PMS_OK; ++dim) {
         const std::vector<int> &vals =

@@ -111,6 +111,32 @@ def test_partial_level_full_size_sampled_seeds(oracle_, l, d, partial_rows):
     c.close()
 
 
+@pytest.mark.parametrize("grab", [1, 32, 128])
+@pytest.mark.parametrize("case", [c for c in SMALL if c[0] > 1] + DEEP, ids=lambda c: "n{}_m{}_l{}_d{}".format(*c[:4]))
+def test_node_filter_modes_match_oracle(oracle_, case, grab):
+    # grab = 1: lane-asynchronous node walk (the default); 32: guided node
+    # batches; 128: fixed breadth-first batches of 128 nodes
+    n, m, l, d, seed = case
+    inst = pi.planted_instance(n, m, l, d, seed)
+    want = oracle_.solve(inst.seqs, l, d, cap=1 << 24)
+    c = pms.Context(0)
+    c.set_options(grab=grab)
+    assert np.array_equal(c.solve(inst.seqs, l, d), want)
+    c.set_options(grab=grab, smem_rows=8)    # rows in global scratch
+    assert np.array_equal(c.solve(inst.seqs, l, d), want)
+    c.set_options(grab=grab, partial_rows=2)
+    assert np.array_equal(c.solve(inst.seqs, l, d), want)
+    c.close()
+
+
+@pytest.mark.parametrize("l,d,grab", [(13, 4, 128), (15, 4, 1), (17, 5, 128), (15, 4, 32)])
+def test_node_filter_modes_full_size_sampled_seeds(oracle_, l, d, grab):
+    c = pms.Context(0)
+    c.set_options(grab=grab)
+    _sampled_parity(c, oracle_, l, d, 3, 4)
+    c.close()
+
+
 def test_plain_9_2_full_size_matches_oracle(ctx, oracle_):
     for seed in (1, 2, 3):
         inst = pi.plain_instance(9, 2, seed=seed)
