@@ -90,6 +90,23 @@ __device__ __forceinline__ uint64_t to_key(uint32_t h, uint32_t lo, int l)
     return key;
 }
 
+// Position of the r-th (0-based) set bit of v, for 0 <= r < popc(v): a binary
+// search over the bit counts of the halves, quarters, ... of the word.
+__device__ __forceinline__ int nth_set_bit(uint32_t v, int r)
+{
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const int cnt = __popc(v & ((1u << w) - 1u));
+        if (r >= cnt) {
+            r -= cnt;
+            v >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
 // A seed's feasible occurrences: per entry the mismatch mask D of the seed
 // and the window, and the window's planes; rows are padded to a multiple of 4
 // entries with copies of their last entry.
@@ -631,7 +648,7 @@ __device__ __forceinline__ int filter_subsets(const WarpCtx &c, int N)
 
 // Lane-asynchronous node filter of a chunk: every lane holds one tree node P
 // and its position in the rows (row rank r, entry quad e4); each step a lane
-// tests the next 8 entries of its own row with the bound popc(D_w ^ P) <= d.
+// tests the next 16 entries of its own row with the bound popc(D_w ^ P) <= d.
 // A hit moves the lane's node to the next row, a row scanned to its end
 // dismisses the node, a node that passes the last filtered row goes to the
 // expansion queue, and a free lane takes the next node of the warp's pool at
@@ -705,12 +722,27 @@ __device__ __forceinline__ int walk_run(const WarpCtx &c, const int *tab, int g0
                 const int got = start < g1 ? min(want, g1 - start) : 0;
                 if (start + want >= g1)
                     exhausted = true;
-                for (int j = c.lane; j < got; j += 32) {
+                // each lane unranks node start + 2j and steps to node start + 2j + 1:
+                // the next k-subset in colex order is the next larger integer with k
+                // bits set (Gosper's step), or the first (k+1)-subset at a level end
+                for (int j = 2 * c.lane; j < got; j += 64) {
                     const int g = start + j;
                     int lev = 0;
                     while (tab[lev + 1] <= g)
                         ++lev;
-                    pool[avail + j] = unrank_subset((uint32_t)(g - tab[lev]), lev, in.l, cs.binom);
+                    const uint32_t P0 = unrank_subset((uint32_t)(g - tab[lev]), lev, in.l, cs.binom);
+                    pool[avail + j] = P0;
+                    if (j + 1 < got) {
+                        uint32_t P1;
+                        if (g + 1 < tab[lev + 1]) {
+                            const uint32_t low = P0 & (0u - P0);
+                            const uint32_t up = P0 + low;
+                            P1 = up | (((P0 ^ up) >> 2) >> (__ffs(P0) - 1));
+                        } else {
+                            P1 = (1u << (lev + 1)) - 1u;
+                        }
+                        pool[avail + j + 1] = P1;
+                    }
                 }
                 __syncwarp();
                 if (kCount && c.lane == 0)
@@ -737,7 +769,7 @@ __device__ __forceinline__ int walk_run(const WarpCtx &c, const int *tab, int g0
             finished = true;
             break;
         }
-        // one step of every lane: the next 8 entries of its row, as selects
+        // one step of every lane: the next 16 entries of its row, as selects
         // rather than branches (a lane without a node reads the first quad of
         // the rows and ignores the result)
         bool done = false;
@@ -745,15 +777,21 @@ __device__ __forceinline__ int walk_run(const WarpCtx &c, const int *tab, int g0
             done = has;
         } else {
             const int a4 = has ? off4 + e4 : 0;
-            const bool second = has && e4 + 1 < len4;
-            const uint4 v = D4[a4];
-            const uint4 u = D4[second ? a4 + 1 : a4];
-            const int mn = min(min(min(__popc(v.x ^ P), __popc(v.y ^ P)), min(__popc(v.z ^ P), __popc(v.w ^ P))),
-                               min(min(__popc(u.x ^ P), __popc(u.y ^ P)), min(__popc(u.z ^ P), __popc(u.w ^ P))));
+            const int lim = has ? len4 - e4 : 1;   // quads left in the row (>= 1)
+            // quads past the row's end re-read quad e4 (no effect on the minimum)
+            const uint4 v0 = D4[a4];
+            const uint4 v1 = D4[lim > 1 ? a4 + 1 : a4];
+            const uint4 v2 = D4[lim > 2 ? a4 + 2 : a4];
+            const uint4 v3 = D4[lim > 3 ? a4 + 3 : a4];
+            const int m0 = min(min(__popc(v0.x ^ P), __popc(v0.y ^ P)), min(__popc(v0.z ^ P), __popc(v0.w ^ P)));
+            const int m1 = min(min(__popc(v1.x ^ P), __popc(v1.y ^ P)), min(__popc(v1.z ^ P), __popc(v1.w ^ P)));
+            const int m2 = min(min(__popc(v2.x ^ P), __popc(v2.y ^ P)), min(__popc(v2.z ^ P), __popc(v2.w ^ P)));
+            const int m3 = min(min(__popc(v3.x ^ P), __popc(v3.y ^ P)), min(__popc(v3.z ^ P), __popc(v3.w ^ P)));
+            const int mn = min(min(m0, m1), min(m2, m3));
             if (kCount && has)
-                c.cnt[kCntCmpReduce] += second ? 8 : 4;
+                c.cnt[kCntCmpReduce] += 4 * min(lim, 4);
             const bool hit = has && mn <= d;
-            e4 = hit ? 0 : e4 + 2;
+            e4 = hit ? 0 : e4 + 4;
             r += hit ? 1 : 0;
             done = hit && r == nrows;
             if (hit && r < nrows) {
@@ -1038,7 +1076,7 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
             int base = 0;
             for (int k0 = 0; k0 < NW; k0 += 32) {
                 const int k = k0 + lane;
-                uint32_t bits = k < NW ? mr[k] : 0u;
+                const uint32_t bits = k < NW ? mr[k] : 0u;
                 const int c = __popc(bits);
                 int incl = c;
                 for (int o = 1; o < 32; o <<= 1) {
@@ -1046,16 +1084,30 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
                     if (lane >= o)
                         incl += y;
                 }
-                int pos = off + base + incl - c;
-                while (bits) {
-                    const int bt = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const uint2 w = s[32 * k + bt];
-                    Hd[pos] = w;
-                    Dd[pos] = (x.x ^ w.x) | (x.y ^ w.y);
-                    ++pos;
+                const int chunk = __shfl_sync(kFull, incl, 31);
+                // entry e of these 32 words goes to lane e % 32: its word t is the
+                // number of words whose inclusive count is <= e, its bit the
+                // (e - exclusive count of t)-th set bit of word t; all lanes load
+                // their window at once
+                for (int e0 = 0; e0 < chunk; e0 += 32) {
+                    const int e = e0 + lane;
+                    int t = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const int v = __shfl_sync(kFull, incl, t + step - 1);
+                        if (v <= e)
+                            t += step;
+                    }
+                    const uint32_t wb = __shfl_sync(kFull, bits, t);
+                    const int before = __shfl_sync(kFull, incl, t) - __shfl_sync(kFull, c, t);
+                    if (e < chunk) {
+                        const int bt = nth_set_bit(wb, e - before);
+                        const uint2 w = s[32 * (k0 + t) + bt];
+                        Hd[off + base + e] = w;
+                        Dd[off + base + e] = (x.x ^ w.x) | (x.y ^ w.y);
+                    }
                 }
-                base += __shfl_sync(kFull, incl, 31);
+                base += chunk;
             }
             __syncwarp();
             const int padded = (len + 3) & ~3;
