@@ -316,7 +316,7 @@ def bench_plain(args, ws, rank, local, dist, l, d) -> dict:
     peaks = load_peaks()
     fmax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak_cmp = probe * sms * fmax
-    achieved = cmp_per_launch / (verify_avg_ms / 1000.0)
+    achieved = cmp_per_launch / (verify_avg_ms / 1000.0) if verify_avg_ms > 0 else float("nan")
     clocks = clk.summary()
     ctx.close()
     W = m - l + 1

@@ -113,6 +113,11 @@ typedef struct {
                               windows of a random sequence are expected within
                               d of a candidate; none otherwise); -1: no partial
                               level; k > 0: k rows. Tree form, q = n. */
+    int graph;             /* one-instance solves (pms_solve, pms_solve_device)
+                              replay a CUDA graph captured on the first call
+                              of each plan (same shape and options), with the
+                              call's input and output pointers patched in:
+                              0 = on (default); -1 = launch kernel by kernel */
 } pms_options;
 
 /* A tuned schedule for one instance class (l, d, n rounded up to a power of

@@ -117,6 +117,9 @@ cudaError_t launch_sort_unique(const InstDev *inst, const int *inst_list, int nl
                                uint64_t *dense, uint32_t dense_cap, uint32_t *dense_total,
                                cudaStream_t st);
 cudaError_t init_tables();
+// Host handles of the pack and sort/unique kernels (to find their nodes in a captured graph).
+const void *pack_kernel_fn();
+const void *sort_unique_kernel_fn();
 cudaError_t launch_probe(int kind, int iters, int blocks, unsigned long long *cycles, unsigned long long *sink,
                          cudaStream_t st);
 

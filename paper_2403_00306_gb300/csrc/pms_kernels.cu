@@ -2186,6 +2186,16 @@ cudaError_t launch_classify(const InstDev *inst, int ninst, const long long *see
     return cudaGetLastError();
 }
 
+const void *pack_kernel_fn()
+{
+    return reinterpret_cast<const void *>(pack_kernel);
+}
+
+const void *sort_unique_kernel_fn()
+{
+    return reinterpret_cast<const void *>(sort_unique_kernel);
+}
+
 cudaError_t launch_pack(const InstDev *inst, int ninst, const long long *win_prefix, long long total_windows,
                         const uint8_t *seqs, uint2 *planes, uint32_t *flags, int blocks, cudaStream_t st)
 {

@@ -85,8 +85,12 @@ uint64_t ball_size(int l, int d)
 }
 
 // The queue chunks of one seed for (l, d): levoff[0..d+1] (first subset index
-// of each level in the seed's subset sequence), then (g0, g1) ranges cut so
-// that each holds about `work` candidate units (3^|P| + a fixed cost per subset).
+// of each level in the seed's subset sequence), then (g0, g1) ranges. A node
+// at level i costs 3^i leaf units plus kNodeUnits for its row filter; the
+// seed's nodes are cut into round(total / work) ranges of equal cost (at
+// least one), so that no chunk is a small remainder.
+constexpr double kNodeUnits = 24.0;
+
 struct ChunkTable {
     std::vector<int> tab;
     int cps = 0;
@@ -98,23 +102,29 @@ ChunkTable make_chunks(int l, int d, int work)
     std::vector<int> lev(d + 2, 0);
     for (int i = 0; i <= d; ++i)
         lev[i + 1] = lev[i] + (int)binom(l, i);
+    double total = 0;
+    for (int i = 0; i <= d; ++i)
+        total += (double)binom(l, i) * (std::pow(3.0, i) + kNodeUnits);
+    const int k = std::max(1, (int)std::lround(total / std::max(1, work)));
     std::vector<int> cuts;
     double acc = 0;
-    int start = 0, g = 0;
+    int start = 0, g = 0, made = 0;
     for (int i = 0; i <= d; ++i) {
-        const double w = std::pow(3.0, i) + 24.0;
+        const double w = std::pow(3.0, i) + kNodeUnits;
         long long remaining = (long long)binom(l, i);
         while (remaining > 0) {
-            long long room = (long long)std::ceil(std::max(1.0, (work - acc) / w));
+            // nodes of this level until the next cut (at (made + 1) / k of the total)
+            const double next_cut = total * (made + 1) / k;
+            const long long room = made + 1 < k ? std::max(1LL, (long long)std::ceil((next_cut - acc) / w)) : remaining;
             const long long take = std::min(room, remaining);
             acc += take * w;
             remaining -= take;
             g += (int)take;
-            if (acc >= work) {
+            if (made + 1 < k && acc >= next_cut - 1e-9) {
                 cuts.push_back(start);
                 cuts.push_back(g);
                 start = g;
-                acc = 0;
+                ++made;
             }
         }
     }
@@ -170,6 +180,47 @@ struct pms_ctx {
     std::vector<std::vector<uint64_t>> owned;   // result codes returned by the last solve call
     Served *served = nullptr;
 
+    // Captured pipelines of one-instance plans (CUDA graphs), keyed by the
+    // options and the plan's descriptors; replayed with the input and output
+    // pointers of each call patched into the pack and sort/unique nodes.
+    struct Graph {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        cudaGraphNode_t pack = nullptr, sort = nullptr;
+        cudaKernelNodeParams pack_p{}, sort_p{};
+        struct {
+            const void *inst;
+            int ninst;
+            const void *win_prefix;
+            long long total;
+            const void *seqs;
+            void *planes;
+            void *flags;
+        } pv{};
+        struct {
+            const void *inst;
+            const void *list;
+            void *raw;
+            void *tmp;
+            const void *raw_count;
+            const void *flags;
+            void *status;
+            void *dense;
+            uint32_t dense_cap;
+            void *dense_total;
+        } sv{};
+        void *pack_args[7] = {};
+        void *sort_args[10] = {};
+        DBuf meta;             // this plan's descriptors (the kernels of the graph read them)
+        uint64_t gen = 0;      // buffer generation the graph was captured with
+        uint64_t candidates = 0;
+        uint64_t last_use = 0;
+    };
+    std::map<std::string, Graph> graphs;
+    cudaStream_t cap_stream = nullptr;
+    uint64_t buf_gen = 0;      // bumped whenever a device buffer is freed or moved
+    uint64_t use_tick = 0;
+
     int fail(int code, const char *fmt, ...)
     {
         char buf[512];
@@ -221,6 +272,7 @@ struct pms_ctx {
             dev_free(b.p, b.cap);
             b.p = nullptr;
             b.cap = 0;
+            ++buf_gen;   // captured graphs that use the old buffer are stale
         }
         const size_t want = std::max(bytes, (size_t)(bytes * 5 / 4));
         void *p = dev_alloc(want);
@@ -538,18 +590,21 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
 // Enqueues the whole pipeline of a plan on h->stream. d_seq_src: device
 // address of the input bytes (internal arena or user memory). Descriptors are
 // staged in h->h_meta and uploaded. Output: status/dense in the result block.
-static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, StatusDev *status_out,
-                        uint64_t *dense_out, uint32_t dense_cap, bool count_mode)
+// Records a timing event; inside a stream capture (a graph's launches) as an
+// external event node, so that every replay records it.
+static void record_event(cudaEvent_t ev, cudaStream_t st, bool capturing)
 {
-    const size_t k = P.inst.size();
-    MetaLayout ml(P);
-    CtrLayout cl(k);
-    int rc;
-    if ((rc = h->ensure(h->d_meta, ml.total)) || (rc = h->ensure(h->d_ctr, cl.total)) ||
-        (rc = h->ensure(h->d_planes, P.planes * sizeof(uint2))) || (rc = h->ensure(h->d_raw, P.raw * 8)) ||
-        (rc = h->ensure(h->d_tmp, P.raw * 8)) || (rc = h->ensure(h->d_compat, P.compat * 4)) ||
-        (rc = h->ensure(h->d_rowlen, P.rowlen * 4)) || (rc = h->ensure(h->d_mode, (size_t)P.total_seeds)))
-        return rc;
+    if (capturing)
+        cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, st);
+}
+
+// CTAs of the verification kernel for a plan: resident CTAs per SM (capped by
+// the option or the tuned value of the first instance's class) x SMs, at most
+// one per queue item.
+static int plan_blocks(const pms_ctx *h, const Plan &P, bool count_mode)
+{
     int occ = h->occ[count_mode ? 1 : 0];
     if (h->opt.ctas_per_sm > 0) {
         occ = std::min(occ, h->opt.ctas_per_sm);
@@ -560,14 +615,12 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
             occ = std::min(occ, t->ctas_per_sm);
     }
     occ = std::max(occ, 1);
-    const long long blocks_ll = std::min<long long>((long long)h->num_sms * occ, std::max<long long>(P.total_items, 1));
-    const int blocks = (int)blocks_ll;
-    if ((rc = h->ensure(h->d_scratch, (size_t)blocks * 3 * (size_t)P.rows_cap * sizeof(uint32_t))))
-        return rc;
-    if ((rc = h->ensure_host(h->h_meta, h->h_meta_cap, ml.total)))
-        return rc;
-    // descriptors
-    char *hm = (char *)h->h_meta;
+    return (int)std::min<long long>((long long)h->num_sms * occ, std::max<long long>(P.total_items, 1));
+}
+
+// Host image of a plan's descriptors (layout ml) at dst.
+static void fill_meta(const Plan &P, const MetaLayout &ml, char *hm)
+{
     std::memcpy(hm + ml.inst, P.inst.data(), P.inst.size() * sizeof(InstDev));
     std::memcpy(hm + ml.seg, P.seg.data(), P.seg.size() * sizeof(Segment));
     std::memcpy(hm + ml.win, P.win_prefix.data(), P.win_prefix.size() * sizeof(long long));
@@ -575,18 +628,43 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     std::memcpy(hm + ml.seedp, P.seed_prefix.data(), P.seed_prefix.size() * sizeof(long long));
     std::memcpy(hm + ml.segp, P.seg_pair.data(), P.seg_pair.size() * sizeof(Segment));
     std::memcpy(hm + ml.ctab, P.ctab.data(), P.ctab.size() * sizeof(int));
+}
+
+// meta_dev: when given, the plan's descriptors are already on the device
+// there (a captured graph's own copy) and are neither staged nor uploaded.
+static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, StatusDev *status_out,
+                        uint64_t *dense_out, uint32_t dense_cap, bool count_mode, char *meta_dev = nullptr)
+{
+    const size_t k = P.inst.size();
+    MetaLayout ml(P);
+    CtrLayout cl(k);
+    int rc;
+    if ((rc = h->ensure(h->d_meta, ml.total)) || (rc = h->ensure(h->d_ctr, cl.total)) ||
+        (rc = h->ensure(h->d_planes, P.planes * sizeof(uint2))) || (rc = h->ensure(h->d_raw, P.raw * 8)) ||
+        (rc = h->ensure(h->d_tmp, P.raw * 8)) || (rc = h->ensure(h->d_compat, P.compat * 4)) ||
+        (rc = h->ensure(h->d_rowlen, P.rowlen * 4)) || (rc = h->ensure(h->d_mode, (size_t)P.total_seeds)))
+        return rc;
+    const int blocks = plan_blocks(h, P, count_mode);
+    if ((rc = h->ensure(h->d_scratch, (size_t)blocks * 3 * (size_t)P.rows_cap * sizeof(uint32_t))))
+        return rc;
     cudaStream_t st = h->stream;
-    char *dm = (char *)h->d_meta.p;
+    char *dm = meta_dev ? meta_dev : (char *)h->d_meta.p;
     char *dc = (char *)h->d_ctr.p;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(dm, hm, ml.total, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return h->cuda_fail(e, "upload descriptors");
+    if (!meta_dev) {
+        if ((rc = h->ensure_host(h->h_meta, h->h_meta_cap, ml.total)))
+            return rc;
+        char *hm = (char *)h->h_meta;
+        fill_meta(P, ml, hm);
+        if ((e = cudaMemcpyAsync(dm, hm, ml.total, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return h->cuda_fail(e, "upload descriptors");
+    }
     if ((e = cudaMemsetAsync(dc, 0, cl.total, st)) != cudaSuccess)
         return h->cuda_fail(e, "clear counters");
     const InstDev *d_inst = (const InstDev *)(dm + ml.inst);
     uint32_t *d_flags = (uint32_t *)(dc + cl.flags);
     uint32_t *d_rawcnt = (uint32_t *)(dc + cl.raw_count);
-    cudaEventRecord(h->ev0, st);
+    record_event(h->ev0, st, meta_dev != nullptr);
     const int pack_blocks = (int)std::min<long long>((P.total_windows + 255) / 256, (long long)h->num_sms * 8);
     if ((e = launch_pack(d_inst, (int)k, (const long long *)(dm + ml.win), P.total_windows, d_seq_src,
                          (uint2 *)h->d_planes.p, d_flags, std::max(pack_blocks, 1), st)) != cudaSuccess)
@@ -624,7 +702,7 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     mp.rows_cap = P.rows_cap;
     mp.smem_rows_cap = h->opt.smem_rows > 0 ? std::min(h->opt.smem_rows, kRowSmemCap) : kRowSmemCap;
     mp.counters = (unsigned long long *)(dc + cl.work);
-    cudaEventRecord(h->evm0, st);
+    record_event(h->evm0, st, meta_dev != nullptr);
     if (P.total_items > 0 && (e = launch_main(mp, blocks, count_mode, st)) != cudaSuccess)
         return h->cuda_fail(e, "verification kernel");
     if (P.pair_mode && P.total_pair_items > 0) {
@@ -641,12 +719,194 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
         if ((e = launch_pairs(pp, pblocks, count_mode, st)) != cudaSuccess)
             return h->cuda_fail(e, "pair kernel");
     }
-    cudaEventRecord(h->evm1, st);
+    record_event(h->evm1, st, meta_dev != nullptr);
     if ((e = launch_sort_unique(d_inst, nullptr, (int)k, (uint64_t *)h->d_raw.p, (uint64_t *)h->d_tmp.p, d_rawcnt,
                                 d_flags, status_out,
                                 dense_out, dense_cap, (uint32_t *)(dc + cl.dense_total), st)) != cudaSuccess)
         return h->cuda_fail(e, "sort/unique kernel");
-    cudaEventRecord(h->ev1, st);
+    record_event(h->ev1, st, meta_dev != nullptr);
+    return PMS_OK;
+}
+
+// ------------------------------------------------------------------ captured graphs
+
+constexpr size_t kMaxGraphs = 32;
+
+static void destroy_graph(pms_ctx *h, pms_ctx::Graph &G)
+{
+    if (G.x)
+        cudaGraphExecDestroy(G.x);
+    if (G.g)
+        cudaGraphDestroy(G.g);
+    h->dev_free(G.meta.p, G.meta.cap);
+    G = pms_ctx::Graph{};
+}
+
+static void clear_graphs(pms_ctx *h)
+{
+    if (h->graphs.empty())
+        return;
+    if (h->stream)
+        cudaStreamSynchronize(h->stream);
+    for (auto &kv : h->graphs)
+        destroy_graph(h, kv.second);
+    h->graphs.clear();
+}
+
+// Captures the launches of plan P (descriptor image `key`, which this call
+// has just run kernel by kernel) into a graph with its own descriptor copy.
+// Failure leaves no graph; the plan then keeps running kernel by kernel.
+static void capture_graph(pms_ctx *h, const std::string &key, const Plan &P, const MetaLayout &ml,
+                          const uint8_t *d_seq_src, StatusDev *status_out, uint64_t *dense_out, uint32_t dense_cap)
+{
+    if (h->graphs.size() >= kMaxGraphs) {
+        auto lru = h->graphs.begin();
+        for (auto it = h->graphs.begin(); it != h->graphs.end(); ++it)
+            if (it->second.last_use < lru->second.last_use)
+                lru = it;
+        cudaStreamSynchronize(h->stream);
+        destroy_graph(h, lru->second);
+        h->graphs.erase(lru);
+    }
+    pms_ctx::Graph G;
+    if (h->ensure(G.meta, ml.total))
+        return;
+    // the descriptors this call uploaded, copied in stream order
+    cudaError_t e = cudaMemcpyAsync(G.meta.p, h->d_meta.p, ml.total, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && !h->cap_stream)
+        e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    const uint64_t gen = h->buf_gen;
+    int rc = PMS_ECUDA;
+    if (e == cudaSuccess && (e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed)) == cudaSuccess) {
+        cudaStream_t saved = h->stream;
+        h->stream = h->cap_stream;
+        rc = enqueue_plan(h, P, d_seq_src, status_out, dense_out, dense_cap, false, (char *)G.meta.p);
+        h->stream = saved;
+        e = cudaStreamEndCapture(h->cap_stream, &G.g);
+    }
+    if (rc == PMS_OK && e == cudaSuccess && G.g && h->buf_gen == gen)
+        e = cudaGraphInstantiate(&G.x, G.g, 0);
+    else if (e == cudaSuccess)
+        e = cudaErrorUnknown;
+    // the two nodes whose arguments change from call to call
+    if (e == cudaSuccess) {
+        size_t nn = 0;
+        cudaGraphGetNodes(G.g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn)
+            cudaGraphGetNodes(G.g, nodes.data(), &nn);
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel)
+                continue;
+            cudaKernelNodeParams kp{};
+            if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess || !kp.kernelParams)
+                continue;
+            if (kp.func == pack_kernel_fn()) {
+                G.pack = nd;
+                G.pack_p = kp;
+                void **a = kp.kernelParams;
+                std::memcpy(&G.pv.inst, a[0], sizeof G.pv.inst);
+                std::memcpy(&G.pv.ninst, a[1], sizeof G.pv.ninst);
+                std::memcpy(&G.pv.win_prefix, a[2], sizeof G.pv.win_prefix);
+                std::memcpy(&G.pv.total, a[3], sizeof G.pv.total);
+                std::memcpy(&G.pv.seqs, a[4], sizeof G.pv.seqs);
+                std::memcpy(&G.pv.planes, a[5], sizeof G.pv.planes);
+                std::memcpy(&G.pv.flags, a[6], sizeof G.pv.flags);
+            } else if (kp.func == sort_unique_kernel_fn()) {
+                G.sort = nd;
+                G.sort_p = kp;
+                void **a = kp.kernelParams;
+                std::memcpy(&G.sv.inst, a[0], sizeof G.sv.inst);
+                std::memcpy(&G.sv.list, a[1], sizeof G.sv.list);
+                std::memcpy(&G.sv.raw, a[2], sizeof G.sv.raw);
+                std::memcpy(&G.sv.tmp, a[3], sizeof G.sv.tmp);
+                std::memcpy(&G.sv.raw_count, a[4], sizeof G.sv.raw_count);
+                std::memcpy(&G.sv.flags, a[5], sizeof G.sv.flags);
+                std::memcpy(&G.sv.status, a[6], sizeof G.sv.status);
+                std::memcpy(&G.sv.dense, a[7], sizeof G.sv.dense);
+                std::memcpy(&G.sv.dense_cap, a[8], sizeof G.sv.dense_cap);
+                std::memcpy(&G.sv.dense_total, a[9], sizeof G.sv.dense_total);
+            }
+        }
+        if (!G.pack || !G.sort)
+            e = cudaErrorUnknown;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        destroy_graph(h, G);
+        return;
+    }
+    G.gen = gen;
+    G.candidates = P.candidates;
+    G.last_use = ++h->use_tick;
+    pms_ctx::Graph &S = h->graphs[key];
+    S = G;
+    // argument pointers into the stored copy
+    S.pack_args[0] = &S.pv.inst;
+    S.pack_args[1] = &S.pv.ninst;
+    S.pack_args[2] = &S.pv.win_prefix;
+    S.pack_args[3] = &S.pv.total;
+    S.pack_args[4] = &S.pv.seqs;
+    S.pack_args[5] = &S.pv.planes;
+    S.pack_args[6] = &S.pv.flags;
+    S.sort_args[0] = &S.sv.inst;
+    S.sort_args[1] = &S.sv.list;
+    S.sort_args[2] = &S.sv.raw;
+    S.sort_args[3] = &S.sv.tmp;
+    S.sort_args[4] = &S.sv.raw_count;
+    S.sort_args[5] = &S.sv.flags;
+    S.sort_args[6] = &S.sv.status;
+    S.sort_args[7] = &S.sv.dense;
+    S.sort_args[8] = &S.sv.dense_cap;
+    S.sort_args[9] = &S.sv.dense_total;
+}
+
+// Enqueues a plan: one-instance plans replay a graph captured on their first
+// call (the same kernels, launch configurations and descriptors, with this
+// call's input and output pointers), everything else goes kernel by kernel.
+static int enqueue_plan_graph(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, StatusDev *status_out,
+                              uint64_t *dense_out, uint32_t dense_cap, bool count_mode)
+{
+    if (h->opt.graph < 0 || count_mode || P.inst.size() != 1)
+        return enqueue_plan(h, P, d_seq_src, status_out, dense_out, dense_cap, count_mode);
+    MetaLayout ml(P);
+    // key: options, the verification kernel's grid, the descriptors
+    std::string key((const char *)&h->opt, sizeof h->opt);
+    const int blocks = plan_blocks(h, P, count_mode);
+    key.append((const char *)&blocks, sizeof blocks);
+    const size_t ko = key.size();
+    key.resize(ko + ml.total, '\0');
+    fill_meta(P, ml, &key[ko]);
+    auto it = h->graphs.find(key);
+    if (it != h->graphs.end() && it->second.gen == h->buf_gen) {
+        pms_ctx::Graph &G = it->second;
+        G.pv.seqs = d_seq_src;
+        G.sv.status = status_out;
+        G.sv.dense = dense_out;
+        G.sv.dense_cap = dense_cap;
+        cudaKernelNodeParams pp = G.pack_p, sp = G.sort_p;
+        pp.kernelParams = G.pack_args;
+        pp.extra = nullptr;
+        sp.kernelParams = G.sort_args;
+        sp.extra = nullptr;
+        cudaError_t e;
+        if ((e = cudaGraphExecKernelNodeSetParams(G.x, G.pack, &pp)) != cudaSuccess ||
+            (e = cudaGraphExecKernelNodeSetParams(G.x, G.sort, &sp)) != cudaSuccess ||
+            (e = cudaGraphLaunch(G.x, h->stream)) != cudaSuccess)
+            return h->cuda_fail(e, "graph launch");
+        G.last_use = ++h->use_tick;
+        return PMS_OK;
+    }
+    if (it != h->graphs.end()) {
+        cudaStreamSynchronize(h->stream);
+        destroy_graph(h, it->second);
+        h->graphs.erase(it);
+    }
+    int rc = enqueue_plan(h, P, d_seq_src, status_out, dense_out, dense_cap, count_mode);
+    if (rc)
+        return rc;
+    capture_graph(h, key, P, ml, d_seq_src, status_out, dense_out, dense_cap);
     return PMS_OK;
 }
 
@@ -729,8 +989,8 @@ static int run_host_plan(pms_ctx *h, const Plan &P, const std::vector<InstSpec> 
     if (e != cudaSuccess)
         return h->cuda_fail(e, "upload sequences");
     char *dr = (char *)h->d_result.p;
-    if ((rc = enqueue_plan(h, P, (const uint8_t *)h->d_seqs.p, (StatusDev *)(dr + rl.status),
-                           (uint64_t *)(dr + rl.dense), rl.dense_cap, count_mode)))
+    if ((rc = enqueue_plan_graph(h, P, (const uint8_t *)h->d_seqs.p, (StatusDev *)(dr + rl.status),
+                                 (uint64_t *)(dr + rl.dense), rl.dense_cap, count_mode)))
         return rc;
     // statuses and the first codes in one download
     const size_t first = std::min(inline_bytes, rl.total);
@@ -909,6 +1169,7 @@ static int autotune_class(pms_ctx *h, int n, int m, int l, int d, pms_ctx::Tunin
         return rc;
     }
     h->tuned[key] = cur;
+    clear_graphs(h);   // tuned launch shapes are not part of a graph's key
     best = cur;
     return PMS_OK;
 }
@@ -1212,7 +1473,7 @@ static bool served_admit(Served *S, Request *r)
     r->chunks_next = 0;
     double units = 0;
     for (int i = 0; i <= r->d; ++i)
-        units += (double)binom(r->l, i) * (std::pow(3.0, i) + 24.0);
+        units += (double)binom(r->l, i) * (std::pow(3.0, i) + kNodeUnits);
     r->units_per_chunk = std::max(1.0, units / ct.cps);
     InstDev &in = S->h_inst[r->slot];
     in = InstDev{};
@@ -1526,7 +1787,7 @@ int pms_set_options(pms_ctx *h, const pms_options *opt)
     if (!h || !opt)
         return PMS_EINVAL;
     if (opt->ctas_per_sm < 0 || opt->chunk_work < 0 || opt->grab < 0 || opt->serve_wave_items < 0 || opt->smem_rows < 0 ||
-        opt->seed_mode < 0 || opt->seed_mode > 1 || opt->quorum < 0 || opt->partial_rows < -1 ||
+        opt->seed_mode < 0 || opt->seed_mode > 1 || opt->quorum < 0 || opt->partial_rows < -1 || opt->graph < -1 ||
         opt->serve_max_inflight < 0 || opt->serve_max_inflight > 1024)
         return h->fail(PMS_EINVAL, "negative option");
     std::lock_guard<std::recursive_mutex> g(h->mu);
@@ -1594,7 +1855,7 @@ int pms_solve_device(pms_ctx *h, const uint8_t *d_seqs, int n, int m, int l, int
         return rc;
     Plan P = make_plan(h, specs);
     const uint32_t cap = (uint32_t)std::min<size_t>(capacity, 0xffffffffu);
-    if ((rc = enqueue_plan(h, P, d_seqs, (StatusDev *)d_status, d_motifs, cap, h->opt.count_work != 0)))
+    if ((rc = enqueue_plan_graph(h, P, d_seqs, (StatusDev *)d_status, d_motifs, cap, h->opt.count_work != 0)))
         return rc;
     begin_stats(h, P, h->opt.count_work != 0, t0);
     return PMS_OK;
@@ -1785,6 +2046,7 @@ int pms_load_tuning(pms_ctx *h, const char *path)
         t.partial_rows = pp;
         t.ms = ms;
         h->tuned[std::make_tuple(l, d, nb, mb)] = t;
+        clear_graphs(h);
         ++loaded;
     }
     std::fclose(f);
@@ -1869,6 +2131,9 @@ void pms_destroy(pms_ctx *h)
     served_stop(h);
     if (h->stream)
         cudaStreamSynchronize(h->stream);
+    clear_graphs(h);
+    if (h->cap_stream)
+        cudaStreamDestroy(h->cap_stream);
     pms_ctx::DBuf *bufs[] = {&h->d_seqs, &h->d_planes, &h->d_raw, &h->d_tmp, &h->d_compat, &h->d_rowlen, &h->d_mode, &h->d_meta, &h->d_ctr, &h->d_scratch, &h->d_result};
     for (auto *b : bufs)
         h->dev_free(b->p, b->cap);

@@ -1,0 +1,71 @@
+"""Captured CUDA graphs of one-instance solves: replays give the same motif sets as
+kernel-by-kernel launches, with each call's own input and output buffers, also after
+the context's buffers were reallocated by a larger instance."""
+import numpy as np
+import pytest
+
+import planted_inputs as pi
+import paper_2403_00306_gb300 as pms
+
+pytestmark = pytest.mark.gpu
+
+
+def _device_solve(ctx, torch, seqs, l, d, cap=4096):
+    n, m = seqs.shape
+    d_in = torch.from_numpy(seqs.copy()).cuda()
+    out = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")
+    ctx.set_stream(torch.cuda.current_stream())     # ordered after the tensors' fills
+    ctx.solve_device(d_in, n, m, l, d, out, cap, st)
+    torch.cuda.synchronize()
+    s = st.cpu().numpy().astype(np.uint32)
+    assert s[2] == 0
+    return out[: int(s[1])].cpu().numpy().astype(np.uint64)
+
+
+def test_graph_replays_match_kernel_by_kernel(oracle_):
+    torch = pytest.importorskip("torch")
+    g = pms.Context(0)
+    k = pms.Context(0)
+    k.set_options(graph=-1)
+    g.set_stream(torch.cuda.current_stream())
+    k.set_stream(torch.cuda.current_stream())
+    for (l, d) in [(15, 4), (9, 2)]:
+        for seed in (1, 2, 3, 4):
+            inst = pi.plain_instance(l, d, seed=seed)
+            want = k.solve(inst.seqs, l, d)
+            assert np.array_equal(g.solve(inst.seqs, l, d), want)
+            # new input and output tensors on every call
+            assert np.array_equal(_device_solve(g, torch, inst.seqs, l, d), want)
+            assert g.stats()["ms_verify"] > 0
+    small = pi.planted_instance(6, 80, 9, 2, 5)
+    assert np.array_equal(g.solve(small.seqs, 9, 2), oracle_.solve(small.seqs, 9, 2))
+    g.close()
+    k.close()
+
+
+def test_graph_after_buffer_reallocation():
+    torch = pytest.importorskip("torch")
+    g = pms.Context(0)
+    k = pms.Context(0)
+    k.set_options(graph=-1)
+    a = pi.planted_instance(8, 100, 11, 3, 7)
+    b = pi.planted_instance(30, 1000, 13, 4, 8)     # larger: the context's buffers grow
+    want_a, want_b = k.solve(a.seqs, 11, 3), k.solve(b.seqs, 13, 4)
+    for _ in range(2):
+        assert np.array_equal(g.solve(a.seqs, 11, 3), want_a)
+    assert np.array_equal(g.solve(b.seqs, 13, 4), want_b)
+    for _ in range(2):
+        assert np.array_equal(g.solve(a.seqs, 11, 3), want_a)
+        assert np.array_equal(_device_solve(g, torch, a.seqs, 11, 3), want_a)
+    g.close()
+    k.close()
+
+
+def test_graph_option_values():
+    c = pms.Context(0)
+    c.set_options(graph=-1)
+    c.set_options(graph=0)
+    with pytest.raises(pms.PMSError):
+        c.set_options(graph=-2)
+    c.close()
