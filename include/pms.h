@@ -114,7 +114,7 @@ typedef struct {
                               d of a candidate; none otherwise); -1: no partial
                               level; k > 0: k rows. Tree form, q = n. */
     int graph;             /* one-instance solves (pms_solve, pms_solve_device)
-                              replay a CUDA graph captured on the first call
+                              replay a CUDA graph captured on the second call
                               of each plan (same shape and options), with the
                               call's input and output pointers patched in:
                               0 = on (default); -1 = launch kernel by kernel */

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <set>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -217,6 +218,7 @@ struct pms_ctx {
         uint64_t last_use = 0;
     };
     std::map<std::string, Graph> graphs;
+    std::set<std::string> seen_plans;   // plans run once kernel by kernel (captured on the next call)
     cudaStream_t cap_stream = nullptr;
     uint64_t buf_gen = 0;      // bumped whenever a device buffer is freed or moved
     uint64_t use_tick = 0;
@@ -906,7 +908,13 @@ static int enqueue_plan_graph(pms_ctx *h, const Plan &P, const uint8_t *d_seq_sr
     int rc = enqueue_plan(h, P, d_seq_src, status_out, dense_out, dense_cap, count_mode);
     if (rc)
         return rc;
-    capture_graph(h, key, P, ml, d_seq_src, status_out, dense_out, dense_cap);
+    // capture on a plan's second call, so that one-off shapes pay no capture
+    if (h->seen_plans.size() > 4 * kMaxGraphs)
+        h->seen_plans.clear();
+    if (!h->seen_plans.insert(key).second) {
+        h->seen_plans.erase(key);
+        capture_graph(h, key, P, ml, d_seq_src, status_out, dense_out, dense_cap);
+    }
     return PMS_OK;
 }
 
