@@ -46,12 +46,17 @@ struct InstDev {
 };
 
 // A contiguous range of queue items: chunks [chunk_lo, chunk_hi) of instance
-// `inst`; work_lo is the global item index of chunk_lo.
+// `inst`; work_lo is the global item index of chunk_lo. cps == 0: the
+// instance's chunking (chunk c is chunk c % cps of seed c / cps); cps > 0: this
+// segment's own, chunk c being chunk c % cps of seed seed_lo + c / cps, with
+// the chunk table at ctab.
 struct Segment {
     long long work_lo;
     int inst;
     int chunk_lo, chunk_hi;
-    int pad;
+    int cps;
+    int seed_lo;
+    int ctab;
 };
 
 // Per-instance status written by the sort/unique kernel.

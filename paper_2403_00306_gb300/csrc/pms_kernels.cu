@@ -62,7 +62,8 @@ struct __align__(16) CtaSmem {
     int rows_in_smem;
     int total_rows;
     int next;                // next subset index of the chunk to claim
-    int pad[3];
+    int ctab;                // chunk table of the current item
+    int pad[2];
 };
 
 // Colex unranking of the rank-th k-subset of {0..l-1} (combinatorial number
@@ -1162,10 +1163,11 @@ __global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
                 }
                 const Segment s = p.seg[lo];
                 const int cidx = s.chunk_lo + (int)((long long)g - s.work_lo);
-                const int cps = p.inst[s.inst].cps;
+                const int cps = s.cps > 0 ? s.cps : p.inst[s.inst].cps;
                 cs.inst = s.inst;
-                cs.seed = cidx / cps;
+                cs.seed = s.seed_lo + cidx / cps;
                 cs.chunk = cidx % cps;
+                cs.ctab = s.cps > 0 ? s.ctab : p.inst[s.inst].ctab;
             }
         }
         __syncthreads();
@@ -1185,7 +1187,7 @@ __global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
                 cs.cached_seed = seed;
             }
         }
-        const int *tab = p.ctab + in.ctab;
+        const int *tab = p.ctab + cs.ctab;
         const int g0 = tab[in.d + 2 + 2 * chunk];
         const int g1 = tab[in.d + 2 + 2 * chunk + 1];
         if (threadIdx.x == 0)

@@ -140,6 +140,15 @@ ChunkTable make_chunks(int l, int d, int work)
 }
 
 
+// The chunks of one seed cut into k ranges of equal cost (as make_chunks).
+ChunkTable make_chunks_k(int l, int d, int k)
+{
+    double total = 0;
+    for (int i = 0; i <= d; ++i)
+        total += (double)binom(l, i) * (std::pow(3.0, i) + kNodeUnits);
+    return make_chunks(l, d, (int)std::max(1.0, std::floor(total / k)));
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------- context
@@ -528,6 +537,21 @@ static int default_prune_rows(int n, int d)
     return n - 1;
 }
 
+// Resident CTAs per SM of the verification kernel for an instance class: the
+// occupancy, capped by the option or by the class's tuned value.
+static int plan_occ(const pms_ctx *h, int n, int m, int l, int d, bool count_mode)
+{
+    int occ = h->occ[count_mode ? 1 : 0];
+    if (h->opt.ctas_per_sm > 0) {
+        occ = std::min(occ, h->opt.ctas_per_sm);
+    } else {
+        const pms_ctx::Tuning *t = h->tuning(n, m, l, d);
+        if (t && t->ctas_per_sm > 0)
+            occ = std::min(occ, t->ctas_per_sm);
+    }
+    return std::max(occ, 1);
+}
+
 static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
 {
     Plan P;
@@ -577,8 +601,25 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
         P.total_pair_items += (long long)in.W * in.cps_b;
         P.rows_cap = std::max(P.rows_cap, (int)round_up((size_t)(s.n - 1) * (in.W + 3), 4));
         const int chunks = (int)(seeds * in.cps);
-        P.seg.push_back(Segment{work, (int)k, 0, chunks, 0});
-        work += chunks;
+        // one instance of whole-seed items whose last round would occupy only r
+        // of the B CTAs: the r seeds of that round are cut into floor(B / r)
+        // equal-cost chunks each, so that the round ends with all CTAs busy
+        const long long B = (long long)h->num_sms * plan_occ(h, s.n, s.m, s.l, s.d, h->opt.count_work != 0);
+        const long long r = seeds % B;
+        const int kk = r > 0 ? (int)std::min<long long>(B / r, 16) : 0;
+        if (specs.size() == 1 && in.cps == 1 && seeds > B && kk >= 2) {
+            const ChunkTable ct2 = make_chunks_k(s.l, s.d, kk);
+            const int whole = (int)(seeds - r);
+            P.seg.push_back(Segment{work, (int)k, 0, whole, 0, 0, 0});
+            work += whole;
+            const int ctab2 = (int)P.ctab.size();
+            P.ctab.insert(P.ctab.end(), ct2.tab.begin(), ct2.tab.end());
+            P.seg.push_back(Segment{work, (int)k, 0, (int)(r * ct2.cps), ct2.cps, whole, ctab2});
+            work += r * ct2.cps;
+        } else {
+            P.seg.push_back(Segment{work, (int)k, 0, chunks, 0, 0, 0});
+            work += chunks;
+        }
         P.candidates += (uint64_t)seeds * ball_size(s.l, s.d);
         if (in.q < in.n)
             quorum_used = true;
@@ -607,16 +648,8 @@ static void record_event(cudaEvent_t ev, cudaStream_t st, bool capturing)
 // one per queue item.
 static int plan_blocks(const pms_ctx *h, const Plan &P, bool count_mode)
 {
-    int occ = h->occ[count_mode ? 1 : 0];
-    if (h->opt.ctas_per_sm > 0) {
-        occ = std::min(occ, h->opt.ctas_per_sm);
-    } else if (!P.inst.empty()) {
-        const InstDev &i0 = P.inst[0];
-        const pms_ctx::Tuning *t = h->tuning(i0.n, i0.m, i0.l, i0.d);
-        if (t && t->ctas_per_sm > 0)
-            occ = std::min(occ, t->ctas_per_sm);
-    }
-    occ = std::max(occ, 1);
+    const int occ = P.inst.empty() ? std::max(1, h->occ[count_mode ? 1 : 0])
+                                   : plan_occ(h, P.inst[0].n, P.inst[0].m, P.inst[0].l, P.inst[0].d, count_mode);
     return (int)std::min<long long>((long long)h->num_sms * occ, std::max<long long>(P.total_items, 1));
 }
 
