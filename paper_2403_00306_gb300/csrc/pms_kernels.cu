@@ -715,7 +715,7 @@ __device__ __forceinline__ int walk_run(const WarpCtx &c, const int *tab, int g0
                 __syncwarp();
                 if (c.lane < avail)
                     pool[c.lane] = keep;
-                const int want = min(64 - avail, max(32, claim));
+                const int want = min(64 - avail, max(4, claim));
                 int start = 0;
                 if (c.lane == 0)
                     start = atomicAdd(&cs.next, want);
