@@ -561,14 +561,11 @@ __device__ __forceinline__ void expand_subset(const WarpCtx &c, uint32_t P)
     if (nrows > 0 && in.partial_rows > 0 && lev > nlo && lev - nlo <= 20) {
         const uint32_t Plow = b0 | b1 | b2;
         const int h = lev - nlo;
+        // few variants: every one is inlined with its list flush, and at
+        // (19,6) more of them cost more in instruction-cache misses than the
+        // register-held rows save (measured 28.3 -> 18.7 ms with these two)
         if (k0 <= 1)
             listN = partial_walk<kCount, 1>(c, P, Phi, Plow, DhLo, DlLo, active, h, k0, len0, off0);
-        else if (k0 <= 2)
-            listN = partial_walk<kCount, 2>(c, P, Phi, Plow, DhLo, DlLo, active, h, k0, len0, off0);
-        else if (k0 <= 4)
-            listN = partial_walk<kCount, 4>(c, P, Phi, Plow, DhLo, DlLo, active, h, k0, len0, off0);
-        else if (k0 <= 8)
-            listN = partial_walk<kCount, 8>(c, P, Phi, Plow, DhLo, DlLo, active, h, k0, len0, off0);
         else
             listN = partial_walk<kCount, 0>(c, P, Phi, Plow, DhLo, DlLo, active, h, k0, len0, off0);
     } else if (nrows == 0)
@@ -579,8 +576,6 @@ __device__ __forceinline__ void expand_subset(const WarpCtx &c, uint32_t P)
         listN = leaf_loop<kCount, 2>(c, P, Phi, ch0, cl0, active, iters, k0, len0, off0);
     else if (k0 <= 4)
         listN = leaf_loop<kCount, 4>(c, P, Phi, ch0, cl0, active, iters, k0, len0, off0);
-    else if (k0 <= 8)
-        listN = leaf_loop<kCount, 8>(c, P, Phi, ch0, cl0, active, iters, k0, len0, off0);
     else
         listN = leaf_loop<kCount, 0>(c, P, Phi, ch0, cl0, active, iters, k0, len0, off0);
     if (listN > 0)
