@@ -108,10 +108,10 @@ typedef struct {
                               within d; only the kept partials' leaves are
                               tested (the row shrinking of the paper's
                               depth-first search, one level deep).
-                              0: tuned value, else the default (1 row for
-                              d = 5, 4 rows for d >= 6, when fewer than 0.15
-                              windows of a random sequence are expected within
-                              d of a candidate; none otherwise); -1: no partial
+                              0: tuned value, else the default (8 rows when
+                              d >= 5 and fewer than 0.15 windows of a random
+                              sequence are expected within d of a candidate;
+                              none otherwise); -1: no partial
                               level; k > 0: k rows. Tree form, q = n. */
     int graph;             /* one-instance solves (pms_solve, pms_solve_device)
                               replay a CUDA graph captured on the second call

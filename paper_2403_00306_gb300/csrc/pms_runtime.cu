@@ -51,7 +51,7 @@ int default_partial_rows(int n, int m, int l, int d)
         c = c * (l - i) / (i + 1);
     }
     const double E = (m - l + 1) * p;
-    return E < 0.15 ? (d >= 6 ? 4 : 1) : -1;
+    return E < 0.15 ? 8 : -1;
 }
 
 uint32_t pow2_at_least(size_t v)
