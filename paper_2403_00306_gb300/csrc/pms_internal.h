@@ -110,6 +110,11 @@ cudaError_t launch_pack(const InstDev *inst, int ninst, const long long *win_pre
                         const uint8_t *seqs, uint2 *planes, uint32_t *flags, int blocks, cudaStream_t st);
 cudaError_t launch_compat(const InstDev *inst, int ninst, const long long *row_prefix, long long total_rows,
                           const uint2 *planes, uint32_t *compat, int *rowlen, int blocks, cudaStream_t st);
+// One-instance form of launch_compat: a CTA per (sequence, 64 seeds), the
+// sequence's windows staged in shared memory (W <= the staging capacity).
+bool compat_rows_fits(int W);
+cudaError_t launch_compat_rows(const InstDev *inst, int n, long long seeds, const uint2 *planes, uint32_t *compat,
+                               int *rowlen, cudaStream_t st);
 cudaError_t launch_main(const MainParams &p, int blocks, bool count_mode, cudaStream_t st);
 cudaError_t launch_pairs(const MainParams &p, int blocks, bool count_mode, cudaStream_t st);
 cudaError_t pairs_occupancy(int *blocks_per_sm, bool count_mode);

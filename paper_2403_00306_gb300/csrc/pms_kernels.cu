@@ -1825,11 +1825,75 @@ __global__ void compat_kernel(const InstDev *__restrict__ inst, int ninst, const
         uint32_t *out = compat + in.compat_off + (size_t)local * in.NW;
         const int lim = 2 * in.d;
         int total = 0;
-        for (int w0 = 0; w0 < in.W; w0 += 32) {
+        // four 32-window groups per step, their loads issued together
+        for (int w0 = 0; w0 < in.W; w0 += 128) {
+            uint2 e[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int w = w0 + 32 * u + lane;
+                e[u] = w < in.W ? s[w] : make_uint2(~x.x, ~x.y);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int w = w0 + 32 * u + lane;
+                const bool keep = w < in.W && __popc((x.x ^ e[u].x) | (x.y ^ e[u].y)) <= lim;
+                const uint32_t bal = __ballot_sync(kFull, keep);
+                total += __popc(bal);
+                if (lane == 0 && w0 + 32 * u < in.W)
+                    out[(w0 >> 5) + u] = bal;
+            }
+        }
+        if (lane == 0)
+            rowlen[in.rlen_off + local] = total;
+    }
+}
+
+// The same masks for a one-instance plan, by row: a CTA stages the window
+// planes of one sequence i in shared memory and computes the masks of row i
+// for 16 seeds (2 per warp), so that the planes are read from L2 once per 16
+// seeds instead of once per seed, and the seeds' planes are loaded together.
+constexpr int kCompatSeedsPerCta = 16;
+constexpr int kCompatStageMax = 4096;   // windows of one sequence staged in shared memory
+
+__global__ void __launch_bounds__(256) compat_rows_kernel(const InstDev *__restrict__ inst,
+                                                          const uint2 *__restrict__ planes,
+                                                          uint32_t *__restrict__ compat, int *__restrict__ rowlen)
+{
+    __shared__ uint2 srow[kCompatStageMax];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = inst->n, W = inst->W, NW = inst->NW, lim = 2 * inst->d;
+    const int seeds = inst->nseed * W;
+    const int i = (int)(blockIdx.x % (unsigned)n);             // the sequence of this CTA's rows
+    const int jb = (int)(blockIdx.x / (unsigned)n) * kCompatSeedsPerCta;
+    const uint2 *pl = planes + inst->plane_off;
+    for (int w = threadIdx.x; w < W; w += blockDim.x)
+        srow[w] = pl[(size_t)i * W + w];
+    // this warp's seeds and their planes
+    constexpr int kPer = kCompatSeedsPerCta / kWarps;
+    uint2 xs[kPer];
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+        const int j = jb + warp * kPer + t;
+        xs[t] = j < seeds ? pl[j] : make_uint2(0u, 0u);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+        const int j = jb + warp * kPer + t;
+        const int si = j / W;   // the seed's own sequence has no row
+        if (j >= seeds || si == i)
+            continue;
+        const int k = i < si ? i : i - 1;
+        const long long local = (long long)j * (n - 1) + k;
+        uint32_t *out = compat + inst->compat_off + local * NW;
+        const uint2 x = xs[t];
+        int total = 0;
+#pragma unroll 4
+        for (int w0 = 0; w0 < W; w0 += 32) {
             const int w = w0 + lane;
             bool keep = false;
-            if (w < in.W) {
-                const uint2 e = s[w];
+            if (w < W) {
+                const uint2 e = srow[w];
                 keep = __popc((x.x ^ e.x) | (x.y ^ e.y)) <= lim;
             }
             const uint32_t bal = __ballot_sync(kFull, keep);
@@ -1838,7 +1902,7 @@ __global__ void compat_kernel(const InstDev *__restrict__ inst, int ninst, const
                 out[w0 >> 5] = bal;
         }
         if (lane == 0)
-            rowlen[in.rlen_off + local] = total;
+            rowlen[inst->rlen_off + local] = total;
     }
 }
 
@@ -2147,6 +2211,19 @@ cudaError_t launch_compat(const InstDev *inst, int ninst, const long long *row_p
                           const uint2 *planes, uint32_t *compat, int *rowlen, int blocks, cudaStream_t st)
 {
     compat_kernel<<<blocks, 256, 0, st>>>(inst, ninst, row_prefix, total_rows, planes, compat, rowlen);
+    return cudaGetLastError();
+}
+
+bool compat_rows_fits(int W)
+{
+    return W <= kCompatStageMax;
+}
+
+cudaError_t launch_compat_rows(const InstDev *inst, int n, long long seeds, const uint2 *planes, uint32_t *compat,
+                               int *rowlen, cudaStream_t st)
+{
+    const long long blocks = (long long)n * ((seeds + kCompatSeedsPerCta - 1) / kCompatSeedsPerCta);
+    compat_rows_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(inst, planes, compat, rowlen);
     return cudaGetLastError();
 }
 

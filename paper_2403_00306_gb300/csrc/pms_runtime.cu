@@ -704,7 +704,12 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     if ((e = launch_pack(d_inst, (int)k, (const long long *)(dm + ml.win), P.total_windows, d_seq_src,
                          (uint2 *)h->d_planes.p, d_flags, std::max(pack_blocks, 1), st)) != cudaSuccess)
         return h->cuda_fail(e, "pack kernel");
-    if (P.total_rows > 0) {
+    if (P.total_rows > 0 && k == 1 && compat_rows_fits(P.inst[0].W)) {
+        const InstDev &i0 = P.inst[0];
+        if ((e = launch_compat_rows(d_inst, i0.n, (long long)i0.nseed * i0.W, (const uint2 *)h->d_planes.p,
+                                    (uint32_t *)h->d_compat.p, (int *)h->d_rowlen.p, st)) != cudaSuccess)
+            return h->cuda_fail(e, "compatibility kernel");
+    } else if (P.total_rows > 0) {
         const int cw_blocks = (int)std::min<long long>((P.total_rows + 7) / 8, (long long)h->num_sms * 16);
         if ((e = launch_compat(d_inst, (int)k, (const long long *)(dm + ml.rowp), P.total_rows,
                                (const uint2 *)h->d_planes.p, (uint32_t *)h->d_compat.p, (int *)h->d_rowlen.p,
