@@ -15,6 +15,7 @@ constexpr int kRbCap = 128;    // entries of a subset-reduced occurrence row kep
 constexpr int kListCap = 192;  // surviving candidates a warp buffers before checking further rows
 constexpr int kSubBatch = 128; // tree nodes (position subsets) a warp filters together
 constexpr int kRowSmemCap = 2560;  // feasible occurrences of one seed held in shared memory (padded)
+constexpr int kRowSmemCapSmall = 1280;  // the same in the 4-CTAs-per-SM form of the verification kernel
 
 // Flags reported per instance.
 constexpr uint32_t kFlagInvalidByte = 1u;
@@ -115,13 +116,16 @@ cudaError_t launch_compat(const InstDev *inst, int ninst, const long long *row_p
 bool compat_rows_fits(int W);
 cudaError_t launch_compat_rows(const InstDev *inst, int n, long long seeds, const uint2 *planes, uint32_t *compat,
                                int *rowlen, cudaStream_t st);
-cudaError_t launch_main(const MainParams &p, int blocks, bool count_mode, cudaStream_t st);
+// small_rows: the form with kRowSmemCapSmall row entries in shared memory and
+// 4 resident CTAs per SM (for instances whose seeds have few feasible
+// occurrences); otherwise kRowSmemCap entries and 3 CTAs per SM.
+cudaError_t launch_main(const MainParams &p, int blocks, bool count_mode, cudaStream_t st, bool small_rows = false);
 cudaError_t launch_pairs(const MainParams &p, int blocks, bool count_mode, cudaStream_t st);
 cudaError_t pairs_occupancy(int *blocks_per_sm, bool count_mode);
 cudaError_t launch_classify(const InstDev *inst, int ninst, const long long *seed_prefix, long long total_seeds,
                             const uint2 *planes, const uint32_t *compat, uint8_t *mode, int blocks, cudaStream_t st);
-cudaError_t main_occupancy(int *blocks_per_sm, bool count_mode);
-size_t main_smem_bytes();
+cudaError_t main_occupancy(int *blocks_per_sm, bool count_mode, bool small_rows = false);
+size_t main_smem_bytes(bool small_rows = false);
 cudaError_t launch_sort_unique(const InstDev *inst, const int *inst_list, int nlist, uint64_t *raw, uint64_t *tmp,
                                const uint32_t *raw_count, const uint32_t *flags, StatusDev *status,
                                uint64_t *dense, uint32_t dense_cap, uint32_t *dense_total,

@@ -1116,15 +1116,17 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
     __syncthreads();
 }
 
-template <bool kCount>
-__global__ void __launch_bounds__(kThreads, 3) main_kernel(MainParams p)
+// kRowsCap: row entries held in shared memory; kMinBlocks: resident CTAs per
+// SM the register allocation is bounded for (3 with 2560 entries, 4 with 1280).
+template <bool kCount, int kRowsCap, int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) main_kernel(MainParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *wsm = reinterpret_cast<WarpSmem *>(smem_raw);
     uint32_t *smem_D = reinterpret_cast<uint32_t *>(smem_raw + kWarps * sizeof(WarpSmem));
-    uint2 *smem_HL = reinterpret_cast<uint2 *>(smem_raw + kWarps * sizeof(WarpSmem) + kRowSmemCap * sizeof(uint32_t));
+    uint2 *smem_HL = reinterpret_cast<uint2 *>(smem_raw + kWarps * sizeof(WarpSmem) + kRowsCap * sizeof(uint32_t));
     CtaSmem &cs = *reinterpret_cast<CtaSmem *>(smem_raw + kWarps * sizeof(WarpSmem) +
-                                               kRowSmemCap * (sizeof(uint32_t) + sizeof(uint2)));
+                                               kRowsCap * (sizeof(uint32_t) + sizeof(uint2)));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     // rows_cap is a multiple of 4 words, so each CTA's slice and its plane
@@ -2176,34 +2178,51 @@ cudaError_t init_tables()
     return cudaMemcpyToSymbol(c_pow3, pow3, sizeof(pow3));
 }
 
-size_t main_smem_bytes()
+size_t main_smem_bytes(bool small_rows)
 {
-    return kWarps * sizeof(WarpSmem) + kRowSmemCap * (sizeof(uint32_t) + sizeof(uint2)) + sizeof(CtaSmem);
+    const int rows = small_rows ? kRowSmemCapSmall : kRowSmemCap;
+    return kWarps * sizeof(WarpSmem) + rows * (sizeof(uint32_t) + sizeof(uint2)) + sizeof(CtaSmem);
 }
 
-cudaError_t main_occupancy(int *blocks_per_sm, bool count_mode)
+namespace {
+
+template <bool kCount, int kRowsCap, int kMinBlocks>
+cudaError_t occupancy_of(int *blocks_per_sm, size_t smem)
 {
-    const size_t smem = main_smem_bytes();
-    cudaError_t e;
-    if (count_mode) {
-        e = cudaFuncSetAttribute(main_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel<true>, kThreads, smem);
-    }
-    e = cudaFuncSetAttribute(main_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(main_kernel<kCount, kRowsCap, kMinBlocks>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel<false>, kThreads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel<kCount, kRowsCap, kMinBlocks>,
+                                                         kThreads, smem);
 }
 
-cudaError_t launch_main(const MainParams &p, int blocks, bool count_mode, cudaStream_t st)
+}  // namespace
+
+cudaError_t main_occupancy(int *blocks_per_sm, bool count_mode, bool small_rows)
 {
-    const size_t smem = main_smem_bytes();
-    if (count_mode)
-        main_kernel<true><<<blocks, kThreads, smem, st>>>(p);
-    else
-        main_kernel<false><<<blocks, kThreads, smem, st>>>(p);
+    const size_t smem = main_smem_bytes(small_rows);
+    if (small_rows)
+        return count_mode ? occupancy_of<true, kRowSmemCapSmall, 4>(blocks_per_sm, smem)
+                          : occupancy_of<false, kRowSmemCapSmall, 4>(blocks_per_sm, smem);
+    return count_mode ? occupancy_of<true, kRowSmemCap, 3>(blocks_per_sm, smem)
+                      : occupancy_of<false, kRowSmemCap, 3>(blocks_per_sm, smem);
+}
+
+cudaError_t launch_main(const MainParams &p, int blocks, bool count_mode, cudaStream_t st, bool small_rows)
+{
+    const size_t smem = main_smem_bytes(small_rows);
+    if (small_rows) {
+        if (count_mode)
+            main_kernel<true, kRowSmemCapSmall, 4><<<blocks, kThreads, smem, st>>>(p);
+        else
+            main_kernel<false, kRowSmemCapSmall, 4><<<blocks, kThreads, smem, st>>>(p);
+    } else {
+        if (count_mode)
+            main_kernel<true, kRowSmemCap, 3><<<blocks, kThreads, smem, st>>>(p);
+        else
+            main_kernel<false, kRowSmemCap, 3><<<blocks, kThreads, smem, st>>>(p);
+    }
     return cudaGetLastError();
 }
 

@@ -169,6 +169,7 @@ struct pms_ctx {
     pms_options opt{};
     int num_sms = 0;
     int occ[2] = {0, 0};   // CTAs per SM of the verification kernel (plain, count mode)
+    int occ_small[2] = {0, 0};  // same for its small-rows form
     int occ_pair[2] = {0, 0};  // same for the pair-form kernel
     pms_stats stats{};
     std::map<std::tuple<int, int, int>, ChunkTable> ctab_cache;
@@ -433,6 +434,7 @@ struct Plan {
     std::vector<Segment> seg;
     std::vector<long long> win_prefix;
     std::vector<long long> row_prefix;   // compatibility rows: sum of W * (n - 1)
+    bool small_rows = false;             // verification kernel in its small-rows form (4 CTAs per SM)
     std::vector<long long> seed_prefix;  // seeds: sum of W
     std::vector<Segment> seg_pair;       // pair-form queue (blocks of 64 windows of s_2 per seed)
     long long total_pair_items = 0;
@@ -539,9 +541,9 @@ static int default_prune_rows(int n, int d)
 
 // Resident CTAs per SM of the verification kernel for an instance class: the
 // occupancy, capped by the option or by the class's tuned value.
-static int plan_occ(const pms_ctx *h, int n, int m, int l, int d, bool count_mode)
+static int plan_occ(const pms_ctx *h, int n, int m, int l, int d, bool count_mode, bool small_rows)
 {
-    int occ = h->occ[count_mode ? 1 : 0];
+    int occ = small_rows ? h->occ_small[count_mode ? 1 : 0] : h->occ[count_mode ? 1 : 0];
     if (h->opt.ctas_per_sm > 0) {
         occ = std::min(occ, h->opt.ctas_per_sm);
     } else {
@@ -552,9 +554,29 @@ static int plan_occ(const pms_ctx *h, int n, int m, int l, int d, bool count_mod
     return std::max(occ, 1);
 }
 
+// Expected feasible occurrences of one seed of a uniform i.i.d. instance:
+// (n - 1) rows of W windows, each within 2d of the seed with probability
+// P(Binomial(l, 3/4) <= 2d), plus the rows' padding.
+static double expected_seed_rows(int n, int m, int l, int d)
+{
+    double p = 0, c = 1;
+    for (int i = 0; i <= std::min(2 * d, l); ++i) {
+        p += c * std::pow(0.75, i) * std::pow(0.25, l - i);
+        c = c * (l - i) / (i + 1);
+    }
+    return (n - 1) * ((m - l + 1) * p + 3.0);
+}
+
 static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
 {
     Plan P;
+    // the small-rows form when every instance's seeds are expected to keep
+    // their rows in its shared memory (seeds with more, such as those near the
+    // planted copies, read their rows from the CTA's global scratch)
+    P.small_rows = h->occ_small[0] > h->occ[0];
+    for (const InstSpec &s : specs)
+        if (expected_seed_rows(s.n, s.m, s.l, s.d) > kRowSmemCapSmall)
+            P.small_rows = false;
     long long work = 0;
     const int adaptive = kDefaultChunkWork;   // untuned classes: about 2^20 candidate units per queue item
     bool quorum_used = false;
@@ -604,7 +626,8 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
         // one instance of whole-seed items whose last round would occupy only r
         // of the B CTAs: the r seeds of that round are cut into floor(B / r)
         // equal-cost chunks each, so that the round ends with all CTAs busy
-        const long long B = (long long)h->num_sms * plan_occ(h, s.n, s.m, s.l, s.d, h->opt.count_work != 0);
+        const long long B =
+            (long long)h->num_sms * plan_occ(h, s.n, s.m, s.l, s.d, h->opt.count_work != 0, P.small_rows);
         const long long r = seeds % B;
         const int kk = r > 0 ? (int)std::min<long long>(B / r, 16) : 0;
         if (specs.size() == 1 && in.cps == 1 && seeds > B && kk >= 2) {
@@ -648,8 +671,9 @@ static void record_event(cudaEvent_t ev, cudaStream_t st, bool capturing)
 // one per queue item.
 static int plan_blocks(const pms_ctx *h, const Plan &P, bool count_mode)
 {
-    const int occ = P.inst.empty() ? std::max(1, h->occ[count_mode ? 1 : 0])
-                                   : plan_occ(h, P.inst[0].n, P.inst[0].m, P.inst[0].l, P.inst[0].d, count_mode);
+    const int occ = P.inst.empty()
+                        ? std::max(1, h->occ[count_mode ? 1 : 0])
+                        : plan_occ(h, P.inst[0].n, P.inst[0].m, P.inst[0].l, P.inst[0].d, count_mode, P.small_rows);
     return (int)std::min<long long>((long long)h->num_sms * occ, std::max<long long>(P.total_items, 1));
 }
 
@@ -740,10 +764,11 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     mp.flags = d_flags;
     mp.scratch = (uint32_t *)h->d_scratch.p;
     mp.rows_cap = P.rows_cap;
-    mp.smem_rows_cap = h->opt.smem_rows > 0 ? std::min(h->opt.smem_rows, kRowSmemCap) : kRowSmemCap;
+    const int rows_cap_smem = P.small_rows ? kRowSmemCapSmall : kRowSmemCap;
+    mp.smem_rows_cap = h->opt.smem_rows > 0 ? std::min(h->opt.smem_rows, rows_cap_smem) : rows_cap_smem;
     mp.counters = (unsigned long long *)(dc + cl.work);
     record_event(h->evm0, st, meta_dev != nullptr);
-    if (P.total_items > 0 && (e = launch_main(mp, blocks, count_mode, st)) != cudaSuccess)
+    if (P.total_items > 0 && (e = launch_main(mp, blocks, count_mode, st, P.small_rows)) != cudaSuccess)
         return h->cuda_fail(e, "verification kernel");
     if (P.pair_mode && P.total_pair_items > 0) {
         MainParams pp = mp;
@@ -1166,14 +1191,17 @@ static int autotune_class(pms_ctx *h, int n, int m, int l, int d, pms_ctx::Tunin
     pms_ctx::Tuning cur;
     cur.chunk_work = kDefaultChunkWork;
     cur.prune_rows = n - 1;
-    cur.ctas_per_sm = std::max(1, h->occ[0]);
+    // resident CTAs of the kernel form this class's plans use
+    const bool small = h->occ_small[0] > h->occ[0] && expected_seed_rows(n, m, l, d) <= kRowSmemCapSmall;
+    const int occ0 = std::max(1, small ? h->occ_small[0] : h->occ[0]);
+    cur.ctas_per_sm = occ0;
     cur.partial_rows = default_partial_rows(n, m, l, d);
     cur.grab = kDefaultGrab;
     int rc = run(cur, cur.ms);
     std::vector<int> prune_c = {n - 1, 8, 4, 2, 1};
     std::vector<int> work_c = {1 << 16, 1 << 18, 1 << 20, 1 << 22};
     std::vector<int> cta_c;
-    for (int c = std::max(1, h->occ[0]); c >= 1 && (int)cta_c.size() < 2; --c)
+    for (int c = occ0; c >= 1 && (int)cta_c.size() < 2; --c)
         cta_c.push_back(c);
     std::vector<int> grab_c = {1, 128, 32};
     std::vector<int> partial_c = {-1, 1, 2, 4};
@@ -1793,6 +1821,8 @@ int pms_create(pms_ctx **out, int device, size_t mem_budget_bytes)
         (e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess ||
         (e = main_occupancy(&h->occ[0], false)) != cudaSuccess || (e = main_occupancy(&h->occ[1], true)) != cudaSuccess ||
+        (e = main_occupancy(&h->occ_small[0], false, true)) != cudaSuccess ||
+        (e = main_occupancy(&h->occ_small[1], true, true)) != cudaSuccess ||
         (e = pairs_occupancy(&h->occ_pair[0], false)) != cudaSuccess ||
         (e = pairs_occupancy(&h->occ_pair[1], true)) != cudaSuccess ||
         (e = cudaEventCreate(&h->ev0)) != cudaSuccess || (e = cudaEventCreate(&h->ev1)) != cudaSuccess ||
