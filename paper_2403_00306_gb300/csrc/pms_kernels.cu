@@ -542,6 +542,8 @@ __device__ __forceinline__ void expand_bits(const WarpCtx &c, uint32_t P, int le
         }
     }
     const int nleaf = (int)c_pow3[lev];
+    if (kCount && c.lane == 0)
+        c.cnt[kCntTested] += nleaf;
     uint32_t alive[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -628,8 +630,6 @@ __device__ __forceinline__ void expand_bits(const WarpCtx &c, uint32_t P, int le
         N += __popc(alive[q]);
     }
     __syncwarp();
-    if (kCount && c.lane == 0)
-        c.cnt[kCntTested] += nleaf;
     emit<kCount>(c, list, N);
 }
 
