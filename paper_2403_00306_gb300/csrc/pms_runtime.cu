@@ -2378,7 +2378,7 @@ extern "C" int pms_solve_device_noalloc(const uint8_t *d_seqs, int n, int m, int
     in.W = m - l + 1;
     in.NW = (in.W + 31) / 32;
     in.cps = cps;
-    in.grab = 0;
+    in.grab = kDefaultGrab;   // the lane-asynchronous node walk, as in the other paths
     in.prune_rows = default_prune_rows(n, d);
     {
         const int pr = default_partial_rows(n, m, l, d);
