@@ -338,12 +338,12 @@ class Context:
         n, m = a.shape
         out = ctypes.POINTER(ctypes.c_uint64)()
         cnt = ctypes.c_size_t()
-        rc = self._lib.pms_solve(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), n, m, int(l), int(d),
-                                 ctypes.byref(out), ctypes.byref(cnt))
+        rc = self._lib.pms_solve(self._h, ctypes.cast(a.__array_interface__["data"][0], ctypes.POINTER(ctypes.c_uint8)),
+                                 n, m, int(l), int(d), ctypes.byref(out), ctypes.byref(cnt))
         self._check(rc, "pms_solve")
         if cnt.value == 0:
             return np.zeros(0, dtype=np.uint64)
-        return np.ctypeslib.as_array(out, shape=(cnt.value,)).copy()
+        return np.frombuffer(ctypes.string_at(out, cnt.value * 8), dtype=np.uint64).copy()
 
     def solve_device(self, d_seqs, n: int, m: int, l: int, d: int, d_motifs, capacity: int, d_status) -> None:
         """Enqueues a solve on device buffers (torch tensors or raw pointers); does not wait."""

@@ -410,11 +410,26 @@ static int check_params(pms_ctx *h, int n, int m, int l, int d)
 
 static int check_bytes(pms_ctx *h, const uint8_t *s, size_t len)
 {
-    for (size_t i = 0; i < len; ++i) {
-        const uint8_t c = s[i];
-        if (c != 'A' && c != 'C' && c != 'G' && c != 'T')
-            return h->fail(PMS_EINVAL, "byte %zu (0x%02x) is not one of A, C, G, T", i, c);
+    // a table lookup per byte, OR-accumulated over blocks (no branch per byte)
+    static const struct Table {
+        uint8_t bad[256];
+        Table()
+        {
+            for (int c = 0; c < 256; ++c)
+                bad[c] = (c == 'A' || c == 'C' || c == 'G' || c == 'T') ? 0 : 1;
+        }
+    } t;
+    size_t i = 0;
+    for (; i + 64 <= len; i += 64) {
+        unsigned acc = 0;
+        for (size_t j = 0; j < 64; ++j)
+            acc |= t.bad[s[i + j]];
+        if (acc)
+            break;
     }
+    for (; i < len; ++i)
+        if (t.bad[s[i]])
+            return h->fail(PMS_EINVAL, "byte %zu (0x%02x) is not one of A, C, G, T", i, s[i]);
     return PMS_OK;
 }
 
