@@ -78,7 +78,8 @@ typedef struct {
                               (g >= 128: fixed batches of 128) */
     size_t max_motifs;     /* raw motif capacity per instance (rounded to 2^k) */
     int count_work;        /* 1: also count comparisons (slower; for profiling) */
-    int serve_wave_items;  /* served form: queue items per wave launch */
+    int serve_wave_items;  /* served form: size of a verification wave in units of
+                              65536 candidate units (0: about 6.4e9 units) */
     int serve_max_inflight;/* served form: requests resident on the device */
     int smem_rows;         /* at most this many feasible occurrences of a seed are
                               kept in shared memory (0: as many as fit); larger
