@@ -56,3 +56,48 @@ def test_no_gpu_means_a_loud_error():
         pytest.skip("a GPU is present")
     with pytest.raises(pms.PMSError):
         pms.Context(0)
+
+
+STRUCTS = ["pms_instance", "pms_result", "pms_options", "pms_tuning", "pms_stats"]
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # offsetof and sizeof of every field as a C compiler lays out include/pms.h,
+    # against the ctypes structures of the binding
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "pms.h"', "int main(void) {"]
+    for name in STRUCTS:
+        cls = getattr(pms, name)
+        lines.append(f'    printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'    printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    cc = subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                        capture_output=True, text=True)
+    assert cc.returncode == 0, cc.stderr      # also fails if a binding field is missing from the header
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        struct, field, value = line.split()
+        got[(struct, field)] = int(value)
+    for name in STRUCTS:
+        cls = getattr(pms, name)
+        assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def test_header_structs_have_no_field_the_binding_lacks():
+    src = open(os.path.join(ROOT, "include", "pms.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    for body, name in re.findall(r"typedef struct \{(.*?)\}\s*(pms_[a-z]+);", src, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            # "int n, m, l, d" or "const uint64_t *motifs"
+            names = [t.strip().lstrip("*").split()[-1].lstrip("*") for t in decl.split(",")]
+            fields += names
+        assert [f for f, _ in getattr(pms, name)._fields_] == fields, name
