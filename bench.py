@@ -338,7 +338,7 @@ def bench_plain(args, ws, rank, local, dist, l, d) -> dict:
                      "share_of_step": verify_avg_ms / (total_ms / K)},
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": n * m,
                 "d2h_bytes_per_step": 16 + 512 * 8, "ms_per_step": e2e_total / K},
-        "gpu_launches": 4 * K,   # pack, compatibility masks, verification, sort/unique
+        "gpu_launches": 3 * K,   # packing + compatibility masks, verification, sort/unique
         "clocks": clocks,
         "candidates_tested_per_step": tested / K,
     }

@@ -111,11 +111,14 @@ cudaError_t launch_pack(const InstDev *inst, int ninst, const long long *win_pre
                         const uint8_t *seqs, uint2 *planes, uint32_t *flags, int blocks, cudaStream_t st);
 cudaError_t launch_compat(const InstDev *inst, int ninst, const long long *row_prefix, long long total_rows,
                           const uint2 *planes, uint32_t *compat, int *rowlen, int blocks, cudaStream_t st);
-// One-instance form of launch_compat: a CTA per (sequence, 64 seeds), the
-// sequence's windows staged in shared memory (W <= the staging capacity).
+// One-instance form of launch_pack + launch_compat: a CTA per (sequence, 16
+// seeds) packs the sequence's windows in shared memory (W <= the staging
+// capacity), writes the planes and builds the masks; bytes other than A/C/G/T
+// set flags[0].
 bool compat_rows_fits(int W);
-cudaError_t launch_compat_rows(const InstDev *inst, int n, long long seeds, const uint2 *planes, uint32_t *compat,
-                               int *rowlen, cudaStream_t st);
+cudaError_t launch_compat_rows(const InstDev *inst, int n, long long seeds, const uint8_t *seqs, uint2 *planes,
+                               uint32_t *compat, int *rowlen, uint32_t *flags, cudaStream_t st);
+const void *compat_rows_kernel_fn();
 // small_rows: the form with kRowSmemCapSmall row entries in shared memory and
 // 4 resident CTAs per SM (for instances whose seeds have few feasible
 // occurrences); otherwise kRowSmemCap entries and 3 CTAs per SM.

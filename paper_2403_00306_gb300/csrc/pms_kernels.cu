@@ -1978,34 +1978,86 @@ __global__ void compat_kernel(const InstDev *__restrict__ inst, int ninst, const
     }
 }
 
-// The same masks for a one-instance plan, by row: a CTA stages the window
-// planes of one sequence i in shared memory and computes the masks of row i
-// for 16 seeds (2 per warp), so that the planes are read from L2 once per 16
-// seeds instead of once per seed, and the seeds' planes are loaded together.
+// The same masks for a one-instance plan, by row, with the packing folded in:
+// a CTA reads the bytes of one sequence i once, as two bit-planes of the whole
+// sequence (a ballot per 32 positions), cuts every window's planes out of them
+// with funnel shifts (the CTA of the first seed block also writes them out for
+// the later kernels and flags bytes other than A/C/G/T), packs the planes of
+// its 16 seeds (2 per warp, one byte per lane and two ballots), and builds row
+// i of those seeds' masks from the staged planes. The planes are thus read
+// from L2 not at all, and the separate pack launch is not needed.
 constexpr int kCompatSeedsPerCta = 16;
 constexpr int kCompatStageMax = 4096;   // windows of one sequence staged in shared memory
 
+__device__ __forceinline__ uint32_t base_code(uint32_t ch)
+{
+    return ((ch >> 1) ^ (ch >> 2)) & 3u;   // A0 C1 G2 T3
+}
+
 __global__ void __launch_bounds__(256) compat_rows_kernel(const InstDev *__restrict__ inst,
-                                                          const uint2 *__restrict__ planes,
-                                                          uint32_t *__restrict__ compat, int *__restrict__ rowlen)
+                                                          const uint8_t *__restrict__ seqs, uint2 *__restrict__ planes,
+                                                          uint32_t *__restrict__ compat, int *__restrict__ rowlen,
+                                                          uint32_t *__restrict__ flags)
 {
     __shared__ uint2 srow[kCompatStageMax];
+    __shared__ uint32_t shi[(kCompatStageMax + kLMax) / 32 + 2], slo[(kCompatStageMax + kLMax) / 32 + 2];
+    __shared__ int sbad;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int n = inst->n, W = inst->W, NW = inst->NW, lim = 2 * inst->d;
+    const int n = inst->n, m = inst->m, l = inst->l, W = inst->W, NW = inst->NW, lim = 2 * inst->d;
     const int seeds = inst->nseed * W;
     const int i = (int)(blockIdx.x % (unsigned)n);             // the sequence of this CTA's rows
     const int jb = (int)(blockIdx.x / (unsigned)n) * kCompatSeedsPerCta;
-    const uint2 *pl = planes + inst->plane_off;
-    for (int w = threadIdx.x; w < W; w += blockDim.x)
-        srow[w] = pl[(size_t)i * W + w];
-    // this warp's seeds and their planes
+    const uint8_t *sq = seqs + inst->seq_off;
+    const uint32_t lmask = l == 32 ? ~0u : (1u << l) - 1u;
+    if (threadIdx.x == 0)
+        sbad = 0;
+    __syncthreads();
+    // sequence i as two bit-planes of m bits (32 positions per word, a ballot each)
+    const int nwords = (m + 31) / 32;
+    bool bad = false;
+    for (int wi = warp; wi < nwords; wi += kWarps) {
+        const int k = 32 * wi + lane;
+        const uint32_t ch = k < m ? sq[(size_t)i * m + k] : (uint32_t)'A';
+        bad |= !(ch == 'A' || ch == 'C' || ch == 'G' || ch == 'T');
+        const uint32_t code = base_code(ch);
+        const uint32_t hb = __ballot_sync(kFull, (code >> 1) & 1u), lb = __ballot_sync(kFull, code & 1u);
+        if (lane == 0) {
+            shi[wi] = hb;
+            slo[wi] = lb;
+        }
+    }
+    if (threadIdx.x < 2) {   // the word past the end, read by the last windows' funnel shifts
+        shi[nwords + threadIdx.x] = 0u;
+        slo[nwords + threadIdx.x] = 0u;
+    }
+    if (bad)
+        sbad = 1;
+    // this warp's seeds: windows of the seed sequences, packed from the bytes
     constexpr int kPer = kCompatSeedsPerCta / kWarps;
     uint2 xs[kPer];
 #pragma unroll
     for (int t = 0; t < kPer; ++t) {
         const int j = jb + warp * kPer + t;
-        xs[t] = j < seeds ? pl[j] : make_uint2(0u, 0u);
+        xs[t] = make_uint2(0u, 0u);
+        if (j < seeds) {   // uniform across the warp
+            const int si = j / W, w = j - si * W;
+            const uint32_t code = lane < l ? base_code(sq[(size_t)si * m + w + lane]) : 0u;
+            xs[t] = make_uint2(__ballot_sync(kFull, (code >> 1) & 1u) & lmask, __ballot_sync(kFull, code & 1u) & lmask);
+        }
     }
+    __syncthreads();
+    // window w: bits w .. w + l - 1 of the sequence's planes
+    uint2 *pl_i = planes + inst->plane_off + (size_t)i * W;
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        const int q = w >> 5, r = w & 31;
+        const uint2 e = make_uint2(__funnelshift_r(shi[q], shi[q + 1], r) & lmask,
+                                   __funnelshift_r(slo[q], slo[q + 1], r) & lmask);
+        srow[w] = e;
+        if (jb == 0)
+            pl_i[w] = e;
+    }
+    if (jb == 0 && threadIdx.x == 0 && sbad)
+        atomicOr(&flags[0], kFlagInvalidByte);
     __syncthreads();
 #pragma unroll
     for (int t = 0; t < kPer; ++t) {
@@ -2374,12 +2426,17 @@ bool compat_rows_fits(int W)
     return W <= kCompatStageMax;
 }
 
-cudaError_t launch_compat_rows(const InstDev *inst, int n, long long seeds, const uint2 *planes, uint32_t *compat,
-                               int *rowlen, cudaStream_t st)
+cudaError_t launch_compat_rows(const InstDev *inst, int n, long long seeds, const uint8_t *seqs, uint2 *planes,
+                               uint32_t *compat, int *rowlen, uint32_t *flags, cudaStream_t st)
 {
     const long long blocks = (long long)n * ((seeds + kCompatSeedsPerCta - 1) / kCompatSeedsPerCta);
-    compat_rows_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(inst, planes, compat, rowlen);
+    compat_rows_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(inst, seqs, planes, compat, rowlen, flags);
     return cudaGetLastError();
+}
+
+const void *compat_rows_kernel_fn()
+{
+    return reinterpret_cast<const void *>(compat_rows_kernel);
 }
 
 cudaError_t pairs_occupancy(int *blocks_per_sm, bool count_mode)

@@ -193,7 +193,8 @@ struct pms_ctx {
 
     // Captured pipelines of one-instance plans (CUDA graphs), keyed by the
     // options and the plan's descriptors; replayed with the input and output
-    // pointers of each call patched into the pack and sort/unique nodes.
+    // pointers of each call patched into the packing node (the pack kernel, or
+    // the pack + masks kernel of one-instance plans) and the sort/unique node.
     struct Graph {
         cudaGraph_t g = nullptr;
         cudaGraphExec_t x = nullptr;
@@ -220,7 +221,17 @@ struct pms_ctx {
             uint32_t dense_cap;
             void *dense_total;
         } sv{};
+        struct {
+            const void *inst;
+            const void *seqs;
+            void *planes;
+            void *compat;
+            void *rowlen;
+            void *flags;
+        } rv{};                // the one-instance pack + masks kernel, when the plan uses it
+        bool input_rows = false;   // the node `pack` is that kernel (input pointer: argument 1)
         void *pack_args[7] = {};
+        void *rows_args[6] = {};
         void *sort_args[10] = {};
         DBuf meta;             // this plan's descriptors (the kernels of the graph read them)
         uint64_t gen = 0;      // buffer generation the graph was captured with
@@ -739,16 +750,20 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     uint32_t *d_flags = (uint32_t *)(dc + cl.flags);
     uint32_t *d_rawcnt = (uint32_t *)(dc + cl.raw_count);
     record_event(h->ev0, st, meta_dev != nullptr);
-    const int pack_blocks = (int)std::min<long long>((P.total_windows + 255) / 256, (long long)h->num_sms * 8);
-    if ((e = launch_pack(d_inst, (int)k, (const long long *)(dm + ml.win), P.total_windows, d_seq_src,
-                         (uint2 *)h->d_planes.p, d_flags, std::max(pack_blocks, 1), st)) != cudaSuccess)
-        return h->cuda_fail(e, "pack kernel");
-    if (P.total_rows > 0 && k == 1 && compat_rows_fits(P.inst[0].W)) {
+    const bool by_rows = P.total_rows > 0 && k == 1 && compat_rows_fits(P.inst[0].W);
+    if (by_rows) {
+        // one instance: packing and masks in one kernel, a CTA per (sequence, 16 seeds)
         const InstDev &i0 = P.inst[0];
-        if ((e = launch_compat_rows(d_inst, i0.n, (long long)i0.nseed * i0.W, (const uint2 *)h->d_planes.p,
-                                    (uint32_t *)h->d_compat.p, (int *)h->d_rowlen.p, st)) != cudaSuccess)
+        if ((e = launch_compat_rows(d_inst, i0.n, (long long)i0.nseed * i0.W, d_seq_src, (uint2 *)h->d_planes.p,
+                                    (uint32_t *)h->d_compat.p, (int *)h->d_rowlen.p, d_flags, st)) != cudaSuccess)
             return h->cuda_fail(e, "compatibility kernel");
-    } else if (P.total_rows > 0) {
+    } else {
+        const int pack_blocks = (int)std::min<long long>((P.total_windows + 255) / 256, (long long)h->num_sms * 8);
+        if ((e = launch_pack(d_inst, (int)k, (const long long *)(dm + ml.win), P.total_windows, d_seq_src,
+                             (uint2 *)h->d_planes.p, d_flags, std::max(pack_blocks, 1), st)) != cudaSuccess)
+            return h->cuda_fail(e, "pack kernel");
+    }
+    if (P.total_rows > 0 && !by_rows) {
         const int cw_blocks = (int)std::min<long long>((P.total_rows + 7) / 8, (long long)h->num_sms * 16);
         if ((e = launch_compat(d_inst, (int)k, (const long long *)(dm + ml.rowp), P.total_rows,
                                (const uint2 *)h->d_planes.p, (uint32_t *)h->d_compat.p, (int *)h->d_rowlen.p,
@@ -882,7 +897,18 @@ static void capture_graph(pms_ctx *h, const std::string &key, const Plan &P, con
             cudaKernelNodeParams kp{};
             if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess || !kp.kernelParams)
                 continue;
-            if (kp.func == pack_kernel_fn()) {
+            if (kp.func == compat_rows_kernel_fn()) {
+                G.pack = nd;
+                G.pack_p = kp;
+                G.input_rows = true;
+                void **a = kp.kernelParams;
+                std::memcpy(&G.rv.inst, a[0], sizeof G.rv.inst);
+                std::memcpy(&G.rv.seqs, a[1], sizeof G.rv.seqs);
+                std::memcpy(&G.rv.planes, a[2], sizeof G.rv.planes);
+                std::memcpy(&G.rv.compat, a[3], sizeof G.rv.compat);
+                std::memcpy(&G.rv.rowlen, a[4], sizeof G.rv.rowlen);
+                std::memcpy(&G.rv.flags, a[5], sizeof G.rv.flags);
+            } else if (kp.func == pack_kernel_fn()) {
                 G.pack = nd;
                 G.pack_p = kp;
                 void **a = kp.kernelParams;
@@ -930,6 +956,12 @@ static void capture_graph(pms_ctx *h, const std::string &key, const Plan &P, con
     S.pack_args[4] = &S.pv.seqs;
     S.pack_args[5] = &S.pv.planes;
     S.pack_args[6] = &S.pv.flags;
+    S.rows_args[0] = &S.rv.inst;
+    S.rows_args[1] = &S.rv.seqs;
+    S.rows_args[2] = &S.rv.planes;
+    S.rows_args[3] = &S.rv.compat;
+    S.rows_args[4] = &S.rv.rowlen;
+    S.rows_args[5] = &S.rv.flags;
     S.sort_args[0] = &S.sv.inst;
     S.sort_args[1] = &S.sv.list;
     S.sort_args[2] = &S.sv.raw;
@@ -962,11 +994,12 @@ static int enqueue_plan_graph(pms_ctx *h, const Plan &P, const uint8_t *d_seq_sr
     if (it != h->graphs.end() && it->second.gen == h->buf_gen) {
         pms_ctx::Graph &G = it->second;
         G.pv.seqs = d_seq_src;
+        G.rv.seqs = d_seq_src;
         G.sv.status = status_out;
         G.sv.dense = dense_out;
         G.sv.dense_cap = dense_cap;
         cudaKernelNodeParams pp = G.pack_p, sp = G.sort_p;
-        pp.kernelParams = G.pack_args;
+        pp.kernelParams = G.input_rows ? G.rows_args : G.pack_args;
         pp.extra = nullptr;
         sp.kernelParams = G.sort_args;
         sp.extra = nullptr;
