@@ -39,6 +39,8 @@ METRIC = "PMS solves/s and candidate checks/s per (l,d); batched/served vs plain
 WORKLOADS = {
     "plain9_2": (9, 2), "plain15_4": (15, 4), "plain17_5": (17, 5), "plain19_6": (19, 6),
 }
+# quorum form: (l, d, q), n = 20, m = 600
+QUORUM_WORKLOADS = {"quorum15_4_q10": (15, 4, 10), "quorum13_4_q15": (13, 4, 15)}
 L2_FLUSH_BYTES = 512 << 20
 
 # DRAM bytes (read + write) per launch of the verification kernel from one ncu
@@ -171,17 +173,25 @@ def n_ball(l: int, d: int) -> int:
 
 # ------------------------------------------------------------------ CPU baseline (oracle)
 
-def cpu_oracle_rate(l: int, d: int, n: int, m: int, seed: int, budget_s: float) -> dict:
-    """The oracle as it stands, on a bounded slice of seeds of one instance, scaled to solves/s."""
+def cpu_oracle_rate(l: int, d: int, n: int, m: int, seed: int, budget_s: float, q: int = 0) -> dict:
+    """The oracle as it stands, on a bounded slice of seeds of one instance, scaled to solves/s
+    (q > 0: the quorum form, seeds over s_1 .. s_{n-q+1})."""
     import oracle
     o = oracle.Oracle()
     inst = pi.planted_instance(n, m, l, d, seed)
-    W = m - l + 1
+    W = (m - l + 1) * (n - q + 1 if q > 0 else 1)
     cores = os.cpu_count() or 1
+
+    def run(lo, hi):
+        if q > 0:
+            o.solve_quorum_seeds(inst.seqs, l, d, q, lo, hi, threads=cores)
+        else:
+            o.solve_seeds(inst.seqs, l, d, lo, hi, threads=cores)
+
     # calibrate on one seed per core, then grow to about budget_s
     k = min(W, cores)
     t0 = time.perf_counter()
-    o.solve_seeds(inst.seqs, l, d, 0, k, threads=cores)
+    run(0, k)
     t1 = time.perf_counter() - t0
     total_t, total_seeds, lo = t1, k, k
     while total_t < budget_s and lo < W:
@@ -189,13 +199,14 @@ def cpu_oracle_rate(l: int, d: int, n: int, m: int, seed: int, budget_s: float) 
         take = int(min(W - lo, max(cores, (budget_s - total_t) / per_seed)))
         take = max(1, take)
         t0 = time.perf_counter()
-        o.solve_seeds(inst.seqs, l, d, lo, lo + take, threads=cores)
+        run(lo, lo + take)
         total_t += time.perf_counter() - t0
         total_seeds += take
         lo += take
     solves_per_s = (total_seeds / W) / total_t
     return {"value": solves_per_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": f"{total_seeds} of {W} seeds of one ({l},{d}) n={n} m={m} instance, {total_t:.1f} s, "
+            "sample": f"{total_seeds} of {W} seeds of one ({l},{d}{f',q={q}' if q else ''}) n={n} m={m} instance, "
+                      f"{total_t:.1f} s, "
                       f"scaled by {W}/{total_seeds}",
             "candidate_checks_per_s": total_seeds * n_ball(l, d) / total_t}
 
@@ -203,19 +214,22 @@ def cpu_oracle_rate(l: int, d: int, n: int, m: int, seed: int, budget_s: float) 
 def run_reference(args, ws, rank) -> None:
     if rank != 0:
         return
-    l, d = WORKLOADS.get(args.workload, (15, 4))
+    l, d, q = QUORUM_WORKLOADS[args.workload] if args.workload in QUORUM_WORKLOADS \
+        else (*WORKLOADS.get(args.workload, (15, 4)), 0)
     n, m = 20, 600
     budget = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
     for s in range(args.warmup):
-        cpu_oracle_rate(l, d, n, m, 1000 + s, budget / 4)
+        cpu_oracle_rate(l, d, n, m, 1000 + s, budget / 4, q=q)
     rates = []
     for s in range(args.steps):
-        rates.append(cpu_oracle_rate(l, d, n, m, 1 + s, budget))
+        rates.append(cpu_oracle_rate(l, d, n, m, 1 + s, budget, q=q))
     value = statistics.mean(r["value"] for r in rates)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic", "config": {"workload": f"plain ({l},{d}) n={n} m={m}, CPU oracle on bounded seed samples"},
+            "data": "synthetic",
+            "config": {"workload": (f"quorum ({l},{d}) q={q}" if q else f"plain ({l},{d})")
+                                   + f" n={n} m={m}, CPU oracle on bounded seed samples"},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": rates[0]["cores"], "kind": "oracle",
                              "sample": rates[0]["sample"]},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -232,7 +246,7 @@ def make_flush(torch, dev):
     return flush
 
 
-def bench_plain(args, ws, rank, local, dist, l, d) -> dict:
+def bench_plain(args, ws, rank, local, dist, l, d, q: int = 0) -> dict:
     import torch
     import paper_2403_00306_gb300 as pms
     dev = torch.device("cuda", local)
@@ -248,6 +262,8 @@ def bench_plain(args, ws, rank, local, dist, l, d) -> dict:
     stream = torch.cuda.Stream(device=dev)
     ctx = pms.Context(local)
     ctx.set_stream(stream)
+    if q:
+        ctx.set_options(quorum=q)
     flush = make_flush(torch, dev)
 
     # parity spot-check of the timed launch configuration against the host path
@@ -285,14 +301,15 @@ def bench_plain(args, ws, rank, local, dist, l, d) -> dict:
 
     # algorithmic work of the dominant kernel (count mode, same instances, untimed)
     cctx = pms.Context(local)
-    cctx.set_options(count_work=1)
+    cctx.set_options(count_work=1, quorum=q)
     cmp_total = 0
     tested = 0
     for k in range(K):
         cctx.solve(insts[Wm + k].seqs, l, d)
         s = cctx.stats()
-        W = m - l + 1
-        cmp_total += (n - 1) * W * W + s["cmp_reduce"] + s["cmp_verify"]
+        # comparisons of the verification kernel only (the (n - 1) W^2 of the
+        # compatibility masks are another kernel's)
+        cmp_total += s["cmp_reduce"] + s["cmp_verify"]
         tested += s["candidates_tested"]
     cctx.close()
     cmp_per_launch = cmp_total / K
@@ -324,10 +341,11 @@ def bench_plain(args, ws, rank, local, dist, l, d) -> dict:
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": K, "warmup": Wm,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"plain ({l},{d}) n={n} m={m}, one seeded FM-model instance per step",
+        "config": {"workload": (f"quorum ({l},{d}) q={q}" if q else f"plain ({l},{d})")
+                               + f" n={n} m={m}, one seeded FM-model instance per step",
                    "l": l, "d": d, "n": n, "m": m, "l2": "flushed between steps (512 MiB write, untimed)",
                    "timing": "CUDA events on the library stream around pms_solve_device"},
-        "candidate_checks_per_s": solves * W * n_ball(l, d) / (total_ms / 1000.0),
+        "candidate_checks_per_s": solves * W * (n - q + 1 if q else 1) * n_ball(l, d) / (total_ms / 1000.0),
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_cmp / 1e12,
                      "unit": "Tcmp/s", "frac": achieved / peak_cmp,
                      "traffic": measured_traffic(f"plain{l}_{d}"),
@@ -479,7 +497,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="plain15_4", choices=sorted(WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--workload", default="plain15_4",
+                    choices=sorted(WORKLOADS) + sorted(QUORUM_WORKLOADS) + ["batch", "serve"])
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
@@ -497,10 +516,10 @@ def main():
     elif args.workload == "serve":
         line = bench_serve(args, ws, rank, local, dist)
     else:
-        l, d = WORKLOADS[args.workload]
-        line = bench_plain(args, ws, rank, local, dist, l, d)
+        l, d, q = QUORUM_WORKLOADS[args.workload] if args.workload in QUORUM_WORKLOADS else (*WORKLOADS[args.workload], 0)
+        line = bench_plain(args, ws, rank, local, dist, l, d, q)
         if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_oracle_rate(l, d, 20, 600, 424242, budget_s=15.0)
+            line["cpu_baseline"] = cpu_oracle_rate(l, d, 20, 600, 424242, budget_s=15.0, q=q)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
