@@ -40,7 +40,7 @@ WORKLOADS = {
     "plain9_2": (9, 2), "plain15_4": (15, 4), "plain17_5": (17, 5), "plain19_6": (19, 6),
 }
 # quorum form: (l, d, q), n = 20, m = 600
-QUORUM_WORKLOADS = {"quorum15_4_q10": (15, 4, 10), "quorum13_4_q15": (13, 4, 15)}
+QUORUM_WORKLOADS = {"quorum15_4_q10": (15, 4, 10)}
 L2_FLUSH_BYTES = 512 << 20
 
 # DRAM bytes (read + write) per launch of the verification kernel from one ncu
@@ -348,7 +348,7 @@ def bench_plain(args, ws, rank, local, dist, l, d, q: int = 0) -> dict:
         "candidate_checks_per_s": solves * W * (n - q + 1 if q else 1) * n_ball(l, d) / (total_ms / 1000.0),
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_cmp / 1e12,
                      "unit": "Tcmp/s", "frac": achieved / peak_cmp,
-                     "traffic": measured_traffic(f"plain{l}_{d}"),
+                     "traffic": measured_traffic(f"quorum{l}_{d}_q{q}" if q else f"plain{l}_{d}"),
                      "kernel": "main_kernel (verification)", "cmp_per_launch": cmp_per_launch,
                      "verify_ms_per_launch": verify_avg_ms,
                      "peak_basis": f"{probe:.2f} comparisons/clk/SM (probe) x {sms} SMs x {fmax/1e6:.0f} MHz; "
