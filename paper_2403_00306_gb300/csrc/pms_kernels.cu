@@ -17,6 +17,11 @@
 //     it mismatches w wherever w agrees with x, and off P it mismatches w
 //     wherever x does. A node with an empty reduced row has no motif among
 //     its 3^|P| leaves (the branch-and-bound of qPMSPrune, applied per node);
+//     each lane walks one node through the rows with this bound;
+//   * below a surviving node, partial candidates (letters fixed above the
+//     three lowest changed positions) are tested with the exact bound over
+//     their leaves, or the 81 leaves of a 4-position node are handled as a
+//     bit set;
 //   * each surviving leaf is verified against the reduced rows with packed
 //     XOR/OR/popc, warp ballots compact the survivors between rows, and the
 //     motifs are appended with one atomic per warp, then sorted and
@@ -778,8 +783,9 @@ __device__ __forceinline__ int filter_subsets(const WarpCtx &c, int N)
 // expansion queue, and a free lane takes the next node of the warp's pool at
 // once. So every node stops scanning a row at its own first hit (the
 // sequential early-exit rule) instead of waiting for the slowest node of a
-// batch. The pool holds nodes claimed 32 to 64 at a time and unranked by all
-// lanes together. subs[0..64) is the pool, subs[64..128) the queue.
+// batch. The pool holds nodes claimed a sixteenth of the chunk (4 to 64) at a
+// time, each lane unranking one and stepping to the next by Gosper's step.
+// subs[0..64) is the pool, subs[64..128) the queue.
 //
 // walk_run runs the walk until 32 or more nodes are queued or the chunk is
 // done, and returns the queue length; the caller expands the queued nodes
