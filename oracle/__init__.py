@@ -11,7 +11,9 @@ q = n): the set of l-mers M over {A,C,G,T} such that every input sequence has
 a window within Hamming distance d of M. The candidate set is restricted by
 Observation 3.1 (every motif lies in B(x, d) for some l-mer x of s_1), which
 is exact for q = n. Variants: the pair form of Observation 3.3, and the
-pattern-driven brute force over all 4^l strings for tiny l.
+pattern-driven brute force over all 4^l strings for tiny l. The same
+definitions over a general alphabet (qPMS-Sigma: sigma distinct letters,
+ceil(log2 sigma) bit-plane groups) are the ``sigma_*`` methods.
 """
 from __future__ import annotations
 
@@ -69,6 +71,14 @@ def _declare(lib):
         "oracle_solve_quorum_seeds": (c_long, [u8p, c_int, c_int, c_int, c_int, c_int, c_long, c_long, c_int, u64p,
                                                 c_long]),
         "oracle_bruteforce_quorum": (c_long, [u8p, c_int, c_int, c_int, c_int, c_int, u64p, c_long]),
+        "oracle_sigma_groups": (c_int, [c_int]),
+        "oracle_sigma_compress": (c_int, [u8p, c_int, u8p, c_int, u32p]),
+        "oracle_sigma_compressed_distance": (c_int, [u32p, u32p, c_int, c_int]),
+        "oracle_sigma_neighbourhood_visits": (c_long, [u8p, c_int, u8p, c_int, c_int]),
+        "oracle_sigma_solve": (c_long, [u8p, c_int, u8p, c_int, c_int, c_int, c_int, c_int, c_int, u8p, c_long]),
+        "oracle_sigma_solve_seeds": (c_long, [u8p, c_int, u8p, c_int, c_int, c_int, c_int, c_int, c_long, c_long,
+                                               c_int, u8p, c_long]),
+        "oracle_sigma_bruteforce": (c_long, [u8p, c_int, u8p, c_int, c_int, c_int, c_int, c_int, u8p, c_long]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -228,3 +238,63 @@ class Oracle:
 
     def decode_all(self, keys, l: int) -> list[str]:
         return [self.decode(int(k), l) for k in keys]
+
+    # --- general alphabets (qPMS-Sigma) ---
+    def sigma_groups(self, sigma: int) -> int:
+        return int(self.lib.oracle_sigma_groups(sigma))
+
+    def sigma_compress(self, alphabet, x) -> np.ndarray:
+        alphabet, x = _bytes(alphabet), _bytes(x)
+        words = (len(x) + 31) // 32
+        groups = self.sigma_groups(len(alphabet))
+        out = np.zeros(groups * words, dtype=np.uint32)
+        (aa, pa), (xa, px) = _u8(alphabet), _u8(x)
+        rc = self.lib.oracle_sigma_compress(pa, len(alphabet), px, len(x),
+                                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+        if rc != 0:
+            raise ValueError("invalid alphabet or letter")
+        return out.reshape(groups, words)
+
+    def sigma_compressed_distance(self, a: np.ndarray, b: np.ndarray, l: int) -> int:
+        groups = np.asarray(a).shape[0]
+        a = np.ascontiguousarray(a, dtype=np.uint32).ravel()
+        b = np.ascontiguousarray(b, dtype=np.uint32).ravel()
+        p = ctypes.POINTER(ctypes.c_uint32)
+        return int(self.lib.oracle_sigma_compressed_distance(a.ctypes.data_as(p), b.ctypes.data_as(p), l, groups))
+
+    def sigma_neighbourhood_visits(self, alphabet, x, d: int) -> int:
+        alphabet, x = _bytes(alphabet), _bytes(x)
+        (aa, pa), (xa, px) = _u8(alphabet), _u8(x)
+        return int(self.lib.oracle_sigma_neighbourhood_visits(pa, len(alphabet), px, len(x), d))
+
+    def _sigma(self, fn, alphabet, seqs, l, d, q, *extra, cap):
+        alphabet = _bytes(alphabet)
+        seqs = np.ascontiguousarray(seqs, dtype=np.uint8)
+        n, m = seqs.shape
+        out = np.zeros(cap * l, dtype=np.uint8)
+        aa, pa = _u8(alphabet)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        res = fn(pa, len(alphabet), seqs.ctypes.data_as(u8p), n, m, l, d, q, *extra, out.ctypes.data_as(u8p), cap)
+        if res == -1:
+            raise ValueError("invalid input")
+        if res == -2:
+            raise MemoryError("oracle ran out of memory")
+        if res > cap:
+            raise OverflowError(f"{res} motifs exceed the output capacity {cap}")
+        return out[: res * l].reshape(res, l).copy()
+
+    def sigma_solve(self, seqs, l: int, d: int, alphabet, q: int = 0, threads: int | None = None,
+                    cap: int = 1 << 20) -> np.ndarray:
+        """All (l,d,q)-motifs over ``alphabet`` (q = 0: q = n) as an (count, l) uint8 array of letters,
+        rows in lexicographic order of the alphabet's indices."""
+        return self._sigma(self.lib.oracle_sigma_solve, alphabet, seqs, l, d, q, threads or os.cpu_count() or 1,
+                           cap=cap)
+
+    def sigma_solve_seeds(self, seqs, l: int, d: int, alphabet, seed_lo: int, seed_hi: int, q: int = 0,
+                          threads: int | None = None, cap: int = 1 << 20) -> np.ndarray:
+        """The motifs inside B(x, d) for seeds [seed_lo, seed_hi) numbered over s_1..s_{n-q+1}."""
+        return self._sigma(self.lib.oracle_sigma_solve_seeds, alphabet, seqs, l, d, q, seed_lo, seed_hi,
+                           threads or os.cpu_count() or 1, cap=cap)
+
+    def sigma_bruteforce(self, seqs, l: int, d: int, alphabet, q: int = 0, cap: int = 1 << 20) -> np.ndarray:
+        return self._sigma(self.lib.oracle_sigma_bruteforce, alphabet, seqs, l, d, q, cap=cap)

@@ -21,7 +21,10 @@
  *   - "within d" means Hamming distance <= d (Definition 5: no more than d);
  *   - a motif set is reported as sorted, unique 64-bit keys holding 2 bits per
  *     base with position 0 in the most significant used bits, so ascending
- *     keys are lexicographic order.
+ *     keys are lexicographic order;
+ *   - the oracle_sigma_* functions at the end restate the same definitions
+ *     over a general alphabet of 2..32 letters (the "Sigma" of qPMS-Sigma),
+ *     reporting motifs as letters in the alphabet's own order.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -484,4 +487,310 @@ long oracle_bruteforce(const uint8_t *seqs, int n, int m, int l, int d, uint64_t
             kv_push(&kv, key);
     }
     return kv_finish(&kv, out, cap);
+}
+
+/* ==== general alphabets (chapter "Our Approach": qPMS-Sigma) ====
+ * The same definitions over an alphabet Sigma given as sigma distinct bytes,
+ * 2 <= sigma <= 32; letter b of the alphabet has index b, and motif sets are
+ * ordered lexicographically by index (for the alphabet "ACGT" this is the
+ * order above). Motifs come back as l bytes each, in that order, unique. */
+
+static int sigma_index(const uint8_t *alphabet, int sigma, uint8_t ch)
+{
+    for (int b = 0; b < sigma; ++b)
+        if (alphabet[b] == ch)
+            return b;
+    return -1;
+}
+
+static int valid_alphabet(const uint8_t *alphabet, int sigma)
+{
+    if (!alphabet || sigma < 2 || sigma > 32)
+        return 0;
+    for (int a = 0; a < sigma; ++a)
+        for (int b = a + 1; b < sigma; ++b)
+            if (alphabet[a] == alphabet[b])
+                return 0;
+    return 1;
+}
+
+/* ceil(log2 sigma): the number of bit-plane groups of the compression. */
+int oracle_sigma_groups(int sigma)
+{
+    int g = 0;
+    while ((1 << g) < sigma)
+        g += 1;
+    return g;
+}
+
+/* String Compression for a general alphabet: ceil(log2 sigma) groups of
+ * ceil(l/32) words; bit g of the index of character k goes to bit (k mod 32)
+ * of word (k div 32) of group g. out holds groups * ceil(l/32) words. */
+int oracle_sigma_compress(const uint8_t *alphabet, int sigma, const uint8_t *s, int l, uint32_t *out)
+{
+    if (!valid_alphabet(alphabet, sigma))
+        return ORACLE_EINVAL;
+    int words = (l + 31) / 32, groups = oracle_sigma_groups(sigma);
+    for (int w = 0; w < groups * words; ++w)
+        out[w] = 0;
+    for (int k = 0; k < l; ++k) {
+        int c = sigma_index(alphabet, sigma, s[k]);
+        if (c < 0)
+            return ORACLE_EINVAL;
+        for (int g = 0; g < groups; ++g)
+            if ((c >> g) & 1)
+                out[g * words + k / 32] |= (uint32_t)1 << (k % 32);
+    }
+    return ORACLE_OK;
+}
+
+/* Distance of two compressed l-mers: XOR group by group, OR across groups,
+ * count the set bits. */
+int oracle_sigma_compressed_distance(const uint32_t *a, const uint32_t *b, int l, int groups)
+{
+    int words = (l + 31) / 32;
+    int h = 0;
+    for (int w = 0; w < words; ++w) {
+        uint32_t acc = 0;
+        for (int g = 0; g < groups; ++g)
+            acc |= a[g * words + w] ^ b[g * words + w];
+        h += count_set_bits(acc);
+    }
+    return h;
+}
+
+/* Growable array of motifs as 32-byte records of letter indices (zero padded,
+ * so byte-wise comparison is the lexicographic order by index). */
+typedef struct {
+    uint8_t *v;
+    long n, cap;
+    int oom;
+} recvec;
+
+static void rv_push(recvec *rv, const uint8_t *rec)
+{
+    if (rv->oom)
+        return;
+    if (rv->n == rv->cap) {
+        long nc = rv->cap ? 2 * rv->cap : 256;
+        uint8_t *nv = (uint8_t *)realloc(rv->v, (size_t)nc * 32);
+        if (!nv) {
+            rv->oom = 1;
+            return;
+        }
+        rv->v = nv;
+        rv->cap = nc;
+    }
+    memcpy(rv->v + (size_t)rv->n * 32, rec, 32);
+    rv->n += 1;
+}
+
+static int cmp_rec(const void *a, const void *b)
+{
+    return memcmp(a, b, 32);
+}
+
+/* Sorts and de-duplicates the records and writes up to cap motifs (l letters
+ * each) to out. Returns the number of unique motifs (may exceed cap). */
+static long rv_finish(recvec *rv, const uint8_t *alphabet, int l, uint8_t *out, long cap)
+{
+    if (rv->oom) {
+        free(rv->v);
+        return ORACLE_ENOMEM;
+    }
+    qsort(rv->v, (size_t)rv->n, 32, cmp_rec);
+    long u = 0;
+    for (long i = 0; i < rv->n; ++i)
+        if (u == 0 || memcmp(rv->v + (size_t)i * 32, rv->v + (size_t)(u - 1) * 32, 32) != 0)
+            memmove(rv->v + (size_t)u++ * 32, rv->v + (size_t)i * 32, 32);
+    for (long i = 0; i < u && i < cap; ++i)
+        for (int k = 0; k < l; ++k)
+            out[(size_t)i * l + k] = alphabet[rv->v[(size_t)i * 32 + k]];
+    free(rv->v);
+    return u;
+}
+
+static int valid_sigma_input(const uint8_t *alphabet, int sigma, const uint8_t *seqs, int n, int m, int l, int d,
+                             int q)
+{
+    if (!valid_alphabet(alphabet, sigma) || n < 1 || l < 1 || l > 32 || m < l || d < 0 || d >= l || q < 0 || q > n)
+        return 0;
+    for (long k = 0; k < (long)n * m; ++k)
+        if (sigma_index(alphabet, sigma, seqs[k]) < 0)
+            return 0;
+    return 1;
+}
+
+/* B(x, d) over Sigma as the tree T_d(x) of qPMSPrune: a child changes one
+ * position to the right of its parent's last change to one of the sigma - 1
+ * other letters. */
+typedef struct {
+    const uint8_t *alphabet;
+    int sigma;
+    const uint8_t *x;
+    uint8_t *cur;
+    int l, d, q;           /* q = 0: all n strings */
+    const uint8_t *seqs;
+    int n, m;
+    int mode;              /* 0: motif test, 1: collect every node */
+    recvec *out;
+    long visited;
+} swalk_t;
+
+static void sigma_visit(swalk_t *w)
+{
+    w->visited += 1;
+    if (w->mode == 1 ||
+        (w->q > 0 ? oracle_is_qmotif(w->cur, w->l, w->d, w->q, w->seqs, w->n, w->m)
+                  : oracle_is_motif(w->cur, w->l, w->d, w->seqs, w->n, w->m))) {
+        uint8_t rec[32] = {0};
+        for (int k = 0; k < w->l; ++k)
+            rec[k] = (uint8_t)sigma_index(w->alphabet, w->sigma, w->cur[k]);
+        rv_push(w->out, rec);
+    }
+}
+
+static void sigma_walk(swalk_t *w, int first_pos, int depth)
+{
+    sigma_visit(w);
+    if (depth < w->d) {
+        for (int p = first_pos; p < w->l; ++p) {
+            uint8_t orig = w->cur[p];
+            for (int b = 0; b < w->sigma; ++b) {
+                if (w->alphabet[b] == w->x[p])
+                    continue;
+                w->cur[p] = w->alphabet[b];
+                sigma_walk(w, p + 1, depth + 1);
+            }
+            w->cur[p] = orig;
+        }
+    }
+}
+
+/* Number of nodes the walk of B(x, d) over Sigma visits (= |B(x, d)|). */
+long oracle_sigma_neighbourhood_visits(const uint8_t *alphabet, int sigma, const uint8_t *x, int l, int d)
+{
+    if (!valid_alphabet(alphabet, sigma) || l < 1 || l > 32 || d < 0)
+        return ORACLE_EINVAL;
+    uint8_t cur[32];
+    memcpy(cur, x, (size_t)l);
+    recvec rv = {0};
+    swalk_t w = {alphabet, sigma, x, cur, l, d, 0, NULL, 0, 0, 1, &rv, 0};
+    sigma_walk(&w, 0, 0);
+    free(rv.v);
+    return w.visited;
+}
+
+typedef struct {
+    const uint8_t *alphabet;
+    int sigma;
+    const uint8_t *seqs;
+    int n, m, l, d, q;
+    int tid, nthreads;
+    long seed_lo, seed_hi;
+    recvec out;
+} sjob_t;
+
+static void *sigma_worker(void *arg)
+{
+    sjob_t *j = (sjob_t *)arg;
+    uint8_t cur[32];
+    const long W = (long)j->m - j->l + 1;
+    for (long x0 = j->seed_lo + j->tid; x0 < j->seed_hi; x0 += j->nthreads) {
+        /* Observation 3.1: every (l,d,q)-motif is within d of an l-mer of one
+         * of s_1..s_{n-q+1}; seeds are numbered over those strings, W each */
+        const uint8_t *x = j->seqs + (x0 / W) * (long)j->m + (x0 % W);
+        memcpy(cur, x, (size_t)j->l);
+        swalk_t w = {j->alphabet, j->sigma, x, cur, j->l, j->d, j->q, j->seqs, j->n, j->m, 0, &j->out, 0};
+        sigma_walk(&w, 0, 0);
+    }
+    return NULL;
+}
+
+/* All (l,d,q)-motifs over Sigma (q = 0 or q = n: the PMS problem) lying in
+ * B(x, d) for the seeds x numbered [seed_lo, seed_hi) over the l-mers of
+ * s_1..s_{n-q+1}; seed_hi < 0 means all seeds. out receives up to cap motifs
+ * of l bytes; returns their number or a negative error. */
+long oracle_sigma_solve_seeds(const uint8_t *alphabet, int sigma, const uint8_t *seqs, int n, int m, int l, int d,
+                              int q, long seed_lo, long seed_hi, int threads, uint8_t *out, long cap)
+{
+    if (!valid_sigma_input(alphabet, sigma, seqs, n, m, l, d, q))
+        return ORACLE_EINVAL;
+    if (q == n)
+        q = 0;
+    const long W = (long)m - l + 1;
+    const long nseeds = (long)(q > 0 ? n - q + 1 : 1) * W;
+    if (seed_lo < 0)
+        seed_lo = 0;
+    if (seed_hi < 0 || seed_hi > nseeds)
+        seed_hi = nseeds;
+    if (threads < 1)
+        threads = 1;
+    if (threads > 256)
+        threads = 256;
+    sjob_t *jobs = (sjob_t *)calloc((size_t)threads, sizeof(sjob_t));
+    pthread_t *th = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    if (!jobs || !th) {
+        free(jobs);
+        free(th);
+        return ORACLE_ENOMEM;
+    }
+    for (int t = 0; t < threads; ++t) {
+        jobs[t] = (sjob_t){alphabet, sigma, seqs, n, m, l, d, q, t, threads, seed_lo, seed_hi, {0}};
+        if (threads == 1 || pthread_create(&th[t], NULL, sigma_worker, &jobs[t]) != 0) {
+            sigma_worker(&jobs[t]);
+            th[t] = 0;
+        }
+    }
+    recvec all = {0};
+    for (int t = 0; t < threads; ++t) {
+        if (th[t])
+            pthread_join(th[t], NULL);
+        if (jobs[t].out.oom)
+            all.oom = 1;
+        for (long i = 0; i < jobs[t].out.n; ++i)
+            rv_push(&all, jobs[t].out.v + (size_t)i * 32);
+        free(jobs[t].out.v);
+    }
+    free(jobs);
+    free(th);
+    return rv_finish(&all, alphabet, l, out, cap);
+}
+
+long oracle_sigma_solve(const uint8_t *alphabet, int sigma, const uint8_t *seqs, int n, int m, int l, int d, int q,
+                        int threads, uint8_t *out, long cap)
+{
+    return oracle_sigma_solve_seeds(alphabet, sigma, seqs, n, m, l, d, q, 0, -1, threads, out, cap);
+}
+
+/* Pattern-driven exhaustive search over Sigma: all sigma^l strings, each
+ * tested against Definition 5. Only for sigma^l <= 2^24. */
+long oracle_sigma_bruteforce(const uint8_t *alphabet, int sigma, const uint8_t *seqs, int n, int m, int l, int d,
+                             int q, uint8_t *out, long cap)
+{
+    if (!valid_sigma_input(alphabet, sigma, seqs, n, m, l, d, q))
+        return ORACLE_EINVAL;
+    double total = 1.0;
+    for (int k = 0; k < l; ++k)
+        total *= sigma;
+    if (total > (double)(1 << 24))
+        return ORACLE_EINVAL;
+    if (q == n)
+        q = 0;
+    recvec rv = {0};
+    uint8_t idx[32] = {0}, cand[32];
+    for (;;) {
+        for (int k = 0; k < l; ++k)
+            cand[k] = alphabet[idx[k]];
+        if (q > 0 ? oracle_is_qmotif(cand, l, d, q, seqs, n, m) : oracle_is_motif(cand, l, d, seqs, n, m))
+            rv_push(&rv, idx);
+        /* next string: base-sigma counter, last position fastest */
+        int k = l - 1;
+        while (k >= 0 && idx[k] == sigma - 1)
+            idx[k--] = 0;
+        if (k < 0)
+            break;
+        idx[k] += 1;
+    }
+    return rv_finish(&rv, alphabet, l, out, cap);
 }

@@ -95,6 +95,43 @@ def planted_instance(n: int, m: int, l: int, d: int, seed: int) -> Instance:
                     l=l, d=d, seed=seed)
 
 
+#: the twenty amino acids, one-letter codes in alphabetical order
+PROTEIN = b"ACDEFGHIKLMNPQRSTVWY"
+
+
+def planted_instance_sigma(n: int, m: int, l: int, d: int, seed: int, alphabet: bytes = PROTEIN) -> Instance:
+    """The FM recipe over a general alphabet of sigma letters: letters i.i.d. uniform, one uniform
+    motif, per string one copy with exactly d distinct positions each changed to one of the
+    sigma - 1 other letters uniformly."""
+    alphabet = bytes(alphabet)
+    sigma = len(alphabet)
+    if sigma < 2 or len(set(alphabet)) != sigma:
+        raise ValueError("need at least two distinct letters")
+    if not (1 <= l <= m) or not (0 <= d <= l) or n < 1:
+        raise ValueError("need n >= 1, 1 <= l <= m, 0 <= d <= l")
+    nm = n * m
+    u = splitmix64(seed, np.arange(nm + l + n * (1 + 2 * d), dtype=np.uint64))
+    alpha = np.frombuffer(alphabet, dtype=np.uint8)
+    codes = bounded(u[:nm], sigma).astype(np.int64).reshape(n, m)
+    motif = bounded(u[nm:nm + l], sigma).astype(np.int64)
+    positions = np.zeros(n, dtype=np.int64)
+    for i in range(n):
+        c0 = nm + l + i * (1 + 2 * d)
+        pos = int(bounded(u[c0], m - l + 1))
+        copy = motif.copy()
+        order = list(range(l))
+        for k in range(d):
+            j = k + int(bounded(u[c0 + 1 + k], l - k))
+            order[k], order[j] = order[j], order[k]
+            p = order[k]
+            copy[p] = (copy[p] + 1 + int(bounded(u[c0 + 1 + d + k], sigma - 1))) % sigma
+        codes[i, pos:pos + l] = copy
+        positions[i] = pos
+    seqs = alpha[codes].astype(np.uint8)
+    return Instance(seqs=np.ascontiguousarray(seqs), motif=bytes(alpha[motif]), positions=positions,
+                    l=l, d=d, seed=seed)
+
+
 def random_sequences(n: int, m: int, seed: int) -> np.ndarray:
     """n i.i.d. uniform DNA sequences of length m (no planted motif)."""
     u = splitmix64(seed, np.arange(n * m, dtype=np.uint64))
@@ -106,6 +143,9 @@ def random_sequences(n: int, m: int, seed: int) -> np.ndarray:
 
 #: plain single-instance configurations: (l, d) with n = 20, m = 600
 PLAIN_LD = [(9, 2), (15, 4), (17, 5), (19, 6)]
+
+#: protein (20-letter) single-instance configurations: (l, d) with n = 20, m = 600
+PROTEIN_LD = [(11, 4), (13, 5), (15, 6)]
 
 
 def plain_instance(l: int, d: int, seed: int = 1, n: int = 20, m: int = 600) -> Instance:

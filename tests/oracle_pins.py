@@ -258,6 +258,146 @@ def check_quorum(o) -> None:
     assert [int(k) for k in o.solve_quorum(seqs, l, d, 1, threads=1)] == sorted(want)
 
 
+# ------------------------------------------------------------- general alphabets (qPMS-Sigma)
+
+PROTEIN = pi.PROTEIN.decode()
+
+
+def n_ball_sigma(l: int, d: int, sigma: int) -> int:
+    """|B(x, d)| over sigma letters: choose i positions, sigma - 1 other letters each."""
+    return sum(math.comb(l, i) * (sigma - 1) ** i for i in range(d + 1))
+
+
+def alphabet_of(sigma: int) -> str:
+    # sigma distinct printable letters, deliberately not in ASCII order
+    return "".join(reversed("ACDEFGHIKLMNPQRSTVWYBJOUXZ0123456789"[:sigma]))
+
+
+def random_over(rng, alphabet: str, shape) -> np.ndarray:
+    letters = np.frombuffer(alphabet.encode(), dtype=np.uint8)
+    return letters[rng.integers(0, len(alphabet), size=shape)].astype(np.uint8)
+
+
+def py_sigma_motifs(seqs: np.ndarray, l: int, d: int, alphabet: str, q: int = 0) -> list[str]:
+    """Definition 5 over every string of alphabet^l, written out in Python (tiny cases only)."""
+    rows = [bytes(r).decode() for r in seqs]
+    need = q or len(rows)
+    out = []
+    for t in itertools.product(alphabet, repeat=l):
+        s = "".join(t)
+        hits = sum(1 for r in rows if any(py_hamming(s, r[j:j + l]) <= d for j in range(len(r) - l + 1)))
+        if hits >= need:
+            out.append(s)
+    return out          # itertools.product yields the alphabet's index order
+
+
+def as_strings(arr: np.ndarray) -> list[str]:
+    return [bytes(r).decode() for r in arr]
+
+
+def check_sigma_compression(o) -> None:
+    # ceil(log2 sigma) groups
+    assert [o.sigma_groups(s) for s in (2, 3, 4, 5, 8, 9, 16, 17, 20, 32)] == [1, 2, 2, 3, 3, 4, 4, 5, 5, 5]
+    rng = np.random.default_rng(21)
+    for sigma in (2, 3, 5, 17, 20, 32):
+        alpha = alphabet_of(sigma)
+        for _ in range(60):
+            l = int(rng.integers(1, 33))
+            a = bytes(random_over(rng, alpha, l)).decode()
+            b = bytes(random_over(rng, alpha, l)).decode()
+            pa, pb = o.sigma_compress(alpha, a), o.sigma_compress(alpha, b)
+            assert pa.shape == (o.sigma_groups(sigma), 1)
+            assert o.sigma_compressed_distance(pa, pb, l) == py_hamming(a, b), (sigma, a, b)
+            # group g, bit k holds bit g of the index of letter k
+            for k in (0, l - 1):
+                idx = alpha.index(a[k])
+                assert [(int(pa[g, 0]) >> k) & 1 for g in range(pa.shape[0])] == \
+                    [(idx >> g) & 1 for g in range(pa.shape[0])]
+    # over A, C, G, T the groups are the DNA planes of the paper's example
+    for s in ("AGGCTA", "GAGCAT", "ACGTTGCA"):
+        assert np.array_equal(o.sigma_compress(ACGT, s), o.compress(s))
+
+
+def check_sigma_neighbourhood_counts(o) -> None:
+    rng = np.random.default_rng(22)
+    for sigma, l, d in [(2, 10, 3), (3, 8, 8), (5, 6, 3), (20, 7, 2), (20, 5, 4), (32, 4, 2), (4, 13, 4)]:
+        alpha = alphabet_of(sigma)
+        x = bytes(random_over(rng, alpha, l)).decode()
+        assert o.sigma_neighbourhood_visits(alpha, x, d) == n_ball_sigma(l, d, sigma), (sigma, l, d)
+
+
+def check_sigma_bruteforce(o) -> None:
+    rng = np.random.default_rng(23)
+    # the oracle's brute force against the definition written out in Python
+    for sigma, n, m, l, d, q in [(3, 3, 8, 4, 1, 0), (5, 2, 7, 3, 1, 0), (2, 4, 9, 5, 1, 3), (20, 2, 5, 2, 1, 0)]:
+        alpha = alphabet_of(sigma)
+        seqs = random_over(rng, alpha, (n, m))
+        want = py_sigma_motifs(seqs, l, d, alpha, q)
+        assert as_strings(o.sigma_bruteforce(seqs, l, d, alpha, q=q)) == want, (sigma, n, m, l, d, q)
+        assert as_strings(o.sigma_solve(seqs, l, d, alpha, q=q, threads=1)) == want, (sigma, n, m, l, d, q)
+    # the tree search against the brute force on planted and random inputs, every quorum
+    for sigma, n, m, l, d, seed in [(2, 4, 20, 8, 2, 31), (3, 5, 18, 6, 2, 32), (5, 4, 16, 5, 2, 33),
+                                    (7, 3, 14, 5, 2, 34), (20, 3, 12, 4, 1, 35), (20, 4, 10, 3, 2, 36)]:
+        alpha = alphabet_of(sigma)
+        inst = pi.planted_instance_sigma(n, m, l, d, seed, alpha.encode())
+        for q in [0] + list(range(1, n)):
+            bf = o.sigma_bruteforce(inst.seqs, l, d, alpha, q=q)
+            got = o.sigma_solve(inst.seqs, l, d, alpha, q=q, threads=2)
+            assert np.array_equal(got, bf), (sigma, n, m, l, d, q)
+            assert inst.motif.decode() in as_strings(got)
+        seqs = random_over(rng, alpha, (n, m))
+        assert np.array_equal(o.sigma_solve(seqs, l, d, alpha, threads=2), o.sigma_bruteforce(seqs, l, d, alpha))
+
+
+def check_sigma_matches_dna(o) -> None:
+    # over A, C, G, T the general search is the DNA search
+    for (n, m, l, d, seed) in [(8, 60, 9, 2, 41), (6, 40, 10, 3, 42)]:
+        inst = pi.planted_instance(n, m, l, d, seed)
+        want = [o.decode(int(k), l) for k in o.solve(inst.seqs, l, d, threads=2)]
+        assert as_strings(o.sigma_solve(inst.seqs, l, d, ACGT, threads=2)) == want
+    inst = pi.planted_instance(6, 40, 8, 2, 43)
+    wq = [o.decode(int(k), 8) for k in o.solve_quorum(inst.seqs, 8, 2, 4, threads=2)]
+    assert as_strings(o.sigma_solve(inst.seqs, 8, 2, ACGT, q=4, threads=2)) == wq
+
+
+def check_sigma_relabelling(o) -> None:
+    # renaming the letters renames the motifs; the output order follows the alphabet given
+    inst = pi.planted_instance_sigma(5, 30, 6, 2, 51, PROTEIN.encode())
+    base = as_strings(o.sigma_solve(inst.seqs, 6, 2, PROTEIN, threads=2))
+    assert inst.motif.decode() in base
+    perm = np.random.default_rng(52).permutation(20)
+    alt = "".join("abcdefghijklmnopqrst"[i] for i in perm)        # letter PROTEIN[k] -> alt[k]
+    table = bytes.maketrans(PROTEIN.encode(), alt.encode())
+    seqs2 = np.frombuffer(inst.seqs.tobytes().translate(table), dtype=np.uint8).reshape(inst.seqs.shape)
+    got = as_strings(o.sigma_solve(seqs2, 6, 2, alt, threads=2))
+    assert sorted(got) == sorted(s.translate(str.maketrans(PROTEIN, alt)) for s in base)
+    key = [[alt.index(ch) for ch in s] for s in got]
+    assert key == sorted(key)                                      # index order of the given alphabet
+    assert len(set(got)) == len(got)
+
+
+def check_sigma_special_cases(o) -> None:
+    # d = 0: the l-mers present in every sequence
+    inst = pi.planted_instance_sigma(4, 40, 3, 0, 61, b"ACD")
+    sets = [lmers(bytes(row), 3) for row in inst.seqs]
+    want = sorted(set.intersection(*sets), key=lambda s: ["ACD".index(c) for c in s])
+    assert as_strings(o.sigma_solve(inst.seqs, 3, 0, "ACD", threads=1)) == want
+    # n = 1, m = l: exactly the sphere B(x, d)
+    x = "MKVLA"
+    got = as_strings(o.sigma_solve(np.frombuffer(x.encode(), np.uint8).reshape(1, 5), 5, 2, PROTEIN, threads=1))
+    assert len(got) == n_ball_sigma(5, 2, 20)
+    assert all(py_hamming(x, s) <= 2 for s in got)
+    # protein instances: the planted motif is found and every answer is a motif
+    for (l, d, seed) in [(7, 2, 62), (8, 3, 63)]:
+        inst = pi.planted_instance_sigma(10, 50, l, d, seed)
+        got = as_strings(o.sigma_solve(inst.seqs, l, d, PROTEIN))
+        assert inst.motif.decode() in got
+        for s in got:
+            assert o.is_motif(s, inst.seqs, d)
+
+
 ALL_PINS = [check_compression_example, check_distance_definitions, check_neighbourhood_counts,
             check_neighbourhood_members, check_pair_intersections, check_bruteforce_agreement,
-            check_planted_motif_found, check_special_cases, check_invariants, check_quorum]
+            check_planted_motif_found, check_special_cases, check_invariants, check_quorum,
+            check_sigma_compression, check_sigma_neighbourhood_counts, check_sigma_bruteforce,
+            check_sigma_matches_dna, check_sigma_relabelling, check_sigma_special_cases]

@@ -39,6 +39,19 @@ MUTANTS = {
     "quorum_seeds_first_only": ("(q > 0 ? (long)(n - q + 1) : 1L) * W", "1L * W"),
     # quorum test off by one
     "quorum_threshold": ("if (hits >= q)\n            return 1;", "if (hits > q)\n            return 1;"),
+    # general alphabets: the last letter of the alphabet never substituted
+    "sigma_last_letter_skipped": ("for (int b = 0; b < w->sigma; ++b) {\n                if (w->alphabet[b]",
+                                  "for (int b = 0; b < w->sigma - 1; ++b) {\n                if (w->alphabet[b]"),
+    # general alphabets: one bit-plane group too few when sigma is one above a power of two
+    "sigma_groups_short": ("while ((1 << g) < sigma)", "while ((1 << g) < sigma - 1)"),
+    # general alphabets: duplicates across seeds kept
+    "sigma_duplicates_kept": ("if (u == 0 || memcmp(", "if (u >= 0 || memcmp("),
+    # general alphabets: the sphere stops one level early
+    "sigma_tree_too_shallow": ("if (depth < w->d) {", "if (depth + 1 < w->d) {"),
+    # general alphabets: quorum seeds only from s_1
+    "sigma_quorum_seeds_first_only": ("(long)(q > 0 ? n - q + 1 : 1) * W", "(long)1 * W"),
+    # general alphabets: brute force skips the last letter at the last position
+    "sigma_bruteforce_counter": ("while (k >= 0 && idx[k] == sigma - 1)", "while (k >= 0 && idx[k] == sigma - 2)"),
     # Hamming distance counts matches instead of mismatches at the first position
     "hamming_first_position": ("for (int k = 0; k < l; ++k)\n        if (a[k] != b[k])",
                                "for (int k = 1; k < l; ++k)\n        if (a[k] != b[k])"),

@@ -128,3 +128,25 @@ def test_batch_and_served_workloads_follow_their_ranges():
     assert abs(np.mean(np.diff(times)) - 0.01) < 0.002
     for _, inst in reqs[:20]:
         assert inst.n == 20 and 200 <= inst.m <= 1200 and (inst.l, inst.d) in ((13, 4), (15, 4), (17, 5))
+
+
+@pytest.mark.parametrize("alphabet,l,d,seed", [(b"ACDEFGHIKLMNPQRSTVWY", 11, 4, 1), (b"01", 8, 3, 2),
+                                                (b"ACG", 6, 6, 3), (b"ACDEFGHIKLMNPQRSTVWY", 9, 0, 4)])
+def test_planting_rule_over_a_general_alphabet(alphabet, l, d, seed):
+    from planted_inputs import planted_instance_sigma
+    inst = planted_instance_sigma(12, 80, l, d, seed, alphabet)
+    assert set(inst.seqs.tobytes()) <= set(alphabet) and set(inst.motif) <= set(alphabet)
+    for i in range(inst.n):
+        p = int(inst.positions[i])
+        assert hamming(inst.seqs[i, p:p + l].tobytes(), inst.motif) == d
+    again = planted_instance_sigma(12, 80, l, d, seed, alphabet)
+    assert np.array_equal(inst.seqs, again.seqs) and inst.motif == again.motif
+
+
+def test_protein_background_uses_every_letter_uniformly():
+    from planted_inputs import PROTEIN, planted_instance_sigma
+    s = planted_instance_sigma(40, 1000, 5, 0, 9).seqs
+    counts = np.array([np.count_nonzero(s == ch) for ch in PROTEIN])
+    assert np.all(np.abs(counts / s.size - 1 / 20) < 0.005)
+    with pytest.raises(ValueError):
+        planted_instance_sigma(2, 10, 3, 1, 1, b"AA")
