@@ -10,8 +10,12 @@ the timed events). `e2e` times the host-buffer C-ABI call (pms_solve):
 upload, all kernels and the download of the result inside the clock.
 
 Other workloads (--workload): plain9_2, plain17_5, plain19_6 (single
-instances), batch (256 mixed instances in one persistent launch, compared
-with the same instances one by one), serve (Poisson request stream).
+instances), quorum15_4_q10 (the quorum form), protein9_3 / protein9_4 (the
+general-alphabet search over the twenty amino acids, n = 20, m = 600,
+through the host-buffer call pms_solve_sigma: `value` from the device time
+of its kernels, `e2e` from the call's wall time), batch (256 mixed instances
+in one persistent launch, compared with the same instances one by one),
+serve (Poisson request stream).
 `--impl reference` times the CPU oracle on bounded samples instead.
 Under torchrun each rank solves its own instances (no data exchange); the
 line reports the max over ranks of the timed region.
@@ -41,6 +45,8 @@ WORKLOADS = {
 }
 # quorum form: (l, d, q), n = 20, m = 600
 QUORUM_WORKLOADS = {"quorum15_4_q10": (15, 4, 10)}
+# general alphabet, the twenty amino acids: (l, d), n = 20, m = 600
+PROTEIN_WORKLOADS = {"protein9_3": (9, 3), "protein9_4": (9, 4)}
 L2_FLUSH_BYTES = 512 << 20
 
 # DRAM bytes (read + write) per launch of the verification kernel from one ncu
@@ -167,23 +173,27 @@ def rank_seeds(rank: int, count: int, base: int = 1) -> list[int]:
     return [base + rank * 100000 + i for i in range(count)]
 
 
-def n_ball(l: int, d: int) -> int:
-    return sum(math.comb(l, i) * 3 ** i for i in range(d + 1))
+def n_ball(l: int, d: int, sigma: int = 4) -> int:
+    return sum(math.comb(l, i) * (sigma - 1) ** i for i in range(d + 1))
 
 
 # ------------------------------------------------------------------ CPU baseline (oracle)
 
-def cpu_oracle_rate(l: int, d: int, n: int, m: int, seed: int, budget_s: float, q: int = 0) -> dict:
+def cpu_oracle_rate(l: int, d: int, n: int, m: int, seed: int, budget_s: float, q: int = 0,
+                    alphabet: bytes | None = None) -> dict:
     """The oracle as it stands, on a bounded slice of seeds of one instance, scaled to solves/s
-    (q > 0: the quorum form, seeds over s_1 .. s_{n-q+1})."""
+    (q > 0: the quorum form, seeds over s_1 .. s_{n-q+1}; alphabet: the general-alphabet search)."""
     import oracle
     o = oracle.Oracle()
-    inst = pi.planted_instance(n, m, l, d, seed)
+    inst = pi.planted_instance_sigma(n, m, l, d, seed, alphabet) if alphabet else pi.planted_instance(n, m, l, d, seed)
     W = (m - l + 1) * (n - q + 1 if q > 0 else 1)
     cores = os.cpu_count() or 1
+    sigma = len(alphabet) if alphabet else 4
 
     def run(lo, hi):
-        if q > 0:
+        if alphabet:
+            o.sigma_solve_seeds(inst.seqs, l, d, alphabet, lo, hi, q=q, threads=cores)
+        elif q > 0:
             o.solve_quorum_seeds(inst.seqs, l, d, q, lo, hi, threads=cores)
         else:
             o.solve_seeds(inst.seqs, l, d, lo, hi, threads=cores)
@@ -205,30 +215,34 @@ def cpu_oracle_rate(l: int, d: int, n: int, m: int, seed: int, budget_s: float, 
         lo += take
     solves_per_s = (total_seeds / W) / total_t
     return {"value": solves_per_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": f"{total_seeds} of {W} seeds of one ({l},{d}{f',q={q}' if q else ''}) n={n} m={m} instance, "
-                      f"{total_t:.1f} s, "
-                      f"scaled by {W}/{total_seeds}",
-            "candidate_checks_per_s": total_seeds * n_ball(l, d) / total_t}
+            "sample": f"{total_seeds} of {W} seeds of one ({l},{d}{f',q={q}' if q else ''}) n={n} m={m} "
+                      f"{'protein ' if alphabet else ''}instance, {total_t:.1f} s, scaled by {W}/{total_seeds}",
+            "candidate_checks_per_s": total_seeds * n_ball(l, d, sigma) / total_t}
 
 
 def run_reference(args, ws, rank) -> None:
     if rank != 0:
         return
-    l, d, q = QUORUM_WORKLOADS[args.workload] if args.workload in QUORUM_WORKLOADS \
-        else (*WORKLOADS.get(args.workload, (15, 4)), 0)
+    alphabet = pi.PROTEIN if args.workload in PROTEIN_WORKLOADS else None
+    if alphabet:
+        (l, d), q = PROTEIN_WORKLOADS[args.workload], 0
+    else:
+        l, d, q = QUORUM_WORKLOADS[args.workload] if args.workload in QUORUM_WORKLOADS \
+            else (*WORKLOADS.get(args.workload, (15, 4)), 0)
     n, m = 20, 600
     budget = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
     for s in range(args.warmup):
-        cpu_oracle_rate(l, d, n, m, 1000 + s, budget / 4, q=q)
+        cpu_oracle_rate(l, d, n, m, 1000 + s, budget / 4, q=q, alphabet=alphabet)
     rates = []
     for s in range(args.steps):
-        rates.append(cpu_oracle_rate(l, d, n, m, 1 + s, budget, q=q))
+        rates.append(cpu_oracle_rate(l, d, n, m, 1 + s, budget, q=q, alphabet=alphabet))
     value = statistics.mean(r["value"] for r in rates)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
-            "config": {"workload": (f"quorum ({l},{d}) q={q}" if q else f"plain ({l},{d})")
+            "config": {"workload": (f"quorum ({l},{d}) q={q}" if q else
+                                    f"protein ({l},{d})" if alphabet else f"plain ({l},{d})")
                                    + f" n={n} m={m}, CPU oracle on bounded seed samples"},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": rates[0]["cores"], "kind": "oracle",
                              "sample": rates[0]["sample"]},
@@ -359,6 +373,77 @@ def bench_plain(args, ws, rank, local, dist, l, d, q: int = 0) -> dict:
         "gpu_launches": 3 * K,   # packing + compatibility masks, verification, sort/unique
         "clocks": clocks,
         "candidates_tested_per_step": tested / K,
+    }
+
+
+def bench_sigma(args, ws, rank, local, dist, l, d) -> dict:
+    """The general-alphabet search on protein instances through pms_solve_sigma (host buffers)."""
+    import torch
+    import paper_2403_00306_gb300 as pms
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    n, m = 20, 600
+    K, Wm = args.steps, args.warmup
+    seeds = rank_seeds(rank, K + Wm)
+    insts = [pi.planted_instance_sigma(n, m, l, d, s) for s in seeds]
+    stream = torch.cuda.Stream(device=dev)
+    ctx = pms.Context(local)
+    ctx.set_stream(stream)
+    flush = make_flush(torch, dev)
+    for i in range(Wm):
+        ctx.solve_sigma(insts[i].seqs, l, d, pi.PROTEIN)
+    kern_ms, verify_ms, e2e_ms, cmps = [], [], [], []
+    barrier(dist)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(K):
+            with torch.cuda.stream(stream):
+                flush(k)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            out = ctx.solve_sigma(insts[Wm + k].seqs, l, d, pi.PROTEIN)
+            e2e_ms.append((time.perf_counter() - t0) * 1000.0)
+            s = ctx.stats()
+            kern_ms.append(s["ms_kernel"])
+            verify_ms.append(s["ms_verify"])
+            # one POPC per comparison: window vs seed, node bound, candidate vs row
+            cmps.append(s["cmp_rows"] + s["cmp_reduce"] + s["cmp_verify"])
+            assert insts[Wm + k].motif in {bytes(r) for r in out}, "planted motif missing"
+        torch.cuda.synchronize(dev)
+    barrier(dist)
+    total_ms = max_over_ranks(dist, sum(kern_ms))
+    solves = sum_over_ranks(dist, K)
+    value = solves / (total_ms / 1000.0)
+    e2e_total = max_over_ranks(dist, sum(e2e_ms))
+    probe_popc = ctx.probe_int_rate(0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = load_peaks()
+    fmax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak = probe_popc * sms * fmax
+    verify_avg = statistics.mean(verify_ms)
+    achieved = statistics.mean(cmps) / (verify_avg / 1000.0) if verify_avg > 0 else float("nan")
+    clocks = clk.summary()
+    ctx.close()
+    W = m - l + 1
+    return {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": K, "warmup": Wm,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"protein ({l},{d}) n={n} m={m}, 20-letter alphabet, one seeded FM-model "
+                               f"instance per step", "l": l, "d": d, "n": n, "m": m, "sigma": 20,
+                   "l2": "flushed between steps (512 MiB write, untimed)",
+                   "timing": "CUDA events on the library stream from the packing kernel to the sort kernel"},
+        "candidate_checks_per_s": solves * W * n_ball(l, d, 20) / (total_ms / 1000.0),
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tcmp/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "sigma_main_kernel (search)",
+                     "cmp_per_launch": statistics.mean(cmps), "verify_ms_per_launch": verify_avg,
+                     "peak_basis": f"one POPC per comparison: {probe_popc:.2f} POPC/clk/SM (probe) x {sms} SMs x "
+                                   f"{fmax/1e6:.0f} MHz",
+                     "share_of_step": verify_avg / (total_ms / K)},
+        "e2e": {"value": solves / (e2e_total / 1000.0), "unit": "solves/s", "h2d_bytes_per_step": n * m,
+                "d2h_bytes_per_step": 32 + 8 * 9 + l, "ms_per_step": e2e_total / K},
+        "gpu_launches": 3 * K,   # packing, search, sort/unique
+        "clocks": clocks,
     }
 
 
@@ -498,7 +583,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="plain15_4",
-                    choices=sorted(WORKLOADS) + sorted(QUORUM_WORKLOADS) + ["batch", "serve"])
+                    choices=sorted(WORKLOADS) + sorted(QUORUM_WORKLOADS) + sorted(PROTEIN_WORKLOADS)
+                    + ["batch", "serve"])
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
@@ -515,6 +601,11 @@ def main():
         line = bench_batch(args, ws, rank, local, dist)
     elif args.workload == "serve":
         line = bench_serve(args, ws, rank, local, dist)
+    elif args.workload in PROTEIN_WORKLOADS:
+        l, d = PROTEIN_WORKLOADS[args.workload]
+        line = bench_sigma(args, ws, rank, local, dist, l, d)
+        if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_oracle_rate(l, d, 20, 600, 424242, budget_s=15.0, alphabet=pi.PROTEIN)
     else:
         l, d, q = QUORUM_WORKLOADS[args.workload] if args.workload in QUORUM_WORKLOADS else (*WORKLOADS[args.workload], 0)
         line = bench_plain(args, ws, rank, local, dist, l, d, q)

@@ -188,6 +188,34 @@ int pms_solve(pms_ctx *h, const uint8_t *seqs, int n, int m, int l, int d,
 int pms_solve_device(pms_ctx *h, const uint8_t *d_seqs, int n, int m, int l, int d,
                      uint64_t *d_motifs, size_t capacity, uint32_t *d_status);
 
+/* General alphabets (the "Sigma" of qPMS-Sigma, chapter "Our Approach"):
+ * the (l,d,q)-motifs of n strings over an alphabet of sigma letters
+ * (Definitions 1-5), e.g. the twenty amino acids of protein sequences.
+ *   alphabet: host, sigma distinct bytes (no terminator needed), 2 <= sigma
+ *             <= 32; letter a of the alphabet has index a, and every
+ *             l-mer is compressed into ceil(log2 sigma) bit-planes
+ *             (section "String Compression").
+ *   seqs:     host, row-major n x m bytes, each one of the alphabet's letters;
+ *             read only during the call.
+ *   q:        quorum (0 or n: every string must hold an occurrence, the PMS
+ *             problem; 1 <= q < n: at least q strings, seeds then taken from
+ *             s_1..s_{n-q+1} by Observation 3.1).
+ * Limits: those of pms_solve (1 <= n <= PMS_NMAX, 1 <= l <= PMS_LMAX,
+ * l <= m <= 65536, 0 <= d < l) and d <= 16.
+ * On success *motifs points to *count motifs of l bytes each (letters of the
+ * alphabet, motif after motif, no separators), sorted lexicographically by
+ * letter index (the alphabet's own order) and unique; the memory is owned by
+ * h and valid until the next pms_solve_sigma on h or pms_destroy. The raw
+ * candidate buffer holds max_motifs keys (default 65536) and grows once, up
+ * to 2^22, when the first pass needs more; past that (or past an explicit
+ * max_motifs) the call returns PMS_ETOOMANY with *count = the raw count.
+ * Errors: PMS_EINVAL (null pointer, bad sigma, repeated letter, a byte not in
+ * the alphabet, parameters out of range), PMS_ENOMEM, PMS_ECUDA,
+ * PMS_ETOOMANY. Blocks until the result is on the host; pms_get_stats then
+ * reports this solve's counters (always counted) and device times. */
+int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_t *seqs, int n, int m, int l,
+                    int d, int q, const uint8_t **motifs, size_t *count);
+
 /* Solves k independent instances in one pass: one upload, one packing
  * launch, one persistent verification launch whose CTAs take (instance,
  * seed, chunk) items from a device work queue, one segmented sort/unique

@@ -26,7 +26,11 @@ LMAX, NMAX = 32, 64
 ABI_FUNCTIONS = ["pms_create", "pms_set_stream", "pms_set_allocator", "pms_set_options", "pms_get_options",
                  "pms_solve", "pms_solve_device", "pms_solve_batch", "pms_submit", "pms_wait", "pms_release",
                  "pms_get_stats", "pms_decode", "pms_last_error", "pms_probe_int_rate", "pms_destroy",
-                 "pms_solve_device_noalloc", "pms_autotune", "pms_save_tuning", "pms_load_tuning"]
+                 "pms_solve_device_noalloc", "pms_autotune", "pms_save_tuning", "pms_load_tuning",
+                 "pms_solve_sigma"]
+
+#: the twenty amino acids, one-letter codes (an alphabet for solve_sigma)
+PROTEIN = b"ACDEFGHIKLMNPQRSTVWY"
 
 
 class PMSError(RuntimeError):
@@ -114,6 +118,7 @@ def load(build_if_missing: bool = True):
             "pms_autotune": (ci, [vp, ci, ci, ci, ci, ctypes.c_void_p]),
             "pms_save_tuning": (ci, [vp, ctypes.c_char_p]),
             "pms_load_tuning": (ci, [vp, ctypes.c_char_p]),
+            "pms_solve_sigma": (ci, [vp, u8p, ci, u8p, ci, ci, ci, ci, ci, ctypes.POINTER(u8p), ctypes.POINTER(sz)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -344,6 +349,23 @@ class Context:
         if cnt.value == 0:
             return np.zeros(0, dtype=np.uint64)
         return np.frombuffer(ctypes.string_at(out, cnt.value * 8), dtype=np.uint64).copy()
+
+    def solve_sigma(self, seqs, l: int, d: int, alphabet=PROTEIN, q: int = 0) -> np.ndarray:
+        """Motifs over a general alphabet (bytes, 2..32 distinct letters) as a (count, l) uint8 array of
+        letters, rows in the alphabet's lexicographic order; q = 0: every sequence (PMS)."""
+        a = _as_seqs(seqs)
+        n, m = a.shape
+        alpha = np.frombuffer(alphabet.encode() if isinstance(alphabet, str) else bytes(alphabet), dtype=np.uint8)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        out = u8p()
+        cnt = ctypes.c_size_t()
+        rc = self._lib.pms_solve_sigma(self._h, ctypes.cast(alpha.__array_interface__["data"][0], u8p), len(alpha),
+                                       ctypes.cast(a.__array_interface__["data"][0], u8p), n, m, int(l), int(d),
+                                       int(q), ctypes.byref(out), ctypes.byref(cnt))
+        self._check(rc, "pms_solve_sigma")
+        if cnt.value == 0:
+            return np.zeros((0, int(l)), dtype=np.uint8)
+        return np.frombuffer(ctypes.string_at(out, cnt.value * int(l)), dtype=np.uint8).reshape(-1, int(l)).copy()
 
     def solve_device(self, d_seqs, n: int, m: int, l: int, d: int, d_motifs, capacity: int, d_status) -> None:
         """Enqueues a solve on device buffers (torch tensors or raw pointers); does not wait."""

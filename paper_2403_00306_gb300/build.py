@@ -1,6 +1,6 @@
 """Builds libpms.so (the CUDA library behind include/pms.h) in-tree for sm_103a.
 
-Both translation units are compiled in parallel with nvcc, then linked into
+The translation units are compiled in parallel with nvcc, then linked into
 one shared library with the CUDA runtime linked statically. The build is
 skipped when the library is newer than every source.
 """
@@ -19,7 +19,7 @@ LIB = os.path.join(OUT_DIR, "libpms.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-diag-suppress", "550", "-I", os.path.join(ROOT, "include")]
-UNITS = ["pms_kernels.cu", "pms_runtime.cu"]
+UNITS = ["pms_kernels.cu", "pms_runtime.cu", "pms_sigma.cu"]
 
 
 def _nvcc() -> str:

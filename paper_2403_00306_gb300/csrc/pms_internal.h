@@ -140,4 +140,62 @@ const void *sort_unique_kernel_fn();
 cudaError_t launch_probe(int kind, int iters, int blocks, unsigned long long *cycles, unsigned long long *sink,
                          cudaStream_t st);
 
+// ---------------------------------------------------------------- general alphabets (pms_sigma.cu)
+//
+// The qPMS-Sigma form over an alphabet of 2..32 letters: ceil(log2 sigma)
+// bit-planes per window, one seed per queue item, the tree of changed-position
+// sets walked by the threads of a CTA, letters enumerated depth-first per node.
+
+constexpr int kSigMaxD = 16;        // changed positions per candidate
+constexpr int kSigMaxPlanes = 5;    // ceil(log2 32)
+constexpr int kSigThreads = 256;    // threads of the search kernel's CTA
+constexpr int kSigSortThreads = 1024;
+constexpr int kSigSmemBytes = 64 * 1024;   // rows of one seed kept in shared memory
+
+// Work counters of the search kernel (always on), indices into a uint64 array.
+enum SigCounter {
+    kSgSeeds = 0,        // seeds taken from the queue
+    kSgSeedsInfeasible,  // seeds with too many sequences lacking a feasible occurrence
+    kSgNodes,            // position subsets (tree nodes) visited
+    kSgNodesPruned,      // subsets dismissed by the node bound
+    kSgChecks,           // depth-first checks of partial and full candidates
+    kSgLeaves,           // checks of full candidates (every changed position fixed)
+    kSgCmpRows,          // window comparisons building the rows
+    kSgCmpReduce,        // node-bound comparisons popc(D ^ P)
+    kSgCmpVerify,        // candidate-versus-row comparisons
+    kSgCntNum
+};
+
+// byte -> letter index (0xFF: not a letter of the alphabet), or index -> letter
+struct SigmaMap {
+    uint8_t v[256];
+};
+
+struct SigmaParams {
+    const uint32_t *planes;        // plane g of window (i, j) at g * n * W + i * W + j
+    int n, m, l, d, b, sigma, W;
+    int miss_max;                  // sequences a motif may miss: n - q
+    int nseeds;                    // seeds: the windows of s_1..s_{n-q+1}
+    long long nodes;               // position subsets per seed: sum over k <= d of C(l, k)
+    unsigned int *head;            // seed queue head (zeroed before the launch)
+    unsigned long long *raw;       // motif keys, 3 words each (most significant first)
+    unsigned long long *raw_count; // keys emitted (may exceed raw_cap)
+    unsigned long long raw_cap;    // keys the raw buffer holds (a power of two)
+    unsigned long long *counters;  // kSgCntNum
+    uint32_t *scratch;             // per CTA (1 + b) * scratch_rows words, for seeds whose rows exceed smem_rows
+    int scratch_rows;
+    int smem_rows;                 // rows a seed keeps in shared memory
+};
+
+int sigma_planes(int sigma);
+int sigma_smem_rows(int b);
+cudaError_t sigma_init_tables();
+cudaError_t sigma_main_occupancy(int b, int *blocks_per_sm);
+cudaError_t launch_sigma_pack(const uint8_t *seqs, int n, int m, int l, int b, const SigmaMap &map, uint32_t *planes,
+                              uint32_t *flags, cudaStream_t st);
+cudaError_t launch_sigma_main(const SigmaParams &p, int blocks, cudaStream_t st);
+cudaError_t launch_sigma_sort_unique(unsigned long long *raw, const unsigned long long *raw_count,
+                                     unsigned long long cap, int l, int b, const SigmaMap &letters, uint8_t *out,
+                                     unsigned long long *unique_count, cudaStream_t st);
+
 }  // namespace pms

@@ -179,6 +179,12 @@ struct pms_ctx {
         size_t cap = 0;
     };
     DBuf d_seqs, d_planes, d_raw, d_tmp, d_compat, d_rowlen, d_mode, d_meta, d_ctr, d_scratch, d_result;
+    // general-alphabet solves (pms_solve_sigma)
+    DBuf d_sg_seqs, d_sg_planes, d_sg_ctr, d_sg_raw, d_sg_out, d_sg_scratch;
+    bool sigma_ready = false;   // binomial table and kernel attributes loaded on the device
+    void *h_sg = nullptr;       // pinned: counters block, then the input letters
+    size_t h_sg_cap = 0;
+    std::vector<uint8_t> owned_sigma;   // letters returned by the last pms_solve_sigma
     void *h_result = nullptr;   // pinned
     size_t h_result_cap = 0;
     void *h_meta = nullptr;     // pinned staging for descriptors and inputs
@@ -2251,6 +2257,164 @@ int pms_probe_int_rate(pms_ctx *h, int kind, double *per_clk_per_sm)
     return PMS_OK;
 }
 
+// General alphabets (qPMS-Sigma). Host input, one seed per queue item of the
+// search kernel; the raw key buffer grows once if the first pass overflows it.
+int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_t *seqs, int n, int m, int l, int d,
+                    int q, const uint8_t **motifs, size_t *count)
+{
+    if (!h)
+        return PMS_EINVAL;
+    std::lock_guard<std::recursive_mutex> g(h->mu);
+    const double t0 = now_ms();
+    h->err.clear();
+    if (!alphabet || !seqs || !motifs || !count)
+        return h->fail(PMS_EINVAL, "null argument");
+    *motifs = nullptr;
+    *count = 0;
+    if (sigma < 2 || sigma > 32)
+        return h->fail(PMS_EINVAL, "sigma = %d outside [2, 32]", sigma);
+    SigmaMap map, letters;
+    memset(map.v, 0xFF, sizeof map.v);
+    memset(letters.v, 0, sizeof letters.v);
+    for (int a = 0; a < sigma; ++a) {
+        if (map.v[alphabet[a]] != 0xFF)
+            return h->fail(PMS_EINVAL, "letter 0x%02x repeated in the alphabet", alphabet[a]);
+        map.v[alphabet[a]] = (uint8_t)a;
+        letters.v[a] = alphabet[a];
+    }
+    int rc;
+    if ((rc = check_params(h, n, m, l, d)))
+        return rc;
+    if (d > kSigMaxD)
+        return h->fail(PMS_EINVAL, "d = %d above %d", d, kSigMaxD);
+    if (q < 0 || q > n)
+        return h->fail(PMS_EINVAL, "q = %d outside [0, n]", q);
+    const size_t nm = (size_t)n * m;
+    for (size_t i = 0; i < nm; ++i)
+        if (map.v[seqs[i]] == 0xFF)
+            return h->fail(PMS_EINVAL, "byte %zu (0x%02x) is not a letter of the alphabet", i, seqs[i]);
+    cudaSetDevice(h->device);
+    cudaError_t e;
+    if (!h->sigma_ready) {
+        if ((e = sigma_init_tables()) != cudaSuccess)
+            return h->cuda_fail(e, "general-alphabet tables");
+        h->sigma_ready = true;
+    }
+    const int qe = q == 0 ? n : q;
+    const int b = sigma_planes(sigma), W = m - l + 1;
+    long long nodes = 0;
+    for (int k = 0; k <= d; ++k)
+        nodes += (long long)binom(l, k);
+    const int nseeds = (n - qe + 1) * W;
+    int occ = 0;
+    if ((e = sigma_main_occupancy(b, &occ)) != cudaSuccess)
+        return h->cuda_fail(e, "occupancy");
+    occ = std::max(occ, 1);
+    const int per_sm = h->opt.ctas_per_sm > 0 ? std::min(h->opt.ctas_per_sm, occ) : occ;
+    const int blocks = (int)std::max(1LL, std::min<long long>((long long)h->num_sms * per_sm, nseeds));
+    const int smem_rows = sigma_smem_rows(b);
+    const int max_rows = (n - 1) * W;
+    const size_t NW = (size_t)n * W;
+    const size_t ctr_bytes = 32 + 8 * (size_t)kSgCntNum;   // head, raw count, unique count, flags, work counters
+    const bool capped = h->opt.max_motifs > 0;
+    unsigned long long cap = pow2_at_least(capped ? h->opt.max_motifs : ((size_t)1 << 16));
+    constexpr unsigned long long kRetryMax = 1ull << 22;
+    if ((rc = h->ensure(h->d_sg_seqs, nm)) || (rc = h->ensure(h->d_sg_planes, (size_t)4 * b * NW)) ||
+        (rc = h->ensure(h->d_sg_ctr, ctr_bytes)))
+        return rc;
+    if (max_rows > smem_rows && (rc = h->ensure(h->d_sg_scratch, (size_t)4 * blocks * (1 + b) * max_rows)))
+        return rc;
+    if ((rc = h->ensure_host(h->h_sg, h->h_sg_cap, 256 + nm)))
+        return rc;
+    char *h_ctr = (char *)h->h_sg;
+    memcpy(h_ctr + 256, seqs, nm);
+    unsigned long long raw = 0, uniq = 0, ctr[kSgCntNum] = {};
+    uint32_t flags = 0;
+    cudaStream_t st = h->stream;
+    for (int attempt = 0;; ++attempt) {
+        if ((rc = h->ensure(h->d_sg_raw, (size_t)24 * cap)) || (rc = h->ensure(h->d_sg_out, (size_t)l * cap)))
+            return rc;
+        char *c = (char *)h->d_sg_ctr.p;
+        SigmaParams p{};
+        p.planes = (const uint32_t *)h->d_sg_planes.p;
+        p.n = n;
+        p.m = m;
+        p.l = l;
+        p.d = d;
+        p.b = b;
+        p.sigma = sigma;
+        p.W = W;
+        p.miss_max = n - qe;
+        p.nseeds = nseeds;
+        p.nodes = nodes;
+        p.head = (unsigned int *)c;
+        p.raw = (unsigned long long *)h->d_sg_raw.p;
+        p.raw_count = (unsigned long long *)(c + 8);
+        p.raw_cap = cap;
+        p.counters = (unsigned long long *)(c + 32);
+        p.scratch = max_rows > smem_rows ? (uint32_t *)h->d_sg_scratch.p : nullptr;
+        p.scratch_rows = max_rows;
+        p.smem_rows = smem_rows;
+        if ((e = cudaMemcpyAsync(h->d_sg_seqs.p, h_ctr + 256, nm, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(c, 0, ctr_bytes, st)) != cudaSuccess || (e = cudaEventRecord(h->ev0, st)) != cudaSuccess ||
+            (e = launch_sigma_pack((const uint8_t *)h->d_sg_seqs.p, n, m, l, b, map, (uint32_t *)h->d_sg_planes.p,
+                                   (uint32_t *)(c + 24), st)) != cudaSuccess ||
+            (e = cudaEventRecord(h->evm0, st)) != cudaSuccess || (e = launch_sigma_main(p, blocks, st)) != cudaSuccess ||
+            (e = cudaEventRecord(h->evm1, st)) != cudaSuccess ||
+            (e = launch_sigma_sort_unique(p.raw, p.raw_count, cap, l, b, letters, (uint8_t *)h->d_sg_out.p,
+                                          (unsigned long long *)(c + 16), st)) != cudaSuccess ||
+            (e = cudaEventRecord(h->ev1, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(h_ctr, c, ctr_bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return h->cuda_fail(e, "general-alphabet solve");
+        memcpy(&raw, h_ctr + 8, 8);
+        memcpy(&uniq, h_ctr + 16, 8);
+        memcpy(&flags, h_ctr + 24, 4);
+        memcpy(ctr, h_ctr + 32, sizeof ctr);
+        if (raw > cap && !capped && attempt == 0 && raw <= kRetryMax) {
+            cap = pow2_at_least((size_t)raw);
+            continue;
+        }
+        break;
+    }
+    if (flags & 1u)
+        return h->fail(PMS_EINVAL, "byte outside the alphabet");
+    const size_t keep = (size_t)std::min(uniq, cap);
+    h->owned_sigma.resize(std::max<size_t>(keep * l, 1));
+    if (keep && ((e = cudaMemcpyAsync(h->owned_sigma.data(), h->d_sg_out.p, keep * l, cudaMemcpyDeviceToHost, st)) !=
+                     cudaSuccess ||
+                 (e = cudaStreamSynchronize(st)) != cudaSuccess))
+        return h->cuda_fail(e, "result copy");
+    pms_stats s{};
+    double nb = 0;
+    for (int k = 0; k <= d; ++k)
+        nb += (double)binom(l, k) * std::pow((double)(sigma - 1), k);
+    s.candidates = (uint64_t)std::min(nb * nseeds, 1.8e19);
+    s.subsets = ctr[kSgNodes];
+    s.subsets_pruned = ctr[kSgNodesPruned];
+    s.candidates_tested = ctr[kSgLeaves];
+    s.cmp_rows = ctr[kSgCmpRows];
+    s.cmp_reduce = ctr[kSgCmpReduce];
+    s.cmp_verify = ctr[kSgCmpVerify];
+    s.seeds_infeasible = ctr[kSgSeedsInfeasible];
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess)
+        s.ms_kernel = ms;
+    if (cudaEventElapsedTime(&ms, h->evm0, h->evm1) == cudaSuccess)
+        s.ms_verify = ms;
+    cudaGetLastError();
+    s.ms_total = now_ms() - t0;
+    h->stats = s;
+    h->stats_pending = false;
+    *motifs = h->owned_sigma.data();
+    *count = keep;
+    if (raw > cap) {
+        *count = (size_t)raw;
+        return h->fail(PMS_ETOOMANY, "%llu motifs (with duplicates) exceed the capacity; raise max_motifs", raw);
+    }
+    return PMS_OK;
+}
+
 void pms_destroy(pms_ctx *h)
 {
     if (!h)
@@ -2262,13 +2426,16 @@ void pms_destroy(pms_ctx *h)
     clear_graphs(h);
     if (h->cap_stream)
         cudaStreamDestroy(h->cap_stream);
-    pms_ctx::DBuf *bufs[] = {&h->d_seqs, &h->d_planes, &h->d_raw, &h->d_tmp, &h->d_compat, &h->d_rowlen, &h->d_mode, &h->d_meta, &h->d_ctr, &h->d_scratch, &h->d_result};
+    pms_ctx::DBuf *bufs[] = {&h->d_seqs, &h->d_planes, &h->d_raw, &h->d_tmp, &h->d_compat, &h->d_rowlen, &h->d_mode, &h->d_meta, &h->d_ctr, &h->d_scratch, &h->d_result,
+                             &h->d_sg_seqs, &h->d_sg_planes, &h->d_sg_ctr, &h->d_sg_raw, &h->d_sg_out, &h->d_sg_scratch};
     for (auto *b : bufs)
         h->dev_free(b->p, b->cap);
     if (h->h_result)
         cudaFreeHost(h->h_result);
     if (h->h_meta)
         cudaFreeHost(h->h_meta);
+    if (h->h_sg)
+        cudaFreeHost(h->h_sg);
     if (h->ev0)
         cudaEventDestroy(h->ev0);
     if (h->ev1)

@@ -1,0 +1,705 @@
+// pms_sigma.cu -- exact (l,d,q)-motif search over a general alphabet (the
+// qPMS-Sigma form of the paper's chapter "Our Approach": an alphabet Sigma of
+// sigma letters, every l-mer compressed into ceil(log2 sigma) groups of 32-bit
+// words, the distance of two compressed l-mers = popc of the OR over groups of
+// the group-wise XOR; section "String Compression").
+//
+// What is searched (Definitions 1-5, Observation 3.1). Every motif M lies in
+// B(x, d) for a window x of one of s_1..s_{n-q+1}; these windows are the seeds.
+// For a seed x the candidates are the strings c with d_H(c, x) <= d, organised
+// as the tree T_d(x) of qPMSPrune ("Previous Works"): a node is the set P of
+// changed positions (|P| <= d), its leaves the choices of a letter other than
+// x[p] at every p in P.
+//
+// Data per seed (one CTA). Rows: the feasible occurrences of x, i.e. the
+// windows w of the other sequences with d_H(x, w) <= 2d (no candidate of B(x, d)
+// can be within d of any other window), stored as D_w = mismatch mask of x and
+// w plus w's bit-planes, grouped by sequence, in shared memory (global memory
+// scratch when a seed has more rows than fit).
+//
+// Work per node P (one thread):
+//  1. node bound: any candidate c of node P has d_H(c, w) >= popc(D_w ^ P)
+//     (positions of D_w outside P keep x's letter and mismatch w; positions of
+//     P outside D_w carry a letter other than x[p] = w[p]), so P survives only
+//     if all but n - q of the other sequences hold a row with
+//     popc(D_w ^ P) <= d;
+//  2. letter classes: at a changed position p the letters that matter are the
+//     ones the surviving rows hold there (L_p); every other letter differs
+//     from all of them and from x[p], so all such letters are interchangeable
+//     and one representative stands for them (expanded at output);
+//  3. depth-first over the positions of P in ascending order: with the letters
+//     of the first t positions fixed, a row's distance is at least the
+//     mismatches outside the positions not fixed yet, and a prefix is
+//     abandoned as soon as more than n - q sequences have no row within d
+//     under that bound; at full depth the bound is the exact distance.
+// Output keys hold ceil(log2 sigma) bits per letter index, first letter most
+// significant (192 bits, three words), so ascending keys are the lexicographic
+// order of the alphabet as given; one CTA sorts, de-duplicates and decodes
+// them into letters.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pms_internal.h"
+
+namespace pms {
+
+__constant__ uint32_t c_sg_binom[33][33];
+static uint32_t h_sg_binom[33][33];   // host copy (filled by sigma_init_tables)
+
+__host__ __device__ inline uint32_t sg_binom(int a, int k)
+{
+#ifdef __CUDA_ARCH__
+    return c_sg_binom[a][k];
+#else
+    return h_sg_binom[a][k];
+#endif
+}
+
+__host__ __device__ inline int sg_popc(uint32_t v)
+{
+#ifdef __CUDA_ARCH__
+    return __popc(v);
+#else
+    return __builtin_popcount(v);
+#endif
+}
+
+// index of the lowest set bit (v != 0)
+__host__ __device__ inline int sg_ctz(uint32_t v)
+{
+#ifdef __CUDA_ARCH__
+    return __ffs(v) - 1;
+#else
+    return __builtin_ctz(v);
+#endif
+}
+
+// bit j of v's set bits, counted from the lowest (j < popc(v))
+__host__ __device__ inline int sg_nth_bit(uint32_t v, int j)
+{
+    for (; j > 0; --j)
+        v &= v - 1;
+    return sg_ctz(v);
+}
+
+// letter index at position p of an l-mer held as b planes (plane g at pl[g * stride])
+__host__ __device__ inline int sg_letter_at(const uint32_t *pl, int stride, int b, int p)
+{
+    int a = 0;
+    for (int g = 0; g < b; ++g)
+        a |= (int)((pl[g * stride] >> p) & 1u) << g;
+    return a;
+}
+
+// appends b bits to a 192-bit key (k0 most significant)
+__host__ __device__ inline void sg_key_push(unsigned long long &k0, unsigned long long &k1, unsigned long long &k2,
+                                            int b, int a)
+{
+    k0 = (k0 << b) | (k1 >> (64 - b));
+    k1 = (k1 << b) | (k2 >> (64 - b));
+    k2 = (k2 << b) | (unsigned long long)a;
+}
+
+// The r-th position subset in the order |P| = 0, 1, ..., d, and within a size
+// colexicographically (combinatorial number system: the subset
+// {c_k > ... > c_1} has rank sum_i C(c_i, i)). r < sum_{k <= d} C(l, k).
+__host__ __device__ inline uint32_t sg_unrank(long long r, int l)
+{
+    int k = 0;
+    while (r >= (long long)sg_binom(l, k)) {
+        r -= sg_binom(l, k);
+        ++k;
+    }
+    uint32_t P = 0;
+    for (int i = k; i >= 1; --i) {
+        int c = i - 1;
+        while (c + 1 < l && (long long)sg_binom(c + 1, i) <= r)
+            ++c;
+        P |= 1u << c;
+        r -= sg_binom(c, i);
+    }
+    return P;
+}
+
+// One seed's rows as the node search reads them.
+struct SgSeed {
+    const uint32_t *D;    // row e: mismatch mask against x
+    const uint32_t *Pl;   // row e: plane g at Pl[g * stride + e]
+    int stride;
+    const int *off;       // rows of sequence i: [off[i], off[i + 1]); the seed's own sequence has none
+    int n, l, d, b, miss_max, sx;
+    uint32_t full;        // the sigma letter bits
+    uint32_t x[kSigMaxPlanes];
+};
+
+struct SgCount {
+    unsigned long long nodes, pruned, checks, leaves, reduce, verify;
+};
+
+// The threads that search one node together: a warp on the GPU (rows split
+// over the lanes, decisions by vote), a single thread in host builds.
+struct SgWarp {
+    int lane;
+    static constexpr int width = 32;
+    __device__ bool any(bool p) const { return __any_sync(0xFFFFFFFFu, p); }
+    __device__ uint32_t or_all(uint32_t v) const
+    {
+        for (int s = 16; s > 0; s >>= 1)
+            v |= __shfl_xor_sync(0xFFFFFFFFu, v, s);
+        return v;
+    }
+    __device__ unsigned long long bcast(unsigned long long v) const { return __shfl_sync(0xFFFFFFFFu, v, 0); }
+};
+
+struct SgSingle {
+    int lane = 0;
+    static constexpr int width = 1;
+    __host__ __device__ bool any(bool p) const { return p; }
+    __host__ __device__ uint32_t or_all(uint32_t v) const { return v; }
+    __host__ __device__ unsigned long long bcast(unsigned long long v) const { return v; }
+};
+
+// Does sequence i hold a row within d of c, positions in U (changed positions
+// whose letter is not fixed yet) ignored? Rows failing the node bound
+// popc(D ^ P) <= d cannot be within d of any candidate of node P and are
+// passed over. The lanes take every width-th row; the trip count is uniform.
+template <class G>
+__host__ __device__ inline bool sg_seq_hit(const SgSeed &S, const G &grp, int i, uint32_t P, const uint32_t *c,
+                                           uint32_t keep, SgCount &ct)
+{
+    for (int e0 = S.off[i]; e0 < S.off[i + 1]; e0 += G::width) {
+        const int e = e0 + grp.lane;
+        bool hit = false;
+        if (e < S.off[i + 1]) {
+            ct.reduce++;
+            if (sg_popc(S.D[e] ^ P) <= S.d) {
+                ct.verify++;
+                uint32_t mm = 0;
+                for (int g = 0; g < S.b; ++g)
+                    mm |= c[g] ^ S.Pl[g * S.stride + e];
+                hit = sg_popc(mm & keep) <= S.d;
+            }
+        }
+        if (grp.any(hit))
+            return true;
+    }
+    return false;
+}
+
+// Step 3's test: all but miss_max of the other sequences hold such a row.
+template <class G>
+__host__ __device__ inline bool sg_check(const SgSeed &S, const G &grp, uint32_t P, const uint32_t *c, uint32_t U,
+                                         SgCount &ct)
+{
+    int misses = 0;
+    for (int i = 0; i < S.n; ++i) {
+        if (i == S.sx)
+            continue;
+        if (!sg_seq_hit(S, grp, i, P, c, ~U, ct) && ++misses > S.miss_max)
+            return false;
+    }
+    return true;
+}
+
+// Step 1, the node bound: all but miss_max of the other sequences hold a row
+// with popc(D ^ P) <= d.
+template <class G>
+__host__ __device__ inline bool sg_bound(const SgSeed &S, const G &grp, uint32_t P, SgCount &ct)
+{
+    int misses = 0;
+    for (int i = 0; i < S.n; ++i) {
+        if (i == S.sx)
+            continue;
+        bool found = false;
+        for (int e0 = S.off[i]; e0 < S.off[i + 1]; e0 += G::width) {
+            const int e = e0 + grp.lane;
+            bool hit = false;
+            if (e < S.off[i + 1]) {
+                ct.reduce++;
+                hit = sg_popc(S.D[e] ^ P) <= S.d;
+            }
+            if (grp.any(hit)) {
+                found = true;
+                break;
+            }
+        }
+        if (!found && ++misses > S.miss_max)
+            return false;
+    }
+    return true;
+}
+
+// Writes the motifs a full candidate stands for: at a position whose letter is
+// the representative of the interchangeable letters Wl[t], every letter of
+// Wl[t]. k = 0: the seed itself. One lane reserves the slots, the lanes split
+// the writes.
+template <class G, class Sink>
+__host__ __device__ void sg_emit(const SgSeed &S, const G &grp, const int *pos, const int *ch, const uint32_t *Wl,
+                                 int k, Sink &sink)
+{
+    unsigned long long count = 1;
+    for (int t = 0; t < k; ++t)
+        if (Wl[t] && ch[t] == sg_ctz(Wl[t])) {
+            count *= (unsigned long long)sg_popc(Wl[t]);
+            if (count > (1ull << 40))
+                count = 1ull << 40;   // far beyond any capacity: reported as overflow
+        }
+    unsigned long long base = 0;
+    if (grp.lane == 0)
+        base = sink.reserve(count);
+    base = grp.bcast(base);
+    const unsigned long long todo = sink.room(base, count);
+    for (unsigned long long e = grp.lane; e < todo; e += G::width) {
+        int letter[kSigMaxD];
+        unsigned long long r = e;
+        for (int t = 0; t < k; ++t) {
+            if (Wl[t] && ch[t] == sg_ctz(Wl[t])) {
+                const unsigned long long nt = (unsigned long long)sg_popc(Wl[t]);
+                letter[t] = sg_nth_bit(Wl[t], (int)(r % nt));
+                r /= nt;
+            } else {
+                letter[t] = ch[t];
+            }
+        }
+        unsigned long long k0 = 0, k1 = 0, k2 = 0;
+        int t = 0;
+        for (int p = 0; p < S.l; ++p) {
+            int a;
+            if (t < k && pos[t] == p)
+                a = letter[t++];
+            else
+                a = sg_letter_at(S.x, 1, S.b, p);
+            sg_key_push(k0, k1, k2, S.b, a);
+        }
+        sink.put(base + e, k0, k1, k2);
+    }
+}
+
+// The search below one tree node P (steps 1-3 of the file comment), by one
+// group of threads in lockstep: every branch below depends only on values the
+// whole group shares.
+template <class G, class Sink>
+__host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCount &ct, Sink &sink)
+{
+    const bool lead = grp.lane == 0;
+    if (lead)
+        ct.nodes++;
+    if (!sg_bound(S, grp, P, ct)) {
+        if (lead)
+            ct.pruned++;
+        return;
+    }
+    const int k = sg_popc(P);
+    if (k == 0) {   // the seed itself; the bound was its exact distance to every row
+        if (lead) {
+            ct.checks++;
+            ct.leaves++;
+        }
+        sg_emit(S, grp, nullptr, nullptr, nullptr, 0, sink);
+        return;
+    }
+    int pos[kSigMaxD], ch[kSigMaxD];
+    uint32_t L[kSigMaxD], T[kSigMaxD], Wl[kSigMaxD];
+    {
+        uint32_t M = P;
+        for (int t = 0; t < k; ++t) {
+            pos[t] = sg_ctz(M);
+            M &= M - 1;
+            L[t] = 0;
+        }
+    }
+    // step 2: the letters the rows passing the bound hold at the changed positions
+    for (int e = grp.lane; e < S.off[S.n]; e += G::width) {
+        ct.reduce++;
+        const uint32_t De = S.D[e];
+        if (sg_popc(De ^ P) > S.d)
+            continue;
+        uint32_t M = De & P;
+        while (M) {
+            const int p = sg_ctz(M);
+            M &= M - 1;
+            L[sg_popc(P & ((1u << p) - 1u))] |= 1u << sg_letter_at(S.Pl + e, S.stride, S.b, p);
+        }
+    }
+    for (int t = 0; t < k; ++t) {
+        L[t] = grp.or_all(L[t]);
+        Wl[t] = S.full & ~L[t] & ~(1u << sg_letter_at(S.x, 1, S.b, pos[t]));
+        T[t] = L[t] | (Wl[t] & (0u - Wl[t]));   // the rows' letters and one representative of the rest
+    }
+    // step 3: depth-first over the letter choices
+    uint32_t c[kSigMaxPlanes];
+    for (int g = 0; g < kSigMaxPlanes; ++g)
+        c[g] = S.x[g];
+    int t = 0;
+    ch[0] = sg_ctz(T[0]);
+    for (;;) {
+        const uint32_t bit = 1u << pos[t];
+        for (int g = 0; g < S.b; ++g)
+            c[g] = ((ch[t] >> g) & 1) ? (c[g] | bit) : (c[g] & ~bit);
+        const uint32_t U = P & ~(uint32_t)((2ull << pos[t]) - 1ull);   // changed positions above pos[t]
+        if (lead) {
+            ct.checks++;
+            if (t == k - 1)
+                ct.leaves++;
+        }
+        if (sg_check(S, grp, P, c, U, ct)) {
+            if (t == k - 1) {
+                sg_emit(S, grp, pos, ch, Wl, k, sink);
+            } else {
+                ++t;
+                ch[t] = sg_ctz(T[t]);
+                continue;
+            }
+        }
+        // the next choice at this depth, else back up
+        for (;;) {
+            const uint32_t rest = T[t] & ~(uint32_t)((2ull << ch[t]) - 1ull);
+            if (rest) {
+                ch[t] = sg_ctz(rest);
+                break;
+            }
+            if (--t < 0)
+                return;
+        }
+    }
+}
+
+// --------------------------------------------------------------------- kernels
+
+// Output of the search kernel: room for raw_cap keys, the count may run past it.
+struct SgDeviceSink {
+    unsigned long long *raw;
+    unsigned long long *count;
+    unsigned long long cap;
+    __host__ __device__ unsigned long long reserve(unsigned long long c)
+    {
+#ifdef __CUDA_ARCH__
+        return atomicAdd(count, c);
+#else
+        const unsigned long long b = *count;
+        *count += c;
+        return b;
+#endif
+    }
+    __host__ __device__ unsigned long long room(unsigned long long base, unsigned long long c) const
+    {
+        return base >= cap ? 0ull : (c < cap - base ? c : cap - base);
+    }
+    __host__ __device__ void put(unsigned long long slot, unsigned long long k0, unsigned long long k1,
+                                 unsigned long long k2)
+    {
+        raw[3 * slot] = k0;
+        raw[3 * slot + 1] = k1;
+        raw[3 * slot + 2] = k2;
+    }
+};
+
+// One thread per window: letter indices into b bit-planes; a byte outside the
+// alphabet sets flags[0] bit 0.
+__global__ void sigma_pack_kernel(const uint8_t *__restrict__ seqs, int n, int m, int l, int b, SigmaMap map,
+                                  uint32_t *__restrict__ planes, uint32_t *__restrict__ flags)
+{
+    const int W = m - l + 1;
+    const long long NW = (long long)n * W;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < NW;
+         w += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(w / W);
+        const int j = (int)(w - (long long)i * W);
+        const uint8_t *s = seqs + (size_t)i * m + j;
+        uint32_t pl[kSigMaxPlanes] = {0u, 0u, 0u, 0u, 0u};
+        bool bad = false;
+        for (int k = 0; k < l; ++k) {
+            const unsigned a = map.v[s[k]];
+            if (a == 0xFFu) {
+                bad = true;
+                continue;
+            }
+            for (int g = 0; g < kSigMaxPlanes; ++g)
+                pl[g] |= ((a >> g) & 1u) << k;
+        }
+        if (bad)
+            atomicOr(flags, 1u);
+        for (int g = 0; g < b; ++g)
+            planes[(size_t)g * NW + w] = pl[g];
+    }
+}
+
+// Persistent CTAs take one seed at a time from the queue: rows of the seed
+// (two passes over every window: count per sequence, then place), then the
+// tree nodes of the seed, claimed one at a time by the CTA's warps.
+__global__ void __launch_bounds__(kSigThreads) sigma_main_kernel(SigmaParams p)
+{
+    extern __shared__ uint32_t sg_rows_smem[];
+    __shared__ int s_cnt[kNMax], s_cur[kNMax], s_off[kNMax + 1];
+    __shared__ int s_seed, s_skip;
+    __shared__ unsigned long long s_next;
+    __shared__ unsigned long long s_ct[kSgCntNum];
+    const int tid = threadIdx.x;
+    for (int c = tid; c < kSgCntNum; c += blockDim.x)
+        s_ct[c] = 0;
+    SgCount ct{};
+    unsigned long long cmp_rows = 0, seeds = 0, infeasible = 0;
+    SgDeviceSink sink{p.raw, p.raw_count, p.raw_cap};
+    const int NW = p.n * p.W;
+    for (;;) {
+        if (tid == 0)
+            s_seed = (int)atomicAdd(p.head, 1u);
+        if (tid < p.n)
+            s_cnt[tid] = 0;
+        __syncthreads();
+        const int seed = s_seed;
+        if (seed >= p.nseeds)
+            break;
+        const int sx = seed / p.W;
+        const int xw = sx * p.W + (seed - sx * p.W);
+        SgSeed S;
+        for (int g = 0; g < kSigMaxPlanes; ++g)
+            S.x[g] = g < p.b ? p.planes[(size_t)g * NW + xw] : 0u;
+        for (int w = tid; w < NW; w += blockDim.x) {
+            const int i = w / p.W;
+            if (i == sx)
+                continue;
+            uint32_t mm = 0;
+            for (int g = 0; g < p.b; ++g)
+                mm |= S.x[g] ^ p.planes[(size_t)g * NW + w];
+            cmp_rows++;
+            if (__popc(mm) <= 2 * p.d)
+                atomicAdd(&s_cnt[i], 1);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int o = 0, misses = 0;
+            for (int i = 0; i < p.n; ++i) {
+                s_off[i] = o;
+                s_cur[i] = o;
+                o += s_cnt[i];
+                if (i != sx && s_cnt[i] == 0)
+                    ++misses;
+            }
+            s_off[p.n] = o;
+            s_skip = misses > p.miss_max;
+            s_next = 0;
+            seeds++;
+            if (s_skip)
+                infeasible++;
+        }
+        __syncthreads();
+        if (!s_skip) {
+            const int total = s_off[p.n];
+            uint32_t *rows;
+            int stride;
+            if (total <= p.smem_rows) {
+                rows = sg_rows_smem;
+                stride = p.smem_rows;
+            } else {
+                rows = p.scratch + (size_t)blockIdx.x * (1 + p.b) * p.scratch_rows;
+                stride = p.scratch_rows;
+            }
+            for (int w = tid; w < NW; w += blockDim.x) {
+                const int i = w / p.W;
+                if (i == sx)
+                    continue;
+                uint32_t pl[kSigMaxPlanes];
+                uint32_t mm = 0;
+                for (int g = 0; g < p.b; ++g) {
+                    pl[g] = p.planes[(size_t)g * NW + w];
+                    mm |= S.x[g] ^ pl[g];
+                }
+                if (__popc(mm) <= 2 * p.d) {
+                    const int e = atomicAdd(&s_cur[i], 1);
+                    rows[e] = mm;
+                    for (int g = 0; g < p.b; ++g)
+                        rows[(size_t)(1 + g) * stride + e] = pl[g];
+                }
+            }
+            __syncthreads();
+            S.D = rows;
+            S.Pl = rows + stride;
+            S.stride = stride;
+            S.off = s_off;
+            S.n = p.n;
+            S.l = p.l;
+            S.d = p.d;
+            S.b = p.b;
+            S.miss_max = p.miss_max;
+            S.sx = sx;
+            S.full = p.sigma == 32 ? 0xFFFFFFFFu : (1u << p.sigma) - 1u;
+            // each warp claims the seed's nodes one at a time
+            const SgWarp grp{tid & 31};
+            for (;;) {
+                unsigned long long r = 0;
+                if (grp.lane == 0)
+                    r = atomicAdd(&s_next, 1ull);
+                r = grp.bcast(r);
+                if (r >= (unsigned long long)p.nodes)
+                    break;
+                sg_node(S, grp, sg_unrank((long long)r, p.l), ct, sink);
+            }
+        }
+        __syncthreads();   // rows, offsets and s_seed are rewritten for the next seed
+    }
+    atomicAdd(&s_ct[kSgNodes], ct.nodes);
+    atomicAdd(&s_ct[kSgNodesPruned], ct.pruned);
+    atomicAdd(&s_ct[kSgChecks], ct.checks);
+    atomicAdd(&s_ct[kSgLeaves], ct.leaves);
+    atomicAdd(&s_ct[kSgCmpReduce], ct.reduce);
+    atomicAdd(&s_ct[kSgCmpVerify], ct.verify);
+    atomicAdd(&s_ct[kSgCmpRows], cmp_rows);
+    if (tid == 0) {
+        s_ct[kSgSeeds] += seeds;
+        s_ct[kSgSeedsInfeasible] += infeasible;
+    }
+    __syncthreads();
+    if (tid < kSgCntNum)
+        atomicAdd(&p.counters[tid], s_ct[tid]);
+}
+
+__host__ __device__ inline bool sg_less(const unsigned long long *a, const unsigned long long *b)
+{
+    if (a[0] != b[0])
+        return a[0] < b[0];
+    if (a[1] != b[1])
+        return a[1] < b[1];
+    return a[2] < b[2];
+}
+
+// One CTA: bitonic sort of the raw keys (padded with all-ones keys to a power
+// of two, within the buffer's power-of-two capacity), then unique + decode into
+// l letters per motif.
+__global__ void __launch_bounds__(kSigSortThreads) sigma_sort_unique_kernel(
+    unsigned long long *__restrict__ raw, const unsigned long long *__restrict__ raw_count, unsigned long long cap,
+    int l, int b, SigmaMap letters, uint8_t *__restrict__ out, unsigned long long *__restrict__ unique_count)
+{
+    __shared__ unsigned int s_warp[kSigSortThreads / 32];
+    __shared__ unsigned int s_total;
+    __shared__ unsigned long long s_base;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const unsigned long long N = *raw_count < cap ? *raw_count : cap;
+    unsigned long long P2 = 1;
+    while (P2 < N)
+        P2 <<= 1;
+    for (unsigned long long i = tid; i < P2; i += nt)
+        if (i >= N)
+            raw[3 * i] = raw[3 * i + 1] = raw[3 * i + 2] = ~0ull;
+    __syncthreads();
+    for (unsigned long long k = 2; k <= P2; k <<= 1) {
+        for (unsigned long long j = k >> 1; j > 0; j >>= 1) {
+            for (unsigned long long i = tid; i < P2; i += nt) {
+                const unsigned long long ixj = i ^ j;
+                if (ixj > i) {
+                    unsigned long long *a = raw + 3 * i, *c = raw + 3 * ixj;
+                    const bool up = (i & k) == 0;
+                    if (up ? sg_less(c, a) : sg_less(a, c)) {
+                        for (int w = 0; w < 3; ++w) {
+                            const unsigned long long v = a[w];
+                            a[w] = c[w];
+                            c[w] = v;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (tid == 0)
+        s_base = 0;
+    __syncthreads();
+    const int lane = tid & 31, wid = tid >> 5;
+    for (unsigned long long start = 0; start < N; start += nt) {
+        const unsigned long long i = start + tid;
+        const bool f = i < N && (i == 0 || raw[3 * i] != raw[3 * i - 3] || raw[3 * i + 1] != raw[3 * i - 2] ||
+                                 raw[3 * i + 2] != raw[3 * i - 1]);
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, f);
+        if (lane == 0)
+            s_warp[wid] = __popc(bal);
+        __syncthreads();
+        if (tid == 0) {
+            unsigned acc = 0;
+            for (int w = 0; w < nt / 32; ++w) {
+                const unsigned v = s_warp[w];
+                s_warp[w] = acc;
+                acc += v;
+            }
+            s_total = acc;
+        }
+        __syncthreads();
+        if (f) {
+            const unsigned long long idx = s_base + s_warp[wid] + __popc(bal & ((1u << lane) - 1u));
+            const unsigned long long key[3] = {raw[3 * i], raw[3 * i + 1], raw[3 * i + 2]};
+            for (int p = 0; p < l; ++p) {
+                const int s = b * (l - 1 - p);
+                int a = 0;
+                for (int j = 0; j < b; ++j) {
+                    const int bit = s + j;
+                    a |= (int)((key[2 - (bit >> 6)] >> (bit & 63)) & 1ull) << j;
+                }
+                out[idx * l + p] = letters.v[a];
+            }
+        }
+        __syncthreads();
+        if (tid == 0)
+            s_base += s_total;
+        __syncthreads();
+    }
+    if (tid == 0)
+        *unique_count = s_base;
+}
+
+// --------------------------------------------------------------------- host side
+
+int sigma_planes(int sigma)
+{
+    int g = 0;
+    while ((1 << g) < sigma)
+        ++g;
+    return g;
+}
+
+int sigma_smem_rows(int b)
+{
+    return kSigSmemBytes / (4 * (1 + b));
+}
+
+cudaError_t sigma_init_tables()
+{
+    for (int a = 0; a <= 32; ++a)
+        for (int k = 0; k <= 32; ++k)
+            h_sg_binom[a][k] = k > a ? 0u : (k == 0 || k == a ? 1u : h_sg_binom[a - 1][k - 1] + h_sg_binom[a - 1][k]);
+    cudaError_t e = cudaMemcpyToSymbol(c_sg_binom, h_sg_binom, sizeof h_sg_binom);
+    if (e != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(sigma_main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSigSmemBytes);
+}
+
+cudaError_t sigma_main_occupancy(int b, int *blocks_per_sm)
+{
+    const size_t smem = (size_t)4 * (1 + b) * sigma_smem_rows(b);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sigma_main_kernel, kSigThreads, smem);
+}
+
+cudaError_t launch_sigma_pack(const uint8_t *seqs, int n, int m, int l, int b, const SigmaMap &map, uint32_t *planes,
+                              uint32_t *flags, cudaStream_t st)
+{
+    const long long NW = (long long)n * (m - l + 1);
+    const int threads = 256;
+    const int blocks = (int)((NW + threads - 1) / threads);
+    sigma_pack_kernel<<<blocks, threads, 0, st>>>(seqs, n, m, l, b, map, planes, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sigma_main(const SigmaParams &p, int blocks, cudaStream_t st)
+{
+    const size_t smem = (size_t)4 * (1 + p.b) * p.smem_rows;
+    sigma_main_kernel<<<blocks, kSigThreads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sigma_sort_unique(unsigned long long *raw, const unsigned long long *raw_count,
+                                     unsigned long long cap, int l, int b, const SigmaMap &letters, uint8_t *out,
+                                     unsigned long long *unique_count, cudaStream_t st)
+{
+    sigma_sort_unique_kernel<<<1, kSigSortThreads, 0, st>>>(raw, raw_count, cap, l, b, letters, out, unique_count);
+    return cudaGetLastError();
+}
+
+}  // namespace pms
