@@ -132,8 +132,9 @@ struct SgSeed {
     uint32_t x[kSigMaxPlanes];
 };
 
+// Work of one node by one thread (32-bit; summed over the warp into 64-bit counters after each node).
 struct SgCount {
-    unsigned long long nodes, pruned, checks, leaves, reduce, verify;
+    unsigned int nodes, pruned, checks, leaves, reduce, verify;
 };
 
 // The threads that search one node together: a warp on the GPU (rows split
@@ -149,6 +150,14 @@ struct SgWarp {
         return v;
     }
     __device__ unsigned long long bcast(unsigned long long v) const { return __shfl_sync(0xFFFFFFFFu, v, 0); }
+    __device__ uint32_t ballot(bool p) const { return __ballot_sync(0xFFFFFFFFu, p); }
+    __device__ void sync() const { __syncwarp(); }
+    __device__ unsigned long long sum(unsigned long long v) const
+    {
+        for (int s = 16; s > 0; s >>= 1)
+            v += __shfl_xor_sync(0xFFFFFFFFu, v, s);
+        return v;
+    }
 };
 
 struct SgSingle {
@@ -157,14 +166,18 @@ struct SgSingle {
     __host__ __device__ bool any(bool p) const { return p; }
     __host__ __device__ uint32_t or_all(uint32_t v) const { return v; }
     __host__ __device__ unsigned long long bcast(unsigned long long v) const { return v; }
+    __host__ __device__ uint32_t ballot(bool p) const { return p ? 1u : 0u; }
+    __host__ __device__ void sync() const {}
+    __host__ __device__ unsigned long long sum(unsigned long long v) const { return v; }
 };
 
-// Does sequence i hold a row within d of c, positions in U (changed positions
-// whose letter is not fixed yet) ignored? Rows failing the node bound
-// popc(D ^ P) <= d cannot be within d of any candidate of node P and are
-// passed over. The lanes take every width-th row; the trip count is uniform.
+// The first row of sequence i (in the lanes' scan order) within d of c,
+// positions in U (changed positions whose letter is not fixed yet) ignored, or
+// -1. Rows failing the node bound popc(D ^ P) <= d cannot be within d of any
+// candidate of node P and are passed over. The lanes take every width-th row;
+// the trip count and the result are uniform.
 template <class G>
-__host__ __device__ inline bool sg_seq_hit(const SgSeed &S, const G &grp, int i, uint32_t P, const uint32_t *c,
+__host__ __device__ inline int sg_seq_find(const SgSeed &S, const G &grp, int i, uint32_t P, const uint32_t *c,
                                            uint32_t keep, SgCount &ct)
 {
     for (int e0 = S.off[i]; e0 < S.off[i + 1]; e0 += G::width) {
@@ -180,23 +193,50 @@ __host__ __device__ inline bool sg_seq_hit(const SgSeed &S, const G &grp, int i,
                 hit = sg_popc(mm & keep) <= S.d;
             }
         }
-        if (grp.any(hit))
-            return true;
+        const uint32_t bal = grp.ballot(hit);
+        if (bal)
+            return e0 + sg_ctz(bal);
     }
-    return false;
+    return -1;
 }
 
-// Step 3's test: all but miss_max of the other sequences hold such a row.
+// Step 3's test: all but miss_max of the other sequences hold a row within d
+// of c (positions in U ignored). Two orderings make it cheap without changing
+// its answer: the row that held sequence i's occurrence at an earlier check
+// (wit[i]) is tried before the scan -- any row of the sequence gives a valid
+// lower bound -- and the sequence that failed the previous check (fail) is
+// tested first, since the siblings of a rejected prefix tend to fail on it too.
+// Every lane writes the same witness, so each lane reads back its own write.
 template <class G>
 __host__ __device__ inline bool sg_check(const SgSeed &S, const G &grp, uint32_t P, const uint32_t *c, uint32_t U,
-                                         SgCount &ct)
+                                         SgCount &ct, int *wit, int &fail)
 {
+    const uint32_t keep = ~U;
     int misses = 0;
-    for (int i = 0; i < S.n; ++i) {
-        if (i == S.sx)
+    for (int step = -1; step < S.n; ++step) {
+        const int i = step < 0 ? fail : step;
+        if (i < 0 || i == S.sx || (step >= 0 && i == fail))
             continue;
-        if (!sg_seq_hit(S, grp, i, P, c, ~U, ct) && ++misses > S.miss_max)
+        const int w = wit[i];
+        bool hit = false;
+        if (w >= 0) {
+            ct.verify++;
+            uint32_t mm = 0;
+            for (int g = 0; g < S.b; ++g)
+                mm |= c[g] ^ S.Pl[g * S.stride + w];
+            hit = sg_popc(mm & keep) <= S.d;
+        }
+        if (!hit) {
+            const int e = sg_seq_find(S, grp, i, P, c, keep, ct);
+            if (e >= 0) {
+                hit = true;
+                wit[i] = e;
+            }
+        }
+        if (!hit && ++misses > S.miss_max) {
+            fail = i;
             return false;
+        }
     }
     return true;
 }
@@ -275,74 +315,40 @@ __host__ __device__ void sg_emit(const SgSeed &S, const G &grp, const int *pos, 
     }
 }
 
-// The search below one tree node P (steps 1-3 of the file comment), by one
-// group of threads in lockstep: every branch below depends only on values the
-// whole group shares.
+// Step 3: depth-first over the letter choices T[t] of the changed positions
+// pos[0..k-1]. With a pivot row (wl non-null: the row's letter at each changed
+// position where it differs from x, -1 at the others) a choice is taken only
+// while at most `slack` of those positions carry a letter other than the
+// row's, which keeps the row within d of the candidate.
 template <class G, class Sink>
-__host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCount &ct, Sink &sink)
+__host__ __device__ void sg_dfs(const SgSeed &S, const G &grp, uint32_t P, int k, const int *pos, const uint32_t *T,
+                                const uint32_t *Wl, const int *wl, int slack, SgCount &ct, Sink &sink, int *wit,
+                                int &fail)
 {
     const bool lead = grp.lane == 0;
-    if (lead)
-        ct.nodes++;
-    if (!sg_bound(S, grp, P, ct)) {
-        if (lead)
-            ct.pruned++;
-        return;
-    }
-    const int k = sg_popc(P);
-    if (k == 0) {   // the seed itself; the bound was its exact distance to every row
-        if (lead) {
-            ct.checks++;
-            ct.leaves++;
-        }
-        sg_emit(S, grp, nullptr, nullptr, nullptr, 0, sink);
-        return;
-    }
-    int pos[kSigMaxD], ch[kSigMaxD];
-    uint32_t L[kSigMaxD], T[kSigMaxD], Wl[kSigMaxD];
-    {
-        uint32_t M = P;
-        for (int t = 0; t < k; ++t) {
-            pos[t] = sg_ctz(M);
-            M &= M - 1;
-            L[t] = 0;
-        }
-    }
-    // step 2: the letters the rows passing the bound hold at the changed positions
-    for (int e = grp.lane; e < S.off[S.n]; e += G::width) {
-        ct.reduce++;
-        const uint32_t De = S.D[e];
-        if (sg_popc(De ^ P) > S.d)
-            continue;
-        uint32_t M = De & P;
-        while (M) {
-            const int p = sg_ctz(M);
-            M &= M - 1;
-            L[sg_popc(P & ((1u << p) - 1u))] |= 1u << sg_letter_at(S.Pl + e, S.stride, S.b, p);
-        }
-    }
-    for (int t = 0; t < k; ++t) {
-        L[t] = grp.or_all(L[t]);
-        Wl[t] = S.full & ~L[t] & ~(1u << sg_letter_at(S.x, 1, S.b, pos[t]));
-        T[t] = L[t] | (Wl[t] & (0u - Wl[t]));   // the rows' letters and one representative of the rest
-    }
-    // step 3: depth-first over the letter choices
+    int ch[kSigMaxD], used[kSigMaxD];
     uint32_t c[kSigMaxPlanes];
     for (int g = 0; g < kSigMaxPlanes; ++g)
         c[g] = S.x[g];
     int t = 0;
     ch[0] = sg_ctz(T[0]);
     for (;;) {
-        const uint32_t bit = 1u << pos[t];
-        for (int g = 0; g < S.b; ++g)
-            c[g] = ((ch[t] >> g) & 1) ? (c[g] | bit) : (c[g] & ~bit);
-        const uint32_t U = P & ~(uint32_t)((2ull << pos[t]) - 1ull);   // changed positions above pos[t]
-        if (lead) {
-            ct.checks++;
-            if (t == k - 1)
-                ct.leaves++;
+        bool ok = false;
+        const int u = (t > 0 ? used[t - 1] : 0) + ((wl && wl[t] >= 0 && ch[t] != wl[t]) ? 1 : 0);
+        if (!wl || u <= slack) {
+            used[t] = u;
+            const uint32_t bit = 1u << pos[t];
+            for (int g = 0; g < S.b; ++g)
+                c[g] = ((ch[t] >> g) & 1) ? (c[g] | bit) : (c[g] & ~bit);
+            const uint32_t U = P & ~(uint32_t)((2ull << pos[t]) - 1ull);   // changed positions above pos[t]
+            if (lead) {
+                ct.checks++;
+                if (t == k - 1)
+                    ct.leaves++;
+            }
+            ok = sg_check(S, grp, P, c, U, ct, wit, fail);
         }
-        if (sg_check(S, grp, P, c, U, ct)) {
+        if (ok) {
             if (t == k - 1) {
                 sg_emit(S, grp, pos, ch, Wl, k, sink);
             } else {
@@ -361,6 +367,104 @@ __host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCo
             if (--t < 0)
                 return;
         }
+    }
+}
+
+// The search below one tree node P (steps 1-3 of the file comment), by one
+// group of threads in lockstep: every branch below depends only on values the
+// whole group shares.
+template <class G, class Sink>
+__host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCount &ct, Sink &sink, int *wit)
+{
+    const bool lead = grp.lane == 0;
+    if (lead)
+        ct.nodes++;
+    if (!sg_bound(S, grp, P, ct)) {
+        if (lead)
+            ct.pruned++;
+        return;
+    }
+    const int k = sg_popc(P);
+    if (k == 0) {   // the seed itself; the bound was its exact distance to every row
+        if (lead) {
+            ct.checks++;
+            ct.leaves++;
+        }
+        sg_emit(S, grp, nullptr, nullptr, nullptr, 0, sink);
+        return;
+    }
+    int pos[kSigMaxD];
+    uint32_t L[kSigMaxD], T[kSigMaxD], Wl[kSigMaxD];
+    {
+        uint32_t M = P;
+        for (int t = 0; t < k; ++t) {
+            pos[t] = sg_ctz(M);
+            M &= M - 1;
+            L[t] = 0;
+        }
+    }
+    // step 2: the letters the rows passing the bound hold at the changed
+    // positions, and the sequence with the fewest such rows (the pivot)
+    int piv = -1, piv_rows = 0;
+    for (int i = 0; i < S.n; ++i) {
+        if (i == S.sx)
+            continue;
+        int cnt = 0;
+        for (int e0 = S.off[i]; e0 < S.off[i + 1]; e0 += G::width) {
+            const int e = e0 + grp.lane;
+            bool pass = false;
+            if (e < S.off[i + 1]) {
+                ct.reduce++;
+                const uint32_t De = S.D[e];
+                pass = sg_popc(De ^ P) <= S.d;
+                if (pass) {
+                    uint32_t M = De & P;
+                    while (M) {
+                        const int p = sg_ctz(M);
+                        M &= M - 1;
+                        L[sg_popc(P & ((1u << p) - 1u))] |= 1u << sg_letter_at(S.Pl + e, S.stride, S.b, p);
+                    }
+                }
+            }
+            cnt += sg_popc(grp.ballot(pass));
+        }
+        if (piv < 0 || cnt < piv_rows) {
+            piv = i;
+            piv_rows = cnt;
+        }
+    }
+    for (int t = 0; t < k; ++t) {
+        L[t] = grp.or_all(L[t]);
+        Wl[t] = S.full & ~L[t] & ~(1u << sg_letter_at(S.x, 1, S.b, pos[t]));
+        T[t] = L[t] | (Wl[t] & (0u - Wl[t]));   // the rows' letters and one representative of the rest
+    }
+    for (int j = grp.lane; j < S.n; j += G::width)
+        wit[j] = -1;
+    grp.sync();
+    int fail = -1;
+    // Pivot form (q = n; Observation 3.3 applied to the node): every motif of
+    // node P lies within d of one of the pivot's rows that pass the bound, so
+    // walking, row by row, only the letters that keep that row within d covers
+    // them all (a motif near several such rows is found once per row; the
+    // sort/unique step removes the copies). Chosen when the pivot has few rows
+    // against large choice sets.
+    const int est_plain = sg_popc(T[0]) * (k >= 2 ? sg_popc(T[1]) : 1);
+    if (S.miss_max == 0 && piv >= 0 && piv_rows * k < est_plain) {
+        for (int e = S.off[piv]; e < S.off[piv + 1]; ++e) {
+            const uint32_t De = S.D[e];
+            if (lead)
+                ct.reduce++;
+            const int slack = S.d - sg_popc(De ^ P);
+            if (slack < 0)
+                continue;
+            int wl[kSigMaxD];
+            for (int t = 0; t < k; ++t)
+                wl[t] = ((De >> pos[t]) & 1u) ? sg_letter_at(S.Pl + e, S.stride, S.b, pos[t]) : -1;
+            wit[piv] = e;
+            sg_dfs(S, grp, P, k, pos, T, Wl, wl, slack, ct, sink, wit, fail);
+        }
+    } else {
+        sg_dfs(S, grp, P, k, pos, T, Wl, nullptr, 0, ct, sink, wit, fail);
     }
 }
 
@@ -427,17 +531,17 @@ __global__ void sigma_pack_kernel(const uint8_t *__restrict__ seqs, int n, int m
 // Persistent CTAs take one seed at a time from the queue: rows of the seed
 // (two passes over every window: count per sequence, then place), then the
 // tree nodes of the seed, claimed one at a time by the CTA's warps.
-__global__ void __launch_bounds__(kSigThreads) sigma_main_kernel(SigmaParams p)
+__global__ void __launch_bounds__(kSigThreads, 3) sigma_main_kernel(SigmaParams p)
 {
     extern __shared__ uint32_t sg_rows_smem[];
     __shared__ int s_cnt[kNMax], s_cur[kNMax], s_off[kNMax + 1];
     __shared__ int s_seed, s_skip;
     __shared__ unsigned long long s_next;
+    __shared__ int s_wit[kSigThreads / 32][kNMax];   // per warp: witness row of each sequence
     __shared__ unsigned long long s_ct[kSgCntNum];
     const int tid = threadIdx.x;
     for (int c = tid; c < kSgCntNum; c += blockDim.x)
         s_ct[c] = 0;
-    SgCount ct{};
     unsigned long long cmp_rows = 0, seeds = 0, infeasible = 0;
     SgDeviceSink sink{p.raw, p.raw_count, p.raw_cap};
     const int NW = p.n * p.W;
@@ -533,17 +637,21 @@ __global__ void __launch_bounds__(kSigThreads) sigma_main_kernel(SigmaParams p)
                 r = grp.bcast(r);
                 if (r >= (unsigned long long)p.nodes)
                     break;
-                sg_node(S, grp, sg_unrank((long long)r, p.l), ct, sink);
+                SgCount ct{};
+                sg_node(S, grp, sg_unrank((long long)r, p.l), ct, sink, s_wit[tid >> 5]);
+                const unsigned long long red = grp.sum(ct.reduce), ver = grp.sum(ct.verify);
+                if (grp.lane == 0) {   // node, check and leaf counts are the lead lane's
+                    atomicAdd(&s_ct[kSgNodes], (unsigned long long)ct.nodes);
+                    atomicAdd(&s_ct[kSgNodesPruned], (unsigned long long)ct.pruned);
+                    atomicAdd(&s_ct[kSgChecks], (unsigned long long)ct.checks);
+                    atomicAdd(&s_ct[kSgLeaves], (unsigned long long)ct.leaves);
+                    atomicAdd(&s_ct[kSgCmpReduce], red);
+                    atomicAdd(&s_ct[kSgCmpVerify], ver);
+                }
             }
         }
         __syncthreads();   // rows, offsets and s_seed are rewritten for the next seed
     }
-    atomicAdd(&s_ct[kSgNodes], ct.nodes);
-    atomicAdd(&s_ct[kSgNodesPruned], ct.pruned);
-    atomicAdd(&s_ct[kSgChecks], ct.checks);
-    atomicAdd(&s_ct[kSgLeaves], ct.leaves);
-    atomicAdd(&s_ct[kSgCmpReduce], ct.reduce);
-    atomicAdd(&s_ct[kSgCmpVerify], ct.verify);
     atomicAdd(&s_ct[kSgCmpRows], cmp_rows);
     if (tid == 0) {
         s_ct[kSgSeeds] += seeds;
