@@ -152,6 +152,7 @@ struct SgWarp {
     __device__ unsigned long long bcast(unsigned long long v) const { return __shfl_sync(0xFFFFFFFFu, v, 0); }
     __device__ uint32_t ballot(bool p) const { return __ballot_sync(0xFFFFFFFFu, p); }
     __device__ void sync() const { __syncwarp(); }
+    __device__ void or_into(uint32_t *a, uint32_t v) const { atomicOr(a, v); }
     __device__ unsigned long long sum(unsigned long long v) const
     {
         for (int s = 16; s > 0; s >>= 1)
@@ -168,6 +169,7 @@ struct SgSingle {
     __host__ __device__ unsigned long long bcast(unsigned long long v) const { return v; }
     __host__ __device__ uint32_t ballot(bool p) const { return p ? 1u : 0u; }
     __host__ __device__ void sync() const {}
+    __host__ __device__ void or_into(uint32_t *a, uint32_t v) const { *a |= v; }
     __host__ __device__ unsigned long long sum(unsigned long long v) const { return v; }
 };
 
@@ -269,6 +271,21 @@ __host__ __device__ inline bool sg_bound(const SgSeed &S, const G &grp, uint32_t
     return true;
 }
 
+// The state of one node's search. Every value in it is the same for all the
+// threads of the group, so a warp keeps one copy in shared memory: each lane
+// writes the same value and a warp barrier follows every write, so no lane
+// reads a value a lagging lane is about to overwrite. The letter masks L are
+// built with atomic ORs between two barriers.
+struct SgState {
+    int pos[kSigMaxD];     // the changed positions, ascending
+    int ch[kSigMaxD];      // the letter chosen at each
+    int used[kSigMaxD];    // mismatches against the pivot row up to each depth
+    int wl[kSigMaxD];      // the pivot row's letter where it differs from x (-1 elsewhere)
+    uint32_t L[kSigMaxD];  // letters the rows passing the bound hold there
+    uint32_t T[kSigMaxD];  // the choices: L and one representative of the rest
+    uint32_t Wl[kSigMaxD]; // the interchangeable letters the representative stands for
+};
+
 // Writes the motifs a full candidate stands for: at a position whose letter is
 // the representative of the interchangeable letters Wl[t], every letter of
 // Wl[t]. k = 0: the seed itself. One lane reserves the slots, the lanes split
@@ -316,31 +333,32 @@ __host__ __device__ void sg_emit(const SgSeed &S, const G &grp, const int *pos, 
 }
 
 // Step 3: depth-first over the letter choices T[t] of the changed positions
-// pos[0..k-1]. With a pivot row (wl non-null: the row's letter at each changed
-// position where it differs from x, -1 at the others) a choice is taken only
-// while at most `slack` of those positions carry a letter other than the
-// row's, which keeps the row within d of the candidate.
+// pos[0..k-1]. With a pivot row (pivot: its letters in wl) a choice is taken
+// only while at most `slack` of the changed positions where the row differs
+// from x carry a letter other than the row's, which keeps the row within d of
+// the candidate.
 template <class G, class Sink>
-__host__ __device__ void sg_dfs(const SgSeed &S, const G &grp, uint32_t P, int k, const int *pos, const uint32_t *T,
-                                const uint32_t *Wl, const int *wl, int slack, SgCount &ct, Sink &sink, int *wit,
-                                int &fail)
+__host__ __device__ void sg_dfs(const SgSeed &S, const G &grp, uint32_t P, int k, SgState &st, bool pivot, int slack,
+                                SgCount &ct, Sink &sink, int *wit, int &fail)
 {
     const bool lead = grp.lane == 0;
-    int ch[kSigMaxD], used[kSigMaxD];
     uint32_t c[kSigMaxPlanes];
     for (int g = 0; g < kSigMaxPlanes; ++g)
         c[g] = S.x[g];
     int t = 0;
-    ch[0] = sg_ctz(T[0]);
+    st.ch[0] = sg_ctz(st.T[0]);
+    grp.sync();
     for (;;) {
         bool ok = false;
-        const int u = (t > 0 ? used[t - 1] : 0) + ((wl && wl[t] >= 0 && ch[t] != wl[t]) ? 1 : 0);
-        if (!wl || u <= slack) {
-            used[t] = u;
-            const uint32_t bit = 1u << pos[t];
+        const int ct_t = st.ch[t];
+        const int u = (t > 0 ? st.used[t - 1] : 0) + ((pivot && st.wl[t] >= 0 && ct_t != st.wl[t]) ? 1 : 0);
+        if (!pivot || u <= slack) {
+            st.used[t] = u;
+            grp.sync();
+            const uint32_t bit = 1u << st.pos[t];
             for (int g = 0; g < S.b; ++g)
-                c[g] = ((ch[t] >> g) & 1) ? (c[g] | bit) : (c[g] & ~bit);
-            const uint32_t U = P & ~(uint32_t)((2ull << pos[t]) - 1ull);   // changed positions above pos[t]
+                c[g] = ((ct_t >> g) & 1) ? (c[g] | bit) : (c[g] & ~bit);
+            const uint32_t U = P & ~(uint32_t)((2ull << st.pos[t]) - 1ull);   // changed positions above pos[t]
             if (lead) {
                 ct.checks++;
                 if (t == k - 1)
@@ -350,18 +368,22 @@ __host__ __device__ void sg_dfs(const SgSeed &S, const G &grp, uint32_t P, int k
         }
         if (ok) {
             if (t == k - 1) {
-                sg_emit(S, grp, pos, ch, Wl, k, sink);
+                sg_emit(S, grp, st.pos, st.ch, st.Wl, k, sink);
             } else {
                 ++t;
-                ch[t] = sg_ctz(T[t]);
+                st.ch[t] = sg_ctz(st.T[t]);
+                grp.sync();
                 continue;
             }
         }
         // the next choice at this depth, else back up
         for (;;) {
-            const uint32_t rest = T[t] & ~(uint32_t)((2ull << ch[t]) - 1ull);
+            const uint32_t rest = st.T[t] & ~(uint32_t)((2ull << st.ch[t]) - 1ull);
             if (rest) {
-                ch[t] = sg_ctz(rest);
+                const int nx = sg_ctz(rest);
+                grp.sync();
+                st.ch[t] = nx;
+                grp.sync();
                 break;
             }
             if (--t < 0)
@@ -374,7 +396,8 @@ __host__ __device__ void sg_dfs(const SgSeed &S, const G &grp, uint32_t P, int k
 // group of threads in lockstep: every branch below depends only on values the
 // whole group shares.
 template <class G, class Sink>
-__host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCount &ct, Sink &sink, int *wit)
+__host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCount &ct, Sink &sink, int *wit,
+                                 SgState &st)
 {
     const bool lead = grp.lane == 0;
     if (lead)
@@ -393,16 +416,15 @@ __host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCo
         sg_emit(S, grp, nullptr, nullptr, nullptr, 0, sink);
         return;
     }
-    int pos[kSigMaxD];
-    uint32_t L[kSigMaxD], T[kSigMaxD], Wl[kSigMaxD];
     {
         uint32_t M = P;
         for (int t = 0; t < k; ++t) {
-            pos[t] = sg_ctz(M);
+            st.pos[t] = sg_ctz(M);
             M &= M - 1;
-            L[t] = 0;
+            st.L[t] = 0;
         }
     }
+    grp.sync();
     // step 2: the letters the rows passing the bound hold at the changed
     // positions, and the sequence with the fewest such rows (the pivot)
     int piv = -1, piv_rows = 0;
@@ -422,7 +444,8 @@ __host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCo
                     while (M) {
                         const int p = sg_ctz(M);
                         M &= M - 1;
-                        L[sg_popc(P & ((1u << p) - 1u))] |= 1u << sg_letter_at(S.Pl + e, S.stride, S.b, p);
+                        grp.or_into(&st.L[sg_popc(P & ((1u << p) - 1u))],
+                                    1u << sg_letter_at(S.Pl + e, S.stride, S.b, p));
                     }
                 }
             }
@@ -433,10 +456,12 @@ __host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCo
             piv_rows = cnt;
         }
     }
+    grp.sync();
     for (int t = 0; t < k; ++t) {
-        L[t] = grp.or_all(L[t]);
-        Wl[t] = S.full & ~L[t] & ~(1u << sg_letter_at(S.x, 1, S.b, pos[t]));
-        T[t] = L[t] | (Wl[t] & (0u - Wl[t]));   // the rows' letters and one representative of the rest
+        const uint32_t Lt = st.L[t];
+        const uint32_t Wt = S.full & ~Lt & ~(1u << sg_letter_at(S.x, 1, S.b, st.pos[t]));
+        st.Wl[t] = Wt;
+        st.T[t] = Lt | (Wt & (0u - Wt));   // the rows' letters and one representative of the rest
     }
     for (int j = grp.lane; j < S.n; j += G::width)
         wit[j] = -1;
@@ -448,7 +473,7 @@ __host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCo
     // them all (a motif near several such rows is found once per row; the
     // sort/unique step removes the copies). Chosen when the pivot has few rows
     // against large choice sets.
-    const int est_plain = sg_popc(T[0]) * (k >= 2 ? sg_popc(T[1]) : 1);
+    const int est_plain = sg_popc(st.T[0]) * (k >= 2 ? sg_popc(st.T[1]) : 1);
     if (S.miss_max == 0 && piv >= 0 && piv_rows * k < est_plain) {
         for (int e = S.off[piv]; e < S.off[piv + 1]; ++e) {
             const uint32_t De = S.D[e];
@@ -457,14 +482,15 @@ __host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCo
             const int slack = S.d - sg_popc(De ^ P);
             if (slack < 0)
                 continue;
-            int wl[kSigMaxD];
+            grp.sync();
             for (int t = 0; t < k; ++t)
-                wl[t] = ((De >> pos[t]) & 1u) ? sg_letter_at(S.Pl + e, S.stride, S.b, pos[t]) : -1;
+                st.wl[t] = ((De >> st.pos[t]) & 1u) ? sg_letter_at(S.Pl + e, S.stride, S.b, st.pos[t]) : -1;
             wit[piv] = e;
-            sg_dfs(S, grp, P, k, pos, T, Wl, wl, slack, ct, sink, wit, fail);
+            grp.sync();
+            sg_dfs(S, grp, P, k, st, true, slack, ct, sink, wit, fail);
         }
     } else {
-        sg_dfs(S, grp, P, k, pos, T, Wl, nullptr, 0, ct, sink, wit, fail);
+        sg_dfs(S, grp, P, k, st, false, 0, ct, sink, wit, fail);
     }
 }
 
@@ -538,6 +564,7 @@ __global__ void __launch_bounds__(kSigThreads, 3) sigma_main_kernel(SigmaParams 
     __shared__ int s_seed, s_skip;
     __shared__ unsigned long long s_next;
     __shared__ int s_wit[kSigThreads / 32][kNMax];   // per warp: witness row of each sequence
+    __shared__ SgState s_state[kSigThreads / 32];     // per warp: the node search's state
     __shared__ unsigned long long s_ct[kSgCntNum];
     const int tid = threadIdx.x;
     for (int c = tid; c < kSgCntNum; c += blockDim.x)
@@ -638,7 +665,7 @@ __global__ void __launch_bounds__(kSigThreads, 3) sigma_main_kernel(SigmaParams 
                 if (r >= (unsigned long long)p.nodes)
                     break;
                 SgCount ct{};
-                sg_node(S, grp, sg_unrank((long long)r, p.l), ct, sink, s_wit[tid >> 5]);
+                sg_node(S, grp, sg_unrank((long long)r, p.l), ct, sink, s_wit[tid >> 5], s_state[tid >> 5]);
                 const unsigned long long red = grp.sum(ct.reduce), ver = grp.sum(ct.verify);
                 if (grp.lane == 0) {   // node, check and leaf counts are the lead lane's
                     atomicAdd(&s_ct[kSgNodes], (unsigned long long)ct.nodes);
