@@ -150,7 +150,8 @@ constexpr int kSigMaxD = 16;        // changed positions per candidate
 constexpr int kSigMaxPlanes = 5;    // ceil(log2 32)
 constexpr int kSigThreads = 256;    // threads of the search kernel's CTA
 constexpr int kSigSortThreads = 1024;
-constexpr int kSigSmemBytes = 64 * 1024;   // rows of one seed kept in shared memory
+constexpr int kSigSmemSmall = 64 * 1024;    // rows of one seed in shared memory: 3 CTAs per SM
+constexpr int kSigSmemLarge = 104 * 1024;   // the same for seeds with many rows: 2 CTAs per SM
 
 // Work counters of the search kernel (always on), indices into a uint64 array.
 enum SigCounter {
@@ -188,9 +189,9 @@ struct SigmaParams {
 };
 
 int sigma_planes(int sigma);
-int sigma_smem_rows(int b);
+int sigma_smem_rows(int b, bool large);
 cudaError_t sigma_init_tables();
-cudaError_t sigma_main_occupancy(int b, int *blocks_per_sm);
+cudaError_t sigma_main_occupancy(int b, bool large, int *blocks_per_sm);
 cudaError_t launch_sigma_pack(const uint8_t *seqs, int n, int m, int l, int b, const SigmaMap &map, uint32_t *planes,
                               uint32_t *flags, cudaStream_t st);
 cudaError_t launch_sigma_main(const SigmaParams &p, int blocks, cudaStream_t st);

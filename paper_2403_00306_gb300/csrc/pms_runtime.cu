@@ -2306,14 +2306,24 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
     for (int k = 0; k <= d; ++k)
         nodes += (long long)binom(l, k);
     const int nseeds = (n - qe + 1) * W;
+    // rows a seed is expected to have: the windows of the other sequences
+    // within 2d of it, each position differing with probability (sigma-1)/sigma;
+    // the larger shared-memory form when the smaller would send seeds to global memory
+    const int max_rows = (n - 1) * W;
+    double p_row = 0;
+    {
+        const double pm = (double)(sigma - 1) / sigma;
+        for (int j = 0; j <= std::min(2 * d, l); ++j)
+            p_row += (double)binom(l, j) * std::pow(pm, j) * std::pow(1.0 - pm, l - j);
+    }
+    const bool large = p_row * max_rows > 0.8 * sigma_smem_rows(b, false);
     int occ = 0;
-    if ((e = sigma_main_occupancy(b, &occ)) != cudaSuccess)
+    if ((e = sigma_main_occupancy(b, large, &occ)) != cudaSuccess)
         return h->cuda_fail(e, "occupancy");
     occ = std::max(occ, 1);
     const int per_sm = h->opt.ctas_per_sm > 0 ? std::min(h->opt.ctas_per_sm, occ) : occ;
     const int blocks = (int)std::max(1LL, std::min<long long>((long long)h->num_sms * per_sm, nseeds));
-    const int smem_rows = sigma_smem_rows(b);
-    const int max_rows = (n - 1) * W;
+    const int smem_rows = sigma_smem_rows(b, large);
     const size_t NW = (size_t)n * W;
     const size_t ctr_bytes = 32 + 8 * (size_t)kSgCntNum;   // head, raw count, unique count, flags, work counters
     const bool capped = h->opt.max_motifs > 0;

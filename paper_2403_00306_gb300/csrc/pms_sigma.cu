@@ -790,9 +790,9 @@ int sigma_planes(int sigma)
     return g;
 }
 
-int sigma_smem_rows(int b)
+int sigma_smem_rows(int b, bool large)
 {
-    return kSigSmemBytes / (4 * (1 + b));
+    return (large ? kSigSmemLarge : kSigSmemSmall) / (4 * (1 + b));
 }
 
 cudaError_t sigma_init_tables()
@@ -803,12 +803,12 @@ cudaError_t sigma_init_tables()
     cudaError_t e = cudaMemcpyToSymbol(c_sg_binom, h_sg_binom, sizeof h_sg_binom);
     if (e != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(sigma_main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSigSmemBytes);
+    return cudaFuncSetAttribute(sigma_main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSigSmemLarge);
 }
 
-cudaError_t sigma_main_occupancy(int b, int *blocks_per_sm)
+cudaError_t sigma_main_occupancy(int b, bool large, int *blocks_per_sm)
 {
-    const size_t smem = (size_t)4 * (1 + b) * sigma_smem_rows(b);
+    const size_t smem = (size_t)4 * (1 + b) * sigma_smem_rows(b, large);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sigma_main_kernel, kSigThreads, smem);
 }
 

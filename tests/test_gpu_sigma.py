@@ -38,7 +38,7 @@ SMALL = [
     (20, 6, 30, 4, 0, 0, 17),   # d = 0: common l-mers
     (5, 4, 6, 6, 3, 0, 18),     # m = l: one window per sequence
     (20, 7, 33, 32, 1, 0, 19),  # l = 32: the whole plane word
-    (2, 12, 800, 8, 4, 0, 20),  # every window is a row: more rows than shared memory holds
+    (2, 20, 800, 8, 4, 0, 20),  # every window is a row: more rows than shared memory holds
 ]
 
 
