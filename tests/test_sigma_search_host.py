@@ -1,0 +1,75 @@
+"""The general-alphabet node search, compiled for the host from the kernel's own source
+(tests/host/sigma_search_host.cu: one-thread group, rows built on the host in the kernel's
+layout), against the oracle on small instances. No GPU is used; this keeps the search logic
+(node bound, letter classes, depth-first prefixes, pivot rows, witness rows) checked on CPU."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import planted_inputs as pi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "tests", "host", "sigma_search_host.cu")
+
+
+def _nvcc():
+    cand = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    return cand if os.path.exists(cand) else shutil.which("nvcc")
+
+
+@pytest.fixture(scope="module")
+def search(tmp_path_factory):
+    nvcc = _nvcc()
+    if not nvcc:
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path_factory.mktemp("sigma") / "sigma_search_host")
+    subprocess.run([nvcc, "-O2", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
+                    "-diag-suppress", "550", "-I", os.path.join(ROOT, "include"), SRC, "-o", exe],
+                   check=True, capture_output=True)
+
+    def run(seqs, l, d, alphabet, q=0):
+        n, m = seqs.shape
+        inp = f"{alphabet} {n} {m} {l} {d} {q}\n" + "\n".join(bytes(r).decode() for r in seqs) + "\n"
+        r = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True)
+        return r.stdout.split()
+    return run
+
+
+def alphabet_of(sigma: int) -> str:
+    return "".join(reversed("ACDEFGHIKLMNPQRSTVWYBJOUXZ0123456789"[:sigma]))
+
+
+CASES = [
+    # sigma, n, m, l, d, q, seed
+    (2, 6, 40, 10, 2, 0, 1), (3, 5, 30, 7, 3, 4, 4), (4, 8, 60, 9, 2, 0, 5), (7, 5, 40, 6, 2, 3, 7),
+    (17, 5, 30, 5, 2, 0, 9), (20, 6, 50, 6, 3, 0, 11), (20, 5, 40, 6, 3, 3, 12), (32, 5, 30, 5, 2, 4, 15),
+    (20, 1, 9, 5, 2, 0, 16), (20, 6, 30, 4, 0, 0, 17), (5, 4, 6, 6, 3, 0, 18), (20, 7, 33, 32, 1, 0, 19),
+]
+
+
+@pytest.mark.parametrize("sigma,n,m,l,d,q,seed", CASES)
+def test_host_search_matches_the_oracle(search, oracle_, sigma, n, m, l, d, q, seed):
+    alpha = alphabet_of(sigma)
+    inst = pi.planted_instance_sigma(n, m, l, d, seed, alpha.encode())
+    want = [bytes(r).decode() for r in oracle_.sigma_solve(inst.seqs, l, d, alpha, q=q, cap=1 << 22)]
+    assert search(inst.seqs, l, d, alpha, q) == want
+
+
+def test_host_search_over_acgt_matches_the_dna_oracle(search, oracle_):
+    inst = pi.planted_instance(10, 120, 10, 3, 21)
+    want = [oracle_.decode(int(k), 10) for k in oracle_.solve(inst.seqs, 10, 3)]
+    assert search(inst.seqs, 10, 3, "ACGT") == want
+
+
+def test_host_search_on_random_backgrounds(search, oracle_):
+    rng = np.random.default_rng(5)
+    for sigma, n, m, l, d in [(20, 6, 40, 6, 3), (3, 8, 60, 9, 3), (2, 10, 50, 12, 3)]:
+        alpha = alphabet_of(sigma)
+        letters = np.frombuffer(alpha.encode(), np.uint8)
+        seqs = letters[rng.integers(0, sigma, size=(n, m))].astype(np.uint8)
+        for q in (0, n - 1):
+            want = [bytes(r).decode() for r in oracle_.sigma_solve(seqs, l, d, alpha, q=q, cap=1 << 22)]
+            assert search(seqs, l, d, alpha, q) == want, (sigma, n, m, l, d, q)
