@@ -46,7 +46,7 @@ WORKLOADS = {
 # quorum form: (l, d, q), n = 20, m = 600
 QUORUM_WORKLOADS = {"quorum15_4_q10": (15, 4, 10)}
 # general alphabet, the twenty amino acids: (l, d), n = 20, m = 600
-PROTEIN_WORKLOADS = {"protein9_3": (9, 3), "protein9_4": (9, 4)}
+PROTEIN_WORKLOADS = {f"protein{l}_{d}": (l, d) for (l, d) in pi.PROTEIN_LD}
 L2_FLUSH_BYTES = 512 << 20
 
 # DRAM bytes (read + write) per launch of the verification kernel from one ncu

@@ -145,7 +145,7 @@ def random_sequences(n: int, m: int, seed: int) -> np.ndarray:
 PLAIN_LD = [(9, 2), (15, 4), (17, 5), (19, 6)]
 
 #: protein (20-letter) single-instance configurations: (l, d) with n = 20, m = 600
-PROTEIN_LD = [(11, 4), (13, 5), (15, 6)]
+PROTEIN_LD = [(9, 3), (9, 4)]
 
 
 def plain_instance(l: int, d: int, seed: int = 1, n: int = 20, m: int = 600) -> Instance:
