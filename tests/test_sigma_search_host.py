@@ -1,7 +1,13 @@
-"""The general-alphabet node search, compiled for the host from the kernel's own source
-(tests/host/sigma_search_host.cu: one-thread group, rows built on the host in the kernel's
-layout), against the oracle on small instances. No GPU is used; this keeps the search logic
-(node bound, letter classes, depth-first prefixes, pivot rows, witness rows) checked on CPU."""
+"""The general-alphabet node search, compiled for the host from the kernel's own source,
+against the oracle on small instances, with no GPU:
+
+* tests/host/sigma_search_host.cu runs it with a one-thread group (rows built on the host
+  in the kernel's layout): the search logic (node bound, letter classes, depth-first
+  prefixes, pivot rows, witness rows);
+* tests/host/sigma_search_lockstep.cu runs it with 32 host threads per node whose votes,
+  broadcasts and sums go through barriers, sharing the per-warp state and witness rows:
+  the lane-parallel form the GPU warp executes (row scans split over 32 lanes, one lane
+  reserving output slots, every lane writing the shared state)."""
 import os
 import shutil
 import subprocess
@@ -73,3 +79,36 @@ def test_host_search_on_random_backgrounds(search, oracle_):
         for q in (0, n - 1):
             want = [bytes(r).decode() for r in oracle_.sigma_solve(seqs, l, d, alpha, q=q, cap=1 << 22)]
             assert search(seqs, l, d, alpha, q) == want, (sigma, n, m, l, d, q)
+
+
+@pytest.fixture(scope="module")
+def lockstep(tmp_path_factory):
+    nvcc = _nvcc()
+    if not nvcc:
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path_factory.mktemp("sigma_lockstep") / "sigma_search_lockstep")
+    subprocess.run([nvcc, "-O2", "-std=c++20", "-gencode", "arch=compute_103a,code=sm_103a",
+                    "-diag-suppress", "550,177", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "host", "sigma_search_lockstep.cu"), "-o", exe],
+                   check=True, capture_output=True)
+
+    def run(seqs, l, d, alphabet, q=0):
+        n, m = seqs.shape
+        inp = f"{alphabet} {n} {m} {l} {d} {q}\n" + "\n".join(bytes(r).decode() for r in seqs) + "\n"
+        r = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True, timeout=300)
+        return r.stdout.split()
+    return run
+
+
+# tiny cases (every collective is a barrier of 32 host threads): protein and DNA instances that
+# take the pivot form, a quorum and n = 1 that take the plain depth-first form
+LOCKSTEP_CASES = [(20, 4, 20, 5, 2, 0, 31), (3, 4, 16, 6, 2, 3, 33), (20, 1, 7, 4, 2, 0, 34),
+                  (4, 6, 30, 8, 2, 0, 35), (4, 8, 60, 9, 2, 0, 5)]
+
+
+@pytest.mark.parametrize("sigma,n,m,l,d,q,seed", LOCKSTEP_CASES)
+def test_lane_parallel_search_matches_the_oracle(lockstep, oracle_, sigma, n, m, l, d, q, seed):
+    alpha = alphabet_of(sigma)
+    inst = pi.planted_instance_sigma(n, m, l, d, seed, alpha.encode())
+    want = [bytes(r).decode() for r in oracle_.sigma_solve(inst.seqs, l, d, alpha, q=q, cap=1 << 22)]
+    assert lockstep(inst.seqs, l, d, alpha, q) == want
