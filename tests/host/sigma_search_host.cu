@@ -2,7 +2,8 @@
 // code the search kernel runs, with a one-thread group) for the CPU tests:
 // rows are built on the host in the kernel's layout, every node of every seed
 // is searched, and the sorted unique motifs are printed, one per line.
-// Input on stdin: "alphabet n m l d q" then the n sequences.
+// Input on stdin: "alphabet n m l d q" then the n sequences; or "unrank l d",
+// which prints the position subset (as a bit mask) of every node rank instead.
 #include "../../paper_2403_00306_gb300/csrc/pms_sigma.cu"
 
 #include <algorithm>
@@ -43,7 +44,21 @@ int main()
 {
     char alpha[64];
     int n, m, l, d, q;
-    if (scanf("%63s %d %d %d %d %d", alpha, &n, &m, &l, &d, &q) != 6)
+    if (scanf("%63s", alpha) != 1)
+        return 2;
+    if (strcmp(alpha, "unrank") == 0) {
+        if (scanf("%d %d", &l, &d) != 2)
+            return 2;
+        sigma_init_tables();
+        cudaGetLastError();
+        long long nodes = 0;
+        for (int k = 0; k <= d; ++k)
+            nodes += sg_binom(l, k);
+        for (long long r = 0; r < nodes; ++r)
+            printf("%u\n", sg_unrank(r, l));
+        return 0;
+    }
+    if (scanf("%d %d %d %d %d", &n, &m, &l, &d, &q) != 5)
         return 2;
     std::vector<std::string> seqs(n);
     static char buf[70000];

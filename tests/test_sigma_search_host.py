@@ -41,7 +41,21 @@ def search(tmp_path_factory):
         inp = f"{alphabet} {n} {m} {l} {d} {q}\n" + "\n".join(bytes(r).decode() for r in seqs) + "\n"
         r = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True)
         return r.stdout.split()
+    run.exe = exe
     return run
+
+
+def test_node_ranks_are_a_bijection_onto_the_subsets(search):
+    # rank r -> position subset: every subset of at most d of the l positions exactly once,
+    # sizes in increasing order (the search visits the tree's nodes through these ranks)
+    import itertools
+    for l, d in [(1, 0), (5, 5), (9, 4), (12, 3), (32, 2)]:
+        r = subprocess.run([search.exe], input=f"unrank {l} {d}\n", capture_output=True, text=True, check=True)
+        got = [int(v) for v in r.stdout.split()]
+        want = {sum(1 << p for p in c) for k in range(d + 1) for c in itertools.combinations(range(l), k)}
+        assert len(got) == len(want) and set(got) == want, (l, d)
+        sizes = [bin(v).count("1") for v in got]
+        assert sizes == sorted(sizes)
 
 
 def alphabet_of(sigma: int) -> str:
