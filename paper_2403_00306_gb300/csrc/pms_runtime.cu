@@ -2322,8 +2322,14 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
         return h->cuda_fail(e, "occupancy");
     occ = std::max(occ, 1);
     const int per_sm = h->opt.ctas_per_sm > 0 ? std::min(h->opt.ctas_per_sm, occ) : occ;
-    const int blocks = (int)std::max(1LL, std::min<long long>((long long)h->num_sms * per_sm, nseeds));
+    int blocks = (int)std::max(1LL, std::min<long long>((long long)h->num_sms * per_sm, nseeds));
     const int smem_rows = sigma_smem_rows(b, large);
+    if (max_rows > smem_rows) {
+        // every CTA may need global scratch for a seed's rows: keep it within 2 GiB
+        // (the persistent CTAs take seeds from a queue, so fewer CTAs only take longer)
+        const size_t per_cta = (size_t)4 * (1 + b) * max_rows;
+        blocks = (int)std::max<size_t>(1, std::min<size_t>(blocks, ((size_t)2 << 30) / per_cta));
+    }
     const size_t NW = (size_t)n * W;
     const size_t ctr_bytes = 32 + 8 * (size_t)kSgCntNum;   // head, raw count, unique count, flags, work counters
     const bool capped = h->opt.max_motifs > 0;
