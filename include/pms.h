@@ -133,8 +133,11 @@ typedef struct {
 } pms_tuning;
 
 /* Work counters of the last solve (pms_solve / pms_solve_device /
- * pms_solve_batch). The comparison counters are filled only when
- * pms_options.count_work was set for that solve. */
+ * pms_solve_batch / pms_solve_sigma). For the DNA solves the comparison
+ * counters are filled only when pms_options.count_work was set for that
+ * solve; pms_solve_sigma always fills them (subsets = tree nodes visited,
+ * candidates_tested = checks of full candidates, cmp_rows / cmp_reduce /
+ * cmp_verify = window, node-bound and candidate-versus-row comparisons). */
 typedef struct {
     uint64_t candidates;        /* size of the searched space: sum over seeds of |B(x,d)| */
     uint64_t subsets;           /* position subsets visited (tree nodes at which substitutions start) */
