@@ -65,6 +65,9 @@ def _declare(lib):
         "oracle_solve": (c_long, [u8p, c_int, c_int, c_int, c_int, c_int, u64p, c_long]),
         "oracle_solve_seeds": (c_long, [u8p, c_int, c_int, c_int, c_int, c_long, c_long, c_int, u64p, c_long]),
         "oracle_solve_pairs": (c_long, [u8p, c_int, c_int, c_int, c_int, c_int, u64p, c_long]),
+        "oracle_solve_pairs_seeds": (c_long, [u8p, c_int, c_int, c_int, c_int, c_long, c_long, c_int, u64p,
+                                               c_long]),
+        "oracle_solve_packed": (c_long, [u8p, c_int, c_int, c_int, c_int, c_long, c_long, c_int, u64p, c_long]),
         "oracle_bruteforce": (c_long, [u8p, c_int, c_int, c_int, c_int, u64p, c_long]),
         "oracle_is_qmotif": (c_int, [u8p, c_int, c_int, c_int, u8p, c_int, c_int]),
         "oracle_solve_quorum": (c_long, [u8p, c_int, c_int, c_int, c_int, c_int, c_int, u64p, c_long]),
@@ -210,6 +213,21 @@ class Oracle:
 
     def solve_pairs(self, seqs, l: int, d: int, threads: int | None = None, cap: int = 1 << 22) -> np.ndarray:
         return self._solve(self.lib.oracle_solve_pairs, seqs, l, d, threads or os.cpu_count() or 1, cap=cap)
+
+    def solve_pairs_seeds(self, seqs, l: int, d: int, seed_lo: int, seed_hi: int, threads: int | None = None,
+                          cap: int = 1 << 22) -> np.ndarray:
+        """solve_pairs restricted to the seeds x = s_1[j..j+l-1], seed_lo <= j < seed_hi."""
+        return self._solve(self.lib.oracle_solve_pairs_seeds, seqs, l, d, seed_lo, seed_hi,
+                           threads or os.cpu_count() or 1, cap=cap)
+
+    def solve_packed(self, seqs, l: int, d: int, seed_lo: int = 0, seed_hi: int | None = None,
+                     threads: int | None = None, cap: int = 1 << 22) -> np.ndarray:
+        """The motifs inside B(x_j, d) for seeds j in [seed_lo, seed_hi) of s_1 (all of them by
+        default, i.e. the whole motif set), with the motif test run on compressed l-mers."""
+        W = np.asarray(seqs).shape[1] - l + 1
+        hi = W if seed_hi is None else seed_hi
+        return self._solve(self.lib.oracle_solve_packed, seqs, l, d, seed_lo, hi, threads or os.cpu_count() or 1,
+                           cap=cap)
 
     def bruteforce(self, seqs, l: int, d: int, cap: int = 1 << 22) -> np.ndarray:
         return self._solve(self.lib.oracle_bruteforce, seqs, l, d, cap=cap)

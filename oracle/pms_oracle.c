@@ -249,13 +249,73 @@ typedef struct {
     int mode;               /* 0: motif test, 1: collect every node */
     keyvec *out;
     long visited;
+    const struct packed_seqs *pk;   /* if non-NULL: the motif test on compressed l-mers */
 } walk_t;
+
+/* Every window of every sequence in compressed form (Sec. "String
+ * Compression"): for l <= 32 one word per group, group 0 (bit 0 of the codes)
+ * in lo[], group 1 (bit 1) in hi[], window j of string i at i * W + j. */
+typedef struct packed_seqs {
+    uint32_t *lo, *hi;
+    int n, W, l, d;
+} packed_seqs;
+
+static int packed_build(packed_seqs *pk, const uint8_t *seqs, int n, int m, int l, int d)
+{
+    pk->n = n;
+    pk->W = m - l + 1;
+    pk->l = l;
+    pk->d = d;
+    pk->lo = (uint32_t *)malloc((size_t)n * pk->W * sizeof(uint32_t));
+    pk->hi = (uint32_t *)malloc((size_t)n * pk->W * sizeof(uint32_t));
+    if (!pk->lo || !pk->hi)
+        return ORACLE_ENOMEM;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < pk->W; ++j) {
+            uint32_t g[2];
+            oracle_compress(seqs + (long)i * m + j, l, g);
+            pk->lo[(long)i * pk->W + j] = g[0];
+            pk->hi[(long)i * pk->W + j] = g[1];
+        }
+    return ORACLE_OK;
+}
+
+static void packed_free(packed_seqs *pk)
+{
+    free(pk->lo);
+    free(pk->hi);
+}
+
+/* Definition 5 (q = n) on compressed l-mers: every string holds a window
+ * whose compressed distance to the candidate (set bits of the OR of the two
+ * groups' XORs) is at most d. The strings are taken in the order s_2, ...,
+ * s_n, s_1; the order of a conjunction does not change its value. */
+static int packed_is_motif(const packed_seqs *pk, const uint32_t cand[2])
+{
+    for (int t = 1; t <= pk->n; ++t) {
+        const int i = t % pk->n;
+        const uint32_t *lo = pk->lo + (long)i * pk->W, *hi = pk->hi + (long)i * pk->W;
+        int found = 0;
+        for (int j = 0; j < pk->W && !found; ++j)
+            found = __builtin_popcount((cand[0] ^ lo[j]) | (cand[1] ^ hi[j])) <= pk->d;
+        if (!found)
+            return 0;
+    }
+    return 1;
+}
 
 static void visit_node(walk_t *w)
 {
     w->visited += 1;
     if (w->other && oracle_hamming(w->cur, w->other, w->l) > w->d)
         return;
+    if (w->pk) {
+        uint32_t g[2];
+        oracle_compress(w->cur, w->l, g);
+        if (packed_is_motif(w->pk, g))
+            kv_push(w->out, oracle_key(w->cur, w->l));
+        return;
+    }
     if (w->mode == 1 ||
         (w->q > 0 ? oracle_is_qmotif(w->cur, w->l, w->d, w->q, w->seqs, w->n, w->m)
                   : oracle_is_motif(w->cur, w->l, w->d, w->seqs, w->n, w->m)))
@@ -326,10 +386,12 @@ typedef struct {
     const uint8_t *seqs;
     int n, m, l, d;
     int q;              /* quorum (0: n, the PMS problem) */
-    int variant;        /* 0: seeds x in S_1; 1: pairs (x in S_1, r in S_2) */
+    int variant;        /* 0: seeds x in S_1; 1: pairs (x in S_1, r in S_2);
+                           2: seeds x in S_1, motif test on compressed l-mers */
     int tid, nthreads;
     long seed_lo, seed_hi;   /* range of windows of s_1 used as seeds */
     keyvec out;
+    const packed_seqs *pk;   /* variant 2 */
 } job_t;
 
 static void *solve_worker(void *arg)
@@ -342,11 +404,12 @@ static void *solve_worker(void *arg)
     for (long x0 = j->seed_lo + j->tid; x0 < j->seed_hi; x0 += j->nthreads) {
         /* seed x0 numbers the l-mers of s_1, s_2, ... in order (W per string) */
         const uint8_t *x = s1 + (x0 / W) * (long)j->m + (x0 % W);
-        if (j->variant == 0 || s2 == NULL) {
+        if (j->variant != 1 || s2 == NULL) {
             /* Observation 3.1 with q = n: every motif is within d of some
              * l-mer x of s_1, so the candidates are the union of B(x, d). */
             memcpy(cur, x, (size_t)j->l);
-            walk_t w = {x, j->q, cur, j->l, j->d, j->seqs, j->n, j->m, NULL, 0, &j->out, 0};
+            walk_t w = {x, j->q, cur, j->l, j->d, j->seqs, j->n, j->m, NULL, 0, &j->out, 0,
+                        j->variant == 2 ? j->pk : NULL};
             walk_tree(&w, 0, 0);
         } else {
             /* Observation 3.3 with q = n: a motif is within d of an l-mer x
@@ -381,15 +444,21 @@ static long run_solver(const uint8_t *seqs, int n, int m, int l, int d, int q, i
         threads = 1;
     if (threads > 256)
         threads = 256;
+    packed_seqs pk = {0};
+    if (variant == 2 && packed_build(&pk, seqs, n, m, l, d) != ORACLE_OK) {
+        packed_free(&pk);
+        return ORACLE_ENOMEM;
+    }
     job_t *jobs = (job_t *)calloc((size_t)threads, sizeof(job_t));
     pthread_t *th = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
     if (!jobs || !th) {
         free(jobs);
         free(th);
+        packed_free(&pk);
         return ORACLE_ENOMEM;
     }
     for (int t = 0; t < threads; ++t) {
-        jobs[t] = (job_t){seqs, n, m, l, d, q, variant, t, threads, seed_lo, seed_hi, {0}};
+        jobs[t] = (job_t){seqs, n, m, l, d, q, variant, t, threads, seed_lo, seed_hi, {0}, &pk};
         if (threads == 1 || pthread_create(&th[t], NULL, solve_worker, &jobs[t]) != 0) {
             solve_worker(&jobs[t]);
             th[t] = 0;
@@ -407,6 +476,7 @@ static long run_solver(const uint8_t *seqs, int n, int m, int l, int d, int q, i
     }
     free(jobs);
     free(th);
+    packed_free(&pk);
     return kv_finish(&all, out, cap);
 }
 
@@ -432,6 +502,26 @@ long oracle_solve_pairs(const uint8_t *seqs, int n, int m, int l, int d, int thr
                         uint64_t *out, long cap)
 {
     return run_solver(seqs, n, m, l, d, 0, 1, 0, (long)m - l + 1, threads, out, cap);
+}
+
+/* oracle_solve_pairs restricted to the seeds x = s_1[j..j+l-1], j in
+ * [seed_lo, seed_hi): a bounded slice of its work. */
+long oracle_solve_pairs_seeds(const uint8_t *seqs, int n, int m, int l, int d, long seed_lo, long seed_hi,
+                              int threads, uint64_t *out, long cap)
+{
+    return run_solver(seqs, n, m, l, d, 0, 1, seed_lo, seed_hi, threads, out, cap);
+}
+
+/* The motifs lying in B(x, d) for the seeds x = s_1[j..j+l-1], j in
+ * [seed_lo, seed_hi), as oracle_solve_seeds, with the motif test of
+ * Definition 5 run on compressed l-mers (Sec. "String Compression": every
+ * window is compressed once, a candidate's distance to it is the set bits of
+ * the OR of the XORed groups, equal to Definition 3). Same result, a few
+ * times faster; used to write expected motif sets of large instances. */
+long oracle_solve_packed(const uint8_t *seqs, int n, int m, int l, int d, long seed_lo, long seed_hi, int threads,
+                         uint64_t *out, long cap)
+{
+    return run_solver(seqs, n, m, l, d, 0, 2, seed_lo, seed_hi, threads, out, cap);
 }
 
 /* qPMS (the qPMS definition, quorum q <= n): all (l,d,q)-motifs. Seeds are

@@ -258,6 +258,48 @@ def check_quorum(o) -> None:
     assert [int(k) for k in o.solve_quorum(seqs, l, d, 1, threads=1)] == sorted(want)
 
 
+def check_packed_solver(o) -> None:
+    """The solver on compressed l-mers: brute force over 4^l, the definition written out in
+    Python (d = 0, n = 1), the char-level solver on edge shapes, and seed slices partitioning."""
+    cases = [(3, 20, 5, 1, 601), (5, 30, 6, 2, 602), (4, 16, 4, 2, 603), (1, 9, 5, 2, 604), (6, 25, 8, 2, 605)]
+    for (n, m, l, d, seed) in cases:
+        inst = pi.planted_instance(n, m, l, d, seed)
+        assert np.array_equal(o.solve_packed(inst.seqs, l, d, threads=2), o.bruteforce(inst.seqs, l, d)), \
+            (n, m, l, d)
+        seqs = pi.random_sequences(n, m, seed + 1000)
+        assert np.array_equal(o.solve_packed(seqs, l, d, threads=2), o.bruteforce(seqs, l, d))
+    # d = 0: the l-mers present in every sequence
+    inst = pi.planted_instance(4, 30, 5, 0, 610)
+    want = sorted(py_key(s) for s in set.intersection(*[lmers(bytes(row), 5) for row in inst.seqs]))
+    assert [int(k) for k in o.solve_packed(inst.seqs, 5, 0, threads=1)] == want
+    # n = 1: every string within d of some l-mer of the single sequence
+    seqs = pi.random_sequences(1, 11, 611)
+    want = set()
+    for x in lmers(bytes(seqs[0]), 5):
+        for t in itertools.product(ACGT, repeat=5):
+            if py_hamming(x, "".join(t)) <= 1:
+                want.add(py_key("".join(t)))
+    assert [int(k) for k in o.solve_packed(seqs, 5, 1, threads=1)] == sorted(want)
+    # the char-level solver at l = 32, m = l, and on instances with many motifs
+    for (n, m, l, d, seed) in [(3, 40, 32, 2, 612), (4, 9, 9, 3, 613), (20, 120, 9, 2, 614), (6, 60, 7, 2, 615),
+                               (10, 80, 10, 3, 616)]:
+        inst = pi.planted_instance(n, m, l, d, seed)
+        want = o.solve(inst.seqs, l, d, threads=2)
+        got = o.solve_packed(inst.seqs, l, d, threads=2)
+        assert np.array_equal(got, want), (n, m, l, d, len(got), len(want))
+        assert py_key(inst.motif.decode()) in set(int(k) for k in got)
+    # seed slices partition the work
+    inst = pi.planted_instance(8, 60, 7, 2, 617)
+    parts = set()
+    for lo in range(0, 54, 9):
+        parts |= set(int(k) for k in o.solve_packed(inst.seqs, 7, 2, lo, lo + 9, threads=1))
+    assert parts == set(int(k) for k in o.solve(inst.seqs, 7, 2, threads=2))
+    parts = set()
+    for lo in range(0, 54, 18):
+        parts |= set(int(k) for k in o.solve_pairs_seeds(inst.seqs, 7, 2, lo, lo + 18, threads=1))
+    assert parts == set(int(k) for k in o.solve(inst.seqs, 7, 2, threads=2))
+
+
 # ------------------------------------------------------------- general alphabets (qPMS-Sigma)
 
 PROTEIN = pi.PROTEIN.decode()
@@ -398,6 +440,6 @@ def check_sigma_special_cases(o) -> None:
 
 ALL_PINS = [check_compression_example, check_distance_definitions, check_neighbourhood_counts,
             check_neighbourhood_members, check_pair_intersections, check_bruteforce_agreement,
-            check_planted_motif_found, check_special_cases, check_invariants, check_quorum,
+            check_planted_motif_found, check_special_cases, check_invariants, check_quorum, check_packed_solver,
             check_sigma_compression, check_sigma_neighbourhood_counts, check_sigma_bruteforce,
             check_sigma_matches_dna, check_sigma_relabelling, check_sigma_special_cases]

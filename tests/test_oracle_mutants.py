@@ -52,6 +52,16 @@ MUTANTS = {
     "sigma_quorum_seeds_first_only": ("(long)(q > 0 ? n - q + 1 : 1) * W", "(long)1 * W"),
     # general alphabets: brute force skips the last letter at the last position
     "sigma_bruteforce_counter": ("while (k >= 0 && idx[k] == sigma - 1)", "while (k >= 0 && idx[k] == sigma - 2)"),
+    # compressed motif test: strict threshold
+    "packed_strict_threshold": ("(cand[1] ^ hi[j])) <= pk->d;", "(cand[1] ^ hi[j])) < pk->d;"),
+    # compressed motif test: group 1 ignored
+    "packed_group_dropped": ("__builtin_popcount((cand[0] ^ lo[j]) | (cand[1] ^ hi[j]))",
+                             "__builtin_popcount(cand[0] ^ lo[j])"),
+    # compressed motif test: the last window of each string dropped
+    "packed_last_window_dropped": ("for (int j = 0; j < pk->W && !found; ++j)",
+                                   "for (int j = 0; j < pk->W - 1 && !found; ++j)"),
+    # compressed motif test: s_n never checked (the strings run s_2 .. s_{n-1}, s_1)
+    "packed_string_skipped": ("const int i = t % pk->n;", "const int i = (t % pk->n == pk->n - 1) ? 0 : t % pk->n;"),
     # Hamming distance counts matches instead of mismatches at the first position
     "hamming_first_position": ("for (int k = 0; k < l; ++k)\n        if (a[k] != b[k])",
                                "for (int k = 1; k < l; ++k)\n        if (a[k] != b[k])"),
