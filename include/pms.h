@@ -275,6 +275,14 @@ const char *pms_last_error(const pms_ctx *h);
  * (thread-level operations), from `clock64` deltas inside the kernel. */
 int pms_probe_int_rate(pms_ctx *h, int kind, double *per_clk_per_sm);
 
+/* The architecture the library's device code was built for, as the CUDA
+ * runtime reports it for the packing kernel on `device`
+ * (cudaFuncGetAttributes binaryVersion: major * 10 + minor, 103 for
+ * sm_103a). No counterpart in the paper; a build check. Returns PMS_OK,
+ * PMS_EINVAL (null pointer) or PMS_ECUDA (no such device, or no device code
+ * for it). */
+int pms_kernel_binary_version(int device, int *version);
+
 /* Releases the context, its device memory, stream and scheduler thread. */
 void pms_destroy(pms_ctx *h);
 
@@ -294,7 +302,9 @@ void pms_destroy(pms_ctx *h);
  * ASCII input bytes, to room for `capacity` motif codes (d_motifs), and to
  * 4 x uint32 of status {raw count, unique count, flags, 0}; the work is
  * enqueued on `cuda_stream` (NULL: the legacy default stream) of the
- * current device and the call returns without waiting.
+ * current device and the call returns without waiting. The call's small
+ * descriptor block travels inside the launches' parameters, so no host
+ * memory of the call is read after it returns.
  *
  * Limits: besides the pms_solve_device limits, the instance's buffers plus
  * the row scratch of at least one CTA must fit in the 16 MiB (n = 20,

@@ -27,7 +27,7 @@ ABI_FUNCTIONS = ["pms_create", "pms_set_stream", "pms_set_allocator", "pms_set_o
                  "pms_solve", "pms_solve_device", "pms_solve_batch", "pms_submit", "pms_wait", "pms_release",
                  "pms_get_stats", "pms_decode", "pms_last_error", "pms_probe_int_rate", "pms_destroy",
                  "pms_solve_device_noalloc", "pms_autotune", "pms_save_tuning", "pms_load_tuning",
-                 "pms_solve_sigma"]
+                 "pms_solve_sigma", "pms_kernel_binary_version"]
 
 #: the twenty amino acids, one-letter codes (an alphabet for solve_sigma)
 PROTEIN = b"ACDEFGHIKLMNPQRSTVWY"
@@ -119,6 +119,7 @@ def load(build_if_missing: bool = True):
             "pms_save_tuning": (ci, [vp, ctypes.c_char_p]),
             "pms_load_tuning": (ci, [vp, ctypes.c_char_p]),
             "pms_solve_sigma": (ci, [vp, u8p, ci, u8p, ci, ci, ci, ci, ci, ctypes.POINTER(u8p), ctypes.POINTER(sz)]),
+            "pms_kernel_binary_version": (ci, [ci, ctypes.POINTER(ci)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -215,6 +216,15 @@ def pms_save_tuning(ctx: "Context", path: str) -> None:
 
 def pms_load_tuning(ctx: "Context", path: str) -> None:
     ctx.load_tuning(path)
+
+
+def pms_kernel_binary_version(device: int = 0) -> int:
+    """cudaFuncGetAttributes' binaryVersion of the library's device code on `device` (103: sm_103a)."""
+    v = ctypes.c_int(0)
+    rc = load().pms_kernel_binary_version(int(device), ctypes.byref(v))
+    if rc:
+        raise PMSError(rc, "pms_kernel_binary_version")
+    return int(v.value)
 
 
 def pms_solve_device_noalloc(d_seqs, n: int, m: int, l: int, d: int, d_motifs, capacity: int, d_status,

@@ -2257,6 +2257,26 @@ int pms_probe_int_rate(pms_ctx *h, int kind, double *per_clk_per_sm)
     return PMS_OK;
 }
 
+int pms_kernel_binary_version(int device, int *version)
+{
+    if (!version)
+        return PMS_EINVAL;
+    int prev = 0;
+    if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return PMS_ECUDA;
+    }
+    cudaFuncAttributes a{};
+    const cudaError_t e = cudaFuncGetAttributes(&a, pack_kernel_fn());
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PMS_ECUDA;
+    }
+    *version = a.binaryVersion;
+    return PMS_OK;
+}
+
 // General alphabets (qPMS-Sigma). Host input, one seed per queue item of the
 // search kernel; the raw key buffer grows once if the first pass overflows it.
 int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_t *seqs, int n, int m, int l, int d,
@@ -2493,6 +2513,37 @@ struct NoAllocDevice {
 std::mutex g_noalloc_mu;
 NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
 
+// The descriptor block reaches the fixed array as kernel parameters, a piece
+// of up to kParamPieceBytes per launch: the bytes are copied into the launch
+// when it is enqueued, so no host buffer has to outlive the call (a copy
+// from a stack buffer would leave the stream reading freed host memory).
+constexpr int kParamPieceBytes = 4000;   // within the classic 4 KiB parameter space
+
+struct ParamPiece {
+    unsigned char b[kParamPieceBytes];
+};
+
+__global__ void store_piece_kernel(ParamPiece piece, unsigned char *dst, int nbytes)
+{
+    for (int i = threadIdx.x; i < nbytes; i += blockDim.x)
+        dst[i] = piece.b[i];
+}
+
+cudaError_t store_bytes(unsigned char *dst, const void *src, size_t nbytes, cudaStream_t st)
+{
+    const unsigned char *s = static_cast<const unsigned char *>(src);
+    for (size_t o = 0; o < nbytes; o += kParamPieceBytes) {
+        ParamPiece piece;
+        const int k = (int)std::min<size_t>(kParamPieceBytes, nbytes - o);
+        std::memcpy(piece.b, s + o, (size_t)k);
+        store_piece_kernel<<<1, 256, 0, st>>>(piece, dst + o, k);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
 // Once per device, with that device current: the array's device address,
 // the kernels' constant tables and launch attributes.
 int noalloc_setup(int dev, NoAllocDevice **out)
@@ -2590,7 +2641,7 @@ extern "C" int pms_solve_device_noalloc(const uint8_t *d_seqs, int n, int m, int
         return rc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
 
-    // descriptors, built on the stack
+    // descriptors, built on the stack and enqueued by value (store_bytes)
     struct Meta {
         InstDev inst;
         Segment seg;
@@ -2660,7 +2711,7 @@ extern "C" int pms_solve_device_noalloc(const uint8_t *d_seqs, int n, int m, int
     unsigned char *base = nd->base;
 
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(base + o_meta, &meta, meta_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+    if ((e = store_bytes(base + o_meta, &meta, meta_bytes, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(base + o_ctr, 0, cl.total, st)) != cudaSuccess) {
         cudaGetLastError();
         return PMS_ECUDA;

@@ -73,3 +73,62 @@ def test_noalloc_rejects_too_large():
     rc = lib.pms_solve_device_noalloc(ctypes.c_void_p(d_in.data_ptr()), 64, 4096, 20, 5, ctypes.c_void_p(out.data_ptr()),
                                       16, ctypes.c_void_p(st.data_ptr()), None)
     assert rc == pms.PMS_ESCRATCH
+
+
+def test_noalloc_raw_limit_reported_without_overrun():
+    # n = 1 and a loose (l, d): B(x, 3) over 31 seeds holds far more than the
+    # 65536 raw codes the fixed array keeps; the status reports the overflow
+    # (flag bit 1, the full raw count) and no code is written past `capacity`
+    import torch
+    lib = pms.load()
+    seqs = pi.random_sequences(1, 40, 91)
+    n, m, l, d = 1, 40, 10, 3
+    cap, slack = 1000, 64
+    d_in = torch.from_numpy(seqs.copy()).cuda()
+    out = torch.full((cap + slack,), -7, dtype=torch.int64, device="cuda")
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    rc = lib.pms_solve_device_noalloc(ctypes.c_void_p(d_in.data_ptr()), n, m, l, d, ctypes.c_void_p(out.data_ptr()),
+                                      cap, ctypes.c_void_p(st.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    assert rc == pms.PMS_OK
+    stream.synchronize()
+    s = st.cpu().numpy().astype(np.uint32)
+    assert s[2] & 2, s
+    assert s[0] > 65536, s
+    o = out.cpu().numpy()
+    assert np.all(o[cap:] == -7)
+    written = o[: min(cap, int(s[1]))].astype(np.uint64)
+    assert np.all(np.diff(written.astype(np.int64)) > 0)
+    # every written code is a true motif of the single sequence (within d of one of its l-mers)
+    import oracle
+    orc = oracle.Oracle()
+    for k in written[:50]:
+        assert orc.is_motif(orc.decode(int(k), l), seqs, d)
+
+
+def test_noalloc_few_ctas_matches_device_entry_point():
+    # n = 64, m = 1100: the masks and planes leave room in the 16 MiB array for
+    # the row scratch of only a few CTAs; the result must not depend on that
+    import torch
+    lib = pms.load()
+    stream = torch.cuda.Stream()
+    ctx = pms.Context(0)
+    ctx.set_stream(stream)
+    inst = pi.planted_instance(64, 1100, 15, 4, 93)
+    cap = 4096
+    for _ in range(2):
+        with torch.cuda.stream(stream):
+            want_st, want = _reference(ctx, torch, inst.seqs, inst.l, inst.d, cap)
+            got_st, got = _noalloc(lib, torch, stream, inst.seqs, inst.l, inst.d, cap)
+        assert got_st[2] == want_st[2] == 0
+        assert np.array_equal(got, want)
+        assert pi_key(inst.motif) in set(int(k) for k in got)
+    ctx.close()
+
+
+def pi_key(motif: bytes) -> int:
+    k = 0
+    for ch in motif.decode():
+        k = 4 * k + "ACGT".index(ch)
+    return k
