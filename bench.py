@@ -179,48 +179,83 @@ def n_ball(l: int, d: int, sigma: int = 4) -> int:
 
 # ------------------------------------------------------------------ CPU baseline (oracle)
 
-def cpu_oracle_rate(l: int, d: int, n: int, m: int, seed: int, budget_s: float, q: int = 0,
-                    alphabet: bytes | None = None) -> dict:
-    """The oracle as it stands, on a bounded slice of seeds of one instance, scaled to solves/s
-    (q > 0: the quorum form, seeds over s_1 .. s_{n-q+1}; alphabet: the general-alphabet search)."""
+def _oracle():
     import oracle
-    o = oracle.Oracle()
+    return oracle.Oracle()
+
+
+def cpu_oracle_whole(l: int, d: int, n: int, m: int, seed: int, threads: int) -> dict:
+    """One whole solve of one seeded instance by the oracle as it stands (char-level motif test)."""
+    o = _oracle()
+    inst = pi.planted_instance(n, m, l, d, seed)
+    t0 = time.perf_counter()
+    motifs = o.solve(inst.seqs, l, d, threads=threads)
+    t = time.perf_counter() - t0
+    return {"seconds": t, "motifs": int(len(motifs)), "value": 1.0 / t}
+
+
+def cpu_oracle_slice(l: int, d: int, n: int, m: int, seed: int, budget_s: float, threads: int,
+                     variant: str = "seeds", q: int = 0, alphabet: bytes | None = None) -> dict:
+    """The oracle on a bounded slice of the seeds of one instance, timed and scaled to solves/s
+    (variant "seeds": candidates B(x, d) over the l-mers x of s_1 (of s_1..s_{n-q+1} with a quorum);
+    "pairs": the Observation 3.3 pair form; alphabet: the general-alphabet search)."""
+    o = _oracle()
     inst = pi.planted_instance_sigma(n, m, l, d, seed, alphabet) if alphabet else pi.planted_instance(n, m, l, d, seed)
     W = (m - l + 1) * (n - q + 1 if q > 0 else 1)
-    cores = os.cpu_count() or 1
-    sigma = len(alphabet) if alphabet else 4
 
     def run(lo, hi):
         if alphabet:
-            o.sigma_solve_seeds(inst.seqs, l, d, alphabet, lo, hi, q=q, threads=cores)
+            o.sigma_solve_seeds(inst.seqs, l, d, alphabet, lo, hi, q=q, threads=threads)
         elif q > 0:
-            o.solve_quorum_seeds(inst.seqs, l, d, q, lo, hi, threads=cores)
+            o.solve_quorum_seeds(inst.seqs, l, d, q, lo, hi, threads=threads)
+        elif variant == "pairs":
+            o.solve_pairs_seeds(inst.seqs, l, d, lo, hi, threads=threads)
         else:
-            o.solve_seeds(inst.seqs, l, d, lo, hi, threads=cores)
+            o.solve_seeds(inst.seqs, l, d, lo, hi, threads=threads)
 
-    # calibrate on one seed per core, then grow to about budget_s
-    k = min(W, cores)
+    k = min(W, threads)
     t0 = time.perf_counter()
     run(0, k)
-    t1 = time.perf_counter() - t0
-    total_t, total_seeds, lo = t1, k, k
+    total_t, total_seeds, lo = time.perf_counter() - t0, k, k
     while total_t < budget_s and lo < W:
         per_seed = max(total_t / total_seeds, 1e-6)
-        take = int(min(W - lo, max(cores, (budget_s - total_t) / per_seed)))
-        take = max(1, take)
+        take = max(1, int(min(W - lo, max(threads, (budget_s - total_t) / per_seed))))
         t0 = time.perf_counter()
         run(lo, lo + take)
         total_t += time.perf_counter() - t0
         total_seeds += take
         lo += take
-    solves_per_s = (total_seeds / W) / total_t
-    return {"value": solves_per_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": f"{total_seeds} of {W} seeds of one ({l},{d}{f',q={q}' if q else ''}) n={n} m={m} "
-                      f"{'protein ' if alphabet else ''}instance, {total_t:.1f} s, scaled by {W}/{total_seeds}",
-            "candidate_checks_per_s": total_seeds * n_ball(l, d, sigma) / total_t}
+    return {"value": (total_seeds / W) / total_t, "unit": "solves/s", "threads": threads, "seconds": total_t,
+            "sample": f"seeds 0..{total_seeds - 1} of the {W} of one {'protein ' if alphabet else ''}"
+                      f"({l},{d}{f',q={q}' if q else ''}) n={n} m={m} instance ({variant} form), "
+                      f"{total_t:.1f} s, rate scaled by {W}/{total_seeds}"}
+
+
+def cpu_baseline_plain(l: int, d: int, n: int = 20, m: int = 600, seed: int = 424242) -> dict:
+    """cpu_baseline of a plain configuration. (9,2), (15,4): one whole solve on every host core,
+    plus a single-thread seed slice. (17,5), (19,6): a whole char-level solve takes tens of
+    minutes (about 35 s of one core per seed at (17,5)), so the timed baseline is the oracle's
+    Observation 3.3 pair form on one seed per host core, scaled to solves/s."""
+    cores = os.cpu_count() or 1
+    out = {"unit": "solves/s", "cores": cores, "kind": "oracle"}
+    if (l, d) in ((9, 2), (15, 4)):
+        w = cpu_oracle_whole(l, d, n, m, seed, cores)
+        out.update(value=w["value"], threads=cores,
+                   sample=f"one whole ({l},{d}) n={n} m={m} instance (seed {seed}), {w['seconds']:.1f} s on "
+                          f"{cores} threads, {w['motifs']} motifs")
+        st = cpu_oracle_slice(l, d, n, m, seed, 4.0, 1)
+        out["single_thread"] = {"value": st["value"], "unit": "solves/s", "threads": 1, "sample": st["sample"]}
+    else:
+        pr = cpu_oracle_slice(l, d, n, m, seed, 1.0, cores, variant="pairs")
+        out.update(value=pr["value"], threads=cores, sample=pr["sample"],
+                   note="char-level seed form not timed here: tens of seconds of one core per seed")
+    return out
 
 
 def run_reference(args, ws, rank) -> None:
+    """The reference arm: the CPU oracle as it stands. Plain workloads: each step is one whole
+    solve of a new seeded instance on every host core; --steps is honoured as a cap, so that the
+    run ends within about two minutes; warm-up steps are 16-seed slices (untimed)."""
     if rank != 0:
         return
     alphabet = pi.PROTEIN if args.workload in PROTEIN_WORKLOADS else None
@@ -230,22 +265,43 @@ def run_reference(args, ws, rank) -> None:
         l, d, q = QUORUM_WORKLOADS[args.workload] if args.workload in QUORUM_WORKLOADS \
             else (*WORKLOADS.get(args.workload, (15, 4)), 0)
     n, m = 20, 600
-    budget = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    cores = os.cpu_count() or 1
+    o = _oracle()
     for s in range(args.warmup):
-        cpu_oracle_rate(l, d, n, m, 1000 + s, budget / 4, q=q, alphabet=alphabet)
-    rates = []
-    for s in range(args.steps):
-        rates.append(cpu_oracle_rate(l, d, n, m, 1 + s, budget, q=q, alphabet=alphabet))
-    value = statistics.mean(r["value"] for r in rates)
+        inst = pi.planted_instance(n, m, l, d, 1000 + s)
+        if not alphabet and not q:
+            o.solve_seeds(inst.seqs, l, d, 0, 16, threads=cores)
+    whole = not alphabet and not q and (l, d) in ((9, 2), (15, 4))
+    times, fracs, samples = [], [], []
+    budget = 120.0
+    t_start = time.perf_counter()
+    for k in range(args.steps):
+        if whole:
+            w = cpu_oracle_whole(l, d, n, m, 1 + k, cores)
+            times.append(w["seconds"])
+            fracs.append(1.0)
+            samples.append(f"seed {1 + k}: {w['seconds']:.1f} s, {w['motifs']} motifs")
+        else:
+            sl = cpu_oracle_slice(l, d, n, m, 1 + k, 15.0, cores, q=q, alphabet=alphabet)
+            times.append(sl["seconds"])
+            fracs.append(sl["value"] * sl["seconds"])      # the fraction of one solve this step did
+            samples.append(sl["sample"])
+        elapsed = time.perf_counter() - t_start
+        if elapsed + elapsed / (k + 1) > budget:
+            break
+    steps = len(times)
+    value = sum(fracs) / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic",
+            "steps": steps, "steps_requested": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * sum(times) / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": (f"quorum ({l},{d}) q={q}" if q else
                                     f"protein ({l},{d})" if alphabet else f"plain ({l},{d})")
-                                   + f" n={n} m={m}, CPU oracle on bounded seed samples"},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": rates[0]["cores"], "kind": "oracle",
-                             "sample": rates[0]["sample"]},
+                                   + f" n={n} m={m}, CPU oracle"
+                                   + (", one whole solve per step" if whole else ", a bounded seed slice per step"),
+                       "steps_note": "--steps is a cap: steps stop once about 120 s have been spent"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "threads": cores, "sample": "; ".join(samples)},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -260,21 +316,44 @@ def make_flush(torch, dev):
     return flush
 
 
-def bench_plain(args, ws, rank, local, dist, l, d, q: int = 0) -> dict:
-    import torch
-    import paper_2403_00306_gb300 as pms
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
+class Peaks:
+    """Roofline denominators of the comparison-bound kernels (l-mer comparisons per second)."""
+
+    def __init__(self, ctx, torch, dev):
+        self.popc = ctx.probe_int_rate(0)       # POPC per clock per SM (measured probe)
+        self.mix = ctx.probe_int_rate(3)        # the comparison mix per clock per SM (measured probe)
+        self.sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        self.fmax = float(load_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+        self.peak_popc = self.popc * self.sms * self.fmax
+        # 4 integer issue slots per comparison (2 LOP3, POPC, IMNMX) on 128 lanes per SM
+        self.peak_int4 = self.sms * 128 * self.fmax / 4.0
+
+    def roofline(self, cmp_per_launch: float, ms: float, kernel: str, traffic, share: float) -> dict:
+        achieved = cmp_per_launch / (ms / 1000.0) if ms > 0 else float("nan")
+        return {"bound": "alu", "achieved": achieved / 1e12, "peak": self.peak_popc / 1e12, "unit": "Tcmp/s",
+                "frac": achieved / self.peak_popc, "frac_popc": achieved / self.peak_popc,
+                "frac_int4": achieved / self.peak_int4, "peak_int4": self.peak_int4 / 1e12,
+                "traffic": traffic, "kernel": kernel, "cmp_per_launch": cmp_per_launch,
+                "verify_ms_per_launch": ms,
+                "peak_basis": f"one POPC per comparison: {self.popc:.2f} POPC/clk/SM (measured probe) x {self.sms} "
+                              f"SMs x {self.fmax/1e6:.0f} MHz (of measured); frac_int4 against {self.sms} SMs x "
+                              f"128 lanes x {self.fmax/1e6:.0f} MHz / 4 issue slots per comparison; comparison-mix "
+                              f"probe {self.mix:.2f}/clk/SM",
+                "share_of_step": share}
+
+
+def measure_plain(pms, torch, dev, stream, peaks, l, d, K, Wm, rank, dist, q: int = 0, clk=None) -> dict:
+    """One plain configuration: K timed device-resident solves (CUDA events on the library stream,
+    L2 flushed between steps), the verification kernel's comparisons (count mode, same
+    instances), and K end-to-end solves from host memory through pms_solve."""
     n, m = 20, 600
-    K, Wm = args.steps, args.warmup
     seeds = rank_seeds(rank, K + Wm)
     insts = [pi.planted_instance(n, m, l, d, s) for s in seeds]
     d_in = [torch.from_numpy(i.seqs.copy()).to(dev) for i in insts]
     cap = 1 << 16
     d_out = torch.zeros(cap, dtype=torch.int64, device=dev)
     d_st = torch.zeros(4, dtype=torch.int32, device=dev)
-    stream = torch.cuda.Stream(device=dev)
-    ctx = pms.Context(local)
+    ctx = pms.Context(dev.index)
     ctx.set_stream(stream)
     if q:
         ctx.set_options(quorum=q)
@@ -297,7 +376,7 @@ def bench_plain(args, ws, rank, local, dist, l, d, q: int = 0) -> dict:
     verify_ms = []
     barrier(dist)
     torch.cuda.synchronize(dev)
-    with ClockSampler(local) as clk:
+    with (clk if clk is not None else _Null()):
         for k in range(K):
             with torch.cuda.stream(stream):
                 flush(k)
@@ -308,16 +387,14 @@ def bench_plain(args, ws, rank, local, dist, l, d, q: int = 0) -> dict:
         torch.cuda.synchronize(dev)
     barrier(dist)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    local_total = sum(step_ms)
-    total_ms = max_over_ranks(dist, local_total)
+    total_ms = max_over_ranks(dist, sum(step_ms))
     solves = sum_over_ranks(dist, K)
     value = solves / (total_ms / 1000.0)
 
     # algorithmic work of the dominant kernel (count mode, same instances, untimed)
-    cctx = pms.Context(local)
+    cctx = pms.Context(dev.index)
     cctx.set_options(count_work=1, quorum=q)
-    cmp_total = 0
-    tested = 0
+    cmp_total = tested = 0
     for k in range(K):
         cctx.solve(insts[Wm + k].seqs, l, d)
         s = cctx.stats()
@@ -326,7 +403,6 @@ def bench_plain(args, ws, rank, local, dist, l, d, q: int = 0) -> dict:
         cmp_total += s["cmp_reduce"] + s["cmp_verify"]
         tested += s["candidates_tested"]
     cctx.close()
-    cmp_per_launch = cmp_total / K
     verify_avg_ms = statistics.mean(verify_ms)
 
     # e2e through the host-buffer C-ABI call
@@ -339,41 +415,69 @@ def bench_plain(args, ws, rank, local, dist, l, d, q: int = 0) -> dict:
         ctx.solve(insts[Wm + k].seqs, l, d)
         e2e_ms.append((time.perf_counter() - t0) * 1000.0)
     e2e_total = max_over_ranks(dist, sum(e2e_ms))
-    e2e_value = solves / (e2e_total / 1000.0)
-
-    probe = ctx.probe_int_rate(3)   # comparisons per clock per SM (measured)
-    probe_popc = ctx.probe_int_rate(0)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peaks = load_peaks()
-    fmax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    peak_cmp = probe * sms * fmax
-    achieved = cmp_per_launch / (verify_avg_ms / 1000.0) if verify_avg_ms > 0 else float("nan")
-    clocks = clk.summary()
     ctx.close()
     W = m - l + 1
+    tested_total = sum_over_ranks(dist, tested)
     return {
-        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": K, "warmup": Wm,
-        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u32", "data": "synthetic",
+        "value": value, "unit": "solves/s", "steps": K, "warmup": Wm, "ms_per_step": total_ms / K,
         "config": {"workload": (f"quorum ({l},{d}) q={q}" if q else f"plain ({l},{d})")
                                + f" n={n} m={m}, one seeded FM-model instance per step",
                    "l": l, "d": d, "n": n, "m": m, "l2": "flushed between steps (512 MiB write, untimed)",
                    "timing": "CUDA events on the library stream around pms_solve_device"},
-        "candidate_checks_per_s": solves * W * (n - q + 1 if q else 1) * n_ball(l, d) / (total_ms / 1000.0),
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_cmp / 1e12,
-                     "unit": "Tcmp/s", "frac": achieved / peak_cmp,
-                     "traffic": measured_traffic(f"quorum{l}_{d}_q{q}" if q else f"plain{l}_{d}"),
-                     "kernel": "main_kernel (verification)", "cmp_per_launch": cmp_per_launch,
-                     "verify_ms_per_launch": verify_avg_ms,
-                     "peak_basis": f"{probe:.2f} comparisons/clk/SM (probe) x {sms} SMs x {fmax/1e6:.0f} MHz; "
-                                   f"POPC probe {probe_popc:.2f}/clk/SM",
-                     "share_of_step": verify_avg_ms / (total_ms / K)},
-        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": n * m,
+        # candidates generated and compared explicitly against occurrences (count mode)
+        "candidate_checks_per_s": tested_total / (total_ms / 1000.0),
+        "candidates_tested_per_step": tested / K,
+        # the searched space W * |B(x, d)| per solve, for scale (not checks)
+        "search_space_per_s": solves * W * (n - q + 1 if q else 1) * n_ball(l, d) / (total_ms / 1000.0),
+        "roofline": peaks.roofline(cmp_total / K, verify_avg_ms, "main_kernel (verification)",
+                                   measured_traffic(f"quorum{l}_{d}_q{q}" if q else f"plain{l}_{d}"),
+                                   verify_avg_ms / (total_ms / K)),
+        "e2e": {"value": solves / (e2e_total / 1000.0), "unit": "solves/s", "h2d_bytes_per_step": n * m,
                 "d2h_bytes_per_step": 16 + 512 * 8, "ms_per_step": e2e_total / K},
         "gpu_launches": 3 * K,   # packing + compatibility masks, verification, sort/unique
-        "clocks": clocks,
-        "candidates_tested_per_step": tested / K,
     }
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+
+def bench_plain(args, ws, rank, local, dist, l, d, q: int = 0, extras: bool = False) -> dict:
+    import torch
+    import paper_2403_00306_gb300 as pms
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    pctx = pms.Context(local)
+    peaks = Peaks(pctx, torch, dev)
+    pctx.close()
+    clk = ClockSampler(local)
+    r = measure_plain(pms, torch, dev, stream, peaks, l, d, args.steps, args.warmup, rank, dist, q, clk=clk)
+    line = {"metric": METRIC, "value": r["value"], "unit": "solves/s", "n_gpus": ws, "steps": r["steps"],
+            "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": r["config"]}
+    for k in ("candidate_checks_per_s", "candidates_tested_per_step", "search_space_per_s", "roofline", "e2e",
+              "gpu_launches"):
+        line[k] = r[k]
+    line["clocks"] = clk.summary()
+    if extras:
+        # the other BASELINE configurations, each measured the same way (fewer steps)
+        per = {}
+        for (pl, pd), steps in (((9, 2), 10), ((17, 5), 5), ((19, 6), 3)):
+            c2 = ClockSampler(local)
+            pr = measure_plain(pms, torch, dev, stream, peaks, pl, pd, steps, 3, rank, dist, clk=c2)
+            pr["clocks"] = c2.summary()
+            del pr["config"]["l2"]
+            per[f"plain{pl}_{pd}"] = pr
+        line["per_config"] = per
+        line["batch"] = measure_batch(pms, torch, dev, peaks, args, rank, dist)
+        line["served"] = measure_serve(pms, torch, dev, args, rank, dist)
+        line["gpu_launches"] += sum(v["gpu_launches"] for v in per.values())
+    return line
 
 
 def bench_sigma(args, ws, rank, local, dist, l, d) -> dict:
@@ -389,10 +493,11 @@ def bench_sigma(args, ws, rank, local, dist, l, d) -> dict:
     stream = torch.cuda.Stream(device=dev)
     ctx = pms.Context(local)
     ctx.set_stream(stream)
+    peaks = Peaks(ctx, torch, dev)
     flush = make_flush(torch, dev)
     for i in range(Wm):
         ctx.solve_sigma(insts[i].seqs, l, d, pi.PROTEIN)
-    kern_ms, verify_ms, e2e_ms, cmps = [], [], [], []
+    kern_ms, verify_ms, e2e_ms, cmps, tested = [], [], [], [], []
     barrier(dist)
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
@@ -408,6 +513,7 @@ def bench_sigma(args, ws, rank, local, dist, l, d) -> dict:
             verify_ms.append(s["ms_verify"])
             # one POPC per comparison: window vs seed, node bound, candidate vs row
             cmps.append(s["cmp_rows"] + s["cmp_reduce"] + s["cmp_verify"])
+            tested.append(s["candidates_tested"])
             assert insts[Wm + k].motif in {bytes(r) for r in out}, "planted motif missing"
         torch.cuda.synchronize(dev)
     barrier(dist)
@@ -415,13 +521,7 @@ def bench_sigma(args, ws, rank, local, dist, l, d) -> dict:
     solves = sum_over_ranks(dist, K)
     value = solves / (total_ms / 1000.0)
     e2e_total = max_over_ranks(dist, sum(e2e_ms))
-    probe_popc = ctx.probe_int_rate(0)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peaks = load_peaks()
-    fmax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    peak = probe_popc * sms * fmax
     verify_avg = statistics.mean(verify_ms)
-    achieved = statistics.mean(cmps) / (verify_avg / 1000.0) if verify_avg > 0 else float("nan")
     clocks = clk.summary()
     ctx.close()
     W = m - l + 1
@@ -433,13 +533,10 @@ def bench_sigma(args, ws, rank, local, dist, l, d) -> dict:
                                f"instance per step", "l": l, "d": d, "n": n, "m": m, "sigma": 20,
                    "l2": "flushed between steps (512 MiB write, untimed)",
                    "timing": "CUDA events on the library stream from the packing kernel to the sort kernel"},
-        "candidate_checks_per_s": solves * W * n_ball(l, d, 20) / (total_ms / 1000.0),
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tcmp/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "sigma_main_kernel (search)",
-                     "cmp_per_launch": statistics.mean(cmps), "verify_ms_per_launch": verify_avg,
-                     "peak_basis": f"one POPC per comparison: {probe_popc:.2f} POPC/clk/SM (probe) x {sms} SMs x "
-                                   f"{fmax/1e6:.0f} MHz",
-                     "share_of_step": verify_avg / (total_ms / K)},
+        "candidate_checks_per_s": sum(tested) / (sum(kern_ms) / 1000.0),
+        "search_space_per_s": solves * W * n_ball(l, d, 20) / (total_ms / 1000.0),
+        "roofline": peaks.roofline(statistics.mean(cmps), verify_avg, "sigma_main_kernel (search)", None,
+                                   verify_avg / (total_ms / K)),
         "e2e": {"value": solves / (e2e_total / 1000.0), "unit": "solves/s", "h2d_bytes_per_step": n * m,
                 "d2h_bytes_per_step": 32 + 8 * 9 + l, "ms_per_step": e2e_total / K},
         "gpu_launches": 3 * K,   # packing, search, sort/unique
@@ -447,69 +544,83 @@ def bench_sigma(args, ws, rank, local, dist, l, d) -> dict:
     }
 
 
-def bench_batch(args, ws, rank, local, dist) -> dict:
-    import torch
-    import paper_2403_00306_gb300 as pms
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
+def measure_batch(pms, torch, dev, peaks, args, rank, dist, steps: int = 3) -> dict:
+    """256 mixed instances in one persistent launch (autotuned schedule) against the same
+    instances solved one by one on the plain path."""
     insts = pi.batch_instances(count=256, master_seed=2024 + rank)
-    ctx = pms.Context(local)
+    ctx = pms.Context(dev.index)
     batch = [(i.seqs, i.l, i.d) for i in insts]
     t_tune = time.perf_counter()
     ctx.set_options(autotune=1)      # tunes each (l, d, n, m) class once, untimed
     ctx.solve_batch(batch)
     t_tune = time.perf_counter() - t_tune
-    for _ in range(args.warmup):
+    for _ in range(3):
         ctx.solve_batch(batch)
     flush = make_flush(torch, dev)
     barrier(dist)
-    ts = []
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
+    wall, kern, ver = [], [], []
+    with ClockSampler(dev.index) as clk:
+        for k in range(steps):
             flush(k)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             res = ctx.solve_batch(batch)
-            ts.append(time.perf_counter() - t0)
+            wall.append(time.perf_counter() - t0)
+            s = ctx.stats()
+            kern.append(s["ms_kernel"])
+            ver.append(s["ms_verify"])
     barrier(dist)
-    one = []
-    for k in range(max(1, args.steps // 2)):
-        t0 = time.perf_counter()
+    # one by one on the plain path (pms_solve, host buffers; device time from the stats)
+    one_wall, one_kern = [], []
+    for k in range(max(1, steps - 1)):
+        tw = tk = 0.0
         for i in insts:
+            t0 = time.perf_counter()
             ctx.solve(i.seqs, i.l, i.d)
-        one.append(time.perf_counter() - t0)
-    total = max_over_ranks(dist, sum(ts))
-    solves = sum_over_ranks(dist, 256 * args.steps)
-    value = solves / total
-    cand = sum((i.m - i.l + 1) * n_ball(i.l, i.d) for i in insts)
-    ok = all(not isinstance(r, Exception) for r in res)
+            tw += time.perf_counter() - t0
+            tk += ctx.stats()["ms_kernel"]
+        one_wall.append(tw)
+        one_kern.append(tk)
+    # verification-kernel work (count mode, untimed)
+    cctx = pms.Context(dev.index)
+    cctx.set_options(count_work=1)
+    cctx.solve_batch(batch)
+    cs = cctx.stats()
+    cctx.close()
     ctx.close()
-    return {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "batch of 256 instances, (l,d) in {(11,3),(13,4),(15,4)}, n in [10,30], m in [300,1000]",
-                       "timing": "host clock around pms_solve_batch (upload, kernels, download)"},
-            "candidate_checks_per_s": cand * args.steps / sum(ts),
-            "one_by_one_solves_per_s": 256 / statistics.mean(one), "all_ok": ok, "autotune_s": t_tune,
-            "e2e": {"value": value, "unit": "solves/s",
-                    "h2d_bytes_per_step": int(sum(i.n * i.m for i in insts)), "d2h_bytes_per_step": None},
-            "gpu_launches": 4 * args.steps, "clocks": clk.summary()}
+    ok = all(not isinstance(r, Exception) for r in res)
+    kern_ms = statistics.mean(kern)
+    ver_ms = statistics.mean(ver)
+    solves = sum_over_ranks(dist, 256)
+    return {"workload": "batch of 256 instances (master seed 2024), (l,d) in {(11,3),(13,4),(15,4)}, "
+                        "n in [10,30], m in [300,1000]",
+            "value": solves / (max_over_ranks(dist, kern_ms) / 1000.0), "unit": "solves/s",
+            "timing": "value: device time of the batch pipeline (CUDA events, first to last kernel); e2e: "
+                      "host clock around pms_solve_batch (upload, kernels, download)",
+            "steps": steps, "ms_per_step": kern_ms,
+            "e2e": {"value": solves / max_over_ranks(dist, statistics.mean(wall)), "unit": "solves/s",
+                    "ms_per_step": 1000 * statistics.mean(wall),
+                    "h2d_bytes_per_step": int(sum(i.n * i.m for i in insts)),
+                    "d2h_bytes_per_step": int(16 * 256 + 8 * sum(len(r) for r in res if not isinstance(r, Exception)))},
+            "one_by_one": {"value": 256 / (statistics.mean(one_kern) / 1000.0), "unit": "solves/s",
+                           "timing": "sum of the device times of 256 pms_solve calls",
+                           "e2e_value": 256 / statistics.mean(one_wall)},
+            "verify_ms": ver_ms, "share_verify": ver_ms / kern_ms,
+            "candidate_checks_per_s": cs["candidates_tested"] / (kern_ms / 1000.0),
+            "roofline": peaks.roofline(cs["cmp_reduce"] + cs["cmp_verify"], ver_ms, "main_kernel (verification)",
+                                       None, ver_ms / kern_ms),
+            "all_ok": ok, "autotune_s": t_tune, "gpu_launches": 4 * steps, "clocks": clk.summary()}
 
 
-def bench_serve(args, ws, rank, local, dist) -> dict:
+def measure_serve(pms, torch, dev, args, rank, dist) -> dict:
     """Poisson request stream through the served form (continuous batching)."""
     import threading
     from concurrent.futures import ThreadPoolExecutor
 
-    import torch
-    import paper_2403_00306_gb300 as pms
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
     count, rate = args.serve_requests, args.serve_rate
     reqs = list(pi.serve_requests(count=count, rate_per_s=rate, master_seed=7 + rank))
-    ctx = pms.Context(local)
-    # warm-up: a few requests, not timed
-    for _, inst in reqs[: max(3, args.warmup)]:
+    ctx = pms.Context(dev.index)
+    for _, inst in reqs[:8]:      # warm-up, not timed
         ctx.wait(ctx.submit(inst.seqs, inst.l, inst.d))
     lat = [None] * count
     done_t = [None] * count
@@ -529,7 +640,7 @@ def bench_serve(args, ws, rank, local, dist) -> dict:
         ctx.release(t)
 
     barrier(dist)
-    with ClockSampler(local) as clk:
+    with ClockSampler(dev.index) as clk:
         t0 = time.perf_counter()
         futs = []
         for i, (ta, inst) in enumerate(reqs):
@@ -537,7 +648,7 @@ def bench_serve(args, ws, rank, local, dist) -> dict:
             delay = target - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            arrival = max(target, time.perf_counter()) if delay <= 0 else target
+            arrival = target
             t = ctx.submit(inst.seqs, inst.l, inst.d)
             futs.append(pool.submit(waiter, i, t, arrival))
         for f in futs:
@@ -545,7 +656,7 @@ def bench_serve(args, ws, rank, local, dist) -> dict:
         t_end = max(done_t)
     pool.shutdown()
     st = ctx.stats()
-    # saturation: all requests of a slice submitted at once
+    # saturation: a slice of the stream submitted at once
     sat_n = min(count, 2000)
     ts = time.perf_counter()
     tickets = [ctx.submit(inst.seqs, inst.l, inst.d) for _, inst in reqs[:sat_n]]
@@ -558,17 +669,15 @@ def bench_serve(args, ws, rank, local, dist) -> dict:
     solves = sum_over_ranks(dist, count)
     span_max = max_over_ranks(dist, span)
     lat_ms = sorted(1000.0 * x for x in lat)
-    cand = sum((inst.m - inst.l + 1) * n_ball(inst.l, inst.d) for _, inst in reqs)
-    return {"metric": METRIC, "value": solves / span_max, "unit": "solves/s", "n_gpus": ws, "steps": count,
-            "warmup": args.warmup, "ms_per_step": 1000.0 * span_max / count, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"served: {count} Poisson requests at {rate}/s, (l,d) in {{(13,4),(15,4),(17,5)}}, "
-                                   "n=20, m in [200,1200]",
-                       "timing": "host clock from each arrival to pms_wait's return"},
+    return {"workload": f"served: {count} Poisson requests at {rate:g}/s (master seed 7), (l,d) in "
+                        "{(13,4),(15,4),(17,5)}, n=20, m in [200,1200]",
+            "value": solves / span_max, "unit": "solves/s", "requests": count,
+            "timing": "host clock from each request's arrival time to pms_wait's return; value = requests / "
+                      "(last completion - first arrival)",
             "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[int(len(lat_ms) * 0.99) - 1],
                            "max": lat_ms[-1]},
-            "offered_per_s": rate, "saturation_solves_per_s": sat,
-            "candidate_checks_per_s": cand / span, "all_ok": all(ok),
+            "offered_per_s": rate, "saturation_solves_per_s": sat, "saturation_requests": sat_n,
+            "all_ok": all(ok),
             "serve": {"waves": st["serve_waves"], "overlapped_waves": st["serve_overlapped_waves"],
                       "max_requests_per_wave": st["serve_max_requests_per_wave"]},
             "e2e": {"value": solves / span_max, "unit": "solves/s",
@@ -577,14 +686,47 @@ def bench_serve(args, ws, rank, local, dist) -> dict:
             "gpu_launches": 3 * count + int(st["serve_waves"]), "clocks": clk.summary()}
 
 
+def bench_batch(args, ws, rank, local, dist) -> dict:
+    import torch
+    import paper_2403_00306_gb300 as pms
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ctx = pms.Context(local)
+    peaks = Peaks(ctx, torch, dev)
+    ctx.close()
+    b = measure_batch(pms, torch, dev, peaks, args, rank, dist, steps=args.steps)
+    line = {"metric": METRIC, "value": b["value"], "unit": "solves/s", "n_gpus": ws, "steps": b["steps"],
+            "warmup": 3, "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": b["workload"], "timing": b["timing"], "l2": "flushed between steps"}}
+    line.update({k: v for k, v in b.items() if k not in line and k not in ("workload", "timing")})
+    return line
+
+
+def bench_serve(args, ws, rank, local, dist) -> dict:
+    import torch
+    import paper_2403_00306_gb300 as pms
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    s = measure_serve(pms, torch, dev, args, rank, dist)
+    line = {"metric": METRIC, "value": s["value"], "unit": "solves/s", "n_gpus": ws, "steps": s["requests"],
+            "warmup": 8, "ms_per_step": 1000.0 / s["value"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": s["workload"], "timing": s["timing"]}}
+    line.update({k: v for k, v in s.items() if k not in line and k not in ("workload", "timing", "requests")})
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="plain15_4",
-                    choices=sorted(WORKLOADS) + sorted(QUORUM_WORKLOADS) + sorted(PROTEIN_WORKLOADS)
-                    + ["batch", "serve"])
+    ap.add_argument("--workload", default="suite",
+                    choices=["suite"] + sorted(WORKLOADS) + sorted(QUORUM_WORKLOADS) + sorted(PROTEIN_WORKLOADS)
+                    + ["batch", "serve"],
+                    help="suite (default): the plain (15,4) line, with per_config lines for (9,2), (17,5), "
+                         "(19,6), the batched and the served workloads inside it")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
@@ -597,6 +739,7 @@ def main():
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return
+    cpu = rank == 0 and ws == 1 and not args.no_cpu_baseline
     if args.workload == "batch":
         line = bench_batch(args, ws, rank, local, dist)
     elif args.workload == "serve":
@@ -604,13 +747,26 @@ def main():
     elif args.workload in PROTEIN_WORKLOADS:
         l, d = PROTEIN_WORKLOADS[args.workload]
         line = bench_sigma(args, ws, rank, local, dist, l, d)
-        if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_oracle_rate(l, d, 20, 600, 424242, budget_s=15.0, alphabet=pi.PROTEIN)
+        if cpu:
+            c = cpu_oracle_slice(l, d, 20, 600, 424242, 15.0, os.cpu_count() or 1, alphabet=pi.PROTEIN)
+            line["cpu_baseline"] = {"value": c["value"], "unit": "solves/s", "cores": os.cpu_count() or 1,
+                                    "kind": "oracle", "threads": c["threads"], "sample": c["sample"]}
     else:
-        l, d, q = QUORUM_WORKLOADS[args.workload] if args.workload in QUORUM_WORKLOADS else (*WORKLOADS[args.workload], 0)
-        line = bench_plain(args, ws, rank, local, dist, l, d, q)
-        if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_oracle_rate(l, d, 20, 600, 424242, budget_s=15.0, q=q)
+        suite = args.workload == "suite"
+        l, d, q = QUORUM_WORKLOADS[args.workload] if args.workload in QUORUM_WORKLOADS \
+            else (*WORKLOADS["plain15_4" if suite else args.workload], 0)
+        line = bench_plain(args, ws, rank, local, dist, l, d, q, extras=suite)
+        if cpu:
+            if q:
+                c = cpu_oracle_slice(l, d, 20, 600, 424242, 15.0, os.cpu_count() or 1, q=q)
+                line["cpu_baseline"] = {"value": c["value"], "unit": "solves/s", "cores": os.cpu_count() or 1,
+                                        "kind": "oracle", "threads": c["threads"], "sample": c["sample"]}
+            else:
+                line["cpu_baseline"] = cpu_baseline_plain(l, d)
+            if suite:
+                for name, pc in line["per_config"].items():
+                    pl, pd = WORKLOADS[name]
+                    pc["cpu_baseline"] = cpu_baseline_plain(pl, pd)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
