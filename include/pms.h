@@ -119,6 +119,19 @@ typedef struct {
                               of each plan (same shape and options), with the
                               call's input and output pointers patched in:
                               0 = on (default); -1 = launch kernel by kernel */
+    int triple_rows;       /* three-string feasibility below a tree node (the
+                              TraverStringRef feasibility theorem for three
+                              strings, applied to the seed x and pairs of
+                              occurrences): an occurrence u of the smallest
+                              row is kept for a node only if, for each of the
+                              next triple_rows rows, some occurrence w leaves
+                              a string of the node within d of both u and w;
+                              the node is dropped when no u is left, and its
+                              leaves meet only the kept u. Tree form, q = n.
+                              0: the default (d >= 4 and fewer than 0.25
+                              windows of a random sequence expected within d
+                              of a candidate: 4 rows, 8 when d >= 5; off
+                              otherwise); -1: off; k > 0: k rows. */
 } pms_options;
 
 /* A tuned schedule for one instance class (l, d, n rounded up to a power of

@@ -53,7 +53,7 @@ class pms_options(ctypes.Structure):
                 ("max_motifs", ctypes.c_size_t), ("count_work", ctypes.c_int), ("serve_wave_items", ctypes.c_int),
                 ("serve_max_inflight", ctypes.c_int), ("smem_rows", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("seed_mode", ctypes.c_int), ("quorum", ctypes.c_int), ("partial_rows", ctypes.c_int),
-                ("graph", ctypes.c_int)]
+                ("graph", ctypes.c_int), ("triple_rows", ctypes.c_int)]
 
 
 class pms_tuning(ctypes.Structure):

@@ -43,7 +43,8 @@ struct InstDev {
     int partial_rows;      // rows a partial candidate (letters fixed above the 3 lowest changed positions)
                            //   is tested against before its leaves; 0: no partial level
     uint32_t raw_cap;      // capacity of the raw motif buffer (power of two)
-    int pad;
+    int triple_rows;       // rows after the first whose occurrences are tested in pairs with the first
+                           //   row's (three-string feasibility below a node); 0: no such test
 };
 
 // A contiguous range of queue items: chunks [chunk_lo, chunk_hi) of instance
@@ -98,8 +99,15 @@ struct MainParams {
     int rows_cap;                 // max (n - 1) * (W + 3) over the instances, rounded up to a multiple of 4
     int smem_rows_cap;            // row entries a seed may keep in shared memory (<= kRowSmemCap)
     unsigned long long *counters; // kCntNum entries (count mode)
-    int *done;                    // per segment: finished items (served form), may be null
     const uint8_t *mode;          // per seed: 0 = tree over B(x, d), 1 = pairs (x, r); null: all 0
+    // Node-level work sharing of the lane walk (null: each item's nodes are
+    // claimed by its own CTA only). Per queue item g (zeroed before the
+    // launch): item_claim[2g] = nodes claimed so far, item_claim[2g + 1] = the
+    // nodes its claimers last saw unclaimed (a hint for CTAs looking for work).
+    // steal_state[0]: cursor of the candidates examined by CTAs whose queue ran
+    // out; steal_state[1]: items whose nodes are all claimed.
+    int *item_claim;
+    unsigned int *steal_state;
 };
 
 // Seed modes of the pair form.

@@ -36,6 +36,13 @@ namespace {
 
 constexpr uint32_t kFull = 0xffffffffu;
 
+// Row-entry quads a lane of the node walk tests per step (4: 16 entries).
+#ifndef PMS_WALK_QUADS
+#define PMS_WALK_QUADS 4
+#endif
+constexpr int kWalkQuads = PMS_WALK_QUADS;
+static_assert(kWalkQuads >= 2 && kWalkQuads % 2 == 0, "the walk step loads quads in pairs");
+
 __constant__ uint32_t c_binom[kLMax + 1][kLMax + 1];  // C(a, b), 0 when b > a
 __constant__ unsigned long long c_pow3[kLMax + 1];
 // Leaf sets of a node with at most 4 changed positions p_0 < p_1 < ...: leaf
@@ -72,7 +79,8 @@ struct __align__(16) CtaSmem {
     int total_rows;
     int next;                // next subset index of the chunk to claim
     int ctab;                // chunk table of the current item
-    int pad[2];
+    int stolen;              // the current item was joined after the queue ran out
+    int pad;
 };
 
 // Colex unranking of the rank-th k-subset of {0..l-1} (combinatorial number
@@ -522,6 +530,71 @@ __device__ __forceinline__ int partial_walk(const WarpCtx &c, uint32_t P, uint32
     return listN;
 }
 
+// The three-string feasibility test of TraverStringRef, for a node P of seed
+// x and a pair of occurrences: u of row 0 (rb0, reduced by P) and w of a later
+// row. A string c of node P equals x outside P and differs from x on P. Let
+// t_u = popc(D_u ^ P): the mismatches of c and u it cannot avoid (outside P
+// where u differs from x, and on P where u agrees with x); likewise t_w. On the
+// positions of P where u and w both differ from x, c can match both when
+// u = w there, but only one of them when u, w and x are three different
+// letters; with F the number of those positions, some c of node P is within d
+// of both u and w exactly when t_u + t_w + F <= 2d (t_u, t_w <= d hold for
+// reduced rows). Every motif of node P is within d of an occurrence u of row 0
+// that passes this test with some occurrence w of each other row, so row 0
+// keeps only such u (lane i tests entry i, rows 1..triple_rows in size order)
+// and the node is dropped when none is left. Returns the new size of rb0
+// (padded to a multiple of 4 like reduce_row); k0 <= 32.
+template <bool kCount>
+__device__ __forceinline__ int triple_filter(const WarpCtx &c, uint32_t P, int k0)
+{
+    const InstDev &in = c.in;
+    const int d = in.d;
+    const int R = min(in.triple_rows + 1, in.n - 1);
+    uint2 u = make_uint2(0u, 0u);
+    uint32_t Du = 0u;
+    int tu = 0;
+    bool alive = c.lane < k0;
+    if (alive) {
+        u = c.ws->rb0[c.lane];
+        Du = (u.x ^ c.xh) | (u.y ^ c.xl);
+        tu = __popc(Du ^ P);
+    }
+    for (int r = 1; r < R; ++r) {
+        if (!__any_sync(kFull, alive))
+            break;
+        const int ri = c.cs->row_order[r];
+        const int len = c.cs->row_len[ri];
+        const int off = c.cs->row_off[ri];
+        const int k = reduce_row(c.rows.D + off, c.rows.HL + off, len, P, d, c.ws->rb1, c.lane, c.lt);
+        if (kCount && c.lane == 0)
+            c.cnt[kCntCmpReduce] += len;
+        if (k > kRbCap)
+            continue;   // the reduced row did not fit its buffer: this row is not used
+        bool ok = false;
+        if (alive) {
+            for (int i = 0; i < k; ++i) {
+                const uint2 w = c.ws->rb1[i];
+                const uint32_t Dw = (w.x ^ c.xh) | (w.y ^ c.xl);
+                const uint32_t Euw = (u.x ^ w.x) | (u.y ^ w.y);
+                ok |= tu + __popc(Dw ^ P) + __popc(Du & Dw & Euw & P) <= 2 * d;
+            }
+            if (kCount)
+                c.cnt[kCntCmpVerify] += k;
+        }
+        alive = alive && ok;
+    }
+    const uint32_t bal = __ballot_sync(kFull, alive);
+    const int nk = __popc(bal);
+    __syncwarp();
+    if (alive)
+        c.ws->rb0[__popc(bal & c.lt)] = u;
+    __syncwarp();
+    if (nk > 0 && c.lane < 4)
+        c.ws->rb0[nk + c.lane] = c.ws->rb0[nk - 1];
+    __syncwarp();
+    return nk;
+}
+
 // The leaves of a node P with lev <= 4 changed positions as a set of up to 81
 // bits, verified row by row. For an occurrence w of a row reduced by P, a leaf
 // c is within d of w iff the matches of c and w on P reach t = lev + m_out - d,
@@ -532,7 +605,7 @@ __device__ __forceinline__ int partial_walk(const WarpCtx &c, uint32_t P, uint32
 // occurrence, the row's set is the OR over its occurrences and the node's
 // leaves the AND over rows, stopping once it is empty.
 template <bool kCount>
-__device__ __forceinline__ void expand_bits(const WarpCtx &c, uint32_t P, int lev)
+__device__ __forceinline__ void expand_bits(const WarpCtx &c, uint32_t P, int lev, int k0)
 {
     const InstDev &in = c.in;
     const int d = in.d;
@@ -559,9 +632,14 @@ __device__ __forceinline__ void expand_bits(const WarpCtx &c, uint32_t P, int le
         const int ri = c.cs->row_order[r];
         const int len = c.cs->row_len[ri];
         const int off = c.cs->row_off[ri];
-        const int k = reduce_row(c.rows.D + off, c.rows.HL + off, len, P, d, c.ws->rb1, c.lane, c.lt);
-        if (kCount && c.lane == 0)
-            c.cnt[kCntCmpReduce] += len;
+        // row 0 is already reduced (and possibly cut by the three-string test) in rb0
+        int k = k0;
+        if (r > 0) {
+            k = reduce_row(c.rows.D + off, c.rows.HL + off, len, P, d, c.ws->rb1, c.lane, c.lt);
+            if (kCount && c.lane == 0)
+                c.cnt[kCntCmpReduce] += len;
+        }
+        const uint2 *rb = r > 0 ? c.ws->rb1 : c.ws->rb0;
         const bool sm = k <= kRbCap;
         const int cnt = sm ? k : len;   // occurrences scanned: the reduced row, or the full row
         uint32_t rowm[3] = {0u, 0u, 0u};
@@ -569,7 +647,7 @@ __device__ __forceinline__ void expand_bits(const WarpCtx &c, uint32_t P, int le
             const int e = e0 + c.lane;
             uint32_t m0 = 0u, m1 = 0u, m2 = 0u;
             if (e < cnt) {
-                const uint2 w = sm ? c.ws->rb1[e] : c.rows.HL[off + e];
+                const uint2 w = sm ? rb[e] : c.rows.HL[off + e];
                 const uint32_t eh = w.x ^ c.xh, el = w.y ^ c.xl;
                 const uint32_t Dw = eh | el;
                 const int t = lev + __popc(Dw & ~P) - d;
@@ -653,14 +731,6 @@ __device__ __forceinline__ void expand_subset(const WarpCtx &c, uint32_t P)
     const int nrows = in.n - 1;
     const int lev = __popc(P);
 
-    // 81 leaves as a bit set (measured faster than the leaf list at 4 changed
-    // positions, (15,4) 0.132 -> 0.128 ms, (13,4) 1.81 -> 1.77 ms; slower with
-    // fewer leaves, (11,3) 0.316 -> 0.339 ms)
-    if (nrows > 0 && lev == 4 && in.partial_rows == 0) {
-        expand_bits<kCount>(c, P, lev);
-        return;
-    }
-
     int k0 = 0, len0 = 0, off0 = 0;
     if (nrows > 0) {
         const int r0 = c.cs->row_order[0];
@@ -671,6 +741,19 @@ __device__ __forceinline__ void expand_subset(const WarpCtx &c, uint32_t P)
             c.cnt[kCntCmpReduce] += len0;
         if (k0 == 0)
             return;
+        if (in.triple_rows > 0 && nrows > 1 && k0 <= 32) {
+            k0 = triple_filter<kCount>(c, P, k0);
+            if (k0 == 0)
+                return;
+        }
+    }
+
+    // 81 leaves as a bit set (measured faster than the leaf list at 4 changed
+    // positions, (15,4) 0.132 -> 0.128 ms, (13,4) 1.81 -> 1.77 ms; slower with
+    // fewer leaves, (11,3) 0.316 -> 0.339 ms)
+    if (nrows > 0 && lev == 4 && in.partial_rows == 0) {
+        expand_bits<kCount>(c, P, lev, k0);
+        return;
     }
 
     uint32_t t = P;
@@ -777,7 +860,7 @@ __device__ __forceinline__ int filter_subsets(const WarpCtx &c, int N)
 
 // Lane-asynchronous node filter of a chunk: every lane holds one tree node P
 // and its position in the rows (row rank r, entry quad e4); each step a lane
-// tests the next 16 entries of its own row with the bound popc(D_w ^ P) <= d.
+// tests the next 4 * kWalkQuads entries of its own row with the bound popc(D_w ^ P) <= d.
 // A hit moves the lane's node to the next row, a row scanned to its end
 // dismisses the node, a node that passes the last filtered row goes to the
 // expansion queue, and a free lane takes the next node of the warp's pool at
@@ -804,7 +887,8 @@ __device__ __forceinline__ void walk_init(const WarpCtx &c)
 }
 
 template <bool kCount>
-__device__ __forceinline__ int walk_run(const WarpCtx &c, const int *tab, int g0, int g1, CtaSmem &cs, bool &finished)
+__device__ __forceinline__ int walk_run(const WarpCtx &c, const int *tab, int g0, int g1, CtaSmem &cs, int *claim_ctr,
+                                        int claim_base, unsigned int *items_out, bool &finished)
 {
     const InstDev &in = c.in;
     const int d = in.d;
@@ -846,8 +930,15 @@ __device__ __forceinline__ int walk_run(const WarpCtx &c, const int *tab, int g0
                     pool[c.lane] = keep;
                 const int want = min(64 - avail, max(4, claim));
                 int start = 0;
-                if (c.lane == 0)
-                    start = atomicAdd(&cs.next, want);
+                if (c.lane == 0) {
+                    start = claim_base + atomicAdd(claim_ctr, want);
+                    if (items_out) {
+                        // shared counter: publish what is left, count the item once when it runs out
+                        claim_ctr[1] = max(0, g1 - (start + want));
+                        if (start < g1 && start + want >= g1)
+                            atomicAdd(items_out, 1u);
+                    }
+                }
                 start = __shfl_sync(kFull, start, 0);
                 const int got = start < g1 ? min(want, g1 - start) : 0;
                 if (start + want >= g1)
@@ -899,7 +990,7 @@ __device__ __forceinline__ int walk_run(const WarpCtx &c, const int *tab, int g0
             finished = true;
             break;
         }
-        // one step of every lane: the next 16 entries of its row, as selects
+        // one step of every lane: the next 4 * kWalkQuads entries of its row, as selects
         // rather than branches (a lane without a node reads the first quad of
         // the rows and ignores the result)
         bool done = false;
@@ -909,19 +1000,19 @@ __device__ __forceinline__ int walk_run(const WarpCtx &c, const int *tab, int g0
             const int a4 = has ? off4 + e4 : 0;
             const int lim = has ? len4 - e4 : 1;   // quads left in the row (>= 1)
             // quads past the row's end re-read quad e4 (no effect on the minimum)
-            const uint4 v0 = D4[a4];
-            const uint4 v1 = D4[lim > 1 ? a4 + 1 : a4];
-            const uint4 v2 = D4[lim > 2 ? a4 + 2 : a4];
-            const uint4 v3 = D4[lim > 3 ? a4 + 3 : a4];
-            const int m0 = min(min(__popc(v0.x ^ P), __popc(v0.y ^ P)), min(__popc(v0.z ^ P), __popc(v0.w ^ P)));
-            const int m1 = min(min(__popc(v1.x ^ P), __popc(v1.y ^ P)), min(__popc(v1.z ^ P), __popc(v1.w ^ P)));
-            const int m2 = min(min(__popc(v2.x ^ P), __popc(v2.y ^ P)), min(__popc(v2.z ^ P), __popc(v2.w ^ P)));
-            const int m3 = min(min(__popc(v3.x ^ P), __popc(v3.y ^ P)), min(__popc(v3.z ^ P), __popc(v3.w ^ P)));
-            const int mn = min(min(m0, m1), min(m2, m3));
+            int mA = 64, mB = 64;
+#pragma unroll
+            for (int q = 0; q < kWalkQuads; q += 2) {
+                const uint4 u = D4[lim > q ? a4 + q : a4];
+                const uint4 v = D4[lim > q + 1 ? a4 + q + 1 : a4];
+                mA = min(mA, min(min(__popc(u.x ^ P), __popc(u.y ^ P)), min(__popc(u.z ^ P), __popc(u.w ^ P))));
+                mB = min(mB, min(min(__popc(v.x ^ P), __popc(v.y ^ P)), min(__popc(v.z ^ P), __popc(v.w ^ P))));
+            }
+            const int mn = min(mA, mB);
             if (kCount && has)
-                c.cnt[kCntCmpReduce] += 4 * min(lim, 4);
+                c.cnt[kCntCmpReduce] += 4 * min(lim, kWalkQuads);
             const bool hit = has && mn <= d;
-            e4 = hit ? 0 : e4 + 4;
+            e4 = hit ? 0 : e4 + kWalkQuads;
             r += hit ? 1 : 0;
             done = hit && r == nrows;
             if (hit && r < nrows) {
@@ -1134,40 +1225,131 @@ __device__ __forceinline__ int filter_subsets_q(const WarpCtx &c, int N)
     return N;
 }
 
+// Queue item g of a launch: its instance, seed, chunk and chunk table.
+struct ItemRef {
+    int inst, seed, chunk, ctab;
+};
+
+__device__ __forceinline__ ItemRef decode_item(const MainParams &p, long long g)
+{
+    int lo = 0, hi = p.nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.seg[mid].work_lo <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const Segment s = p.seg[lo];
+    const int cidx = s.chunk_lo + (int)(g - s.work_lo);
+    const int cps = s.cps > 0 ? s.cps : p.inst[s.inst].cps;
+    return ItemRef{s.inst, s.seed_lo + cidx / cps, cidx % cps, s.cps > 0 ? s.ctab : p.inst[s.inst].ctab};
+}
+
+// Fewest unclaimed nodes an item must have for a CTA whose queue ran out to
+// join it, and the rounds such a CTA looks for one before it stops.
+constexpr int kStealMinNodes = 64;
+constexpr int kStealTries = 16;
+
+// Warp-cooperative choice of an item to join once the queue has run out: in
+// each round the lanes read the unclaimed-node hints of 32 consecutive
+// steal-cursor positions (the cursor cycles over the last items handed out,
+// newest first) and the warp takes the item with the most if that is at least
+// kStealMinNodes. A fruitless round sleeps a microsecond (items handed out
+// last may not have published a hint yet). Returns the item, or -1 once every
+// item's nodes are claimed or after kStealTries rounds.
+__device__ __forceinline__ long long find_victim(const MainParams &p, int lane)
+{
+    const long long span = min(p.total, 2LL * (long long)gridDim.x);
+    for (int t = 0; t < kStealTries; ++t) {
+        unsigned int c0 = 0, ex = 0;
+        if (lane == 0) {
+            ex = *reinterpret_cast<volatile unsigned int *>(p.steal_state + 1);
+            c0 = atomicAdd(p.steal_state, 32u);
+        }
+        ex = __shfl_sync(kFull, ex, 0);
+        c0 = __shfl_sync(kFull, c0, 0);
+        if ((long long)ex >= p.total)
+            return -1;
+        const long long g = p.total - 1 - (long long)((c0 + (unsigned int)lane) % (unsigned long long)span);
+        const int left = *reinterpret_cast<volatile const int *>(p.item_claim + 2 * g + 1);
+        int best = left;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            best = max(best, __shfl_xor_sync(kFull, best, o));
+        if (best >= kStealMinNodes) {
+            const int src = __ffs(__ballot_sync(kFull, left == best)) - 1;
+            return __shfl_sync(kFull, g, src);
+        }
+        __nanosleep(1000);
+    }
+    return -1;
+}
+
+// Marks all nodes of item g claimed (an item that is done, or whose seed has
+// no motif); the first to do so counts it in steal_state[1].
+__device__ __forceinline__ void exhaust_item(const MainParams &p, long long g, int nodes)
+{
+    const int old = atomicMax(p.item_claim + 2 * g, nodes);
+    if (old < nodes)
+        atomicAdd(p.steal_state + 1, 1u);
+}
+
 // Gathers the feasible occurrences of seed `seed` (windows within 2d, from
 // the compatibility masks) into shared memory when they fit, else into this
-// CTA's global scratch. Every warp derives the smallest-first row order and
-// the row offsets from the precomputed row sizes (two rows per lane, n <= 64)
-// and fills its own rows; warp 0 also records them for the later phases.
+// CTA's global scratch, rows ordered smallest first and padded to multiples of
+// 4 entries with copies of their last entry. Warp 0 derives the row order and
+// offsets from the precomputed row sizes (two rows per lane, n <= 64) while
+// every thread loads mask words; then each row's words are prefix-counted (a
+// warp per row) and every thread fills destination slots directly: the slot's
+// row by a binary search over the row offsets, its mask word by a binary
+// search over the word counts, the window as the word's r-th set bit. So the
+// only dependent global loads are one mask word and one window per slot, all
+// issued by all threads at once. `scratch` (shared memory the warps do not use
+// between items) holds the mask words and counts; rows whose masks exceed it
+// (more than 32 words, i.e. W > 1024, or too many rows) are gathered by the
+// per-warp form below it.
+constexpr int kBuildScratchWords = kWarps * (int)(sizeof(WarpSmem) / sizeof(uint32_t));
+
 __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &in, int seed, CtaSmem &cs,
                                            uint32_t *smem_D, uint2 *smem_HL, uint32_t *glob_D, uint2 *glob_HL,
-                                           int warp, int lane, unsigned long long *cnt)
+                                           int warp, int lane, unsigned long long *cnt, uint32_t *scratch)
 {
     const int n = in.n, NW = in.NW, W = in.W, R = n - 1;
     const int *rl = p.rowlen + in.rlen_off + (size_t)seed * R;
-    const int big = 0x7fffffff;
-    const int la = lane < R ? rl[lane] : big;            // size of row (sequence) lane + 1
-    const int lb = lane + 32 < R ? rl[lane + 32] : big;  // size of row lane + 33
-    int ra = 0, rb = 0;                                  // ranks in smallest-first order
-    for (int j = 0; j < R; ++j) {
-        const int lj = __shfl_sync(kFull, j < 32 ? la : lb, j & 31);
-        ra += (lj < la) || (lj == la && j < lane);
-        rb += (lj < lb) || (lj == lb && j < lane + 32);
+    const uint32_t *mask = p.compat + in.compat_off + (size_t)seed * R * NW;
+    const bool fast = NW <= 32 && 2 * R * NW <= kBuildScratchWords;
+    uint32_t *sbits = scratch, *spre = scratch + R * NW;
+    if (fast) {
+        // every (row, word) of the seed's masks: the bits and their count
+        for (int t = threadIdx.x; t < R * NW; t += kThreads) {
+            const uint32_t b = __ldg(mask + t);
+            sbits[t] = b;
+            spre[t] = (uint32_t)__popc(b);
+        }
     }
-    const int pa = lane < R ? (la + 3) & ~3 : 0, pb = lane + 32 < R ? (lb + 3) & ~3 : 0;
-    int oa = 0, ob = 0, total = 0;                       // offsets: padded sizes of the rows ranked before
-    for (int j = 0; j < R; ++j) {
-        const int rj = __shfl_sync(kFull, j < 32 ? ra : rb, j & 31);
-        const int pj = __shfl_sync(kFull, j < 32 ? pa : pb, j & 31);
-        oa += rj < ra ? pj : 0;
-        ob += rj < rb ? pj : 0;
-        total += pj;
-    }
-    // a seed is hopeless when more rows are empty than the quorum may miss
-    const int nempty = __popc(__ballot_sync(kFull, lane < R && la == 0)) + __popc(__ballot_sync(kFull, lane + 32 < R && lb == 0));
-    const bool empty = nempty > in.n - in.q;
-    const bool in_smem = total <= p.smem_rows_cap;
     if (warp == 0) {
+        const int big = 0x7fffffff;
+        const int la = lane < R ? rl[lane] : big;            // size of row (sequence) lane + 1
+        const int lb = lane + 32 < R ? rl[lane + 32] : big;  // size of row lane + 33
+        int ra = 0, rb = 0;                                  // ranks in smallest-first order
+        for (int j = 0; j < R; ++j) {
+            const int lj = __shfl_sync(kFull, j < 32 ? la : lb, j & 31);
+            ra += (lj < la) || (lj == la && j < lane);
+            rb += (lj < lb) || (lj == lb && j < lane + 32);
+        }
+        const int pa = lane < R ? (la + 3) & ~3 : 0, pb = lane + 32 < R ? (lb + 3) & ~3 : 0;
+        int oa = 0, ob = 0, total = 0;                       // offsets: padded sizes of the rows ranked before
+        for (int j = 0; j < R; ++j) {
+            const int rj = __shfl_sync(kFull, j < 32 ? ra : rb, j & 31);
+            const int pj = __shfl_sync(kFull, j < 32 ? pa : pb, j & 31);
+            oa += rj < ra ? pj : 0;
+            ob += rj < rb ? pj : 0;
+            total += pj;
+        }
+        // a seed is hopeless when more rows are empty than the quorum may miss
+        const int nempty = __popc(__ballot_sync(kFull, lane < R && la == 0)) +
+                           __popc(__ballot_sync(kFull, lane + 32 < R && lb == 0));
         if (lane < R) {
             cs.row_len[lane + 1] = la;
             cs.row_off[lane + 1] = oa;
@@ -1184,67 +1366,113 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
         }
         if (lane == 0) {
             cs.total_rows = total;
-            cs.feasible = !empty;
-            cs.rows_in_smem = in_smem;
+            cs.feasible = nempty <= in.n - in.q;
+            cs.rows_in_smem = total <= p.smem_rows_cap;
             if (cnt)
                 cnt[kCntCmpRows] += (unsigned long long)R * W;
         }
     }
-    if (!empty) {
-        uint32_t *Dd = in_smem ? smem_D : glob_D;
-        uint2 *Hd = in_smem ? smem_HL : glob_HL;
-        const uint2 *pl = p.planes + in.plane_off;
-        const uint2 x = pl[seed];
-        const uint32_t *mask = p.compat + in.compat_off + (size_t)seed * R * NW;
-        const int si = seed / W;   // the seed's own sequence has no row
-        for (int i = 1 + warp; i < n; i += kWarps) {
-            const uint32_t *mr = mask + (size_t)(i - 1) * NW;
-            const uint2 *s = pl + (size_t)(i - 1 < si ? i - 1 : i) * W;
-            const int src = (i - 1) & 31;
-            const int off = __shfl_sync(kFull, i - 1 < 32 ? oa : ob, src);
-            const int len = __shfl_sync(kFull, i - 1 < 32 ? la : lb, src);
-            int base = 0;
-            for (int k0 = 0; k0 < NW; k0 += 32) {
-                const int k = k0 + lane;
-                const uint32_t bits = k < NW ? mr[k] : 0u;
-                const int c = __popc(bits);
-                int incl = c;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o)
-                        incl += y;
-                }
-                const int chunk = __shfl_sync(kFull, incl, 31);
-                // entry e of these 32 words goes to lane e % 32: its word t is the
-                // number of words whose inclusive count is <= e, its bit the
-                // (e - exclusive count of t)-th set bit of word t; all lanes load
-                // their window at once
-                for (int e0 = 0; e0 < chunk; e0 += 32) {
-                    const int e = e0 + lane;
-                    int t = 0;
+    __syncthreads();
+    if (!cs.feasible)
+        return;
+    const bool in_smem = cs.rows_in_smem;
+    uint32_t *Dd = in_smem ? smem_D : glob_D;
+    uint2 *Hd = in_smem ? smem_HL : glob_HL;
+    const uint2 *pl = p.planes + in.plane_off;
+    const uint2 x = pl[seed];
+    const int si = seed / W;   // the seed's own sequence has no row
+    if (fast) {
+        // exclusive prefix counts of each row's words (a warp per row)
+        for (int k = warp; k < R; k += kWarps) {
+            const int c = lane < NW ? (int)spre[k * NW + lane] : 0;
+            int incl = c;
 #pragma unroll
-                    for (int step = 16; step >= 1; step >>= 1) {
-                        const int v = __shfl_sync(kFull, incl, t + step - 1);
-                        if (v <= e)
-                            t += step;
-                    }
-                    const uint32_t wb = __shfl_sync(kFull, bits, t);
-                    const int before = __shfl_sync(kFull, incl, t) - __shfl_sync(kFull, c, t);
-                    if (e < chunk) {
-                        const int bt = nth_set_bit(wb, e - before);
-                        const uint2 w = s[32 * (k0 + t) + bt];
-                        Hd[off + base + e] = w;
-                        Dd[off + base + e] = (x.x ^ w.x) | (x.y ^ w.y);
-                    }
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o)
+                    incl += y;
+            }
+            if (lane < NW)
+                spre[k * NW + lane] = (uint32_t)(incl - c);
+        }
+        __syncthreads();
+        const int total = cs.total_rows;
+        for (int slot = threadIdx.x; slot < total; slot += kThreads) {
+            // the rank whose padded row holds this slot: the last rank with offset <= slot
+            int lo = 0, hi = R - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (cs.rank_off4[mid] * 4 <= slot)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            // (an empty row shares its offset with the next rank and the rows are ordered by
+            // size, so the last rank at or below the slot is a row with entries)
+            const int i = cs.row_order[lo];
+            const int len = cs.row_len[i];
+            const int e = min(slot - cs.rank_off4[lo] * 4, len - 1);   // padding repeats the last entry
+            const uint32_t *pre = spre + (i - 1) * NW;
+            int t = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1)
+                if (t + step < NW && (int)pre[t + step] <= e)
+                    t += step;
+            const int bt = nth_set_bit(sbits[(i - 1) * NW + t], e - (int)pre[t]);
+            const uint2 *s = pl + (size_t)(i - 1 < si ? i - 1 : i) * W;
+            const uint2 w = __ldg(s + 32 * t + bt);
+            Hd[slot] = w;
+            Dd[slot] = (x.x ^ w.x) | (x.y ^ w.y);
+        }
+        __syncthreads();
+        return;
+    }
+    for (int i = 1 + warp; i < n; i += kWarps) {
+        const uint32_t *mr = mask + (size_t)(i - 1) * NW;
+        const uint2 *s = pl + (size_t)(i - 1 < si ? i - 1 : i) * W;
+        const int off = cs.row_off[i];
+        const int len = cs.row_len[i];
+        int base = 0;
+        for (int k0 = 0; k0 < NW; k0 += 32) {
+            const int k = k0 + lane;
+            const uint32_t bits = k < NW ? mr[k] : 0u;
+            const int c = __popc(bits);
+            int incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o)
+                    incl += y;
+            }
+            const int chunk = __shfl_sync(kFull, incl, 31);
+            // entry e of these 32 words goes to lane e % 32: its word t is the
+            // number of words whose inclusive count is <= e, its bit the
+            // (e - exclusive count of t)-th set bit of word t; all lanes load
+            // their window at once
+            for (int e0 = 0; e0 < chunk; e0 += 32) {
+                const int e = e0 + lane;
+                int t = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int v = __shfl_sync(kFull, incl, t + step - 1);
+                    if (v <= e)
+                        t += step;
                 }
-                base += chunk;
+                const uint32_t wb = __shfl_sync(kFull, bits, t);
+                const int before = __shfl_sync(kFull, incl, t) - __shfl_sync(kFull, c, t);
+                if (e < chunk) {
+                    const int bt = nth_set_bit(wb, e - before);
+                    const uint2 w = s[32 * (k0 + t) + bt];
+                    Hd[off + base + e] = w;
+                    Dd[off + base + e] = (x.x ^ w.x) | (x.y ^ w.y);
+                }
             }
-            __syncwarp();
-            const int padded = (len + 3) & ~3;
-            if (len > 0 && lane < padded - len) {
-                Hd[off + len + lane] = Hd[off + len - 1];
-                Dd[off + len + lane] = Dd[off + len - 1];
-            }
+            base += chunk;
+        }
+        __syncwarp();
+        const int padded = (len + 3) & ~3;
+        if (len > 0 && lane < padded - len) {
+            Hd[off + len + lane] = Hd[off + len - 1];
+            Dd[off + len + lane] = Dd[off + len - 1];
         }
     }
     __syncthreads();
@@ -1279,53 +1507,69 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) main_kernel(MainParams p
     }
     for (int i = threadIdx.x; i < (kLMax + 1) * (kLMax + 1); i += blockDim.x)
         (&cs.binom[0][0])[i] = (&c_binom[0][0])[i];
+    bool draining = false;   // warp 0: the queue has run out, items are joined through the steal cursor
     for (;;) {
-        if (threadIdx.x == 0) {
-            const unsigned long long g = atomicAdd(p.head, 1ull);
-            cs.g = g;
-            if (g < (unsigned long long)p.total) {
-                int lo = 0, hi = p.nseg - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (p.seg[mid].work_lo <= (long long)g)
-                        lo = mid;
-                    else
-                        hi = mid - 1;
+        if (warp == 0) {
+            long long g = -1;
+            if (!draining) {
+                unsigned long long h = 0;
+                if (lane == 0)
+                    h = atomicAdd(p.head, 1ull);
+                h = __shfl_sync(kFull, h, 0);
+                if (h < (unsigned long long)p.total)
+                    g = (long long)h;
+                else
+                    draining = p.item_claim != nullptr;
+            }
+            bool stolen = false;
+            if (g < 0 && draining) {
+                g = find_victim(p, lane);
+                stolen = g >= 0;
+            }
+            if (lane == 0) {
+                cs.g = g < 0 ? ~0ull : (unsigned long long)g;
+                cs.stolen = stolen;
+                if (g >= 0) {
+                    const ItemRef it = decode_item(p, g);
+                    cs.inst = it.inst;
+                    cs.seed = it.seed;
+                    cs.chunk = it.chunk;
+                    cs.ctab = it.ctab;
                 }
-                const Segment s = p.seg[lo];
-                const int cidx = s.chunk_lo + (int)((long long)g - s.work_lo);
-                const int cps = s.cps > 0 ? s.cps : p.inst[s.inst].cps;
-                cs.inst = s.inst;
-                cs.seed = s.seed_lo + cidx / cps;
-                cs.chunk = cidx % cps;
-                cs.ctab = s.cps > 0 ? s.ctab : p.inst[s.inst].ctab;
             }
         }
         __syncthreads();
-        if (cs.g >= (unsigned long long)p.total)
+        if (cs.g == ~0ull)
             break;
         const int I = cs.inst, seed = cs.seed, chunk = cs.chunk;
         const InstDev in = p.inst[I];
+        const int *tab = p.ctab + cs.ctab;
+        const int g0 = tab[in.d + 2 + 2 * chunk];
+        const int g1 = tab[in.d + 2 + 2 * chunk + 1];
         if (p.mode && p.mode[in.seed_off + seed] != kModeTree) {
+            if (threadIdx.x == 0 && p.item_claim)
+                exhaust_item(p, (long long)cs.g, g1 - g0);
             __syncthreads();   // this seed is searched by the pair kernel
             continue;
         }
         const bool rebuild = (I != cs.cached_inst) || (seed != cs.cached_seed);
         if (rebuild) {
-            build_rows(p, in, seed, cs, smem_D, smem_HL, glob_D, glob_HL, warp, lane, kCount ? cnt : nullptr);
+            build_rows(p, in, seed, cs, smem_D, smem_HL, glob_D, glob_HL, warp, lane, kCount ? cnt : nullptr,
+                       reinterpret_cast<uint32_t *>(smem_raw));
             if (threadIdx.x == 0) {
                 cs.cached_inst = I;
                 cs.cached_seed = seed;
             }
         }
-        const int *tab = p.ctab + cs.ctab;
-        const int g0 = tab[in.d + 2 + 2 * chunk];
-        const int g1 = tab[in.d + 2 + 2 * chunk + 1];
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             cs.next = g0;
+            // no node of an infeasible seed is searched: nothing for other CTAs to join
+            if (p.item_claim && !cs.feasible)
+                exhaust_item(p, (long long)cs.g, g1 - g0);
+        }
         __syncthreads();
         if constexpr (kCount) {
-            if (threadIdx.x == 0 && chunk == 0 && !cs.feasible)
+            if (threadIdx.x == 0 && chunk == 0 && !cs.feasible && !cs.stolen)
                 cnt[kCntSeedsInfeasible] += 1;
         }
         if (cs.feasible) {
@@ -1366,10 +1610,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) main_kernel(MainParams p
                     __syncwarp();
                 }
             } else if (in.grab == 1) {
+                // nodes are claimed from the item's shared counter when other
+                // CTAs may join it, else from the CTA's own
+                int *ctr = p.item_claim ? p.item_claim + 2 * cs.g : &cs.next;
+                const int base = p.item_claim ? g0 : 0;
+                unsigned int *exh = p.item_claim ? p.steal_state + 1 : nullptr;
                 walk_init(c);
                 for (;;) {
                     bool fin;
-                    const int qn = walk_run<kCount>(c, tab, g0, g1, cs, fin);
+                    const int qn = walk_run<kCount>(c, tab, g0, g1, cs, ctr, base, exh, fin);
                     const uint32_t *queue = wsm[warp].subs + 64;
                     for (int i = 0; i < qn; ++i)
                         expand_subset<kCount>(c, queue[i]);
@@ -1423,6 +1672,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) main_kernel(MainParams p
                 }
             }
         }
+        // warp 0 is past its last claim, so every node of the item is claimed
+        if (threadIdx.x == 0 && p.item_claim)
+            exhaust_item(p, (long long)cs.g, g1 - g0);
         __syncthreads();
     }
     if constexpr (kCount) {
@@ -1838,7 +2090,8 @@ __global__ void __launch_bounds__(kThreads, 2) pair_kernel(MainParams p)
         }
         const bool rebuild = (I != cs.cached_inst) || (seed != cs.cached_seed);
         if (rebuild) {
-            build_rows(p, in, seed, cs, smem_D, smem_HL, glob_D, glob_HL, warp, lane, kCount ? cnt : nullptr);
+            build_rows(p, in, seed, cs, smem_D, smem_HL, glob_D, glob_HL, warp, lane, kCount ? cnt : nullptr,
+                       reinterpret_cast<uint32_t *>(smem_raw));
             if (threadIdx.x == 0) {
                 cs.cached_inst = I;
                 cs.cached_seed = seed;

@@ -40,18 +40,39 @@ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // i.i.d. instance, small for (17,5) and (19,6), about 0.5 for (13,4) and
 // (15,5), where it was measured slower) and the tree has nodes with more than
 // three changed positions (d >= 5).
+// Expected windows of a uniform i.i.d. sequence of length m within d of a
+// fixed l-mer: (m - l + 1) P(Binomial(l, 3/4) <= d).
+double expected_near(int m, int l, int d)
+{
+    double p = 0, c = 1;
+    for (int i = 0; i <= d; ++i) {
+        p += c * std::pow(0.75, i) * std::pow(0.25, l - i);
+        c = c * (l - i) / (i + 1);
+    }
+    return (m - l + 1) * p;
+}
+
 int default_partial_rows(int n, int m, int l, int d)
 {
     (void)n;
     if (d < 5)
         return -1;
-    double p = 0, c = 1;   // P(Binomial(l, 3/4) <= d)
-    for (int i = 0; i <= d; ++i) {
-        p += c * std::pow(0.75, i) * std::pow(0.25, l - i);
-        c = c * (l - i) / (i + 1);
-    }
-    const double E = (m - l + 1) * p;
-    return E < 0.15 ? 8 : -1;
+    return expected_near(m, l, d) < 0.15 ? 8 : -1;
+}
+
+// Rows the three-string test below a tree node pairs with the first when no
+// option selects them (-1: none). It pays where a random window is rarely
+// within d of a candidate (E = expected_near below 0.25: (15,4) E = 0.07,
+// 0.115 -> 0.104 ms with 4 rows; (17,5) 1.69 -> 1.07 ms and (19,6) 18.9 ->
+// 12.7 ms with 8; n = 20, m = 600) and costs where nodes keep many
+// occurrences ((13,4), E = 0.58: 1.79 -> 2.35 ms with 2 rows; (11,3) and
+// (9,2), d < 4, likewise slower).
+int default_triple_rows(int n, int m, int l, int d)
+{
+    (void)n;
+    if (d < 4 || expected_near(m, l, d) >= 0.25)
+        return -1;
+    return d >= 5 ? 8 : 4;
 }
 
 uint32_t pow2_at_least(size_t v)
@@ -388,6 +409,14 @@ struct pms_ctx {
             v = default_partial_rows(n, m, l, d);
         return v < 0 ? 0 : std::min(v, n - 1);
     }
+    // rows the three-string test pairs with the first (0: no test)
+    int triple_rows_for(int n, int m, int l, int d) const
+    {
+        int v = opt.triple_rows;
+        if (v == 0)
+            v = default_triple_rows(n, m, l, d);
+        return v < 0 ? 0 : std::min(v, n - 2);
+    }
     int prune_rows_for(int n, int m, int l, int d) const
     {
         const Tuning *t = tuning(n, m, l, d);
@@ -505,10 +534,12 @@ struct MetaLayout {
     }
 };
 
-// Counters block (d_ctr): head, work counters, dense_total, then per instance raw_count and flags.
+// Counters block (d_ctr): head, work counters, dense_total, then per instance
+// raw_count and flags, then (items > 0) the steal cursor and the nodes claimed
+// of every queue item, for the verification kernel's work sharing.
 struct CtrLayout {
-    size_t head, head_pair, work, dense_total, raw_count, flags, total;
-    CtrLayout(size_t k)
+    size_t head, head_pair, work, dense_total, raw_count, flags, steal, claim, total;
+    CtrLayout(size_t k, size_t items = 0)
     {
         head = 0;
         head_pair = 8;
@@ -516,7 +547,9 @@ struct CtrLayout {
         dense_total = work + kCntNum * 8;
         raw_count = round_up(dense_total + 4, 16);
         flags = round_up(raw_count + 4 * k, 16);
-        total = round_up(flags + 4 * k, 256);
+        steal = round_up(flags + 4 * k, 16);
+        claim = steal + 16;
+        total = round_up(claim + 8 * items, 256);
     }
 };
 
@@ -630,6 +663,7 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
         in.grab = h->grab_for(s.n, s.m, s.l, s.d);
         in.prune_rows = h->prune_rows_for(s.n, s.m, s.l, s.d);
         in.partial_rows = h->partial_rows_for(s.n, s.m, s.l, s.d);
+        in.triple_rows = h->triple_rows_for(s.n, s.m, s.l, s.d);
         in.ctab = (int)P.ctab.size();
         P.ctab.insert(P.ctab.end(), ct.tab.begin(), ct.tab.end());
         in.seq_off = (long long)P.seq_bytes;
@@ -700,13 +734,14 @@ static void record_event(cudaEvent_t ev, cudaStream_t st, bool capturing)
 
 // CTAs of the verification kernel for a plan: resident CTAs per SM (capped by
 // the option or the tuned value of the first instance's class) x SMs, at most
-// one per queue item.
+// two per queue item (CTAs without an item of their own join the items that
+// have the most unclaimed tree nodes).
 static int plan_blocks(const pms_ctx *h, const Plan &P, bool count_mode)
 {
     const int occ = P.inst.empty()
                         ? std::max(1, h->occ[count_mode ? 1 : 0])
                         : plan_occ(h, P.inst[0].n, P.inst[0].m, P.inst[0].l, P.inst[0].d, count_mode, P.small_rows);
-    return (int)std::min<long long>((long long)h->num_sms * occ, std::max<long long>(P.total_items, 1));
+    return (int)std::min<long long>((long long)h->num_sms * occ, std::max<long long>(2 * P.total_items, 1));
 }
 
 // Host image of a plan's descriptors (layout ml) at dst.
@@ -728,7 +763,7 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
 {
     const size_t k = P.inst.size();
     MetaLayout ml(P);
-    CtrLayout cl(k);
+    CtrLayout cl(k, (size_t)P.total_items);
     int rc;
     if ((rc = h->ensure(h->d_meta, ml.total)) || (rc = h->ensure(h->d_ctr, cl.total)) ||
         (rc = h->ensure(h->d_planes, P.planes * sizeof(uint2))) || (rc = h->ensure(h->d_raw, P.raw * 8)) ||
@@ -803,11 +838,15 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     const int rows_cap_smem = P.small_rows ? kRowSmemCapSmall : kRowSmemCap;
     mp.smem_rows_cap = h->opt.smem_rows > 0 ? std::min(h->opt.smem_rows, rows_cap_smem) : rows_cap_smem;
     mp.counters = (unsigned long long *)(dc + cl.work);
+    mp.item_claim = (int *)(dc + cl.claim);
+    mp.steal_state = (unsigned int *)(dc + cl.steal);
     record_event(h->evm0, st, meta_dev != nullptr);
     if (P.total_items > 0 && (e = launch_main(mp, blocks, count_mode, st, P.small_rows)) != cudaSuccess)
         return h->cuda_fail(e, "verification kernel");
     if (P.pair_mode && P.total_pair_items > 0) {
         MainParams pp = mp;
+        pp.item_claim = nullptr;   // the pair kernel claims pairs within its own CTA
+        pp.steal_state = nullptr;
         pp.seg = (const Segment *)(dm + ml.segp);
         pp.nseg = (int)P.seg_pair.size();
         pp.total = P.total_pair_items;
@@ -1615,6 +1654,7 @@ static bool served_admit(Served *S, Request *r)
     in.grab = h->grab_for(r->n, r->m, r->l, r->d);
     in.prune_rows = h->prune_rows_for(r->n, r->m, r->l, r->d);
     in.partial_rows = h->partial_rows_for(r->n, r->m, r->l, r->d);
+    in.triple_rows = h->triple_rows_for(r->n, r->m, r->l, r->d);
     in.q = r->n;
     in.nseed = 1;
     in.seq_off = (long long)(off + L.seqs);
@@ -1921,7 +1961,7 @@ int pms_set_options(pms_ctx *h, const pms_options *opt)
     if (!h || !opt)
         return PMS_EINVAL;
     if (opt->ctas_per_sm < 0 || opt->chunk_work < 0 || opt->grab < 0 || opt->serve_wave_items < 0 || opt->smem_rows < 0 ||
-        opt->seed_mode < 0 || opt->seed_mode > 1 || opt->quorum < 0 || opt->partial_rows < -1 || opt->graph < -1 ||
+        opt->seed_mode < 0 || opt->seed_mode > 1 || opt->quorum < 0 || opt->partial_rows < -1 || opt->graph < -1 || opt->triple_rows < -1 ||
         opt->serve_max_inflight < 0 || opt->serve_max_inflight > 1024)
         return h->fail(PMS_EINVAL, "negative option");
     std::lock_guard<std::recursive_mutex> g(h->mu);

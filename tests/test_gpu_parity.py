@@ -258,3 +258,24 @@ def test_work_counters(ctx):
     assert s["cmp_rows"] >= W * 19 * (600 - 13 + 1)
     assert 0 < s["subsets_pruned"] < s["subsets"]
     c.close()
+
+
+@pytest.mark.parametrize("triple_rows", [1, 3, 63])
+@pytest.mark.parametrize("case", [c for c in SMALL if c[0] > 1] + DEEP, ids=lambda c: "n{}_m{}_l{}_d{}".format(*c[:4]))
+def test_three_string_node_test_matches_oracle(oracle_, case, triple_rows):
+    # the three-string test below a node (pivot occurrences kept only with a
+    # feasible partner in each of the next triple_rows rows) on its own, with
+    # the partial level, and with rows in global scratch
+    n, m, l, d, seed = case
+    inst = pi.planted_instance(n, m, l, d, seed)
+    seqs = pi.random_sequences(n, m, seed + 991)
+    want = oracle_.solve(inst.seqs, l, d, cap=1 << 24)
+    c = pms.Context(0)
+    c.set_options(triple_rows=triple_rows)
+    assert np.array_equal(c.solve(inst.seqs, l, d), want)
+    assert np.array_equal(c.solve(seqs, l, d), oracle_.solve(seqs, l, d, cap=1 << 24))
+    c.set_options(triple_rows=triple_rows, partial_rows=2)
+    assert np.array_equal(c.solve(inst.seqs, l, d), want)
+    c.set_options(triple_rows=triple_rows, smem_rows=8)
+    assert np.array_equal(c.solve(inst.seqs, l, d), want)
+    c.close()

@@ -89,6 +89,31 @@ def test_plain_19_6_on_48_seeds(ctx):
     assert py_key(inst.motif.decode()) in set(int(k) for k in got)
 
 
+@pytest.mark.parametrize("name,triple_rows", [("plain15_4_s1", 4), ("plain15_4_s2", 19), ("plain17_5_s1", 8),
+                                              ("plain17_5_s1", 19)])
+def test_plain_whole_motif_set_three_string(name, triple_rows):
+    g = GOLD[name]
+    inst = pi.plain_instance(g["l"], g["d"], seed=g["seed"])
+    c = pms.Context(0)
+    c.set_options(triple_rows=triple_rows)
+    assert np.array_equal(c.solve(inst.seqs, inst.l, inst.d), _want(name, inst))
+    c.close()
+
+
+def test_plain_19_6_on_48_seeds_three_string():
+    g = GOLD["plain19_6_s1"]
+    inst = pi.plain_instance(19, 6, seed=1)
+    _checked("plain19_6_s1", inst)
+    c = pms.Context(0)
+    c.set_options(triple_rows=8)
+    got = c.solve(inst.seqs, 19, 6)
+    c.close()
+    codes = seq_codes(inst.seqs[0])
+    for j, keys in g["per_seed"].items():
+        j = int(j)
+        assert np.array_equal(keys_within(got, codes[j:j + 19], 19, 6), np.array(keys, dtype=np.uint64)), j
+
+
 def _batch_slice():
     insts = pi.batch_instances(count=256, master_seed=2024)[:32]
     return insts, [_want(f"batch2024_{k}", inst) for k, inst in enumerate(insts)]

@@ -84,3 +84,54 @@ def test_bit_plane_form_of_the_last_inequality():
             E = (bh ^ ch) | (bl ^ cl)
             r2, r3, r4, r5 = classes(a, b, c)
             assert r2 + r3 + r4 + 2 * r5 == bin(Dw & E).count("1") + bin(D).count("1")
+
+
+# ---- the same test below a tree node (the verification kernel's triple_rows option)
+#
+# A node P of seed x holds the strings c with c = x outside P and c != x on P.
+# For occurrences u, w let t_u = popc(mism(x, u) ^ P) and F = the positions of
+# P where x, u and w are three different letters; some string of the node is
+# within d of both u and w iff t_u <= d, t_w <= d and t_u + t_w + F <= 2d.
+
+
+def node_strings(x, P):
+    choices = [[ch for ch in ALPHA if ch != x[p]] if p in P else [x[p]] for p in range(len(x))]
+    for t in itertools.product(*choices):
+        yield "".join(t)
+
+
+def node_pair_feasible(x, u, w, P, d):
+    Du = {p for p in range(len(x)) if u[p] != x[p]}
+    Dw = {p for p in range(len(x)) if w[p] != x[p]}
+    tu = len(Du ^ P)
+    tw = len(Dw ^ P)
+    F = sum(1 for p in P if u[p] != x[p] and w[p] != x[p] and u[p] != w[p])
+    return tu <= d and tw <= d and tu + tw + F <= 2 * d
+
+
+def test_node_pair_test_matches_brute_force():
+    rng = random.Random(2403)
+    for l in (2, 3, 4, 5, 6):
+        for _ in range(300):
+            x, u, w = ("".join(rng.choice(ALPHA) for _ in range(l)) for _ in range(3))
+            P = {p for p in range(l) if rng.random() < 0.5}
+            d = rng.randint(0, l)
+            brute = any(hamming(c, u) <= d and hamming(c, w) <= d for c in node_strings(x, P))
+            assert node_pair_feasible(x, u, w, P, d) == brute, (x, u, w, sorted(P), d)
+
+
+def test_node_pair_test_in_bit_planes():
+    # the kernel's form: Du = mism(x, u), t_u = popc(Du ^ P), F = popc(Du & Dw & mism(u, w) & P)
+    rng = random.Random(7)
+    for l in (5, 9, 15):
+        for _ in range(300):
+            x, u, w = ("".join(rng.choice(ALPHA) for _ in range(l)) for _ in range(3))
+            P = {p for p in range(l) if rng.random() < 0.4}
+            Pm = sum(1 << p for p in P)
+            (xh, xl), (uh, ul), (wh, wl) = planes(x), planes(u), planes(w)
+            Du = (xh ^ uh) | (xl ^ ul)
+            Dw = (xh ^ wh) | (xl ^ wl)
+            Euw = (uh ^ wh) | (ul ^ wl)
+            F = bin(Du & Dw & Euw & Pm).count("1")
+            assert F == sum(1 for p in P if len({x[p], u[p], w[p]}) == 3)
+            assert bin(Du ^ Pm).count("1") == len({p for p in range(l) if u[p] != x[p]} ^ P)
