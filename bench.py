@@ -52,7 +52,7 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) per launch of the verification kernel from one ncu
 # capture (profiles/main_kernel_plain*.md), valid only for the kernel source
 # they were taken on (its sha256 prefix); otherwise the bench reports null.
-NCU_TRAFFIC = {"kernel_sha256": "c1cb4e4a809d7da7", "plain15_4": 1.080064e6, "plain17_5": 1.095680e6}
+NCU_TRAFFIC = {"kernel_sha256": "73f0161dd7dba0e6", "plain15_4": 1.063680e6, "plain19_6": 1.426176e6}
 
 
 def kernel_sha() -> str:
