@@ -686,6 +686,80 @@ def measure_serve(pms, torch, dev, args, rank, dist) -> dict:
             "gpu_launches": 3 * count + int(st["serve_waves"]), "clocks": clk.summary()}
 
 
+def bench_onehot(args, ws, rank, local, dist) -> dict:
+    """The one-hot tensor-core form of the candidate-versus-window distance, timed as a library GEMM.
+
+    With every l-mer as a one-hot vector of 4l entries (padded to 64), the number of positions
+    where a candidate c and a window w agree is the dot product of their vectors, so all
+    candidate-by-window distances of a seed are one GEMM: (|B(x, d)| x 64) by (64 x windows of
+    the other n - 1 sequences). This times that GEMM (torch.matmul, bf16, cuBLAS: a timing copy,
+    not part of the library) for one (15,4) seed, n = 20, m = 600, on one-hot inputs built from
+    a seeded instance, and scales it by the seeds of a solve. The tree search of the library
+    needs no such contraction; this line measures what the dense form would cost."""
+    import torch
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    l, d, n, m = 15, 4, 20, 600
+    inst = pi.plain_instance(l, d, seed=1)
+    codes = np.frombuffer(b"ACGT", dtype=np.uint8)
+    lut = np.zeros(256, dtype=np.int64)
+    lut[codes] = np.arange(4)
+    seq = lut[inst.seqs]                              # n x m letter indices
+    W = m - l + 1
+    win = np.stack([seq[:, j:j + l] for j in range(W)], axis=1)[1:].reshape(-1, l)   # (n-1)W x l
+    K = 64
+    Wt = np.zeros((win.shape[0], K), dtype=np.float32)
+    Wt[np.arange(win.shape[0])[:, None], 4 * np.arange(l)[None, :] + win] = 1.0
+    # the candidates of one seed: B(x, d) enumerated position set by position set
+    x = seq[0, :l]
+    cand = [x.copy()]
+    import itertools
+    for k in range(1, d + 1):
+        for P in itertools.combinations(range(l), k):
+            for lets in itertools.product(range(3), repeat=k):
+                c = x.copy()
+                for p, t in zip(P, lets):
+                    c[p] = (x[p] + 1 + t) % 4
+                cand.append(c)
+    cand = np.array(cand)
+    C = np.zeros((len(cand), K), dtype=np.float32)
+    C[np.arange(len(cand))[:, None], 4 * np.arange(l)[None, :] + cand] = 1.0
+    A = torch.from_numpy(C).to(dev, torch.bfloat16)
+    B = torch.from_numpy(Wt.T.copy()).to(dev, torch.bfloat16)
+    out = torch.empty(A.shape[0], B.shape[1], device=dev, dtype=torch.bfloat16)
+    for _ in range(3):
+        torch.matmul(A, B, out=out)
+    torch.cuda.synchronize(dev)
+    # agreement: matches >= l - d somewhere in each sequence (checked once, untimed)
+    hits = (out.float() >= l - d).view(len(cand), n - 1, W).any(dim=2).all(dim=1)
+    reps = max(3, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(A, B, out=out)
+        e1.record()
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * A.shape[0] * K * B.shape[1]
+    peaks = load_peaks()
+    solve_ms = ms * W
+    return {"metric": METRIC, "value": 1000.0 / solve_ms, "unit": "solves/s", "n_gpus": ws, "steps": reps,
+            "warmup": 3, "ms_per_step": solve_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "one-hot tensor-core form, plain (15,4) n=20 m=600: the GEMM of one seed's "
+                                   f"{A.shape[0]} candidates by the {B.shape[1]} windows of the other sequences "
+                                   "(K = 64), scaled by the 586 seeds of a solve",
+                       "timing": "CUDA events around torch.matmul (cuBLAS bf16), a timing copy"},
+            "gemm_ms_per_seed": ms, "gemm_tflops": flops / (ms / 1000.0) / 1e12,
+            "roofline": {"bound": "tensor", "achieved": flops / (ms / 1000.0) / 1e12,
+                         "peak": float(peaks.get("bf16_tflops", 1900.0)), "unit": "TFLOP/s",
+                         "frac": flops / (ms / 1000.0) / 1e12 / float(peaks.get("bf16_tflops", 1900.0)),
+                         "traffic": None, "kernel": "cuBLAS bf16 GEMM (timing copy)"},
+            "candidates_of_seed_passing_all": int(hits.sum().item()),
+            "e2e": None, "gpu_launches": reps, "clocks": clk.summary()}
+
+
 def bench_batch(args, ws, rank, local, dist) -> dict:
     import torch
     import paper_2403_00306_gb300 as pms
@@ -724,7 +798,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="suite",
                     choices=["suite"] + sorted(WORKLOADS) + sorted(QUORUM_WORKLOADS) + sorted(PROTEIN_WORKLOADS)
-                    + ["batch", "serve"],
+                    + ["batch", "serve", "onehot15_4"],
                     help="suite (default): the plain (15,4) line, with per_config lines for (9,2), (17,5), "
                          "(19,6), the batched and the served workloads inside it")
     ap.add_argument("--serve-requests", type=int, default=10000)
@@ -740,7 +814,9 @@ def main():
         run_reference(args, ws, rank)
         return
     cpu = rank == 0 and ws == 1 and not args.no_cpu_baseline
-    if args.workload == "batch":
+    if args.workload == "onehot15_4":
+        line = bench_onehot(args, ws, rank, local, dist)
+    elif args.workload == "batch":
         line = bench_batch(args, ws, rank, local, dist)
     elif args.workload == "serve":
         line = bench_serve(args, ws, rank, local, dist)

@@ -160,6 +160,10 @@ constexpr int kSigThreads = 256;    // threads of the search kernel's CTA
 constexpr int kSigSortThreads = 1024;
 constexpr int kSigSmemSmall = 64 * 1024;    // rows of one seed in shared memory: 3 CTAs per SM
 constexpr int kSigSmemLarge = 104 * 1024;   // the same for seeds with many rows: 2 CTAs per SM
+#ifndef PMS_SIG_LIST_CAP
+#define PMS_SIG_LIST_CAP 16384
+#endif
+constexpr int kSigListCap = PMS_SIG_LIST_CAP;   // words of row lists per warp of the search kernel
 
 // Work counters of the search kernel (always on), indices into a uint64 array.
 enum SigCounter {
@@ -194,6 +198,8 @@ struct SigmaParams {
     uint32_t *scratch;             // per CTA (1 + b) * scratch_rows words, for seeds whose rows exceed smem_rows
     int scratch_rows;
     int smem_rows;                 // rows a seed keeps in shared memory
+    uint32_t *lists;               // per warp list_cap words: row lists of the depth-first search (may be null)
+    int list_cap;
 };
 
 int sigma_planes(int sigma);

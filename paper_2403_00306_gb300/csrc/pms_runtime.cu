@@ -201,7 +201,7 @@ struct pms_ctx {
     };
     DBuf d_seqs, d_planes, d_raw, d_tmp, d_compat, d_rowlen, d_mode, d_meta, d_ctr, d_scratch, d_result;
     // general-alphabet solves (pms_solve_sigma)
-    DBuf d_sg_seqs, d_sg_planes, d_sg_ctr, d_sg_raw, d_sg_out, d_sg_scratch;
+    DBuf d_sg_seqs, d_sg_planes, d_sg_ctr, d_sg_raw, d_sg_out, d_sg_scratch, d_sg_lists;
     bool sigma_ready = false;   // binomial table and kernel attributes loaded on the device
     void *h_sg = nullptr;       // pinned: counters block, then the input letters
     size_t h_sg_cap = 0;
@@ -2400,6 +2400,13 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
         return rc;
     if (max_rows > smem_rows && (rc = h->ensure(h->d_sg_scratch, (size_t)4 * blocks * (1 + b) * max_rows)))
         return rc;
+    // per warp: the row lists of the search's depths (nodes whose lists would not fit keep the
+    // search without them; without room for the buffer within the budget, every node does)
+    int list_cap = kSigListCap;
+    if (h->ensure(h->d_sg_lists, (size_t)4 * blocks * (kSigThreads / 32) * list_cap) != PMS_OK) {
+        list_cap = 0;
+        h->err.clear();
+    }
     if ((rc = h->ensure_host(h->h_sg, h->h_sg_cap, 256 + nm)))
         return rc;
     char *h_ctr = (char *)h->h_sg;
@@ -2431,6 +2438,8 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
         p.scratch = max_rows > smem_rows ? (uint32_t *)h->d_sg_scratch.p : nullptr;
         p.scratch_rows = max_rows;
         p.smem_rows = smem_rows;
+        p.lists = list_cap > 0 ? (uint32_t *)h->d_sg_lists.p : nullptr;
+        p.list_cap = list_cap;
         if ((e = cudaMemcpyAsync(h->d_sg_seqs.p, h_ctr + 256, nm, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
             (e = cudaMemsetAsync(c, 0, ctr_bytes, st)) != cudaSuccess || (e = cudaEventRecord(h->ev0, st)) != cudaSuccess ||
             (e = launch_sigma_pack((const uint8_t *)h->d_sg_seqs.p, n, m, l, b, map, (uint32_t *)h->d_sg_planes.p,
@@ -2503,7 +2512,8 @@ void pms_destroy(pms_ctx *h)
     if (h->cap_stream)
         cudaStreamDestroy(h->cap_stream);
     pms_ctx::DBuf *bufs[] = {&h->d_seqs, &h->d_planes, &h->d_raw, &h->d_tmp, &h->d_compat, &h->d_rowlen, &h->d_mode, &h->d_meta, &h->d_ctr, &h->d_scratch, &h->d_result,
-                             &h->d_sg_seqs, &h->d_sg_planes, &h->d_sg_ctr, &h->d_sg_raw, &h->d_sg_out, &h->d_sg_scratch};
+                             &h->d_sg_seqs, &h->d_sg_planes, &h->d_sg_ctr, &h->d_sg_raw, &h->d_sg_out, &h->d_sg_scratch,
+                             &h->d_sg_lists};
     for (auto *b : bufs)
         h->dev_free(b->p, b->cap);
     if (h->h_result)

@@ -43,6 +43,14 @@
 
 namespace pms {
 
+// 1: a node whose row lists fit takes the list form even where the pivot form
+// applies (protein (9,4), n = 20, m = 600: 231 -> 121 ms with 16384-word
+// lists; (11,4) 0.79 -> 0.89 ms, (9,3) unchanged)
+#ifndef PMS_SIG_LISTS_BEFORE_PIVOT
+#define PMS_SIG_LISTS_BEFORE_PIVOT 1
+#endif
+constexpr bool kSigListsBeforePivot = PMS_SIG_LISTS_BEFORE_PIVOT != 0;
+
 __constant__ uint32_t c_sg_binom[33][33];
 static uint32_t h_sg_binom[33][33];   // host copy (filled by sigma_init_tables)
 
@@ -61,6 +69,15 @@ __host__ __device__ inline int sg_popc(uint32_t v)
     return __popc(v);
 #else
     return __builtin_popcount(v);
+#endif
+}
+
+__host__ __device__ inline int sg_popc64(unsigned long long v)
+{
+#ifdef __CUDA_ARCH__
+    return __popcll(v);
+#else
+    return __builtin_popcountll(v);
 #endif
 }
 
@@ -153,6 +170,12 @@ struct SgWarp {
     __device__ uint32_t ballot(bool p) const { return __ballot_sync(0xFFFFFFFFu, p); }
     __device__ void sync() const { __syncwarp(); }
     __device__ void or_into(uint32_t *a, uint32_t v) const { atomicOr(a, v); }
+    // lanes below this one with a vote in bal
+    __device__ int rank(uint32_t bal) const { return __popc(bal & ((1u << lane) - 1u)); }
+    __device__ unsigned long long or_all64(unsigned long long v) const
+    {
+        return ((unsigned long long)or_all((uint32_t)(v >> 32)) << 32) | or_all((uint32_t)v);
+    }
     __device__ unsigned long long sum(unsigned long long v) const
     {
         for (int s = 16; s > 0; s >>= 1)
@@ -170,6 +193,8 @@ struct SgSingle {
     __host__ __device__ uint32_t ballot(bool p) const { return p ? 1u : 0u; }
     __host__ __device__ void sync() const {}
     __host__ __device__ void or_into(uint32_t *a, uint32_t v) const { *a |= v; }
+    __host__ __device__ int rank(uint32_t) const { return 0; }
+    __host__ __device__ unsigned long long or_all64(unsigned long long v) const { return v; }
     __host__ __device__ unsigned long long sum(unsigned long long v) const { return v; }
 };
 
@@ -284,7 +309,19 @@ struct SgState {
     uint32_t L[kSigMaxD];  // letters the rows passing the bound hold there
     uint32_t T[kSigMaxD];  // the choices: L and one representative of the rest
     uint32_t Wl[kSigMaxD]; // the interchangeable letters the representative stands for
+    int lo[kSigMaxD];      // list form: the rows alive before depth t are list[lo[t] .. hi[t])
+    int hi[kSigMaxD];
 };
+
+// A group's buffer for the row lists of the list form of the depth-first
+// search (null: that form is not used). An entry packs the row index (bits
+// 0..20), its sequence (bits 21..26) and its distance bound (bits 27..31).
+struct SgLists {
+    uint32_t *buf;
+    int cap;
+};
+constexpr int kSgListRowBits = 21;
+constexpr uint32_t kSgListRowMask = (1u << kSgListRowBits) - 1u;
 
 // Writes the motifs a full candidate stands for: at a position whose letter is
 // the representative of the interchangeable letters Wl[t], every letter of
@@ -392,12 +429,104 @@ __host__ __device__ void sg_dfs(const SgSeed &S, const G &grp, uint32_t P, int k
     }
 }
 
+// Step 3 with the row set shrunk depth by depth (the row filtering of the
+// paper's depth-first search, TraverStringRef_Tree / qPMSPrune): the rows that
+// pass the node bound are listed once with their bound popc(D ^ P), the
+// mismatches no letter choice can avoid. Fixing letter a at the next changed
+// position p raises the bound of a row by one exactly when the row differs
+// from x at p (bit p of D) and holds a letter other than a there (where it
+// agrees with x, a != x[p] already counts); a row whose bound exceeds d is
+// within d of no string below the prefix and leaves the list. The prefix is
+// abandoned when more than miss_max sequences have no row left. So each depth
+// tests only the rows the previous depth kept, each with one letter
+// comparison, instead of looking for an occurrence in every sequence again.
+// The lists of the depths on the current path are kept one after another in
+// the group's buffer (the caller checks they fit: at most n0 (k + 1)).
+template <class G, class Sink>
+__host__ __device__ void sg_dfs_rows(const SgSeed &S, const G &grp, int k, SgState &st, SgCount &ct, Sink &sink,
+                                     uint32_t *buf, int n0)
+{
+    const bool lead = grp.lane == 0;
+    int t = 0;
+    if (lead) {
+        st.lo[0] = 0;
+        st.hi[0] = n0;
+    }
+    grp.sync();
+    st.ch[0] = sg_ctz(st.T[0]);
+    grp.sync();
+    for (;;) {
+        const int plo = st.lo[t], phi = st.hi[t];
+        const int p = st.pos[t], a = st.ch[t];
+        int w = phi;
+        unsigned long long present = 0;
+        for (int j0 = plo; j0 < phi; j0 += G::width) {
+            const int j = j0 + grp.lane;
+            bool keep = false;
+            uint32_t v = 0;
+            if (j < phi) {
+                v = buf[j];
+                const int e = (int)(v & kSgListRowMask);
+                int dist = (int)(v >> 27);
+                if ((S.D[e] >> p) & 1u) {
+                    ct.verify++;
+                    dist += sg_letter_at(S.Pl + e, S.stride, S.b, p) != a ? 1 : 0;
+                }
+                keep = dist <= S.d;
+                v = (v & ((1u << 27) - 1u)) | ((uint32_t)dist << 27);
+                if (keep)
+                    present |= 1ull << ((v >> kSgListRowBits) & 63u);
+            }
+            const uint32_t bal = grp.ballot(keep);
+            if (keep)
+                buf[w + grp.rank(bal)] = v;
+            w += sg_popc(bal);
+        }
+        present = grp.or_all64(present);
+        if (lead) {
+            ct.checks++;
+            if (t == k - 1)
+                ct.leaves++;
+        }
+        const bool ok = (S.n - 1) - sg_popc64(present) <= S.miss_max;   // the seed's own sequence has no rows
+        if (ok) {
+            if (t == k - 1) {
+                sg_emit(S, grp, st.pos, st.ch, st.Wl, k, sink);
+            } else {
+                grp.sync();
+                if (lead) {
+                    st.lo[t + 1] = phi;
+                    st.hi[t + 1] = w;
+                }
+                ++t;
+                grp.sync();
+                st.ch[t] = sg_ctz(st.T[t]);
+                grp.sync();
+                continue;
+            }
+        }
+        // the next choice at this depth, else back up
+        for (;;) {
+            const uint32_t rest = st.T[t] & ~(uint32_t)((2ull << st.ch[t]) - 1ull);
+            if (rest) {
+                const int nx = sg_ctz(rest);
+                grp.sync();
+                st.ch[t] = nx;
+                grp.sync();
+                break;
+            }
+            if (--t < 0)
+                return;
+        }
+    }
+}
+
 // The search below one tree node P (steps 1-3 of the file comment), by one
 // group of threads in lockstep: every branch below depends only on values the
 // whole group shares.
 template <class G, class Sink>
 __host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCount &ct, Sink &sink, int *wit,
-                                 SgState &st)
+                                 SgState &st, SgLists lists)
 {
     const bool lead = grp.lane == 0;
     if (lead)
@@ -426,8 +555,12 @@ __host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCo
     }
     grp.sync();
     // step 2: the letters the rows passing the bound hold at the changed
-    // positions, and the sequence with the fewest such rows (the pivot)
+    // positions, and the sequence with the fewest such rows (the pivot); the
+    // passing rows are also listed for the list form of step 3 while the list
+    // fits the group's buffer
     int piv = -1, piv_rows = 0;
+    const bool listing = lists.buf != nullptr && S.off[S.n] <= (int)kSgListRowMask + 1;
+    int n0 = 0;
     for (int i = 0; i < S.n; ++i) {
         if (i == S.sx)
             continue;
@@ -435,10 +568,12 @@ __host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCo
         for (int e0 = S.off[i]; e0 < S.off[i + 1]; e0 += G::width) {
             const int e = e0 + grp.lane;
             bool pass = false;
+            int bound = 0;
             if (e < S.off[i + 1]) {
                 ct.reduce++;
                 const uint32_t De = S.D[e];
-                pass = sg_popc(De ^ P) <= S.d;
+                bound = sg_popc(De ^ P);
+                pass = bound <= S.d;
                 if (pass) {
                     uint32_t M = De & P;
                     while (M) {
@@ -449,7 +584,11 @@ __host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCo
                     }
                 }
             }
-            cnt += sg_popc(grp.ballot(pass));
+            const uint32_t bal = grp.ballot(pass);
+            if (listing && pass && n0 + grp.rank(bal) < lists.cap)
+                lists.buf[n0 + grp.rank(bal)] = (uint32_t)e | ((uint32_t)i << kSgListRowBits) | ((uint32_t)bound << 27);
+            cnt += sg_popc(bal);
+            n0 += sg_popc(bal);
         }
         if (piv < 0 || cnt < piv_rows) {
             piv = i;
@@ -474,7 +613,8 @@ __host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCo
     // sort/unique step removes the copies). Chosen when the pivot has few rows
     // against large choice sets.
     const int est_plain = sg_popc(st.T[0]) * (k >= 2 ? sg_popc(st.T[1]) : 1);
-    if (S.miss_max == 0 && piv >= 0 && piv_rows * k < est_plain) {
+    const bool lists_fit = listing && (long long)n0 * (k + 1) <= (long long)lists.cap;
+    if (S.miss_max == 0 && piv >= 0 && piv_rows * k < est_plain && !(kSigListsBeforePivot && lists_fit)) {
         for (int e = S.off[piv]; e < S.off[piv + 1]; ++e) {
             const uint32_t De = S.D[e];
             if (lead)
@@ -489,6 +629,8 @@ __host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCo
             grp.sync();
             sg_dfs(S, grp, P, k, st, true, slack, ct, sink, wit, fail);
         }
+    } else if (lists_fit) {
+        sg_dfs_rows(S, grp, k, st, ct, sink, lists.buf, n0);
     } else {
         sg_dfs(S, grp, P, k, st, false, 0, ct, sink, wit, fail);
     }
@@ -665,7 +807,11 @@ __global__ void __launch_bounds__(kSigThreads, 3) sigma_main_kernel(SigmaParams 
                 if (r >= (unsigned long long)p.nodes)
                     break;
                 SgCount ct{};
-                sg_node(S, grp, sg_unrank((long long)r, p.l), ct, sink, s_wit[tid >> 5], s_state[tid >> 5]);
+                const SgLists lists{p.lists ? p.lists + ((size_t)blockIdx.x * (kSigThreads / 32) + (tid >> 5)) *
+                                                              (size_t)p.list_cap
+                                            : nullptr,
+                                    p.list_cap};
+                sg_node(S, grp, sg_unrank((long long)r, p.l), ct, sink, s_wit[tid >> 5], s_state[tid >> 5], lists);
                 const unsigned long long red = grp.sum(ct.reduce), ver = grp.sum(ct.verify);
                 if (grp.lane == 0) {   // node, check and leaf counts are the lead lane's
                     atomicAdd(&s_ct[kSgNodes], (unsigned long long)ct.nodes);

@@ -4,9 +4,12 @@
 // is searched, and the sorted unique motifs are printed, one per line.
 // Input on stdin: "alphabet n m l d q" then the n sequences; or "unrank l d",
 // which prints the position subset (as a bit mask) of every node rank instead.
+// argv[1], if given: the capacity of the group's row-list buffer (0, the
+// default: the depth-first search without row lists).
 #include "../../paper_2403_00306_gb300/csrc/pms_sigma.cu"
 
 #include <algorithm>
+#include <cstdlib>
 #include <array>
 #include <cstdio>
 #include <cstring>
@@ -40,8 +43,10 @@ struct HostSink {
 
 }  // namespace
 
-int main()
+int main(int argc, char **argv)
 {
+    const int list_cap = argc > 1 ? atoi(argv[1]) : 0;
+    std::vector<uint32_t> list_buf((size_t)std::max(list_cap, 1));
     char alpha[64];
     int n, m, l, d, q;
     if (scanf("%63s", alpha) != 1)
@@ -144,7 +149,8 @@ int main()
         S.full = sigma == 32 ? 0xFFFFFFFFu : (1u << sigma) - 1u;
         for (long long r = 0; r < nodes; ++r) {
             SgCount ct{};
-            sg_node(S, one, sg_unrank(r, l), ct, sink, wit, st);
+            sg_node(S, one, sg_unrank(r, l), ct, sink, wit, st,
+                    SgLists{list_cap > 0 ? list_buf.data() : nullptr, list_cap});
             tot_nodes += ct.nodes;
             tot_pruned += ct.pruned;
         }

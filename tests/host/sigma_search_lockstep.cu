@@ -4,10 +4,13 @@
 // with __ballot_sync / __shfl_sync), sharing the per-warp state and witness
 // rows as the kernel's shared memory does, and splitting every row scan over
 // the 32 lanes. Prints the sorted unique motifs, one per line.
-// Input on stdin: "alphabet n m l d q" then the n sequences.
+// Input on stdin: "alphabet n m l d q" then the n sequences; argv[1], if
+// given: the capacity of the warp's shared row-list buffer (0, the default:
+// the depth-first search without row lists).
 #include "../../paper_2403_00306_gb300/csrc/pms_sigma.cu"
 
 #include <algorithm>
+#include <cstdlib>
 #include <array>
 #include <barrier>
 #include <cstdio>
@@ -95,6 +98,19 @@ struct LockstepWarp {
         *a |= v;
 #endif
     }
+    __host__ __device__ int rank(uint32_t bal) const { return __builtin_popcount(bal & ((1u << lane) - 1u)); }
+    __host__ __device__ unsigned long long or_all64(unsigned long long v) const
+    {
+        unsigned long long s = 0;
+#ifndef __CUDA_ARCH__
+        x->val[lane] = v;
+        x->bar.arrive_and_wait();
+        for (int i = 0; i < 32; ++i)
+            s |= x->val[i];
+        x->bar.arrive_and_wait();
+#endif
+        return s;
+    }
 };
 
 // One lane reserves (between two barriers of the group), every lane writes its own slots.
@@ -125,8 +141,10 @@ struct HostSink {
 
 }  // namespace
 
-int main()
+int main(int argc, char **argv)
 {
+    const int list_cap = argc > 1 ? atoi(argv[1]) : 0;
+    std::vector<uint32_t> list_buf((size_t)std::max(list_cap, 1));   // the warp's, shared by its lanes
     char alpha[64];
     int n, m, l, d, q;
     if (scanf("%63s %d %d %d %d %d", alpha, &n, &m, &l, &d, &q) != 6)
@@ -219,7 +237,8 @@ int main()
                 HostSink sink{&keys, &cnt, &sink_mu};
                 for (long long r = 0; r < nodes; ++r) {
                     SgCount ct{};
-                    sg_node(S, grp, sg_unrank(r, l), ct, sink, wit, st);
+                    sg_node(S, grp, sg_unrank(r, l), ct, sink, wit, st,
+                            SgLists{list_cap > 0 ? list_buf.data() : nullptr, list_cap});
                     grp.sync();   // the kernel's next node claim is a warp-wide shuffle
                 }
             });

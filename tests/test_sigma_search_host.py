@@ -3,7 +3,9 @@ against the oracle on small instances, with no GPU:
 
 * tests/host/sigma_search_host.cu runs it with a one-thread group (rows built on the host
   in the kernel's layout): the search logic (node bound, letter classes, depth-first
-  prefixes, pivot rows, witness rows);
+  prefixes, pivot rows, witness rows), and the same search with the row lists shrunk
+  depth by depth (the list form the kernel takes when a node's lists fit, with a small
+  buffer too, so that nodes fall back to the form without lists);
 * tests/host/sigma_search_lockstep.cu runs it with 32 host threads per node whose votes,
   broadcasts and sums go through barriers, sharing the per-warp state and witness rows:
   the lane-parallel form the GPU warp executes (row scans split over 32 lanes, one lane
@@ -36,10 +38,10 @@ def search(tmp_path_factory):
                     "-diag-suppress", "550", "-I", os.path.join(ROOT, "include"), SRC, "-o", exe],
                    check=True, capture_output=True)
 
-    def run(seqs, l, d, alphabet, q=0):
+    def run(seqs, l, d, alphabet, q=0, lists=0):
         n, m = seqs.shape
         inp = f"{alphabet} {n} {m} {l} {d} {q}\n" + "\n".join(bytes(r).decode() for r in seqs) + "\n"
-        r = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True)
+        r = subprocess.run([exe, str(lists)], input=inp, capture_output=True, text=True, check=True)
         return r.stdout.split()
     run.exe = exe
     return run
@@ -70,12 +72,13 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("lists", [0, 4096, 24])
 @pytest.mark.parametrize("sigma,n,m,l,d,q,seed", CASES)
-def test_host_search_matches_the_oracle(search, oracle_, sigma, n, m, l, d, q, seed):
+def test_host_search_matches_the_oracle(search, oracle_, sigma, n, m, l, d, q, seed, lists):
     alpha = alphabet_of(sigma)
     inst = pi.planted_instance_sigma(n, m, l, d, seed, alpha.encode())
     want = [bytes(r).decode() for r in oracle_.sigma_solve(inst.seqs, l, d, alpha, q=q, cap=1 << 22)]
-    assert search(inst.seqs, l, d, alpha, q) == want
+    assert search(inst.seqs, l, d, alpha, q, lists) == want
 
 
 def test_host_search_over_acgt_matches_the_dna_oracle(search, oracle_):
@@ -93,6 +96,7 @@ def test_host_search_on_random_backgrounds(search, oracle_):
         for q in (0, n - 1):
             want = [bytes(r).decode() for r in oracle_.sigma_solve(seqs, l, d, alpha, q=q, cap=1 << 22)]
             assert search(seqs, l, d, alpha, q) == want, (sigma, n, m, l, d, q)
+            assert search(seqs, l, d, alpha, q, 4096) == want, (sigma, n, m, l, d, q, "lists")
 
 
 @pytest.fixture(scope="module")
@@ -106,10 +110,10 @@ def lockstep(tmp_path_factory):
                     os.path.join(ROOT, "tests", "host", "sigma_search_lockstep.cu"), "-o", exe],
                    check=True, capture_output=True)
 
-    def run(seqs, l, d, alphabet, q=0):
+    def run(seqs, l, d, alphabet, q=0, lists=0):
         n, m = seqs.shape
         inp = f"{alphabet} {n} {m} {l} {d} {q}\n" + "\n".join(bytes(r).decode() for r in seqs) + "\n"
-        r = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True, timeout=300)
+        r = subprocess.run([exe, str(lists)], input=inp, capture_output=True, text=True, check=True, timeout=300)
         return r.stdout.split()
     return run
 
@@ -120,9 +124,10 @@ LOCKSTEP_CASES = [(20, 4, 20, 5, 2, 0, 31), (3, 4, 16, 6, 2, 3, 33), (20, 1, 7, 
                   (4, 6, 30, 8, 2, 0, 35), (4, 8, 60, 9, 2, 0, 5)]
 
 
+@pytest.mark.parametrize("lists", [0, 4096])
 @pytest.mark.parametrize("sigma,n,m,l,d,q,seed", LOCKSTEP_CASES)
-def test_lane_parallel_search_matches_the_oracle(lockstep, oracle_, sigma, n, m, l, d, q, seed):
+def test_lane_parallel_search_matches_the_oracle(lockstep, oracle_, sigma, n, m, l, d, q, seed, lists):
     alpha = alphabet_of(sigma)
     inst = pi.planted_instance_sigma(n, m, l, d, seed, alpha.encode())
     want = [bytes(r).decode() for r in oracle_.sigma_solve(inst.seqs, l, d, alpha, q=q, cap=1 << 22)]
-    assert lockstep(inst.seqs, l, d, alpha, q) == want
+    assert lockstep(inst.seqs, l, d, alpha, q, lists) == want
