@@ -1577,16 +1577,29 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) main_kernel(MainParams p
             Rows rows{cs.rows_in_smem ? smem_D : glob_D, cs.rows_in_smem ? smem_HL : glob_HL};
             WarpCtx c{&p, in, I, lane, lt, x.x, x.y, rows, &cs, &wsm[warp], kCount ? cnt : nullptr};
             if (in.q < in.n) {
-                // quorum form: batches of nodes with miss budgets
+                // quorum form: batches of nodes with miss budgets, claimed from the
+                // item's shared counter when other CTAs may join it; batches shrink
+                // (guided) as the item runs out so that its warps finish together
                 uint32_t *subs = wsm[warp].subs;
+                int *ctr = p.item_claim ? p.item_claim + 2 * cs.g : &cs.next;
+                const int base = p.item_claim ? g0 : 0;
                 for (;;) {
-                    int start = 0;
-                    if (lane == 0)
-                        start = atomicAdd(&cs.next, kSubBatch);
+                    int start = 0, batch = kSubBatch;
+                    if (lane == 0) {
+                        const int left = g1 - (base + *reinterpret_cast<volatile int *>(ctr));
+                        batch = min(kSubBatch, max(32, ((left + 2 * kWarps - 1) / (2 * kWarps) + 31) & ~31));
+                        start = base + atomicAdd(ctr, batch);
+                        if (p.item_claim) {
+                            ctr[1] = max(0, g1 - (start + batch));
+                            if (start < g1 && start + batch >= g1)
+                                atomicAdd(p.steal_state + 1, 1u);
+                        }
+                    }
                     start = __shfl_sync(kFull, start, 0);
+                    batch = __shfl_sync(kFull, batch, 0);
                     if (start >= g1)
                         break;
-                    const int N = min(kSubBatch, g1 - start);
+                    const int N = min(batch, g1 - start);
                     for (int j = lane; j < N; j += 32) {
                         const int g = start + j;
                         int lev = 0;
