@@ -570,6 +570,7 @@ def measure_batch(pms, torch, dev, peaks, args, rank, dist, steps: int = 3) -> d
             kern.append(s["ms_kernel"])
             ver.append(s["ms_verify"])
     barrier(dist)
+    replays = ctx.stats()["graph_replays"]
     # one by one on the plain path (pms_solve, host buffers; device time from the stats)
     one_wall, one_kern = [], []
     for k in range(max(1, steps - 1)):
@@ -606,6 +607,8 @@ def measure_batch(pms, torch, dev, peaks, args, rank, dist, steps: int = 3) -> d
                            "timing": "sum of the device times of 256 pms_solve calls",
                            "e2e_value": 256 / statistics.mean(one_wall)},
             "verify_ms": ver_ms, "share_verify": ver_ms / kern_ms,
+            "other_kernels_ms": kern_ms - ver_ms,   # packing, compatibility masks, sort/unique
+            "graph_replays_after_timed_steps": replays,
             "candidate_checks_per_s": cs["candidates_tested"] / (kern_ms / 1000.0),
             "roofline": peaks.roofline(cs["cmp_reduce"] + cs["cmp_verify"], ver_ms, "main_kernel (verification)",
                                        None, ver_ms / kern_ms),

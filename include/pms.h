@@ -114,10 +114,11 @@ typedef struct {
                               sequence are expected within d of a candidate;
                               none otherwise); -1: no partial
                               level; k > 0: k rows. Tree form, q = n. */
-    int graph;             /* one-instance solves (pms_solve, pms_solve_device)
-                              replay a CUDA graph captured on the second call
-                              of each plan (same shape and options), with the
-                              call's input and output pointers patched in:
+    int graph;             /* solves (pms_solve, pms_solve_device,
+                              pms_solve_batch) replay a CUDA graph captured
+                              on the second call of each plan (the same
+                              instance shapes and options), with the call's
+                              input and output pointers patched in:
                               0 = on (default); -1 = launch kernel by kernel */
     int triple_rows;       /* three-string feasibility below a tree node (the
                               TraverStringRef feasibility theorem for three
@@ -166,6 +167,7 @@ typedef struct {
     uint64_t serve_waves;       /* served form, cumulative: verification waves launched */
     uint64_t serve_overlapped_waves;     /* waves holding chunks of more than one request */
     uint64_t serve_max_requests_per_wave;
+    uint64_t graph_replays;     /* cumulative: solves enqueued by replaying a captured graph */
 } pms_stats;
 
 /* Creates a context on CUDA device `device`. mem_budget_bytes caps the device

@@ -67,7 +67,7 @@ class pms_stats(ctypes.Structure):
                 ("cmp_verify", ctypes.c_uint64), ("seeds_infeasible", ctypes.c_uint64), ("ms_total", ctypes.c_double),
                 ("ms_kernel", ctypes.c_double), ("ms_verify", ctypes.c_double),
                 ("serve_waves", ctypes.c_uint64), ("serve_overlapped_waves", ctypes.c_uint64),
-                ("serve_max_requests_per_wave", ctypes.c_uint64)]
+                ("serve_max_requests_per_wave", ctypes.c_uint64), ("graph_replays", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

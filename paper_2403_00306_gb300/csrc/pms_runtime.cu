@@ -270,6 +270,7 @@ struct pms_ctx {
     cudaStream_t cap_stream = nullptr;
     uint64_t buf_gen = 0;      // bumped whenever a device buffer is freed or moved
     uint64_t use_tick = 0;
+    uint64_t graph_replays = 0;   // solves enqueued by replaying a captured graph
 
     int fail(int code, const char *fmt, ...)
     {
@@ -1019,13 +1020,14 @@ static void capture_graph(pms_ctx *h, const std::string &key, const Plan &P, con
     S.sort_args[9] = &S.sv.dense_total;
 }
 
-// Enqueues a plan: one-instance plans replay a graph captured on their first
-// call (the same kernels, launch configurations and descriptors, with this
-// call's input and output pointers), everything else goes kernel by kernel.
+// Enqueues a plan: a plan seen before (one instance or a batch: the same
+// options, grid and descriptors) replays the graph captured on its second
+// call, with this call's input and output pointers; count-mode solves and
+// plans seen once go kernel by kernel.
 static int enqueue_plan_graph(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, StatusDev *status_out,
                               uint64_t *dense_out, uint32_t dense_cap, bool count_mode)
 {
-    if (h->opt.graph < 0 || count_mode || P.inst.size() != 1)
+    if (h->opt.graph < 0 || count_mode)
         return enqueue_plan(h, P, d_seq_src, status_out, dense_out, dense_cap, count_mode);
     MetaLayout ml(P);
     // key: options, the verification kernel's grid, the descriptors
@@ -1054,6 +1056,7 @@ static int enqueue_plan_graph(pms_ctx *h, const Plan &P, const uint8_t *d_seq_sr
             (e = cudaGraphLaunch(G.x, h->stream)) != cudaSuccess)
             return h->cuda_fail(e, "graph launch");
         G.last_use = ++h->use_tick;
+        ++h->graph_replays;
         return PMS_OK;
     }
     if (it != h->graphs.end()) {
@@ -2237,6 +2240,7 @@ int pms_get_stats(const pms_ctx *h, pms_stats *out)
         cudaSetDevice(hm->device);
         collect_stats(hm);
         *out = h->stats;
+        out->graph_replays = h->graph_replays;
     }
     // lock order: the scheduler takes its own lock before the context's, so
     // the context lock is never held while taking the scheduler's

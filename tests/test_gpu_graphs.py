@@ -1,6 +1,6 @@
-"""Captured CUDA graphs of one-instance solves: replays give the same motif sets as
-kernel-by-kernel launches, with each call's own input and output buffers, also after
-the context's buffers were reallocated by a larger instance."""
+"""Captured CUDA graphs of one-instance and batched solves: replays give the same motif
+sets as kernel-by-kernel launches, with each call's own input and output buffers, also
+after the context's buffers were reallocated by a larger instance."""
 import numpy as np
 import pytest
 
@@ -58,6 +58,31 @@ def test_graph_after_buffer_reallocation():
     for _ in range(2):
         assert np.array_equal(g.solve(a.seqs, 11, 3), want_a)
         assert np.array_equal(_device_solve(g, torch, a.seqs, 11, 3), want_a)
+    g.close()
+    k.close()
+
+
+def test_batch_graph_replays_match_kernel_by_kernel():
+    # a batch of uneven instances: the first call runs kernel by kernel, the second is
+    # captured, later calls replay the graph (the replay counter says so)
+    insts = pi.batch_instances(count=12, master_seed=99)
+    batch = [(i.seqs, i.l, i.d) for i in insts]
+    k = pms.Context(0)
+    k.set_options(graph=-1)
+    want = k.solve_batch(batch)
+    g = pms.Context(0)
+    before = g.stats()["graph_replays"]
+    for call in range(4):
+        got = g.solve_batch(batch)
+        for w, r in zip(want, got):
+            assert not isinstance(r, Exception) and np.array_equal(r, w), call
+    assert g.stats()["graph_replays"] - before == 2
+    # another batch shape does not replay the first one's graph
+    other = batch[:5]
+    got = g.solve_batch(other)
+    for w, r in zip(k.solve_batch(other), got):
+        assert np.array_equal(r, w)
+    assert g.stats()["graph_replays"] - before == 2
     g.close()
     k.close()
 
