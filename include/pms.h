@@ -42,6 +42,7 @@ extern "C" {
 #define PMS_ENOTFOUND (-7) /* unknown or already released ticket */
 #define PMS_ESCRATCH (-8)  /* instance too large for the fixed scratch of
                               pms_solve_device_noalloc */
+#define PMS_ECANCELED (-9) /* pms_wait: the ticket was withdrawn by pms_cancel */
 
 #define PMS_LMAX 32
 #define PMS_NMAX 64
@@ -257,6 +258,28 @@ int pms_solve_batch(pms_ctx *h, const pms_instance *inst, int k, pms_result *out
 int pms_submit(pms_ctx *h, const pms_instance *inst, uint64_t *ticket);
 int pms_wait(pms_ctx *h, uint64_t ticket, int timeout_ms, pms_result *out);
 int pms_release(pms_ctx *h, uint64_t ticket);
+
+/* Served form: withdraws a ticket that is still queued (not yet admitted to
+ * the device). Its pms_wait then reports status PMS_ECANCELED, and
+ * pms_release frees it as usual. Returns PMS_OK (also for a ticket that has
+ * already finished: its result stands), PMS_EBUSY (admitted: it runs to
+ * completion), PMS_ENOTFOUND. No counterpart in the paper. */
+int pms_cancel(pms_ctx *h, uint64_t ticket);
+
+/* Fault injection for tests of the error paths (no counterpart in the
+ * paper). Host-side only: the failing call is never made, so no GPU fault
+ * is involved. After `after` further operations of `kind` succeed, the next
+ * `count` fail (count 0 clears the injection):
+ *   PMS_FAULT_ALLOC   device allocations of the context fail, so the call
+ *                     that needs the memory returns PMS_ENOMEM;
+ *   PMS_FAULT_UPLOAD  uploads of input sequences fail: a pms_solve or
+ *                     pms_solve_batch call returns PMS_ECUDA, a served
+ *                     request ends with status PMS_ECUDA (other requests
+ *                     are not affected).
+ * Returns PMS_OK or PMS_EINVAL. */
+#define PMS_FAULT_ALLOC 1
+#define PMS_FAULT_UPLOAD 2
+int pms_inject_fault(pms_ctx *h, int kind, int after, int count);
 
 /* Autotuner (no counterpart in the paper; it picks the schedule of the
  * verification kernel). pms_autotune times the device pipeline on a

@@ -18,8 +18,11 @@ from . import build as _build
 
 PMS_OK, PMS_EINVAL, PMS_ENOMEM, PMS_ECUDA, PMS_ETIMEDOUT, PMS_ETOOMANY, PMS_EBUSY, PMS_ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7
 PMS_ESCRATCH = -8
+PMS_ECANCELED = -9
 ERROR_NAMES = {0: "PMS_OK", -1: "PMS_EINVAL", -2: "PMS_ENOMEM", -3: "PMS_ECUDA", -4: "PMS_ETIMEDOUT",
-               -5: "PMS_ETOOMANY", -6: "PMS_EBUSY", -7: "PMS_ENOTFOUND", -8: "PMS_ESCRATCH"}
+               -5: "PMS_ETOOMANY", -6: "PMS_EBUSY", -7: "PMS_ENOTFOUND", -8: "PMS_ESCRATCH", -9: "PMS_ECANCELED"}
+PMS_FAULT_ALLOC = 1
+PMS_FAULT_UPLOAD = 2
 LMAX, NMAX = 32, 64
 
 #: names the C ABI exports (include/pms.h)
@@ -27,7 +30,7 @@ ABI_FUNCTIONS = ["pms_create", "pms_set_stream", "pms_set_allocator", "pms_set_o
                  "pms_solve", "pms_solve_device", "pms_solve_batch", "pms_submit", "pms_wait", "pms_release",
                  "pms_get_stats", "pms_decode", "pms_last_error", "pms_probe_int_rate", "pms_destroy",
                  "pms_solve_device_noalloc", "pms_autotune", "pms_save_tuning", "pms_load_tuning",
-                 "pms_solve_sigma", "pms_kernel_binary_version"]
+                 "pms_solve_sigma", "pms_kernel_binary_version", "pms_cancel", "pms_inject_fault"]
 
 #: the twenty amino acids, one-letter codes (an alphabet for solve_sigma)
 PROTEIN = b"ACDEFGHIKLMNPQRSTVWY"
@@ -120,6 +123,8 @@ def load(build_if_missing: bool = True):
             "pms_load_tuning": (ci, [vp, ctypes.c_char_p]),
             "pms_solve_sigma": (ci, [vp, u8p, ci, u8p, ci, ci, ci, ci, ci, ctypes.POINTER(u8p), ctypes.POINTER(sz)]),
             "pms_kernel_binary_version": (ci, [ci, ctypes.POINTER(ci)]),
+            "pms_cancel": (ci, [vp, ctypes.c_uint64]),
+            "pms_inject_fault": (ci, [vp, ci, ci, ci]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -225,6 +230,14 @@ def pms_kernel_binary_version(device: int = 0) -> int:
     if rc:
         raise PMSError(rc, "pms_kernel_binary_version")
     return int(v.value)
+
+
+def pms_cancel(ctx: "Context", ticket: int) -> None:
+    ctx.cancel(ticket)
+
+
+def pms_inject_fault(ctx: "Context", kind: int, after: int = 0, count: int = 1) -> None:
+    ctx.inject_fault(kind, after, count)
 
 
 def pms_solve_device_noalloc(d_seqs, n: int, m: int, l: int, d: int, d_motifs, capacity: int, d_status,
@@ -423,6 +436,15 @@ class Context:
 
     def release(self, ticket: int) -> None:
         self._check(self._lib.pms_release(self._h, ctypes.c_uint64(ticket)), "pms_release")
+
+    def cancel(self, ticket: int) -> None:
+        """Withdraws a queued served request (PMSError PMS_EBUSY once it is on the device)."""
+        self._check(self._lib.pms_cancel(self._h, ctypes.c_uint64(ticket)), "pms_cancel")
+
+    def inject_fault(self, kind: int, after: int = 0, count: int = 1) -> None:
+        """Test hook: the next `count` operations of `kind` (PMS_FAULT_ALLOC, PMS_FAULT_UPLOAD) fail on
+        the host after `after` more succeed; count 0 clears it."""
+        self._check(self._lib.pms_inject_fault(self._h, int(kind), int(after), int(count)), "pms_inject_fault")
 
 
 def decode_all(codes, l: int) -> list[str]:

@@ -272,6 +272,25 @@ struct pms_ctx {
     uint64_t use_tick = 0;
     uint64_t graph_replays = 0;   // solves enqueued by replaying a captured graph
 
+    // Injected host-side failures (pms_inject_fault), per kind: operations
+    // that still succeed first, then operations that fail. Read and changed
+    // with mu held.
+    struct Fault {
+        int after = 0, count = 0;
+    } faults[3];
+    bool inject(int kind)
+    {
+        Fault &f = faults[kind];
+        if (f.count <= 0)
+            return false;
+        if (f.after > 0) {
+            --f.after;
+            return false;
+        }
+        --f.count;
+        return true;
+    }
+
     int fail(int code, const char *fmt, ...)
     {
         char buf[512];
@@ -290,6 +309,8 @@ struct pms_ctx {
     void *dev_alloc(size_t bytes)
     {
         if (budget && used + bytes > budget)
+            return nullptr;
+        if (inject(PMS_FAULT_ALLOC))
             return nullptr;
         void *p = nullptr;
         if (ualloc) {
@@ -1152,6 +1173,8 @@ static int run_host_plan(pms_ctx *h, const Plan &P, const std::vector<InstSpec> 
     for (size_t i = 0; i < k; ++i)
         std::memcpy(stage + P.inst[i].seq_off, specs[i].host_seqs, (size_t)specs[i].n * specs[i].m);
     cudaStream_t st = h->stream;
+    if (h->inject(PMS_FAULT_UPLOAD))
+        return h->fail(PMS_ECUDA, "upload sequences: failure injected by pms_inject_fault");
     cudaError_t e = cudaMemcpyAsync(h->d_seqs.p, stage, P.seq_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess)
         return h->cuda_fail(e, "upload sequences");
@@ -1621,6 +1644,10 @@ static bool served_admit(Served *S, Request *r)
     const ChunkTable &ct = h->chunks(r->l, r->d, cw > 0 ? cw : kDefaultChunkWork);
     if ((int)ct.tab.size() > Served::kCtabMax) {
         r->status = PMS_EINVAL;
+        return true;
+    }
+    if (h->inject(PMS_FAULT_UPLOAD)) {   // this request's upload fails: it ends with the error
+        r->status = PMS_ECUDA;
         return true;
     }
     InstSpec spec{r->n, r->m, r->l, r->d, nullptr};
@@ -2157,6 +2184,42 @@ int pms_release(pms_ctx *h, uint64_t ticket)
     if (it->second->state != 3)
         return PMS_EBUSY;
     S->all.erase(it);
+    return PMS_OK;
+}
+
+int pms_cancel(pms_ctx *h, uint64_t ticket)
+{
+    if (!h)
+        return PMS_EINVAL;
+    Served *S = h->served;
+    if (!S)
+        return PMS_ENOTFOUND;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        auto it = S->all.find(ticket);
+        if (it == S->all.end())
+            return PMS_ENOTFOUND;
+        Request *r = it->second.get();
+        if (r->state == 3)
+            return PMS_OK;   // already finished: its result stands
+        auto q = std::find(S->pending.begin(), S->pending.end(), r);
+        if (r->state != 0 || q == S->pending.end())
+            return PMS_EBUSY;   // on the device
+        S->pending.erase(q);
+        r->status = PMS_ECANCELED;
+        r->state = 3;
+    }
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+    return PMS_OK;
+}
+
+int pms_inject_fault(pms_ctx *h, int kind, int after, int count)
+{
+    if (!h || kind < PMS_FAULT_ALLOC || kind > PMS_FAULT_UPLOAD || after < 0 || count < 0)
+        return PMS_EINVAL;
+    std::lock_guard<std::recursive_mutex> g(h->mu);
+    h->faults[kind] = pms_ctx::Fault{after, count};
     return PMS_OK;
 }
 
