@@ -11,6 +11,7 @@
 #include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -2453,9 +2454,16 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
     const int smem_rows = sigma_smem_rows(b, large);
     if (max_rows > smem_rows) {
         // every CTA may need global scratch for a seed's rows: keep it within 2 GiB
-        // (the persistent CTAs take seeds from a queue, so fewer CTAs only take longer)
+        // (the persistent CTAs take seeds from a queue, so fewer CTAs only take longer);
+        // PMS_SIGMA_SCRATCH_CAP (bytes) lowers that cap, so that tests reach the capped grid
+        size_t cap_bytes = (size_t)2 << 30;
+        if (const char *env = std::getenv("PMS_SIGMA_SCRATCH_CAP")) {
+            const unsigned long long v = std::strtoull(env, nullptr, 10);
+            if (v > 0 && v < cap_bytes)
+                cap_bytes = (size_t)v;
+        }
         const size_t per_cta = (size_t)4 * (1 + b) * max_rows;
-        blocks = (int)std::max<size_t>(1, std::min<size_t>(blocks, ((size_t)2 << 30) / per_cta));
+        blocks = (int)std::max<size_t>(1, std::min<size_t>(blocks, cap_bytes / per_cta));
     }
     const size_t NW = (size_t)n * W;
     const size_t ctr_bytes = 32 + 8 * (size_t)kSgCntNum;   // head, raw count, unique count, flags, work counters

@@ -153,3 +153,20 @@ def test_invalid_inputs(ctx):
         assert e.value.code == pms.PMS_EINVAL, kw
     # the context stays usable
     assert inst.motif.decode() in {bytes(r).decode() for r in ctx.solve_sigma(inst.seqs, 6, 2, PROTEIN)}
+
+
+def test_capped_grid_matches_the_oracle(oracle_, monkeypatch):
+    # rows beyond shared memory go to a per-CTA global scratch whose total is capped
+    # (2 GiB; lowered here through PMS_SIGMA_SCRATCH_CAP so that only a few CTAs run)
+    import paper_2403_00306_gb300 as pms
+    sigma, n, m, l, d = 2, 20, 800, 8, 4
+    alpha = alphabet_of(sigma)
+    inst = pi.planted_instance_sigma(n, m, l, d, 20, alpha.encode())
+    want = oracle_.sigma_solve(inst.seqs, l, d, alpha, cap=1 << 22)
+    per_cta = 4 * 2 * (n - 1) * (m - l + 1)          # D words and one plane per row
+    monkeypatch.setenv("PMS_SIGMA_SCRATCH_CAP", str(3 * per_cta))   # three CTAs
+    c = pms.Context(0)
+    assert np.array_equal(c.solve_sigma(inst.seqs, l, d, alpha), want)
+    monkeypatch.delenv("PMS_SIGMA_SCRATCH_CAP")
+    assert np.array_equal(c.solve_sigma(inst.seqs, l, d, alpha), want)
+    c.close()
