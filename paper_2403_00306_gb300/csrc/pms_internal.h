@@ -9,8 +9,14 @@ namespace pms {
 
 constexpr int kLMax = 32;      // one 32-bit word per bit-plane
 constexpr int kNMax = 64;      // sequences per instance
-constexpr int kWarps = 8;      // warps per CTA of the verification kernel
+constexpr int kWarps = 8;      // warps per CTA of the packing, mask and pair kernels
 constexpr int kThreads = kWarps * 32;
+// Warps per CTA of the verification kernel.
+#ifndef PMS_MAIN_WARPS
+#define PMS_MAIN_WARPS 8
+#endif
+constexpr int kMainWarps = PMS_MAIN_WARPS;
+constexpr int kMainThreads = kMainWarps * 32;
 constexpr int kRbCap = 128;    // entries of a subset-reduced occurrence row kept in shared memory
 constexpr int kListCap = 192;  // surviving candidates a warp buffers before checking further rows
 constexpr int kSubBatch = 128; // tree nodes (position subsets) a warp filters together

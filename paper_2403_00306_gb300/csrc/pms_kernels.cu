@@ -897,7 +897,8 @@ __device__ __forceinline__ int walk_run(const WarpCtx &c, const int *tab, int g0
     uint32_t *queue = c.ws->subs + 64;
     uint32_t *st = c.ws->u.stash;
     const uint4 *D4 = reinterpret_cast<const uint4 *>(c.rows.D);
-    const int claim = (g1 - g0 + 2 * kWarps - 1) / (2 * kWarps);
+    const int nw = (int)(blockDim.x >> 5);
+    const int claim = (g1 - g0 + 2 * nw - 1) / (2 * nw);
     const volatile uint32_t *vst = st;
     uint32_t P = vst[c.lane];
     const uint32_t w0 = vst[32 + c.lane];
@@ -1305,11 +1306,10 @@ __device__ __forceinline__ void exhaust_item(const MainParams &p, long long g, i
 // row by a binary search over the row offsets, its mask word by a binary
 // search over the word counts, the window as the word's r-th set bit. So the
 // only dependent global loads are one mask word and one window per slot, all
-// issued by all threads at once. `scratch` (shared memory the warps do not use
+// issued by all threads at once. `scratch` (the warps' per-warp areas, unused
 // between items) holds the mask words and counts; rows whose masks exceed it
 // (more than 32 words, i.e. W > 1024, or too many rows) are gathered by the
-// per-warp form below it.
-constexpr int kBuildScratchWords = kWarps * (int)(sizeof(WarpSmem) / sizeof(uint32_t));
+// per-warp form below it. Works for any number of warps per CTA.
 
 __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &in, int seed, CtaSmem &cs,
                                            uint32_t *smem_D, uint2 *smem_HL, uint32_t *glob_D, uint2 *glob_HL,
@@ -1318,11 +1318,13 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
     const int n = in.n, NW = in.NW, W = in.W, R = n - 1;
     const int *rl = p.rowlen + in.rlen_off + (size_t)seed * R;
     const uint32_t *mask = p.compat + in.compat_off + (size_t)seed * R * NW;
-    const bool fast = NW <= 32 && 2 * R * NW <= kBuildScratchWords;
+    const int nthreads = (int)blockDim.x, nwarps = nthreads >> 5;
+    const int scratch_words = nwarps * (int)(sizeof(WarpSmem) / sizeof(uint32_t));
+    const bool fast = NW <= 32 && 2 * R * NW <= scratch_words;
     uint32_t *sbits = scratch, *spre = scratch + R * NW;
     if (fast) {
         // every (row, word) of the seed's masks: the bits and their count
-        for (int t = threadIdx.x; t < R * NW; t += kThreads) {
+        for (int t = threadIdx.x; t < R * NW; t += nthreads) {
             const uint32_t b = __ldg(mask + t);
             sbits[t] = b;
             spre[t] = (uint32_t)__popc(b);
@@ -1383,7 +1385,7 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
     const int si = seed / W;   // the seed's own sequence has no row
     if (fast) {
         // exclusive prefix counts of each row's words (a warp per row)
-        for (int k = warp; k < R; k += kWarps) {
+        for (int k = warp; k < R; k += nwarps) {
             const int c = lane < NW ? (int)spre[k * NW + lane] : 0;
             int incl = c;
 #pragma unroll
@@ -1397,7 +1399,7 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
         }
         __syncthreads();
         const int total = cs.total_rows;
-        for (int slot = threadIdx.x; slot < total; slot += kThreads) {
+        for (int slot = threadIdx.x; slot < total; slot += nthreads) {
             // the rank whose padded row holds this slot: the last rank with offset <= slot
             int lo = 0, hi = R - 1;
             while (lo < hi) {
@@ -1427,7 +1429,7 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
         __syncthreads();
         return;
     }
-    for (int i = 1 + warp; i < n; i += kWarps) {
+    for (int i = 1 + warp; i < n; i += nwarps) {
         const uint32_t *mr = mask + (size_t)(i - 1) * NW;
         const uint2 *s = pl + (size_t)(i - 1 < si ? i - 1 : i) * W;
         const int off = cs.row_off[i];
@@ -1481,13 +1483,13 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
 // kRowsCap: row entries held in shared memory; kMinBlocks: resident CTAs per
 // SM the register allocation is bounded for (3 with 2560 entries, 4 with 1280).
 template <bool kCount, int kRowsCap, int kMinBlocks>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) main_kernel(MainParams p)
+__global__ void __launch_bounds__(kMainThreads, kMinBlocks) main_kernel(MainParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *wsm = reinterpret_cast<WarpSmem *>(smem_raw);
-    uint32_t *smem_D = reinterpret_cast<uint32_t *>(smem_raw + kWarps * sizeof(WarpSmem));
-    uint2 *smem_HL = reinterpret_cast<uint2 *>(smem_raw + kWarps * sizeof(WarpSmem) + kRowsCap * sizeof(uint32_t));
-    CtaSmem &cs = *reinterpret_cast<CtaSmem *>(smem_raw + kWarps * sizeof(WarpSmem) +
+    uint32_t *smem_D = reinterpret_cast<uint32_t *>(smem_raw + kMainWarps * sizeof(WarpSmem));
+    uint2 *smem_HL = reinterpret_cast<uint2 *>(smem_raw + kMainWarps * sizeof(WarpSmem) + kRowsCap * sizeof(uint32_t));
+    CtaSmem &cs = *reinterpret_cast<CtaSmem *>(smem_raw + kMainWarps * sizeof(WarpSmem) +
                                                kRowsCap * (sizeof(uint32_t) + sizeof(uint2)));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
@@ -1587,7 +1589,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) main_kernel(MainParams p
                     int start = 0, batch = kSubBatch;
                     if (lane == 0) {
                         const int left = g1 - (base + *reinterpret_cast<volatile int *>(ctr));
-                        batch = min(kSubBatch, max(32, ((left + 2 * kWarps - 1) / (2 * kWarps) + 31) & ~31));
+                        batch = min(kSubBatch, max(32, ((left + 2 * kMainWarps - 1) / (2 * kMainWarps) + 31) & ~31));
                         start = base + atomicAdd(ctr, batch);
                         if (p.item_claim) {
                             ctr[1] = max(0, g1 - (start + batch));
@@ -1646,14 +1648,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) main_kernel(MainParams p
                 // so that every warp gets work; with in.grab > 1 batches shrink
                 // toward in.grab as the chunk runs out (guided self-scheduling);
                 // in.grab == 1 selects the lane walk above instead
-                const int per_warp = (g1 - g0 + 2 * kWarps - 1) / (2 * kWarps);
+                const int per_warp = (g1 - g0 + 2 * kMainWarps - 1) / (2 * kMainWarps);
                 const int fixed = min(kSubBatch, max(32, (per_warp + 31) & ~31));
                 for (;;) {
                     int start = 0, batch = fixed;
                     if (lane == 0) {
                         if (in.grab > 1) {
                             const int left = g1 - *reinterpret_cast<volatile int *>(&cs.next);
-                            batch = min(fixed, max(in.grab, ((left + 2 * kWarps - 1) / (2 * kWarps) + 31) & ~31));
+                            batch = min(fixed, max(in.grab, ((left + 2 * kMainWarps - 1) / (2 * kMainWarps) + 31) & ~31));
                         }
                         start = atomicAdd(&cs.next, batch);
                     }
@@ -2638,10 +2640,16 @@ cudaError_t init_tables()
     return cudaMemcpyToSymbol(c_pow3, pow3, sizeof(pow3));
 }
 
+// Resident CTAs per SM each form's registers are bounded for: with 8-warp
+// CTAs 4 (the small-rows form, 64 registers) and 3 (the other, 80); with
+// wider CTAs as many as keep 32 warps per SM (64 registers).
+constexpr int kMinBlocksSmall = kMainWarps >= 32 ? 1 : 32 / kMainWarps;
+constexpr int kMinBlocksLarge = kMainWarps == 8 ? 3 : kMinBlocksSmall;
+
 size_t main_smem_bytes(bool small_rows)
 {
     const int rows = small_rows ? kRowSmemCapSmall : kRowSmemCap;
-    return kWarps * sizeof(WarpSmem) + rows * (sizeof(uint32_t) + sizeof(uint2)) + sizeof(CtaSmem);
+    return kMainWarps * sizeof(WarpSmem) + rows * (sizeof(uint32_t) + sizeof(uint2)) + sizeof(CtaSmem);
 }
 
 namespace {
@@ -2654,7 +2662,7 @@ cudaError_t occupancy_of(int *blocks_per_sm, size_t smem)
     if (e != cudaSuccess)
         return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, main_kernel<kCount, kRowsCap, kMinBlocks>,
-                                                         kThreads, smem);
+                                                         kMainThreads, smem);
 }
 
 }  // namespace
@@ -2663,10 +2671,10 @@ cudaError_t main_occupancy(int *blocks_per_sm, bool count_mode, bool small_rows)
 {
     const size_t smem = main_smem_bytes(small_rows);
     if (small_rows)
-        return count_mode ? occupancy_of<true, kRowSmemCapSmall, 4>(blocks_per_sm, smem)
-                          : occupancy_of<false, kRowSmemCapSmall, 4>(blocks_per_sm, smem);
-    return count_mode ? occupancy_of<true, kRowSmemCap, 3>(blocks_per_sm, smem)
-                      : occupancy_of<false, kRowSmemCap, 3>(blocks_per_sm, smem);
+        return count_mode ? occupancy_of<true, kRowSmemCapSmall, kMinBlocksSmall>(blocks_per_sm, smem)
+                          : occupancy_of<false, kRowSmemCapSmall, kMinBlocksSmall>(blocks_per_sm, smem);
+    return count_mode ? occupancy_of<true, kRowSmemCap, kMinBlocksLarge>(blocks_per_sm, smem)
+                      : occupancy_of<false, kRowSmemCap, kMinBlocksLarge>(blocks_per_sm, smem);
 }
 
 cudaError_t launch_main(const MainParams &p, int blocks, bool count_mode, cudaStream_t st, bool small_rows)
@@ -2674,14 +2682,14 @@ cudaError_t launch_main(const MainParams &p, int blocks, bool count_mode, cudaSt
     const size_t smem = main_smem_bytes(small_rows);
     if (small_rows) {
         if (count_mode)
-            main_kernel<true, kRowSmemCapSmall, 4><<<blocks, kThreads, smem, st>>>(p);
+            main_kernel<true, kRowSmemCapSmall, kMinBlocksSmall><<<blocks, kMainThreads, smem, st>>>(p);
         else
-            main_kernel<false, kRowSmemCapSmall, 4><<<blocks, kThreads, smem, st>>>(p);
+            main_kernel<false, kRowSmemCapSmall, kMinBlocksSmall><<<blocks, kMainThreads, smem, st>>>(p);
     } else {
         if (count_mode)
-            main_kernel<true, kRowSmemCap, 3><<<blocks, kThreads, smem, st>>>(p);
+            main_kernel<true, kRowSmemCap, kMinBlocksLarge><<<blocks, kMainThreads, smem, st>>>(p);
         else
-            main_kernel<false, kRowSmemCap, 3><<<blocks, kThreads, smem, st>>>(p);
+            main_kernel<false, kRowSmemCap, kMinBlocksLarge><<<blocks, kMainThreads, smem, st>>>(p);
     }
     return cudaGetLastError();
 }
