@@ -167,6 +167,7 @@ struct SgWarp {
         return v;
     }
     __device__ unsigned long long bcast(unsigned long long v) const { return __shfl_sync(0xFFFFFFFFu, v, 0); }
+    __device__ int from(int v, int src) const { return __shfl_sync(0xFFFFFFFFu, v, src); }
     __device__ uint32_t ballot(bool p) const { return __ballot_sync(0xFFFFFFFFu, p); }
     __device__ void sync() const { __syncwarp(); }
     __device__ void or_into(uint32_t *a, uint32_t v) const { atomicOr(a, v); }
@@ -190,6 +191,7 @@ struct SgSingle {
     __host__ __device__ bool any(bool p) const { return p; }
     __host__ __device__ uint32_t or_all(uint32_t v) const { return v; }
     __host__ __device__ unsigned long long bcast(unsigned long long v) const { return v; }
+    __host__ __device__ int from(int v, int) const { return v; }
     __host__ __device__ uint32_t ballot(bool p) const { return p ? 1u : 0u; }
     __host__ __device__ void sync() const {}
     __host__ __device__ void or_into(uint32_t *a, uint32_t v) const { *a |= v; }
@@ -311,6 +313,8 @@ struct SgState {
     uint32_t Wl[kSigMaxD]; // the interchangeable letters the representative stands for
     int lo[kSigMaxD];      // list form: the rows alive before depth t are list[lo[t] .. hi[t])
     int hi[kSigMaxD];
+    uint32_t Tc[kSigMaxD]; // list form: the choices left for the current prefix at each depth
+    uint32_t smask[kNMax]; // list form: per sequence, the letters its rows allow at the next position
 };
 
 // A group's buffer for the row lists of the list form of the depth-first
@@ -440,30 +444,95 @@ __host__ __device__ void sg_dfs(const SgSeed &S, const G &grp, uint32_t P, int k
 // abandoned when more than miss_max sequences have no row left. So each depth
 // tests only the rows the previous depth kept, each with one letter
 // comparison, instead of looking for an occurrence in every sequence again.
+// For q = n the kept rows also say which letters can come next: at the next
+// changed position a sequence allows every letter if one of its rows has
+// slack there (a bound below d, or agreement with x at that position), else
+// only the letters its rows hold there; a letter that some sequence does not
+// allow would leave it without a row, so only letters every sequence allows
+// are tried (the same prefixes fail, without a scan of the list).
 // The lists of the depths on the current path are kept one after another in
 // the group's buffer (the caller checks they fit: at most n0 (k + 1)).
+
+// Adds the letters `allow` of a kept entry to the mask of its sequence
+// (st.smask, atomic ORs; sg_allowed synchronises the group before reading).
+template <class G>
+__host__ __device__ inline void sg_allow_into(SgState &st, const G &grp, bool keep, int seq, uint32_t allow)
+{
+    if (keep)
+        grp.or_into(&st.smask[seq], allow);
+}
+
+// The letters every sequence (but the seed's own) allows: the AND of st.smask.
+template <class G>
+__host__ __device__ inline uint32_t sg_allowed(const SgSeed &S, SgState &st, const G &grp)
+{
+    grp.sync();
+    uint32_t miss = 0;
+    for (int i = grp.lane; i < S.n; i += G::width)
+        if (i != S.sx)
+            miss |= ~st.smask[i];
+    return ~grp.or_all(miss);
+}
+
+template <class G>
+__host__ __device__ inline void sg_allow_clear(const SgSeed &S, SgState &st, const G &grp)
+{
+    grp.sync();
+    for (int i = grp.lane; i < S.n; i += G::width)
+        st.smask[i] = 0u;
+    grp.sync();
+}
+
 template <class G, class Sink>
 __host__ __device__ void sg_dfs_rows(const SgSeed &S, const G &grp, int k, SgState &st, SgCount &ct, Sink &sink,
                                      uint32_t *buf, int n0)
 {
     const bool lead = grp.lane == 0;
+    const bool narrow = S.miss_max == 0;   // q = n: choices narrowed by the rows' letters
+    uint32_t tc0 = st.T[0];
+    if (narrow) {   // the letters the node's rows allow at the first position
+        sg_allow_clear(S, st, grp);
+        const int p0 = st.pos[0];
+        for (int j0 = 0; j0 < n0; j0 += G::width) {
+            const int j = j0 + grp.lane;
+            uint32_t allow = 0;
+            int seq = 0;
+            if (j < n0) {
+                const uint32_t v = buf[j];
+                const int e = (int)(v & kSgListRowMask);
+                seq = (int)((v >> kSgListRowBits) & 63u);
+                allow = ((int)(v >> 27) < S.d || !((S.D[e] >> p0) & 1u))
+                            ? ~0u
+                            : 1u << sg_letter_at(S.Pl + e, S.stride, S.b, p0);
+            }
+            sg_allow_into(st, grp, j < n0, seq, allow);
+        }
+        tc0 &= sg_allowed(S, st, grp);
+    }
+    if (!tc0)
+        return;
     int t = 0;
     if (lead) {
         st.lo[0] = 0;
         st.hi[0] = n0;
     }
     grp.sync();
-    st.ch[0] = sg_ctz(st.T[0]);
+    st.Tc[0] = tc0;
+    st.ch[0] = sg_ctz(tc0);
     grp.sync();
     for (;;) {
         const int plo = st.lo[t], phi = st.hi[t];
         const int p = st.pos[t], a = st.ch[t];
+        const bool track = narrow && t + 1 < k;   // the next position's letters
+        const int pn = track ? st.pos[t + 1] : 0;
+        if (track)
+            sg_allow_clear(S, st, grp);
         int w = phi;
         unsigned long long present = 0;
         for (int j0 = plo; j0 < phi; j0 += G::width) {
             const int j = j0 + grp.lane;
             bool keep = false;
-            uint32_t v = 0;
+            uint32_t v = 0, allow = 0;
             if (j < phi) {
                 v = buf[j];
                 const int e = (int)(v & kSgListRowMask);
@@ -474,13 +543,20 @@ __host__ __device__ void sg_dfs_rows(const SgSeed &S, const G &grp, int k, SgSta
                 }
                 keep = dist <= S.d;
                 v = (v & ((1u << 27) - 1u)) | ((uint32_t)dist << 27);
-                if (keep)
+                if (keep) {
                     present |= 1ull << ((v >> kSgListRowBits) & 63u);
+                    if (track)
+                        allow = (dist < S.d || !((S.D[e] >> pn) & 1u))
+                                    ? ~0u
+                                    : 1u << sg_letter_at(S.Pl + e, S.stride, S.b, pn);
+                }
             }
             const uint32_t bal = grp.ballot(keep);
             if (keep)
                 buf[w + grp.rank(bal)] = v;
             w += sg_popc(bal);
+            if (track)
+                sg_allow_into(st, grp, keep, (int)((v >> kSgListRowBits) & 63u), allow);
         }
         present = grp.or_all64(present);
         if (lead) {
@@ -488,7 +564,14 @@ __host__ __device__ void sg_dfs_rows(const SgSeed &S, const G &grp, int k, SgSta
             if (t == k - 1)
                 ct.leaves++;
         }
-        const bool ok = (S.n - 1) - sg_popc64(present) <= S.miss_max;   // the seed's own sequence has no rows
+        bool ok = (S.n - 1) - sg_popc64(present) <= S.miss_max;   // the seed's own sequence has no rows
+        uint32_t tcn = 0;
+        if (ok && t + 1 < k) {
+            tcn = st.T[t + 1];
+            if (track)
+                tcn &= sg_allowed(S, st, grp);
+            ok = tcn != 0;
+        }
         if (ok) {
             if (t == k - 1) {
                 sg_emit(S, grp, st.pos, st.ch, st.Wl, k, sink);
@@ -500,14 +583,15 @@ __host__ __device__ void sg_dfs_rows(const SgSeed &S, const G &grp, int k, SgSta
                 }
                 ++t;
                 grp.sync();
-                st.ch[t] = sg_ctz(st.T[t]);
+                st.Tc[t] = tcn;
+                st.ch[t] = sg_ctz(tcn);
                 grp.sync();
                 continue;
             }
         }
         // the next choice at this depth, else back up
         for (;;) {
-            const uint32_t rest = st.T[t] & ~(uint32_t)((2ull << st.ch[t]) - 1ull);
+            const uint32_t rest = st.Tc[t] & ~(uint32_t)((2ull << st.ch[t]) - 1ull);
             if (rest) {
                 const int nx = sg_ctz(rest);
                 grp.sync();

@@ -99,6 +99,17 @@ struct LockstepWarp {
 #endif
     }
     __host__ __device__ int rank(uint32_t bal) const { return __builtin_popcount(bal & ((1u << lane) - 1u)); }
+    __host__ __device__ int from(int v, int src) const
+    {
+        int r = v;
+#ifndef __CUDA_ARCH__
+        x->val[lane] = (unsigned long long)(unsigned)v;
+        x->bar.arrive_and_wait();
+        r = (int)(unsigned)x->val[src];
+        x->bar.arrive_and_wait();
+#endif
+        return r;
+    }
     __host__ __device__ unsigned long long or_all64(unsigned long long v) const
     {
         unsigned long long s = 0;
