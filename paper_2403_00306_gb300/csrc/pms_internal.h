@@ -165,7 +165,8 @@ constexpr int kSigMaxPlanes = 5;    // ceil(log2 32)
 constexpr int kSigThreads = 256;    // threads of the search kernel's CTA
 constexpr int kSigSortThreads = 1024;
 constexpr int kSigSmemSmall = 64 * 1024;    // rows of one seed in shared memory: 3 CTAs per SM
-constexpr int kSigSmemLarge = 104 * 1024;   // the same for seeds with many rows: 2 CTAs per SM
+constexpr int kSigSmemLarge = 100 * 1024;   // the same for seeds with many rows: 2 CTAs per SM (with the
+                                            // kernel's 10 KB of static per-warp state, 2 x 110 KB <= 228 KB)
 #ifndef PMS_SIG_LIST_CAP
 #define PMS_SIG_LIST_CAP 16384
 #endif
