@@ -49,22 +49,33 @@ QUORUM_WORKLOADS = {"quorum15_4_q10": (15, 4, 10)}
 PROTEIN_WORKLOADS = {f"protein{l}_{d}": (l, d) for (l, d) in pi.PROTEIN_LD}
 L2_FLUSH_BYTES = 512 << 20
 
-# DRAM bytes (read + write) per launch of the verification kernel from one ncu
-# capture (profiles/main_kernel_plain*.md), valid only for the kernel source
-# they were taken on (its sha256 prefix); otherwise the bench reports null.
-NCU_TRAFFIC = {"kernel_sha256": "73f0161dd7dba0e6", "plain15_4": 1.063680e6, "plain19_6": 1.426176e6}
+# DRAM bytes (read + write) per launch of each search kernel from one-pass ncu
+# captures (dram__bytes_read.sum + dram__bytes_write.sum, profiles/*.md), valid
+# only for the sources they were taken on (sha256 prefix of the kernel file and
+# the shared header); otherwise the bench reports null.
+NCU_TRAFFIC = {
+    "pms_kernels.cu": {"sha256": "fc75a4ede7180177+8d4a6b172ee21e22",
+                       "plain9_2": 1.099008e6, "plain15_4": 1.064960e6,
+                       "plain17_5": 1.108736e6, "plain19_6": 1.269760e6},
+    "pms_sigma.cu": {"sha256": "b4f05a2da0801846+8d4a6b172ee21e22", "protein9_4": 1.9118336e7},
+}
 
 
-def kernel_sha() -> str:
+def source_sha(name: str) -> str:
     import hashlib
-    with open(os.path.join(ROOT, "paper_2403_00306_gb300", "csrc", "pms_kernels.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    csrc = os.path.join(ROOT, "paper_2403_00306_gb300", "csrc")
+    parts = []
+    for f in (name, "pms_internal.h"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            parts.append(hashlib.sha256(fh.read()).hexdigest()[:16])
+    return "+".join(parts)
 
 
-def measured_traffic(workload: str):
-    if kernel_sha() != NCU_TRAFFIC["kernel_sha256"]:
+def measured_traffic(source: str, workload: str):
+    entry = NCU_TRAFFIC[source]
+    if source_sha(source) != entry["sha256"]:
         return None
-    return NCU_TRAFFIC.get(workload)
+    return entry.get(workload)
 
 
 def load_peaks() -> dict:
@@ -430,7 +441,7 @@ def measure_plain(pms, torch, dev, stream, peaks, l, d, K, Wm, rank, dist, q: in
         # the searched space W * |B(x, d)| per solve, for scale (not checks)
         "search_space_per_s": solves * W * (n - q + 1 if q else 1) * n_ball(l, d) / (total_ms / 1000.0),
         "roofline": peaks.roofline(cmp_total / K, verify_avg_ms, "main_kernel (verification)",
-                                   measured_traffic(f"quorum{l}_{d}_q{q}" if q else f"plain{l}_{d}"),
+                                   measured_traffic("pms_kernels.cu", f"quorum{l}_{d}_q{q}" if q else f"plain{l}_{d}"),
                                    verify_avg_ms / (total_ms / K)),
         "e2e": {"value": solves / (e2e_total / 1000.0), "unit": "solves/s", "h2d_bytes_per_step": n * m,
                 "d2h_bytes_per_step": 16 + 512 * 8, "ms_per_step": e2e_total / K},
@@ -535,7 +546,8 @@ def bench_sigma(args, ws, rank, local, dist, l, d) -> dict:
                    "timing": "CUDA events on the library stream from the packing kernel to the sort kernel"},
         "candidate_checks_per_s": sum(tested) / (sum(kern_ms) / 1000.0),
         "search_space_per_s": solves * W * n_ball(l, d, 20) / (total_ms / 1000.0),
-        "roofline": peaks.roofline(statistics.mean(cmps), verify_avg, "sigma_main_kernel (search)", None,
+        "roofline": peaks.roofline(statistics.mean(cmps), verify_avg, "sigma_main_kernel (search)",
+                                   measured_traffic("pms_sigma.cu", f"protein{l}_{d}"),
                                    verify_avg / (total_ms / K)),
         "e2e": {"value": solves / (e2e_total / 1000.0), "unit": "solves/s", "h2d_bytes_per_step": n * m,
                 "d2h_bytes_per_step": 32 + 8 * 9 + l, "ms_per_step": e2e_total / K},
