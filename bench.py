@@ -355,8 +355,10 @@ class Peaks:
 
 def measure_plain(pms, torch, dev, stream, peaks, l, d, K, Wm, rank, dist, q: int = 0, clk=None) -> dict:
     """One plain configuration: K timed device-resident solves (CUDA events on the library stream,
-    L2 flushed between steps), the verification kernel's comparisons (count mode, same
-    instances), and K end-to-end solves from host memory through pms_solve."""
+    L2 flushed between steps; the captured graphs replay without timing events), the same K
+    solves again with the device-time events inside the graphs (pms_options.graph = 1) for the
+    verification kernel's own duration, its comparisons (count mode, same instances), and K
+    end-to-end solves from host memory through pms_solve."""
     n, m = 20, 600
     seeds = rank_seeds(rank, K + Wm)
     insts = [pi.planted_instance(n, m, l, d, s) for s in seeds]
@@ -383,7 +385,19 @@ def measure_plain(pms, torch, dev, stream, peaks, l, d, K, Wm, rank, dist, q: in
             ctx.solve_device(d_in[i], n, m, l, d, d_out, cap, d_st)
     stream.synchronize()
 
+    # the verification kernel's duration: the same steps through graphs that carry the
+    # device-time events (an event node between two kernels costs their launch overlap,
+    # so the value pass runs without them)
+    tctx = pms.Context(dev.index)
+    tctx.set_stream(stream)
+    tctx.set_options(graph=1, quorum=q)
+    for i in range(Wm):
+        with torch.cuda.stream(stream):
+            tctx.solve_device(d_in[i], n, m, l, d, d_out, cap, d_st)
+    stream.synchronize()
+
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     verify_ms = []
     barrier(dist)
     torch.cuda.synchronize(dev)
@@ -394,10 +408,21 @@ def measure_plain(pms, torch, dev, stream, peaks, l, d, K, Wm, rank, dist, q: in
                 ev[k][0].record(stream)
                 ctx.solve_device(d_in[Wm + k], n, m, l, d, d_out, cap, d_st)
                 ev[k][1].record(stream)
-            verify_ms.append(ctx.stats()["ms_verify"])   # waits for this step's kernels
+        torch.cuda.synchronize(dev)
+        for k in range(K):
+            with torch.cuda.stream(stream):
+                flush(k)
+                tev[k][0].record(stream)
+                tctx.solve_device(d_in[Wm + k], n, m, l, d, d_out, cap, d_st)
+                tev[k][1].record(stream)
+            s = tctx.stats()   # waits for this step's kernels
+            assert s["ms_verify"] > 0, "timed graph replay without a verification time"
+            verify_ms.append(s["ms_verify"])
         torch.cuda.synchronize(dev)
     barrier(dist)
+    tctx.close()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    timed_step_ms = statistics.mean(a.elapsed_time(b) for a, b in tev)
     total_ms = max_over_ranks(dist, sum(step_ms))
     solves = sum_over_ranks(dist, K)
     value = solves / (total_ms / 1000.0)
@@ -434,7 +459,11 @@ def measure_plain(pms, torch, dev, stream, peaks, l, d, K, Wm, rank, dist, q: in
         "config": {"workload": (f"quorum ({l},{d}) q={q}" if q else f"plain ({l},{d})")
                                + f" n={n} m={m}, one seeded FM-model instance per step",
                    "l": l, "d": d, "n": n, "m": m, "l2": "flushed between steps (512 MiB write, untimed)",
-                   "timing": "CUDA events on the library stream around pms_solve_device"},
+                   "timing": "CUDA events on the library stream around pms_solve_device; graphs replayed "
+                             "without timing events (pms_options.graph = 0)"},
+        # the second pass over the same steps, graphs with the device-time events inside
+        "kernel_timing_pass": {"ms_per_step": timed_step_ms, "verify_ms": statistics.mean(verify_ms),
+                               "graph": "pms_options.graph = 1 (event nodes around each kernel)"},
         # candidates generated and compared explicitly against occurrences (count mode)
         "candidate_checks_per_s": tested_total / (total_ms / 1000.0),
         "candidates_tested_per_step": tested / K,
@@ -442,7 +471,7 @@ def measure_plain(pms, torch, dev, stream, peaks, l, d, K, Wm, rank, dist, q: in
         "search_space_per_s": solves * W * (n - q + 1 if q else 1) * n_ball(l, d) / (total_ms / 1000.0),
         "roofline": peaks.roofline(cmp_total / K, verify_avg_ms, "main_kernel (verification)",
                                    measured_traffic("pms_kernels.cu", f"quorum{l}_{d}_q{q}" if q else f"plain{l}_{d}"),
-                                   verify_avg_ms / (total_ms / K)),
+                                   verify_avg_ms / timed_step_ms),
         "e2e": {"value": solves / (e2e_total / 1000.0), "unit": "solves/s", "h2d_bytes_per_step": n * m,
                 "d2h_bytes_per_step": 16 + 512 * 8, "ms_per_step": e2e_total / K},
         "gpu_launches": 3 * K,   # packing + compatibility masks, verification, sort/unique
@@ -471,8 +500,8 @@ def bench_plain(args, ws, rank, local, dist, l, d, q: int = 0, extras: bool = Fa
     line = {"metric": METRIC, "value": r["value"], "unit": "solves/s", "n_gpus": ws, "steps": r["steps"],
             "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": r["config"]}
-    for k in ("candidate_checks_per_s", "candidates_tested_per_step", "search_space_per_s", "roofline", "e2e",
-              "gpu_launches"):
+    for k in ("candidate_checks_per_s", "candidates_tested_per_step", "search_space_per_s", "roofline",
+              "kernel_timing_pass", "e2e", "gpu_launches"):
         line[k] = r[k]
     line["clocks"] = clk.summary()
     if extras:
@@ -563,7 +592,9 @@ def measure_batch(pms, torch, dev, peaks, args, rank, dist, steps: int = 3) -> d
     ctx = pms.Context(dev.index)
     batch = [(i.seqs, i.l, i.d) for i in insts]
     t_tune = time.perf_counter()
-    ctx.set_options(autotune=1)      # tunes each (l, d, n, m) class once, untimed
+    # tunes each (l, d, n, m) class once, untimed; graph = 1: the replays carry the
+    # device-time events (about 17 us against a launch of hundreds of milliseconds)
+    ctx.set_options(autotune=1, graph=1)
     ctx.solve_batch(batch)
     t_tune = time.perf_counter() - t_tune
     for _ in range(3):

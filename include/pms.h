@@ -120,7 +120,14 @@ typedef struct {
                               on the second call of each plan (the same
                               instance shapes and options), with the call's
                               input and output pointers patched in:
-                              0 = on (default); -1 = launch kernel by kernel */
+                              0 = on (default), replays carry no timing
+                              events: pms_stats.ms_kernel and ms_verify read
+                              -1 after a replay (an event node between two
+                              kernels costs their launch overlap, about
+                              17 us per plain (15,4) solve on GB300);
+                              1 = on, with the device-time events recorded
+                              inside the graph; -1 = launch kernel by kernel
+                              (device times always recorded) */
     int triple_rows;       /* three-string feasibility below a tree node (the
                               TraverStringRef feasibility theorem for three
                               strings, applied to the seed x and pairs of
@@ -163,8 +170,9 @@ typedef struct {
     uint64_t cmp_verify;        /* candidate-versus-occurrence comparisons */
     uint64_t seeds_infeasible;  /* seeds with an empty row (no motif possible) */
     double ms_total;            /* wall time of the call, host clock */
-    double ms_kernel;           /* device time from the first to the last kernel */
-    double ms_verify;           /* device time of the verification kernel alone */
+    double ms_kernel;           /* device time from the first to the last kernel;
+                                   -1 after a graph replay with pms_options.graph = 0 */
+    double ms_verify;           /* device time of the verification kernel alone (-1 as ms_kernel) */
     uint64_t serve_waves;       /* served form, cumulative: verification waves launched */
     uint64_t serve_overlapped_waves;     /* waves holding chunks of more than one request */
     uint64_t serve_max_requests_per_wave;

@@ -1509,6 +1509,10 @@ __global__ void __launch_bounds__(kMainThreads, kMinBlocks) main_kernel(MainPara
     }
     for (int i = threadIdx.x; i < (kLMax + 1) * (kLMax + 1); i += blockDim.x)
         (&cs.binom[0][0])[i] = (&c_binom[0][0])[i];
+    // launched as a programmatic dependent of the previous kernel: nothing
+    // above reads its output; wait here until it has completed and its
+    // writes are visible (without the launch attribute this returns at once)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     bool draining = false;   // warp 0: the queue has run out, items are joined through the steal cursor
     for (;;) {
         if (warp == 0) {
@@ -1541,8 +1545,12 @@ __global__ void __launch_bounds__(kMainThreads, kMinBlocks) main_kernel(MainPara
             }
         }
         __syncthreads();
-        if (cs.g == ~0ull)
+        if (cs.g == ~0ull) {
+            // no item left for this CTA: the sort kernel may launch (it waits
+            // for this grid to complete before it reads anything)
+            asm volatile("griddepcontrol.launch_dependents;");
             break;
+        }
         const int I = cs.inst, seed = cs.seed, chunk = cs.chunk;
         const InstDev in = p.inst[I];
         const int *tab = p.ctab + cs.ctab;
@@ -2283,6 +2291,9 @@ __global__ void __launch_bounds__(256) compat_rows_kernel(const InstDev *__restr
     const int jb = (int)(blockIdx.x / (unsigned)n) * kCompatSeedsPerCta;
     const uint8_t *sq = seqs + inst->seq_off;
     const uint32_t lmask = l == 32 ? ~0u : (1u << l) - 1u;
+    // the verification kernel may launch now: its CTAs set up their shared
+    // memory and then wait for this grid to complete (griddepcontrol.wait)
+    asm volatile("griddepcontrol.launch_dependents;");
     if (threadIdx.x == 0)
         sbad = 0;
     __syncthreads();
@@ -2507,6 +2518,7 @@ __global__ void __launch_bounds__(kSortThreads)
     extern __shared__ __align__(16) uint64_t sk[];
     __shared__ uint32_t warp_tot[32];
     __shared__ uint32_t s_total, s_base, s_run;
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // the producing kernel has completed
     const int I = inst_list ? inst_list[blockIdx.x] : (int)blockIdx.x;
     const InstDev in = inst[I];
     const uint32_t rc = raw_count[I];
@@ -2677,21 +2689,38 @@ cudaError_t main_occupancy(int *blocks_per_sm, bool count_mode, bool small_rows)
                       : occupancy_of<false, kRowSmemCap, kMinBlocksLarge>(blocks_per_sm, smem);
 }
 
+// Launch configuration of a programmatic dependent launch: the kernel may be
+// scheduled before the previous kernel in the stream has completed, and
+// waits for it with griddepcontrol.wait before touching its output. After a
+// copy, a memset or an event the stream orders it as usual.
+static cudaLaunchConfig_t dependent_launch(cudaLaunchAttribute *attr, int blocks, int threads, size_t smem,
+                                           cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
 cudaError_t launch_main(const MainParams &p, int blocks, bool count_mode, cudaStream_t st, bool small_rows)
 {
     const size_t smem = main_smem_bytes(small_rows);
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = dependent_launch(attr, blocks, kMainThreads, smem, st);
     if (small_rows) {
         if (count_mode)
-            main_kernel<true, kRowSmemCapSmall, kMinBlocksSmall><<<blocks, kMainThreads, smem, st>>>(p);
-        else
-            main_kernel<false, kRowSmemCapSmall, kMinBlocksSmall><<<blocks, kMainThreads, smem, st>>>(p);
-    } else {
-        if (count_mode)
-            main_kernel<true, kRowSmemCap, kMinBlocksLarge><<<blocks, kMainThreads, smem, st>>>(p);
-        else
-            main_kernel<false, kRowSmemCap, kMinBlocksLarge><<<blocks, kMainThreads, smem, st>>>(p);
+            return cudaLaunchKernelEx(&cfg, main_kernel<true, kRowSmemCapSmall, kMinBlocksSmall>, p);
+        return cudaLaunchKernelEx(&cfg, main_kernel<false, kRowSmemCapSmall, kMinBlocksSmall>, p);
     }
-    return cudaGetLastError();
+    if (count_mode)
+        return cudaLaunchKernelEx(&cfg, main_kernel<true, kRowSmemCap, kMinBlocksLarge>, p);
+    return cudaLaunchKernelEx(&cfg, main_kernel<false, kRowSmemCap, kMinBlocksLarge>, p);
 }
 
 cudaError_t launch_compat(const InstDev *inst, int ninst, const long long *row_prefix, long long total_rows,
@@ -2783,9 +2812,10 @@ cudaError_t launch_sort_unique(const InstDev *inst, const int *inst_list, int nl
             return e;
         attr_set_dev = dev;
     }
-    sort_unique_kernel<<<nlist, kSortThreads, smem, st>>>(inst, inst_list, raw, tmp, raw_count, flags, status, dense,
-                                                          dense_cap, dense_total);
-    return cudaGetLastError();
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = dependent_launch(attr, nlist, kSortThreads, smem, st);
+    return cudaLaunchKernelEx(&cfg, sort_unique_kernel, inst, inst_list, raw, tmp, raw_count, flags, status, dense,
+                              dense_cap, dense_total);
 }
 
 cudaError_t launch_probe(int kind, int iters, int blocks, unsigned long long *cycles, unsigned long long *sink,

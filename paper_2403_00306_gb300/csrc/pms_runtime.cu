@@ -213,6 +213,7 @@ struct pms_ctx {
     size_t h_meta_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm0 = nullptr, evm1 = nullptr;
     bool stats_pending = false;   // device times / counters of the last solve not read yet
+    bool stats_timed = false;     // the last solve recorded its device-time events
     bool stats_count = false;
     size_t stats_k = 0;
 
@@ -747,12 +748,16 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
 // staged in h->h_meta and uploaded. Output: status/dense in the result block.
 // Records a timing event; inside a stream capture (a graph's launches) as an
 // external event node, so that every replay records it.
-static void record_event(cudaEvent_t ev, cudaStream_t st, bool capturing)
+// Inside a captured graph the device-time events are nodes of their own, and
+// an event node between two kernels costs the launch overlap of the pair
+// (about 17 us per plain (15,4) solve on GB300), so graphs carry them only
+// when pms_options.graph asks for timed replays.
+static void record_event(const pms_ctx *h, cudaEvent_t ev, cudaStream_t st, bool capturing)
 {
-    if (capturing)
-        cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
-    else
+    if (!capturing)
         cudaEventRecord(ev, st);
+    else if (h->opt.graph >= 1)
+        cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
 }
 
 // CTAs of the verification kernel for a plan: resident CTAs per SM (capped by
@@ -797,6 +802,8 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     if ((rc = h->ensure(h->d_scratch, (size_t)blocks * 3 * (size_t)P.rows_cap * sizeof(uint32_t))))
         return rc;
     cudaStream_t st = h->stream;
+    if (!meta_dev)
+        h->stats_timed = true;
     char *dm = meta_dev ? meta_dev : (char *)h->d_meta.p;
     char *dc = (char *)h->d_ctr.p;
     cudaError_t e;
@@ -813,7 +820,7 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     const InstDev *d_inst = (const InstDev *)(dm + ml.inst);
     uint32_t *d_flags = (uint32_t *)(dc + cl.flags);
     uint32_t *d_rawcnt = (uint32_t *)(dc + cl.raw_count);
-    record_event(h->ev0, st, meta_dev != nullptr);
+    record_event(h, h->ev0, st, meta_dev != nullptr);
     const bool by_rows = P.total_rows > 0 && k == 1 && compat_rows_fits(P.inst[0].W);
     if (by_rows) {
         // one instance: packing and masks in one kernel, a CTA per (sequence, 16 seeds)
@@ -863,7 +870,7 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
     mp.counters = (unsigned long long *)(dc + cl.work);
     mp.item_claim = (int *)(dc + cl.claim);
     mp.steal_state = (unsigned int *)(dc + cl.steal);
-    record_event(h->evm0, st, meta_dev != nullptr);
+    record_event(h, h->evm0, st, meta_dev != nullptr);
     if (P.total_items > 0 && (e = launch_main(mp, blocks, count_mode, st, P.small_rows)) != cudaSuccess)
         return h->cuda_fail(e, "verification kernel");
     if (P.pair_mode && P.total_pair_items > 0) {
@@ -882,12 +889,12 @@ static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, Sta
         if ((e = launch_pairs(pp, pblocks, count_mode, st)) != cudaSuccess)
             return h->cuda_fail(e, "pair kernel");
     }
-    record_event(h->evm1, st, meta_dev != nullptr);
+    record_event(h, h->evm1, st, meta_dev != nullptr);
     if ((e = launch_sort_unique(d_inst, nullptr, (int)k, (uint64_t *)h->d_raw.p, (uint64_t *)h->d_tmp.p, d_rawcnt,
                                 d_flags, status_out,
                                 dense_out, dense_cap, (uint32_t *)(dc + cl.dense_total), st)) != cudaSuccess)
         return h->cuda_fail(e, "sort/unique kernel");
-    record_event(h->ev1, st, meta_dev != nullptr);
+    record_event(h, h->ev1, st, meta_dev != nullptr);
     return PMS_OK;
 }
 
@@ -1079,6 +1086,7 @@ static int enqueue_plan_graph(pms_ctx *h, const Plan &P, const uint8_t *d_seq_sr
             return h->cuda_fail(e, "graph launch");
         G.last_use = ++h->use_tick;
         ++h->graph_replays;
+        h->stats_timed = h->opt.graph >= 1;
         return PMS_OK;
     }
     if (it != h->graphs.end()) {
@@ -1117,11 +1125,16 @@ static void collect_stats(pms_ctx *h)
     if (!h->stats_pending)
         return;
     h->stats_pending = false;
+    pms_stats &s = h->stats;
+    if (!h->stats_timed) {   // a graph replayed without its timing events
+        s.ms_kernel = -1.0;
+        s.ms_verify = -1.0;
+        return;
+    }
     if (cudaEventSynchronize(h->ev1) != cudaSuccess) {
         cudaGetLastError();
         return;
     }
-    pms_stats &s = h->stats;
     if (h->stats_count) {
         unsigned long long c[kCntNum] = {};
         CtrLayout cl(h->stats_k);
@@ -1294,6 +1307,7 @@ static int autotune_class(pms_ctx *h, int n, int m, int l, int d, pms_ctx::Tunin
     h->opt.count_work = 0;
     h->opt.grab = 0;
     h->opt.partial_rows = 0;
+    h->opt.graph = -1;   // every trial timed by its own events, never a graph replay
     std::vector<InstSpec> specs{InstSpec{n, m, l, d, seqs.data()}};
     auto run = [&](const pms_ctx::Tuning &t, double &ms) -> int {
         h->tuned[key] = t;

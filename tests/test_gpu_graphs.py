@@ -1,6 +1,7 @@
 """Captured CUDA graphs of one-instance and batched solves: replays give the same motif
 sets as kernel-by-kernel launches, with each call's own input and output buffers, also
-after the context's buffers were reallocated by a larger instance."""
+after the context's buffers were reallocated by a larger instance. Replays carry the
+device-time events only when pms_options.graph = 1."""
 import numpy as np
 import pytest
 
@@ -36,8 +37,13 @@ def test_graph_replays_match_kernel_by_kernel(oracle_):
             want = k.solve(inst.seqs, l, d)
             assert np.array_equal(g.solve(inst.seqs, l, d), want)
             # new input and output tensors on every call
+            before = g.stats()["graph_replays"]
             assert np.array_equal(_device_solve(g, torch, inst.seqs, l, d), want)
-            assert g.stats()["ms_verify"] > 0
+            if g.stats()["graph_replays"] > before:
+                # a replay without timing events reports no device times
+                assert g.stats()["ms_verify"] == -1.0
+            else:
+                assert g.stats()["ms_verify"] > 0
     small = pi.planted_instance(6, 80, 9, 2, 5)
     assert np.array_equal(g.solve(small.seqs, 9, 2), oracle_.solve(small.seqs, 9, 2))
     g.close()
@@ -87,10 +93,34 @@ def test_batch_graph_replays_match_kernel_by_kernel():
     k.close()
 
 
+def test_timed_graph_replays():
+    # graph = 1: the device-time events are nodes of the graph, so replays report the
+    # verification kernel's time; the motif sets are those of the untimed replays
+    torch = pytest.importorskip("torch")
+    t = pms.Context(0)
+    t.set_options(graph=1)
+    u = pms.Context(0)
+    for seed in (1, 2, 3):
+        inst = pi.plain_instance(15, 4, seed=seed)
+        for call in range(3):
+            got = _device_solve(t, torch, inst.seqs, 15, 4)
+            s = t.stats()
+            assert s["ms_verify"] > 0 and s["ms_kernel"] >= s["ms_verify"], (seed, call)
+            assert np.array_equal(got, _device_solve(u, torch, inst.seqs, 15, 4))
+    assert t.stats()["graph_replays"] >= 4 and u.stats()["graph_replays"] >= 4
+    # a solve launched kernel by kernel (count mode never replays) is always timed
+    u.set_options(count_work=1)
+    u.solve(pi.plain_instance(15, 4, seed=1).seqs, 15, 4)
+    assert u.stats()["ms_verify"] > 0
+    t.close()
+    u.close()
+
+
 def test_graph_option_values():
     c = pms.Context(0)
     c.set_options(graph=-1)
     c.set_options(graph=0)
+    c.set_options(graph=1)
     with pytest.raises(pms.PMSError):
         c.set_options(graph=-2)
     c.close()
