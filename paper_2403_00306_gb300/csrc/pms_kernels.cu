@@ -881,7 +881,7 @@ __device__ __forceinline__ void walk_init(const WarpCtx &c)
     uint32_t *st = c.ws->u.stash;
     st[c.lane] = 0u;
     st[32 + c.lane] = 0u;
-    if (c.lane < 3)
+    if (c.lane < 4)
         st[64 + c.lane] = 0u;
     __syncwarp();
 }
@@ -907,6 +907,7 @@ __device__ __forceinline__ int walk_run(const WarpCtx &c, const int *tab, int g0
     bool has = (w0 >> 31) != 0u;
     int pool_pos = (int)vst[64], pool_n = (int)vst[65];
     bool exhausted = vst[66] != 0u;
+    int left_seen = (int)vst[67] - 1;   // unclaimed nodes after this warp's last claim (-1: none yet)
     int off4 = 0, len4 = 0;
     if (nrows > 0) {
         const int rr = min(r, nrows - 1);
@@ -929,7 +930,11 @@ __device__ __forceinline__ int walk_run(const WarpCtx &c, const int *tab, int g0
                 __syncwarp();
                 if (c.lane < avail)
                     pool[c.lane] = keep;
-                const int want = min(64 - avail, max(4, claim));
+                // guided: claim about half a warp's share of what was left unclaimed
+                // at this warp's last claim, so the item's last nodes stay in the
+                // shared counter instead of in one warp's pool
+                const int share = left_seen < 0 ? claim : (left_seen + 2 * nw - 1) / (2 * nw);
+                const int want = min(64 - avail, max(4, min(claim, share)));
                 int start = 0;
                 if (c.lane == 0) {
                     start = claim_base + atomicAdd(claim_ctr, want);
@@ -941,6 +946,7 @@ __device__ __forceinline__ int walk_run(const WarpCtx &c, const int *tab, int g0
                     }
                 }
                 start = __shfl_sync(kFull, start, 0);
+                left_seen = max(0, g1 - (start + want));
                 const int got = start < g1 ? min(want, g1 - start) : 0;
                 if (start + want >= g1)
                     exhausted = true;
@@ -1041,6 +1047,7 @@ __device__ __forceinline__ int walk_run(const WarpCtx &c, const int *tab, int g0
         st[64] = (uint32_t)pool_pos;
         st[65] = (uint32_t)pool_n;
         st[66] = exhausted ? 1u : 0u;
+        st[67] = (uint32_t)(left_seen + 1);
     }
     __syncwarp();
     return qn;
