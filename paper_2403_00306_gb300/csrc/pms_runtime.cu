@@ -229,6 +229,10 @@ struct pms_ctx {
         cudaGraphExec_t x = nullptr;
         cudaGraphNode_t pack = nullptr, sort = nullptr;
         cudaKernelNodeParams pack_p{}, sort_p{};
+        // the pointers the executable graph holds now (its nodes are updated only when a call's differ)
+        const void *applied_seqs = nullptr;
+        const void *applied_status = nullptr, *applied_dense = nullptr;
+        uint32_t applied_cap = 0;
         struct {
             const void *inst;
             int ninst;
@@ -1012,6 +1016,10 @@ static void capture_graph(pms_ctx *h, const std::string &key, const Plan &P, con
         }
         if (!G.pack || !G.sort)
             e = cudaErrorUnknown;
+        G.applied_seqs = G.input_rows ? G.rv.seqs : G.pv.seqs;
+        G.applied_status = G.sv.status;
+        G.applied_dense = G.sv.dense;
+        G.applied_cap = G.sv.dense_cap;
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1069,6 +1077,9 @@ static int enqueue_plan_graph(pms_ctx *h, const Plan &P, const uint8_t *d_seq_sr
     auto it = h->graphs.find(key);
     if (it != h->graphs.end() && it->second.gen == h->buf_gen) {
         pms_ctx::Graph &G = it->second;
+        const bool new_in = d_seq_src != G.applied_seqs;
+        const bool new_out = status_out != G.applied_status || dense_out != G.applied_dense ||
+                             dense_cap != G.applied_cap;
         G.pv.seqs = d_seq_src;
         G.rv.seqs = d_seq_src;
         G.sv.status = status_out;
@@ -1080,10 +1091,14 @@ static int enqueue_plan_graph(pms_ctx *h, const Plan &P, const uint8_t *d_seq_sr
         sp.kernelParams = G.sort_args;
         sp.extra = nullptr;
         cudaError_t e;
-        if ((e = cudaGraphExecKernelNodeSetParams(G.x, G.pack, &pp)) != cudaSuccess ||
-            (e = cudaGraphExecKernelNodeSetParams(G.x, G.sort, &sp)) != cudaSuccess ||
+        if ((new_in && (e = cudaGraphExecKernelNodeSetParams(G.x, G.pack, &pp)) != cudaSuccess) ||
+            (new_out && (e = cudaGraphExecKernelNodeSetParams(G.x, G.sort, &sp)) != cudaSuccess) ||
             (e = cudaGraphLaunch(G.x, h->stream)) != cudaSuccess)
             return h->cuda_fail(e, "graph launch");
+        G.applied_seqs = d_seq_src;
+        G.applied_status = status_out;
+        G.applied_dense = dense_out;
+        G.applied_cap = dense_cap;
         G.last_use = ++h->use_tick;
         ++h->graph_replays;
         h->stats_timed = h->opt.graph >= 1;
