@@ -216,8 +216,10 @@ cudaError_t sigma_main_occupancy(int b, bool large, int *blocks_per_sm);
 cudaError_t launch_sigma_pack(const uint8_t *seqs, int n, int m, int l, int b, const SigmaMap &map, uint32_t *planes,
                               uint32_t *flags, cudaStream_t st);
 cudaError_t launch_sigma_main(const SigmaParams &p, int blocks, cudaStream_t st);
-cudaError_t launch_sigma_sort_unique(unsigned long long *raw, const unsigned long long *raw_count,
-                                     unsigned long long cap, int l, int b, const SigmaMap &letters, uint8_t *out,
-                                     unsigned long long *unique_count, cudaStream_t st);
+// raw: cap keys of three words; tmp: room for as many (the radix sort's second buffer)
+cudaError_t launch_sigma_sort_unique(unsigned long long *raw, unsigned long long *tmp,
+                                     const unsigned long long *raw_count, unsigned long long cap, int l, int b,
+                                     const SigmaMap &letters, uint8_t *out, unsigned long long *unique_count,
+                                     cudaStream_t st);
 
 }  // namespace pms

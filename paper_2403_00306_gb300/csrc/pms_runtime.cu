@@ -2519,7 +2519,8 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
     uint32_t flags = 0;
     cudaStream_t st = h->stream;
     for (int attempt = 0;; ++attempt) {
-        if ((rc = h->ensure(h->d_sg_raw, (size_t)24 * cap)) || (rc = h->ensure(h->d_sg_out, (size_t)l * cap)))
+        // raw keys (three words each) and, after them, the sort's second buffer
+        if ((rc = h->ensure(h->d_sg_raw, (size_t)48 * cap)) || (rc = h->ensure(h->d_sg_out, (size_t)l * cap)))
             return rc;
         char *c = (char *)h->d_sg_ctr.p;
         SigmaParams p{};
@@ -2550,8 +2551,8 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
                                    (uint32_t *)(c + 24), st)) != cudaSuccess ||
             (e = cudaEventRecord(h->evm0, st)) != cudaSuccess || (e = launch_sigma_main(p, blocks, st)) != cudaSuccess ||
             (e = cudaEventRecord(h->evm1, st)) != cudaSuccess ||
-            (e = launch_sigma_sort_unique(p.raw, p.raw_count, cap, l, b, letters, (uint8_t *)h->d_sg_out.p,
-                                          (unsigned long long *)(c + 16), st)) != cudaSuccess ||
+            (e = launch_sigma_sort_unique(p.raw, p.raw + 3 * cap, p.raw_count, cap, l, b, letters,
+                                          (uint8_t *)h->d_sg_out.p, (unsigned long long *)(c + 16), st)) != cudaSuccess ||
             (e = cudaEventRecord(h->ev1, st)) != cudaSuccess ||
             (e = cudaMemcpyAsync(h_ctr, c, ctr_bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
             (e = cudaStreamSynchronize(st)) != cudaSuccess)

@@ -928,21 +928,111 @@ __host__ __device__ inline bool sg_less(const unsigned long long *a, const unsig
     return a[2] < b[2];
 }
 
-// One CTA: bitonic sort of the raw keys (padded with all-ones keys to a power
-// of two, within the buffer's power-of-two capacity), then unique + decode into
-// l letters per motif.
-__global__ void __launch_bounds__(kSigSortThreads) sigma_sort_unique_kernel(
-    unsigned long long *__restrict__ raw, const unsigned long long *__restrict__ raw_count, unsigned long long cap,
-    int l, int b, SigmaMap letters, uint8_t *__restrict__ out, unsigned long long *__restrict__ unique_count)
+// Largest output sorted by the bitonic network; more keys take the radix sort.
+constexpr unsigned long long kSigBitonicMax = 4096;
+// Shared memory of the radix sort: per-warp digit counts and offsets of a tile, and the 256 bin starts.
+constexpr size_t kSigSortSmem = (2 * (kSigSortThreads / 32) * 256 + 256) * sizeof(unsigned int);
+
+// Stable LSD radix sort (8-bit digits) of n keys of three words by one CTA,
+// over the key's low `bits` bits (bit i in word 2 - i / 64; a digit never
+// straddles two words). Ping-pongs between a and t; returns the buffer that
+// holds the sorted keys.
+__device__ unsigned long long *sg_radix_sort(unsigned long long *a, unsigned long long *t, unsigned int n, int bits,
+                                             unsigned int *smem)
 {
+    const int nw = (int)(blockDim.x >> 5);
+    unsigned int *cnt = smem;              // [nw][256] per-warp digit counts of a tile
+    unsigned int *off = smem + nw * 256;   // [nw][256] per-warp digit offsets of a tile
+    unsigned int *bin = smem + 2 * nw * 256;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned int lt = (1u << lane) - 1u;
+    unsigned long long *src = a, *dst = t;
+    for (int shift = 0; shift < bits; shift += 8) {
+        const int word = 2 - (shift >> 6), sh = shift & 63;
+        for (int i = threadIdx.x; i < 2 * nw * 256 + 256; i += blockDim.x)
+            smem[i] = 0u;
+        __syncthreads();
+        for (unsigned int i = threadIdx.x; i < n; i += blockDim.x)
+            atomicAdd(&bin[(unsigned int)(src[3 * i + word] >> sh) & 255u], 1u);
+        __syncthreads();
+        if (warp == 0) {
+            unsigned int run = 0;
+            for (int b0 = 0; b0 < 256; b0 += 32) {
+                const unsigned int v = bin[b0 + lane];
+                unsigned int incl = v;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o)
+                        incl += y;
+                }
+                bin[b0 + lane] = run + incl - v;
+                run += __shfl_sync(0xFFFFFFFFu, incl, 31);
+            }
+        }
+        __syncthreads();
+        for (unsigned int t0 = 0; t0 < n; t0 += blockDim.x) {
+            const unsigned int i = t0 + threadIdx.x;
+            const bool valid = i < n;
+            unsigned long long k0 = 0, k1 = 0, k2 = 0;
+            unsigned int dig = 256u;
+            if (valid) {
+                k0 = src[3 * i];
+                k1 = src[3 * i + 1];
+                k2 = src[3 * i + 2];
+                const unsigned long long w = word == 0 ? k0 : (word == 1 ? k1 : k2);
+                dig = (unsigned int)(w >> sh) & 255u;
+            }
+            const unsigned int peers = __match_any_sync(0xFFFFFFFFu, dig);
+            const unsigned int rank = __popc(peers & lt);
+            if (valid && rank == 0)
+                cnt[warp * 256 + dig] = __popc(peers);
+            __syncthreads();
+            if (threadIdx.x < 256) {
+                unsigned int run = bin[threadIdx.x];
+                for (int w = 0; w < nw; ++w) {
+                    off[w * 256 + threadIdx.x] = run;
+                    run += cnt[w * 256 + threadIdx.x];
+                    cnt[w * 256 + threadIdx.x] = 0u;
+                }
+                bin[threadIdx.x] = run;
+            }
+            __syncthreads();
+            if (valid) {
+                const unsigned int at = off[warp * 256 + dig] + rank;
+                dst[3 * at] = k0;
+                dst[3 * at + 1] = k1;
+                dst[3 * at + 2] = k2;
+            }
+            __syncthreads();
+        }
+        unsigned long long *x = src;
+        src = dst;
+        dst = x;
+    }
+    return src;
+}
+
+// One CTA: the raw keys sorted (up to kSigBitonicMax keys by a bitonic
+// network padded with all-ones keys to a power of two, within the buffer's
+// power-of-two capacity; more by the radix sort through tmp, the buffer's
+// second half), then unique + decode into l letters per motif.
+__global__ void __launch_bounds__(kSigSortThreads) sigma_sort_unique_kernel(
+    unsigned long long *raw, unsigned long long *tmp, const unsigned long long *__restrict__ raw_count, unsigned long long cap, int l, int b, SigmaMap letters,
+    uint8_t *__restrict__ out, unsigned long long *__restrict__ unique_count)
+{
+    extern __shared__ unsigned int sg_sort_smem[];
     __shared__ unsigned int s_warp[kSigSortThreads / 32];
     __shared__ unsigned int s_total;
     __shared__ unsigned long long s_base;
     const int tid = threadIdx.x, nt = blockDim.x;
     const unsigned long long N = *raw_count < cap ? *raw_count : cap;
+    if (N > kSigBitonicMax)
+        raw = sg_radix_sort(raw, tmp, (unsigned int)N, l * b, sg_sort_smem);
     unsigned long long P2 = 1;
-    while (P2 < N)
+    while (P2 < N && N <= kSigBitonicMax)
         P2 <<= 1;
+    if (N > kSigBitonicMax)
+        P2 = 1;   // sorted already: no network
     for (unsigned long long i = tid; i < P2; i += nt)
         if (i >= N)
             raw[3 * i] = raw[3 * i + 1] = raw[3 * i + 2] = ~0ull;
@@ -1033,6 +1123,9 @@ cudaError_t sigma_init_tables()
     cudaError_t e = cudaMemcpyToSymbol(c_sg_binom, h_sg_binom, sizeof h_sg_binom);
     if (e != cudaSuccess)
         return e;
+    e = cudaFuncSetAttribute(sigma_sort_unique_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSigSortSmem);
+    if (e != cudaSuccess)
+        return e;
     return cudaFuncSetAttribute(sigma_main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSigSmemLarge);
 }
 
@@ -1059,11 +1152,13 @@ cudaError_t launch_sigma_main(const SigmaParams &p, int blocks, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_sigma_sort_unique(unsigned long long *raw, const unsigned long long *raw_count,
-                                     unsigned long long cap, int l, int b, const SigmaMap &letters, uint8_t *out,
-                                     unsigned long long *unique_count, cudaStream_t st)
+cudaError_t launch_sigma_sort_unique(unsigned long long *raw, unsigned long long *tmp,
+                                     const unsigned long long *raw_count, unsigned long long cap, int l, int b,
+                                     const SigmaMap &letters, uint8_t *out, unsigned long long *unique_count,
+                                     cudaStream_t st)
 {
-    sigma_sort_unique_kernel<<<1, kSigSortThreads, 0, st>>>(raw, raw_count, cap, l, b, letters, out, unique_count);
+    sigma_sort_unique_kernel<<<1, kSigSortThreads, kSigSortSmem, st>>>(raw, tmp, raw_count, cap, l, b, letters, out,
+                                                                       unique_count);
     return cudaGetLastError();
 }
 

@@ -133,6 +133,17 @@ def test_overflow_grows_once_then_reports(ctx, oracle_):
         ctx.set_options(max_motifs=0)
 
 
+def test_large_output_with_keys_over_two_words(ctx, oracle_):
+    # n = 1 over the twenty amino acids, l = 16: keys of 80 bits (two of the three words),
+    # about 130,000 raw keys, so the sort takes its radix form
+    rng = np.random.default_rng(11)
+    seqs = np.frombuffer(bytes(rng.choice(np.frombuffer(PROTEIN.encode(), np.uint8), 18)), np.uint8).reshape(1, 18)
+    want = oracle_.sigma_solve(seqs, 16, 2, PROTEIN, cap=1 << 22)
+    got = ctx.solve_sigma(seqs, 16, 2, PROTEIN)
+    assert len(want) > 100000
+    assert np.array_equal(got, want)
+
+
 def test_invalid_inputs(ctx):
     import paper_2403_00306_gb300 as pms
     inst = pi.planted_instance_sigma(4, 30, 6, 2, 3)
