@@ -202,7 +202,7 @@ struct SigmaParams {
     unsigned long long *raw_count; // keys emitted (may exceed raw_cap)
     unsigned long long raw_cap;    // keys the raw buffer holds (a power of two)
     unsigned long long *counters;  // kSgCntNum
-    uint32_t *scratch;             // per CTA (1 + b) * scratch_rows words, for seeds whose rows exceed smem_rows
+    uint32_t *scratch;             // per CTA (1 + b) * scratch_rows words (scratch_rows even), for seeds whose rows exceed smem_rows
     int scratch_rows;
     int smem_rows;                 // rows a seed keeps in shared memory
     uint32_t *lists;               // per warp list_cap words: row lists of the depth-first search (may be null)
@@ -210,9 +210,10 @@ struct SigmaParams {
 };
 
 int sigma_planes(int sigma);
-int sigma_smem_rows(int b, bool large);
+size_t sigma_row_bytes(int b, int l);   // shared or scratch bytes of one seed row
+int sigma_smem_rows(int b, int l, bool large);
 cudaError_t sigma_init_tables();
-cudaError_t sigma_main_occupancy(int b, bool large, int *blocks_per_sm);
+cudaError_t sigma_main_occupancy(int b, int l, bool large, int *blocks_per_sm);
 cudaError_t launch_sigma_pack(const uint8_t *seqs, int n, int m, int l, int b, const SigmaMap &map, uint32_t *planes,
                               uint32_t *flags, cudaStream_t st);
 cudaError_t launch_sigma_main(const SigmaParams &p, int blocks, cudaStream_t st);

@@ -2473,14 +2473,15 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
         for (int j = 0; j <= std::min(2 * d, l); ++j)
             p_row += (double)binom(l, j) * std::pow(pm, j) * std::pow(1.0 - pm, l - j);
     }
-    const bool large = p_row * max_rows > 0.8 * sigma_smem_rows(b, false);
+    const bool large = p_row * max_rows > 0.8 * sigma_smem_rows(b, l, false);
     int occ = 0;
-    if ((e = sigma_main_occupancy(b, large, &occ)) != cudaSuccess)
+    if ((e = sigma_main_occupancy(b, l, large, &occ)) != cudaSuccess)
         return h->cuda_fail(e, "occupancy");
     occ = std::max(occ, 1);
     const int per_sm = h->opt.ctas_per_sm > 0 ? std::min(h->opt.ctas_per_sm, occ) : occ;
     int blocks = (int)std::max(1LL, std::min<long long>((long long)h->num_sms * per_sm, nseeds));
-    const int smem_rows = sigma_smem_rows(b, large);
+    const int smem_rows = sigma_smem_rows(b, l, large);
+    const int scratch_rows = (max_rows + 1) & ~1;   // even: packed rows are 8-byte words
     if (max_rows > smem_rows) {
         // every CTA may need global scratch for a seed's rows: keep it within 2 GiB
         // (the persistent CTAs take seeds from a queue, so fewer CTAs only take longer);
@@ -2491,7 +2492,7 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
             if (v > 0 && v < cap_bytes)
                 cap_bytes = (size_t)v;
         }
-        const size_t per_cta = (size_t)4 * (1 + b) * max_rows;
+        const size_t per_cta = (size_t)4 * (1 + b) * scratch_rows;
         blocks = (int)std::max<size_t>(1, std::min<size_t>(blocks, cap_bytes / per_cta));
     }
     const size_t NW = (size_t)n * W;
@@ -2502,7 +2503,7 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
     if ((rc = h->ensure(h->d_sg_seqs, nm)) || (rc = h->ensure(h->d_sg_planes, (size_t)4 * b * NW)) ||
         (rc = h->ensure(h->d_sg_ctr, ctr_bytes)))
         return rc;
-    if (max_rows > smem_rows && (rc = h->ensure(h->d_sg_scratch, (size_t)4 * blocks * (1 + b) * max_rows)))
+    if (max_rows > smem_rows && (rc = h->ensure(h->d_sg_scratch, (size_t)4 * blocks * (1 + b) * scratch_rows)))
         return rc;
     // per warp: the row lists of the search's depths (nodes whose lists would not fit keep the
     // search without them; without room for the buffer within the budget, every node does)
@@ -2541,7 +2542,7 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
         p.raw_cap = cap;
         p.counters = (unsigned long long *)(c + 32);
         p.scratch = max_rows > smem_rows ? (uint32_t *)h->d_sg_scratch.p : nullptr;
-        p.scratch_rows = max_rows;
+        p.scratch_rows = scratch_rows;
         p.smem_rows = smem_rows;
         p.lists = list_cap > 0 ? (uint32_t *)h->d_sg_lists.p : nullptr;
         p.list_cap = list_cap;

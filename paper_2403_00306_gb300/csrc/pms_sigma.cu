@@ -138,16 +138,46 @@ __host__ __device__ inline uint32_t sg_unrank(long long r, int l)
     return P;
 }
 
+// Rows hold their b planes in one 64-bit word (plane g at bits g l .. g l + l - 1)
+// when that fits and saves room: 12 bytes a row instead of 4 (1 + b).
+__host__ __device__ inline bool sg_packed_rows(int b, int l)
+{
+    return b >= 2 && b * l <= 64;
+}
+
 // One seed's rows as the node search reads them.
 struct SgSeed {
     const uint32_t *D;    // row e: mismatch mask against x
-    const uint32_t *Pl;   // row e: plane g at Pl[g * stride + e]
+    const uint32_t *Pl;   // unpacked rows: row e's plane g at Pl[g * stride + e]
+    const unsigned long long *Pk;   // packed rows: row e's planes in Pk[e]
+    bool packed;
     int stride;
     const int *off;       // rows of sequence i: [off[i], off[i + 1]); the seed's own sequence has none
     int n, l, d, b, miss_max, sx;
     uint32_t full;        // the sigma letter bits
     uint32_t x[kSigMaxPlanes];
 };
+
+// plane g of row e
+__host__ __device__ inline uint32_t sg_plane(const SgSeed &S, int g, int e)
+{
+    if (S.packed)
+        return (uint32_t)(S.Pk[e] >> (g * S.l)) & (S.l == 32 ? 0xFFFFFFFFu : (1u << S.l) - 1u);
+    return S.Pl[g * S.stride + e];
+}
+
+// letter index of row e at position p
+__host__ __device__ inline int sg_row_letter(const SgSeed &S, int e, int p)
+{
+    if (S.packed) {
+        const unsigned long long w = S.Pk[e] >> p;
+        int a = 0;
+        for (int g = 0; g < S.b; ++g)
+            a |= (int)((w >> (g * S.l)) & 1ull) << g;
+        return a;
+    }
+    return sg_letter_at(S.Pl + e, S.stride, S.b, p);
+}
 
 // Work of one node by one thread (32-bit; summed over the warp into 64-bit counters after each node).
 struct SgCount {
@@ -218,7 +248,7 @@ __host__ __device__ inline int sg_seq_find(const SgSeed &S, const G &grp, int i,
                 ct.verify++;
                 uint32_t mm = 0;
                 for (int g = 0; g < S.b; ++g)
-                    mm |= c[g] ^ S.Pl[g * S.stride + e];
+                    mm |= c[g] ^ sg_plane(S, g, e);
                 hit = sg_popc(mm & keep) <= S.d;
             }
         }
@@ -252,7 +282,7 @@ __host__ __device__ inline bool sg_check(const SgSeed &S, const G &grp, uint32_t
             ct.verify++;
             uint32_t mm = 0;
             for (int g = 0; g < S.b; ++g)
-                mm |= c[g] ^ S.Pl[g * S.stride + w];
+                mm |= c[g] ^ sg_plane(S, g, w);
             hit = sg_popc(mm & keep) <= S.d;
         }
         if (!hit) {
@@ -503,7 +533,7 @@ __host__ __device__ void sg_dfs_rows(const SgSeed &S, const G &grp, int k, SgSta
                 seq = (int)((v >> kSgListRowBits) & 63u);
                 allow = ((int)(v >> 27) < S.d || !((S.D[e] >> p0) & 1u))
                             ? ~0u
-                            : 1u << sg_letter_at(S.Pl + e, S.stride, S.b, p0);
+                            : 1u << sg_row_letter(S, e, p0);
             }
             sg_allow_into(st, grp, j < n0, seq, allow);
         }
@@ -539,7 +569,7 @@ __host__ __device__ void sg_dfs_rows(const SgSeed &S, const G &grp, int k, SgSta
                 int dist = (int)(v >> 27);
                 if ((S.D[e] >> p) & 1u) {
                     ct.verify++;
-                    dist += sg_letter_at(S.Pl + e, S.stride, S.b, p) != a ? 1 : 0;
+                    dist += sg_row_letter(S, e, p) != a ? 1 : 0;
                 }
                 keep = dist <= S.d;
                 v = (v & ((1u << 27) - 1u)) | ((uint32_t)dist << 27);
@@ -548,7 +578,7 @@ __host__ __device__ void sg_dfs_rows(const SgSeed &S, const G &grp, int k, SgSta
                     if (track)
                         allow = (dist < S.d || !((S.D[e] >> pn) & 1u))
                                     ? ~0u
-                                    : 1u << sg_letter_at(S.Pl + e, S.stride, S.b, pn);
+                                    : 1u << sg_row_letter(S, e, pn);
                 }
             }
             const uint32_t bal = grp.ballot(keep);
@@ -664,7 +694,7 @@ __host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCo
                         const int p = sg_ctz(M);
                         M &= M - 1;
                         grp.or_into(&st.L[sg_popc(P & ((1u << p) - 1u))],
-                                    1u << sg_letter_at(S.Pl + e, S.stride, S.b, p));
+                                    1u << sg_row_letter(S, e, p));
                     }
                 }
             }
@@ -708,7 +738,7 @@ __host__ __device__ void sg_node(const SgSeed &S, const G &grp, uint32_t P, SgCo
                 continue;
             grp.sync();
             for (int t = 0; t < k; ++t)
-                st.wl[t] = ((De >> st.pos[t]) & 1u) ? sg_letter_at(S.Pl + e, S.stride, S.b, st.pos[t]) : -1;
+                st.wl[t] = ((De >> st.pos[t]) & 1u) ? sg_row_letter(S, e, st.pos[t]) : -1;
             wit[piv] = e;
             grp.sync();
             sg_dfs(S, grp, P, k, st, true, slack, ct, sink, wit, fail);
@@ -785,7 +815,7 @@ __global__ void sigma_pack_kernel(const uint8_t *__restrict__ seqs, int n, int m
 // tree nodes of the seed, claimed one at a time by the CTA's warps.
 __global__ void __launch_bounds__(kSigThreads, 3) sigma_main_kernel(SigmaParams p)
 {
-    extern __shared__ uint32_t sg_rows_smem[];
+    extern __shared__ __align__(16) uint32_t sg_rows_smem[];
     __shared__ int s_cnt[kNMax], s_cur[kNMax], s_off[kNMax + 1];
     __shared__ int s_seed, s_skip;
     __shared__ unsigned long long s_next;
@@ -843,6 +873,7 @@ __global__ void __launch_bounds__(kSigThreads, 3) sigma_main_kernel(SigmaParams 
         __syncthreads();
         if (!s_skip) {
             const int total = s_off[p.n];
+            const bool packed = sg_packed_rows(p.b, p.l);
             uint32_t *rows;
             int stride;
             if (total <= p.smem_rows) {
@@ -865,13 +896,22 @@ __global__ void __launch_bounds__(kSigThreads, 3) sigma_main_kernel(SigmaParams 
                 if (__popc(mm) <= 2 * p.d) {
                     const int e = atomicAdd(&s_cur[i], 1);
                     rows[e] = mm;
-                    for (int g = 0; g < p.b; ++g)
-                        rows[(size_t)(1 + g) * stride + e] = pl[g];
+                    if (packed) {
+                        unsigned long long pk = 0;
+                        for (int g = 0; g < p.b; ++g)
+                            pk |= (unsigned long long)pl[g] << (g * p.l);
+                        reinterpret_cast<unsigned long long *>(rows + stride)[e] = pk;
+                    } else {
+                        for (int g = 0; g < p.b; ++g)
+                            rows[(size_t)(1 + g) * stride + e] = pl[g];
+                    }
                 }
             }
             __syncthreads();
             S.D = rows;
             S.Pl = rows + stride;
+            S.Pk = reinterpret_cast<const unsigned long long *>(rows + stride);   // stride is even
+            S.packed = packed;
             S.stride = stride;
             S.off = s_off;
             S.n = p.n;
@@ -1110,9 +1150,14 @@ int sigma_planes(int sigma)
     return g;
 }
 
-int sigma_smem_rows(int b, bool large)
+size_t sigma_row_bytes(int b, int l)
 {
-    return (large ? kSigSmemLarge : kSigSmemSmall) / (4 * (1 + b));
+    return sg_packed_rows(b, l) ? 12 : (size_t)4 * (1 + b);
+}
+
+int sigma_smem_rows(int b, int l, bool large)
+{
+    return (int)((large ? kSigSmemLarge : kSigSmemSmall) / sigma_row_bytes(b, l)) & ~1;   // even: 8-byte packed words
 }
 
 cudaError_t sigma_init_tables()
@@ -1129,9 +1174,9 @@ cudaError_t sigma_init_tables()
     return cudaFuncSetAttribute(sigma_main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSigSmemLarge);
 }
 
-cudaError_t sigma_main_occupancy(int b, bool large, int *blocks_per_sm)
+cudaError_t sigma_main_occupancy(int b, int l, bool large, int *blocks_per_sm)
 {
-    const size_t smem = (size_t)4 * (1 + b) * sigma_smem_rows(b, large);
+    const size_t smem = sigma_row_bytes(b, l) * sigma_smem_rows(b, l, large);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sigma_main_kernel, kSigThreads, smem);
 }
 
@@ -1147,7 +1192,7 @@ cudaError_t launch_sigma_pack(const uint8_t *seqs, int n, int m, int l, int b, c
 
 cudaError_t launch_sigma_main(const SigmaParams &p, int blocks, cudaStream_t st)
 {
-    const size_t smem = (size_t)4 * (1 + p.b) * p.smem_rows;
+    const size_t smem = sigma_row_bytes(p.b, p.l) * p.smem_rows;
     sigma_main_kernel<<<blocks, kSigThreads, smem, st>>>(p);
     return cudaGetLastError();
 }

@@ -5,7 +5,9 @@
 // Input on stdin: "alphabet n m l d q" then the n sequences; or "unrank l d",
 // which prints the position subset (as a bit mask) of every node rank instead.
 // argv[1], if given: the capacity of the group's row-list buffer (0, the
-// default: the depth-first search without row lists).
+// default: the depth-first search without row lists); argv[2], if 1: rows
+// with their planes packed in one 64-bit word where b l <= 64 (the kernel's
+// layout then), else one word per plane.
 #include "../../paper_2403_00306_gb300/csrc/pms_sigma.cu"
 
 #include <algorithm>
@@ -46,6 +48,7 @@ struct HostSink {
 int main(int argc, char **argv)
 {
     const int list_cap = argc > 1 ? atoi(argv[1]) : 0;
+    const bool want_packed = argc > 2 && atoi(argv[2]) != 0;   // packed rows where b and l allow them
     std::vector<uint32_t> list_buf((size_t)std::max(list_cap, 1));
     char alpha[64];
     int n, m, l, d, q;
@@ -129,15 +132,25 @@ int main(int argc, char **argv)
         off[n] = (int)D.size();
         if (misses > n - qe)
             continue;
-        const int stride = std::max<int>(1, (int)D.size());
+        const int stride = (std::max<int>(1, (int)D.size()) + 1) & ~1;
         std::vector<uint32_t> rows((size_t)(1 + b) * stride);
+        const bool packed = want_packed && sg_packed_rows(b, l);
         for (size_t e = 0; e < D.size(); ++e) {
             rows[e] = D[e];
-            for (int g = 0; g < b; ++g)
-                rows[(size_t)(1 + g) * stride + e] = Pl[g][e];
+            if (packed) {
+                unsigned long long pk = 0;
+                for (int g = 0; g < b; ++g)
+                    pk |= (unsigned long long)Pl[g][e] << (g * l);
+                std::memcpy(&rows[stride + 2 * e], &pk, sizeof pk);
+            } else {
+                for (int g = 0; g < b; ++g)
+                    rows[(size_t)(1 + g) * stride + e] = Pl[g][e];
+            }
         }
         S.D = rows.data();
         S.Pl = rows.data() + stride;
+        S.Pk = reinterpret_cast<const unsigned long long *>(rows.data() + stride);
+        S.packed = packed;
         S.stride = stride;
         S.off = off.data();
         S.n = n;

@@ -4,6 +4,7 @@
 // with __ballot_sync / __shfl_sync), sharing the per-warp state and witness
 // rows as the kernel's shared memory does, and splitting every row scan over
 // the 32 lanes. Prints the sorted unique motifs, one per line.
+// argv[2], if 1: packed rows where b l <= 64 (the kernel's layout then).
 // Input on stdin: "alphabet n m l d q" then the n sequences; argv[1], if
 // given: the capacity of the warp's shared row-list buffer (0, the default:
 // the depth-first search without row lists).
@@ -155,6 +156,7 @@ struct HostSink {
 int main(int argc, char **argv)
 {
     const int list_cap = argc > 1 ? atoi(argv[1]) : 0;
+    const bool want_packed = argc > 2 && atoi(argv[2]) != 0;   // packed rows where b and l allow them
     std::vector<uint32_t> list_buf((size_t)std::max(list_cap, 1));   // the warp's, shared by its lanes
     char alpha[64];
     int n, m, l, d, q;
@@ -223,15 +225,25 @@ int main(int argc, char **argv)
         off[n] = (int)D.size();
         if (misses > n - qe)
             continue;
-        const int stride = std::max<int>(1, (int)D.size());
+        const int stride = (std::max<int>(1, (int)D.size()) + 1) & ~1;
         std::vector<uint32_t> rows((size_t)(1 + b) * stride);
+        const bool packed = want_packed && sg_packed_rows(b, l);
         for (size_t e = 0; e < D.size(); ++e) {
             rows[e] = D[e];
-            for (int g = 0; g < b; ++g)
-                rows[(size_t)(1 + g) * stride + e] = Pl[g][e];
+            if (packed) {
+                unsigned long long pk = 0;
+                for (int g = 0; g < b; ++g)
+                    pk |= (unsigned long long)Pl[g][e] << (g * l);
+                std::memcpy(&rows[stride + 2 * e], &pk, sizeof pk);
+            } else {
+                for (int g = 0; g < b; ++g)
+                    rows[(size_t)(1 + g) * stride + e] = Pl[g][e];
+            }
         }
         S.D = rows.data();
         S.Pl = rows.data() + stride;
+        S.Pk = reinterpret_cast<const unsigned long long *>(rows.data() + stride);
+        S.packed = packed;
         S.stride = stride;
         S.off = off.data();
         S.n = n;

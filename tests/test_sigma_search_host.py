@@ -38,10 +38,10 @@ def search(tmp_path_factory):
                     "-diag-suppress", "550", "-I", os.path.join(ROOT, "include"), SRC, "-o", exe],
                    check=True, capture_output=True)
 
-    def run(seqs, l, d, alphabet, q=0, lists=0):
+    def run(seqs, l, d, alphabet, q=0, lists=0, packed=0):
         n, m = seqs.shape
         inp = f"{alphabet} {n} {m} {l} {d} {q}\n" + "\n".join(bytes(r).decode() for r in seqs) + "\n"
-        r = subprocess.run([exe, str(lists)], input=inp, capture_output=True, text=True, check=True)
+        r = subprocess.run([exe, str(lists), str(packed)], input=inp, capture_output=True, text=True, check=True)
         return r.stdout.split()
     run.exe = exe
     return run
@@ -72,13 +72,15 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("lists", [0, 4096, 24])
+# packed = 1: rows in the kernel's packed layout (all planes in one 64-bit word) wherever
+# 2 <= b and b l <= 64, i.e. every case here but sigma = 2 and l = 32
+@pytest.mark.parametrize("lists,packed", [(0, 0), (4096, 0), (24, 0), (0, 1), (4096, 1), (24, 1)])
 @pytest.mark.parametrize("sigma,n,m,l,d,q,seed", CASES)
-def test_host_search_matches_the_oracle(search, oracle_, sigma, n, m, l, d, q, seed, lists):
+def test_host_search_matches_the_oracle(search, oracle_, sigma, n, m, l, d, q, seed, lists, packed):
     alpha = alphabet_of(sigma)
     inst = pi.planted_instance_sigma(n, m, l, d, seed, alpha.encode())
     want = [bytes(r).decode() for r in oracle_.sigma_solve(inst.seqs, l, d, alpha, q=q, cap=1 << 22)]
-    assert search(inst.seqs, l, d, alpha, q, lists) == want
+    assert search(inst.seqs, l, d, alpha, q, lists, packed) == want
 
 
 def test_host_search_over_acgt_matches_the_dna_oracle(search, oracle_):
@@ -97,6 +99,7 @@ def test_host_search_on_random_backgrounds(search, oracle_):
             want = [bytes(r).decode() for r in oracle_.sigma_solve(seqs, l, d, alpha, q=q, cap=1 << 22)]
             assert search(seqs, l, d, alpha, q) == want, (sigma, n, m, l, d, q)
             assert search(seqs, l, d, alpha, q, 4096) == want, (sigma, n, m, l, d, q, "lists")
+            assert search(seqs, l, d, alpha, q, 4096, 1) == want, (sigma, n, m, l, d, q, "lists, packed")
 
 
 @pytest.fixture(scope="module")
@@ -110,10 +113,11 @@ def lockstep(tmp_path_factory):
                     os.path.join(ROOT, "tests", "host", "sigma_search_lockstep.cu"), "-o", exe],
                    check=True, capture_output=True)
 
-    def run(seqs, l, d, alphabet, q=0, lists=0):
+    def run(seqs, l, d, alphabet, q=0, lists=0, packed=0):
         n, m = seqs.shape
         inp = f"{alphabet} {n} {m} {l} {d} {q}\n" + "\n".join(bytes(r).decode() for r in seqs) + "\n"
-        r = subprocess.run([exe, str(lists)], input=inp, capture_output=True, text=True, check=True, timeout=300)
+        r = subprocess.run([exe, str(lists), str(packed)], input=inp, capture_output=True, text=True, check=True,
+                           timeout=300)
         return r.stdout.split()
     return run
 
@@ -124,10 +128,10 @@ LOCKSTEP_CASES = [(20, 4, 20, 5, 2, 0, 31), (3, 4, 16, 6, 2, 3, 33), (20, 1, 7, 
                   (4, 6, 30, 8, 2, 0, 35), (4, 8, 60, 9, 2, 0, 5)]
 
 
-@pytest.mark.parametrize("lists", [0, 4096])
+@pytest.mark.parametrize("lists,packed", [(0, 0), (4096, 0), (4096, 1)])
 @pytest.mark.parametrize("sigma,n,m,l,d,q,seed", LOCKSTEP_CASES)
-def test_lane_parallel_search_matches_the_oracle(lockstep, oracle_, sigma, n, m, l, d, q, seed, lists):
+def test_lane_parallel_search_matches_the_oracle(lockstep, oracle_, sigma, n, m, l, d, q, seed, lists, packed):
     alpha = alphabet_of(sigma)
     inst = pi.planted_instance_sigma(n, m, l, d, seed, alpha.encode())
     want = [bytes(r).decode() for r in oracle_.sigma_solve(inst.seqs, l, d, alpha, q=q, cap=1 << 22)]
-    assert lockstep(inst.seqs, l, d, alpha, q, lists) == want
+    assert lockstep(inst.seqs, l, d, alpha, q, lists, packed) == want
