@@ -69,11 +69,12 @@ CASES = [
     (2, 6, 40, 10, 2, 0, 1), (3, 5, 30, 7, 3, 4, 4), (4, 8, 60, 9, 2, 0, 5), (7, 5, 40, 6, 2, 3, 7),
     (17, 5, 30, 5, 2, 0, 9), (20, 6, 50, 6, 3, 0, 11), (20, 5, 40, 6, 3, 3, 12), (32, 5, 30, 5, 2, 4, 15),
     (20, 1, 9, 5, 2, 0, 16), (20, 6, 30, 4, 0, 0, 17), (5, 4, 6, 6, 3, 0, 18), (20, 7, 33, 32, 1, 0, 19),
+    (4, 5, 40, 32, 2, 0, 20),   # b l = 64: the packed word exactly full
 ]
 
 
 # packed = 1: rows in the kernel's packed layout (all planes in one 64-bit word) wherever
-# 2 <= b and b l <= 64, i.e. every case here but sigma = 2 and l = 32
+# 2 <= b and b l <= 64, i.e. every case here but sigma = 2 and (20 letters, l = 32)
 @pytest.mark.parametrize("lists,packed", [(0, 0), (4096, 0), (24, 0), (0, 1), (4096, 1), (24, 1)])
 @pytest.mark.parametrize("sigma,n,m,l,d,q,seed", CASES)
 def test_host_search_matches_the_oracle(search, oracle_, sigma, n, m, l, d, q, seed, lists, packed):
