@@ -747,15 +747,11 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
     return P;
 }
 
-// Enqueues the whole pipeline of a plan on h->stream. d_seq_src: device
-// address of the input bytes (internal arena or user memory). Descriptors are
-// staged in h->h_meta and uploaded. Output: status/dense in the result block.
-// Records a timing event; inside a stream capture (a graph's launches) as an
-// external event node, so that every replay records it.
-// Inside a captured graph the device-time events are nodes of their own, and
-// an event node between two kernels costs the launch overlap of the pair
-// (about 17 us per plain (15,4) solve on GB300), so graphs carry them only
-// when pms_options.graph asks for timed replays.
+// Records a timing event. Inside a stream capture (a graph's launches) the
+// event is a node of its own, recorded by every replay; an event node between
+// two kernels costs the launch overlap of the pair (about 17 us per plain
+// (15,4) solve on GB300), so graphs carry them only when pms_options.graph
+// asks for timed replays.
 static void record_event(const pms_ctx *h, cudaEvent_t ev, cudaStream_t st, bool capturing)
 {
     if (!capturing)
@@ -788,6 +784,9 @@ static void fill_meta(const Plan &P, const MetaLayout &ml, char *hm)
     std::memcpy(hm + ml.ctab, P.ctab.data(), P.ctab.size() * sizeof(int));
 }
 
+// Enqueues the whole pipeline of a plan on h->stream. d_seq_src: device
+// address of the input bytes (internal arena or user memory). Descriptors are
+// staged in h->h_meta and uploaded. Output: status/dense in the result block.
 // meta_dev: when given, the plan's descriptors are already on the device
 // there (a captured graph's own copy) and are neither staged nor uploaded.
 static int enqueue_plan(pms_ctx *h, const Plan &P, const uint8_t *d_seq_src, StatusDev *status_out,
