@@ -304,8 +304,10 @@ int pms_autotune(pms_ctx *h, int n, int m, int l, int d, pms_tuning *out);
 int pms_save_tuning(const pms_ctx *h, const char *path);
 int pms_load_tuning(pms_ctx *h, const char *path);
 
-/* Work counters and timing of the last solve (waits for that solve's
- * kernels if they are still running). */
+/* Work counters and timing of the last solve. Waits for that solve's kernels
+ * if they are still running and it recorded device-time events; a graph
+ * replayed with pms_options.graph = 0 records none, and its ms_kernel /
+ * ms_verify read -1 without waiting. */
 int pms_get_stats(const pms_ctx *h, pms_stats *out);
 
 /* Writes the l letters of `code` and a terminating NUL to out (l + 1 bytes). */
