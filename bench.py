@@ -658,14 +658,25 @@ def measure_batch(pms, torch, dev, peaks, args, rank, dist, steps: int = 3) -> d
             "all_ok": ok, "autotune_s": t_tune, "gpu_launches": 4 * steps, "clocks": clk.summary()}
 
 
-def measure_serve(pms, torch, dev, args, rank, dist) -> dict:
-    """Poisson request stream through the served form (continuous batching)."""
+def measure_serve(pms, torch, dev, args, rank, dist, tune: bool = True) -> dict:
+    """Poisson request stream through the served form (continuous batching). With `tune`, every
+    instance class of the stream (l, d, n, m rounded up to a power of two) is autotuned first,
+    untimed, as a service would do once for the shapes it expects."""
     import threading
     from concurrent.futures import ThreadPoolExecutor
 
     count, rate = args.serve_requests, args.serve_rate
     reqs = list(pi.serve_requests(count=count, rate_per_s=rate, master_seed=7 + rank))
     ctx = pms.Context(dev.index)
+    t_tune = time.perf_counter()
+    classes = {}
+    if tune:
+        for _, inst in reqs:
+            key = (inst.l, inst.d, 1 << (inst.n - 1).bit_length(), 1 << (inst.m - 1).bit_length())
+            classes.setdefault(key, inst)
+        for inst in classes.values():
+            ctx.autotune(inst.n, inst.m, inst.l, inst.d)
+    t_tune = time.perf_counter() - t_tune
     for _, inst in reqs[:8]:      # warm-up, not timed
         ctx.wait(ctx.submit(inst.seqs, inst.l, inst.d))
     lat = [None] * count
@@ -723,7 +734,7 @@ def measure_serve(pms, torch, dev, args, rank, dist) -> dict:
             "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[int(len(lat_ms) * 0.99) - 1],
                            "max": lat_ms[-1]},
             "offered_per_s": rate, "saturation_solves_per_s": sat, "saturation_requests": sat_n,
-            "all_ok": all(ok),
+            "all_ok": all(ok), "tuned_classes": len(classes), "autotune_s": t_tune,
             "serve": {"waves": st["serve_waves"], "overlapped_waves": st["serve_overlapped_waves"],
                       "max_requests_per_wave": st["serve_max_requests_per_wave"]},
             "e2e": {"value": solves / span_max, "unit": "solves/s",
