@@ -83,8 +83,11 @@ typedef struct {
                               65536 candidate units (0: about 6.4e9 units) */
     int serve_max_inflight;/* served form: requests resident on the device */
     int smem_rows;         /* at most this many feasible occurrences of a seed are
-                              kept in shared memory (0: as many as fit); larger
-                              row sets are read from global memory */
+                              kept in shared memory (0: as many as fit); a seed
+                              with up to three times as many keeps only their
+                              mismatch masks there and reads their planes from
+                              global memory; larger row sets are read from
+                              global memory */
     int autotune;          /* 1: tune each new instance class before solving it */
     int seed_mode;         /* 0: every seed x of s_1 searches B(x, d) as a tree
                               (Observation 3.1); 1: pair seeds (x in s_1, r in s_2,

@@ -75,7 +75,7 @@ struct __align__(16) CtaSmem {
     int inst, seed, chunk;
     int cached_inst, cached_seed;
     int feasible;
-    int rows_in_smem;
+    int rows_in_smem;        // 1: D and planes in shared memory; 2: D only (planes in global scratch); 0: neither
     int total_rows;
     int next;                // next subset index of the chunk to claim
     int ctab;                // chunk table of the current item
@@ -1376,7 +1376,11 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
         if (lane == 0) {
             cs.total_rows = total;
             cs.feasible = nempty <= in.n - in.q;
-            cs.rows_in_smem = total <= p.smem_rows_cap;
+            // the mismatch masks D, which every node scans, stay in shared memory up
+            // to three times as many entries (the planes' room holds them too); only
+            // the planes of occurrences that pass a node's bound are then read from
+            // the global scratch
+            cs.rows_in_smem = total <= p.smem_rows_cap ? 1 : (total <= 3 * p.smem_rows_cap ? 2 : 0);
             if (cnt)
                 cnt[kCntCmpRows] += (unsigned long long)R * W;
         }
@@ -1384,9 +1388,8 @@ __device__ __forceinline__ void build_rows(const MainParams &p, const InstDev &i
     __syncthreads();
     if (!cs.feasible)
         return;
-    const bool in_smem = cs.rows_in_smem;
-    uint32_t *Dd = in_smem ? smem_D : glob_D;
-    uint2 *Hd = in_smem ? smem_HL : glob_HL;
+    uint32_t *Dd = cs.rows_in_smem != 0 ? smem_D : glob_D;
+    uint2 *Hd = cs.rows_in_smem == 1 ? smem_HL : glob_HL;
     const uint2 *pl = p.planes + in.plane_off;
     const uint2 x = pl[seed];
     const int si = seed / W;   // the seed's own sequence has no row
@@ -1591,7 +1594,7 @@ __global__ void __launch_bounds__(kMainThreads, kMinBlocks) main_kernel(MainPara
         }
         if (cs.feasible) {
             const uint2 x = p.planes[in.plane_off + seed];
-            Rows rows{cs.rows_in_smem ? smem_D : glob_D, cs.rows_in_smem ? smem_HL : glob_HL};
+            Rows rows{cs.rows_in_smem != 0 ? smem_D : glob_D, cs.rows_in_smem == 1 ? smem_HL : glob_HL};
             WarpCtx c{&p, in, I, lane, lt, x.x, x.y, rows, &cs, &wsm[warp], kCount ? cnt : nullptr};
             if (in.q < in.n) {
                 // quorum form: batches of nodes with miss budgets, claimed from the
@@ -2133,7 +2136,7 @@ __global__ void __launch_bounds__(kThreads, 2) pair_kernel(MainParams p)
         if (cs.feasible) {
             const uint2 *pl = p.planes + in.plane_off;
             const uint2 x = pl[seed];
-            Rows rows{cs.rows_in_smem ? smem_D : glob_D, cs.rows_in_smem ? smem_HL : glob_HL};
+            Rows rows{cs.rows_in_smem != 0 ? smem_D : glob_D, cs.rows_in_smem == 1 ? smem_HL : glob_HL};
             WarpCtx c{&p, in, I, lane, lt, x.x, x.y, rows, &cs, &wsm[warp], kCount ? cnt : nullptr};
             // the pairs of this block: set bits of x's s_2 mask words 2 chunk, 2 chunk + 1
             const uint32_t *mrow = p.compat + in.compat_off + (size_t)seed * (in.n - 1) * in.NW;

@@ -74,6 +74,20 @@ def test_plain_whole_motif_set(ctx, name):
     c.close()
 
 
+@pytest.mark.parametrize("smem_rows", [256, 128])
+def test_plain_whole_motif_set_rows_off_chip(smem_rows):
+    # (15,4) seeds hold about 630 feasible occurrences: with 256 entries of shared memory the
+    # mismatch masks stay there and the planes are read from global memory; with 128 both are
+    # read from global memory
+    for name in ("plain15_4_s1", "plain15_4_s2"):
+        g = GOLD[name]
+        inst = pi.plain_instance(g["l"], g["d"], seed=g["seed"])
+        c = pms.Context(0)
+        c.set_options(smem_rows=smem_rows)
+        assert np.array_equal(c.solve(inst.seqs, inst.l, inst.d), _want(name, inst)), (name, smem_rows)
+        c.close()
+
+
 def test_plain_19_6_on_48_seeds(ctx):
     g = GOLD["plain19_6_s1"]
     inst = pi.plain_instance(19, 6, seed=1)
