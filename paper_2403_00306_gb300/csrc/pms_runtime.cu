@@ -650,6 +650,14 @@ static int plan_occ(const pms_ctx *h, int n, int m, int l, int d, bool count_mod
 // Expected feasible occurrences of one seed of a uniform i.i.d. instance:
 // (n - 1) rows of W windows, each within 2d of the seed with probability
 // P(Binomial(l, 3/4) <= 2d), plus the rows' padding.
+// Expected feasible occurrences per seed up to which a plan takes the
+// verification kernel's 4-CTA form (1280 entries in shared memory; seeds with
+// up to three times as many keep their mismatch masks there and read the
+// planes of passing occurrences from global memory). Measured: (19,6), about
+// 1900 per seed, 12.1 -> 11.3 ms in this form; (13,4) at m = 600, about 2400
+// per seed, 1.70 -> 1.75 ms, so it keeps the 3-CTA form with 2560 entries.
+constexpr double kSmallFormRows = 1.6 * kRowSmemCapSmall;
+
 static double expected_seed_rows(int n, int m, int l, int d)
 {
     double p = 0, c = 1;
@@ -668,7 +676,7 @@ static Plan make_plan(pms_ctx *h, const std::vector<InstSpec> &specs)
     // planted copies, read their rows from the CTA's global scratch)
     P.small_rows = h->occ_small[0] > h->occ[0];
     for (const InstSpec &s : specs)
-        if (expected_seed_rows(s.n, s.m, s.l, s.d) > kRowSmemCapSmall)
+        if (expected_seed_rows(s.n, s.m, s.l, s.d) > kSmallFormRows)
             P.small_rows = false;
     long long work = 0;
     const int adaptive = kDefaultChunkWork;   // untuned classes: about 2^20 candidate units per queue item
@@ -1340,7 +1348,7 @@ static int autotune_class(pms_ctx *h, int n, int m, int l, int d, pms_ctx::Tunin
     cur.chunk_work = kDefaultChunkWork;
     cur.prune_rows = n - 1;
     // resident CTAs of the kernel form this class's plans use
-    const bool small = h->occ_small[0] > h->occ[0] && expected_seed_rows(n, m, l, d) <= kRowSmemCapSmall;
+    const bool small = h->occ_small[0] > h->occ[0] && expected_seed_rows(n, m, l, d) <= kSmallFormRows;
     const int occ0 = std::max(1, small ? h->occ_small[0] : h->occ[0]);
     cur.ctas_per_sm = occ0;
     cur.partial_rows = default_partial_rows(n, m, l, d);
