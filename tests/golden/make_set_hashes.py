@@ -56,7 +56,7 @@ def served_sample() -> list[int]:
 def entries():
     for k, inst in enumerate(pi.batch_instances(count=256, master_seed=2024)):
         yield f"batch2024_{k}", {"kind": "batch", "index": k, "master_seed": 2024}, inst
-    reqs = pi.serve_requests(count=10000, master_seed=7)
+    reqs = list(pi.serve_requests(count=10000, master_seed=7))
     for k in served_sample():
         yield f"serve7_r{k}", {"kind": "serve", "index": k, "master_seed": 7}, reqs[k][1]
 
