@@ -204,7 +204,10 @@ int pms_get_options(const pms_ctx *h, pms_options *opt);
  * candidate set is the union of B(x, d) over the l-mers x of s_1,
  * Observation 3.1). seqs: host, read only during the call. On success
  * *motifs points to *count sorted unique codes owned by h (valid until the
- * next solve on h or pms_destroy). Blocks until the result is on the host. */
+ * next solve on h or pms_destroy). Blocks until the result is on the host.
+ * Bytes other than A/C/G/T are detected by the packing kernel: the call
+ * then returns PMS_EINVAL, with *count = 0, and pms_last_error names the
+ * first such byte. */
 int pms_solve(pms_ctx *h, const uint8_t *seqs, int n, int m, int l, int d,
               const uint64_t **motifs, size_t *count);
 

@@ -217,10 +217,23 @@ cudaError_t sigma_main_occupancy(int b, int l, bool large, int *blocks_per_sm);
 cudaError_t launch_sigma_pack(const uint8_t *seqs, int n, int m, int l, int b, const SigmaMap &map, uint32_t *planes,
                               uint32_t *flags, cudaStream_t st);
 cudaError_t launch_sigma_main(const SigmaParams &p, int blocks, cudaStream_t st);
+// Device state of the sort/unique kernel's CTAs (one grid, all CTAs resident):
+// hist holds sigma_sort_hist_words(ctas) words (per-CTA digit counts, digit
+// totals, per-CTA unique counts); bar two words, zeroed before the launch.
+// bar[1] != 0 after the launch: a CTA gave up waiting at a grid barrier and
+// the output is not valid.
+struct SigSortGrid {
+    unsigned int *hist;
+    unsigned int *bar;
+    int ctas;
+};
+size_t sigma_sort_hist_words(int ctas);
+// CTAs of the sort/unique grid on the current device (all resident at once).
+cudaError_t sigma_sort_ctas(int *ctas);
 // raw: cap keys of three words; tmp: room for as many (the radix sort's second buffer)
 cudaError_t launch_sigma_sort_unique(unsigned long long *raw, unsigned long long *tmp,
                                      const unsigned long long *raw_count, unsigned long long cap, int l, int b,
                                      const SigmaMap &letters, uint8_t *out, unsigned long long *unique_count,
-                                     cudaStream_t st);
+                                     const SigSortGrid &grid, cudaStream_t st);
 
 }  // namespace pms

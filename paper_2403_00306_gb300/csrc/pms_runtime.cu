@@ -202,8 +202,9 @@ struct pms_ctx {
     };
     DBuf d_seqs, d_planes, d_raw, d_tmp, d_compat, d_rowlen, d_mode, d_meta, d_ctr, d_scratch, d_result;
     // general-alphabet solves (pms_solve_sigma)
-    DBuf d_sg_seqs, d_sg_planes, d_sg_ctr, d_sg_raw, d_sg_out, d_sg_scratch, d_sg_lists;
+    DBuf d_sg_seqs, d_sg_planes, d_sg_ctr, d_sg_raw, d_sg_out, d_sg_scratch, d_sg_lists, d_sg_hist;
     bool sigma_ready = false;   // binomial table and kernel attributes loaded on the device
+    int sg_sort_ctas = 1;       // CTAs of the sort/unique grid
     void *h_sg = nullptr;       // pinned: counters block, then the input letters
     size_t h_sg_cap = 0;
     std::vector<uint8_t> owned_sigma;   // letters returned by the last pms_solve_sigma
@@ -2056,8 +2057,10 @@ int pms_solve(pms_ctx *h, const uint8_t *seqs, int n, int m, int l, int d, const
     *motifs = nullptr;
     *count = 0;
     int rc;
-    if ((rc = check_params(h, n, m, l, d)) || (rc = check_bytes(h, seqs, (size_t)n * m)))
+    if ((rc = check_params(h, n, m, l, d)))
         return rc;
+    // The packing kernels flag bytes other than A/C/G/T in the instance's
+    // status; only then are the bytes scanned here, to name the first one.
     cudaSetDevice(h->device);
     std::vector<InstSpec> specs{InstSpec{n, m, l, d, seqs}};
     std::vector<InstOut> res;
@@ -2072,8 +2075,14 @@ int pms_solve(pms_ctx *h, const uint8_t *seqs, int n, int m, int l, int d, const
         *count = res[0].raw_count;
         return h->fail(rc, "%u motifs (with duplicates) exceed the capacity; raise max_motifs", res[0].raw_count);
     }
-    if (rc)
+    if (rc) {
+        h->owned[0].clear();
+        *motifs = nullptr;
+        *count = 0;
+        if (rc == PMS_EINVAL && check_bytes(h, seqs, (size_t)n * m))
+            return PMS_EINVAL;
         return h->fail(rc, "invalid input byte");
+    }
     return PMS_OK;
 }
 
@@ -2460,7 +2469,7 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
     cudaSetDevice(h->device);
     cudaError_t e;
     if (!h->sigma_ready) {
-        if ((e = sigma_init_tables()) != cudaSuccess)
+        if ((e = sigma_init_tables()) != cudaSuccess || (e = sigma_sort_ctas(&h->sg_sort_ctas)) != cudaSuccess)
             return h->cuda_fail(e, "general-alphabet tables");
         h->sigma_ready = true;
     }
@@ -2503,12 +2512,14 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
         blocks = (int)std::max<size_t>(1, std::min<size_t>(blocks, cap_bytes / per_cta));
     }
     const size_t NW = (size_t)n * W;
-    const size_t ctr_bytes = 32 + 8 * (size_t)kSgCntNum;   // head, raw count, unique count, flags, work counters
+    // head, raw count, unique count, flags, work counters, the sort's grid barrier (2 words)
+    const size_t bar_off = 32 + 8 * (size_t)kSgCntNum, ctr_bytes = bar_off + 8;
     const bool capped = h->opt.max_motifs > 0;
     unsigned long long cap = pow2_at_least(capped ? h->opt.max_motifs : ((size_t)1 << 16));
     constexpr unsigned long long kRetryMax = 1ull << 22;
     if ((rc = h->ensure(h->d_sg_seqs, nm)) || (rc = h->ensure(h->d_sg_planes, (size_t)4 * b * NW)) ||
-        (rc = h->ensure(h->d_sg_ctr, ctr_bytes)))
+        (rc = h->ensure(h->d_sg_ctr, ctr_bytes)) ||
+        (rc = h->ensure(h->d_sg_hist, 4 * sigma_sort_hist_words(h->sg_sort_ctas))))
         return rc;
     if (max_rows > smem_rows && (rc = h->ensure(h->d_sg_scratch, (size_t)4 * blocks * (1 + b) * scratch_rows)))
         return rc;
@@ -2524,7 +2535,7 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
     char *h_ctr = (char *)h->h_sg;
     memcpy(h_ctr + 256, seqs, nm);
     unsigned long long raw = 0, uniq = 0, ctr[kSgCntNum] = {};
-    uint32_t flags = 0;
+    uint32_t flags = 0, bar[2] = {};
     cudaStream_t st = h->stream;
     for (int attempt = 0;; ++attempt) {
         // raw keys (three words each) and, after them, the sort's second buffer
@@ -2560,7 +2571,10 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
             (e = cudaEventRecord(h->evm0, st)) != cudaSuccess || (e = launch_sigma_main(p, blocks, st)) != cudaSuccess ||
             (e = cudaEventRecord(h->evm1, st)) != cudaSuccess ||
             (e = launch_sigma_sort_unique(p.raw, p.raw + 3 * cap, p.raw_count, cap, l, b, letters,
-                                          (uint8_t *)h->d_sg_out.p, (unsigned long long *)(c + 16), st)) != cudaSuccess ||
+                                          (uint8_t *)h->d_sg_out.p, (unsigned long long *)(c + 16),
+                                          SigSortGrid{(unsigned int *)h->d_sg_hist.p, (unsigned int *)(c + bar_off),
+                                                      h->sg_sort_ctas},
+                                          st)) != cudaSuccess ||
             (e = cudaEventRecord(h->ev1, st)) != cudaSuccess ||
             (e = cudaMemcpyAsync(h_ctr, c, ctr_bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
             (e = cudaStreamSynchronize(st)) != cudaSuccess)
@@ -2569,6 +2583,9 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
         memcpy(&uniq, h_ctr + 16, 8);
         memcpy(&flags, h_ctr + 24, 4);
         memcpy(ctr, h_ctr + 32, sizeof ctr);
+        memcpy(bar, h_ctr + bar_off, sizeof bar);
+        if (bar[1] != 0)
+            return h->fail(PMS_ECUDA, "general-alphabet sort: a CTA timed out at a grid barrier");
         if (raw > cap && !capped && attempt == 0 && raw <= kRetryMax) {
             cap = pow2_at_least((size_t)raw);
             continue;
@@ -2626,7 +2643,7 @@ void pms_destroy(pms_ctx *h)
         cudaStreamDestroy(h->cap_stream);
     pms_ctx::DBuf *bufs[] = {&h->d_seqs, &h->d_planes, &h->d_raw, &h->d_tmp, &h->d_compat, &h->d_rowlen, &h->d_mode, &h->d_meta, &h->d_ctr, &h->d_scratch, &h->d_result,
                              &h->d_sg_seqs, &h->d_sg_planes, &h->d_sg_ctr, &h->d_sg_raw, &h->d_sg_out, &h->d_sg_scratch,
-                             &h->d_sg_lists};
+                             &h->d_sg_lists, &h->d_sg_hist};
     for (auto *b : bufs)
         h->dev_free(b->p, b->cap);
     if (h->h_result)

@@ -34,8 +34,9 @@
 //     under that bound; at full depth the bound is the exact distance.
 // Output keys hold ceil(log2 sigma) bits per letter index, first letter most
 // significant (192 bits, three words), so ascending keys are the lexicographic
-// order of the alphabet as given; one CTA sorts, de-duplicates and decodes
-// them into letters.
+// order of the alphabet as given; the sort/unique kernel sorts,
+// de-duplicates and decodes them into letters (one CTA for small outputs,
+// the whole grid otherwise).
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -968,57 +969,250 @@ __host__ __device__ inline bool sg_less(const unsigned long long *a, const unsig
     return a[2] < b[2];
 }
 
-// Largest output sorted by the bitonic network; more keys take the radix sort.
+// Largest output sorted by the bitonic network of one CTA; more keys take the
+// radix sort of the whole grid.
 constexpr unsigned long long kSigBitonicMax = 4096;
-// Shared memory of the radix sort: per-warp digit counts and offsets of a tile, and the 256 bin starts.
+// Shared memory of the sort: per-warp digit counts and offsets of a tile, and the 256 bin starts.
 constexpr size_t kSigSortSmem = (2 * (kSigSortThreads / 32) * 256 + 256) * sizeof(unsigned int);
+// Polls of a grid barrier (about a tenth of a microsecond apart) before a CTA gives up.
+constexpr unsigned int kSigBarrierPolls = 1u << 23;
 
-// Stable LSD radix sort (8-bit digits) of n keys of three words by one CTA,
-// over the key's low `bits` bits (bit i in word 2 - i / 64; a digit never
-// straddles two words). Ping-pongs between a and t; returns the buffer that
-// holds the sorted keys.
-__device__ unsigned long long *sg_radix_sort(unsigned long long *a, unsigned long long *t, unsigned int n, int bits,
-                                             unsigned int *smem)
+__device__ __forceinline__ unsigned int sg_ld_acquire(const unsigned int *p)
 {
-    const int nw = (int)(blockDim.x >> 5);
-    unsigned int *cnt = smem;              // [nw][256] per-warp digit counts of a tile
-    unsigned int *off = smem + nw * 256;   // [nw][256] per-warp digit offsets of a tile
-    unsigned int *bin = smem + 2 * nw * 256;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned int lt = (1u << lane) - 1u;
-    unsigned long long *src = a, *dst = t;
-    for (int shift = 0; shift < bits; shift += 8) {
-        const int word = 2 - (shift >> 6), sh = shift & 63;
-        for (int i = threadIdx.x; i < 2 * nw * 256 + 256; i += blockDim.x)
-            smem[i] = 0u;
-        __syncthreads();
-        for (unsigned int i = threadIdx.x; i < n; i += blockDim.x)
-            atomicAdd(&bin[(unsigned int)(src[3 * i + word] >> sh) & 255u], 1u);
-        __syncthreads();
-        if (warp == 0) {
-            unsigned int run = 0;
-            for (int b0 = 0; b0 < 256; b0 += 32) {
-                const unsigned int v = bin[b0 + lane];
-                unsigned int incl = v;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                    if (lane >= o)
-                        incl += y;
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Barrier of all CTAs of the sort (they are all resident: cooperative
+// launch). bar[0] counts arrivals and is never reset within a launch, so the
+// k-th barrier is passed once it reaches k * gridDim.x. A CTA that polls
+// kSigBarrierPolls times in vain, or finds bar[1] set, sets bar[1] and gets
+// false; so does every CTA after it.
+__device__ bool sg_grid_barrier(unsigned int *bar, unsigned int &k, int *s_ok)
+{
+    __syncthreads();
+    ++k;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const unsigned int target = k * gridDim.x;
+        for (unsigned int poll = 0; sg_ld_acquire(bar) < target; ++poll) {
+            if (poll >= kSigBarrierPolls || sg_ld_acquire(bar + 1) != 0u) {
+                atomicOr(bar + 1, 1u);
+                ok = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// Exclusive prefix sum of v over the CTA's threads in thread order; *total
+// gets the sum. Every thread calls it. scratch: 33 words of shared memory.
+__device__ unsigned int sg_block_scan(unsigned int v, unsigned int *scratch, unsigned int *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o)
+            incl += y;
+    }
+    if (lane == 31)
+        scratch[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned int s = lane < nw ? scratch[lane] : 0u;
+        unsigned int si = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, si, o);
+            if (lane >= o)
+                si += y;
+        }
+        if (lane < nw)
+            scratch[lane] = si - s;
+        if (lane == 31)
+            scratch[32] = si;
+    }
+    __syncthreads();
+    const unsigned int r = scratch[warp] + incl - v;
+    *total = scratch[32];
+    __syncthreads();   // scratch is free for the next call
+    return r;
+}
+
+// Key i of the sorted keys is the first of its value: i == 0 or key i - 1 differs.
+__device__ __forceinline__ bool sg_first_of_value(const unsigned long long *key, unsigned long long i)
+{
+    return i == 0 || __ldcg(key + 3 * i) != __ldcg(key + 3 * i - 3) ||
+           __ldcg(key + 3 * i + 1) != __ldcg(key + 3 * i - 2) || __ldcg(key + 3 * i + 2) != __ldcg(key + 3 * i - 1);
+}
+
+// First occurrences among the sorted keys lo..hi-1.
+__device__ unsigned long long sg_count_unique(const unsigned long long *key, unsigned long long lo,
+                                              unsigned long long hi, unsigned int *scratch)
+{
+    unsigned int c = 0;
+    for (unsigned long long i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        c += sg_first_of_value(key, i) ? 1u : 0u;
+    unsigned int total;
+    sg_block_scan(c, scratch, &total);
+    return total;
+}
+
+// Decodes the first occurrences among the sorted keys lo..hi-1 into l letters
+// each, in key order, as motifs base, base + 1, ... of out. Returns how many.
+__device__ unsigned long long sg_unique_decode(const unsigned long long *key, unsigned long long lo,
+                                               unsigned long long hi, unsigned long long base, int l, int b,
+                                               const SigmaMap &letters, uint8_t *out, unsigned int *scratch)
+{
+    const unsigned long long base0 = base;
+    for (unsigned long long start = lo; start < hi; start += blockDim.x) {
+        const unsigned long long i = start + threadIdx.x;
+        const bool f = i < hi && sg_first_of_value(key, i);
+        unsigned int total;
+        const unsigned int at = sg_block_scan(f ? 1u : 0u, scratch, &total);
+        if (f) {
+            const unsigned long long k3[3] = {__ldcg(key + 3 * i), __ldcg(key + 3 * i + 1), __ldcg(key + 3 * i + 2)};
+            const unsigned long long idx = base + at;
+            for (int p = 0; p < l; ++p) {
+                const int s = b * (l - 1 - p);
+                int a = 0;
+                for (int j = 0; j < b; ++j) {
+                    const int bit = s + j;
+                    a |= (int)((k3[2 - (bit >> 6)] >> (bit & 63)) & 1ull) << j;
                 }
-                bin[b0 + lane] = run + incl - v;
-                run += __shfl_sync(0xFFFFFFFFu, incl, 31);
+                out[idx * l + p] = letters.v[a];
             }
         }
+        base += total;
+    }
+    return base - base0;
+}
+
+// Sorts, de-duplicates and decodes the raw keys. Up to kSigBitonicMax keys:
+// CTA 0 alone, by a bitonic network padded with all-ones keys to a power of
+// two (within the buffer's power-of-two capacity). More: every CTA, by a
+// stable LSD radix sort with 8-bit digits over the key's low l * b bits (bit
+// i in word 2 - i / 64; a digit never straddles two words), ping-ponging
+// between raw and tmp. Each CTA owns a contiguous tile of the keys; a pass
+// counts its tile's digits, turns the counts into exclusive offsets (digit
+// major, CTA minor: the digits are shared out over the CTAs), and scatters
+// the tile blockDim keys at a time (ranks within a warp by __match_any_sync,
+// warps in order), so equal digits keep their order. Grid barriers separate
+// the phases; keys and counts written by other CTAs are read through L2.
+__global__ void __launch_bounds__(kSigSortThreads) sigma_sort_unique_kernel(
+    unsigned long long *raw, unsigned long long *tmp, const unsigned long long *__restrict__ raw_count,
+    unsigned long long cap, int l, int b, SigmaMap letters, uint8_t *__restrict__ out,
+    unsigned long long *__restrict__ unique_count, SigSortGrid grid)
+{
+    extern __shared__ unsigned int sg_sort_smem[];
+    __shared__ unsigned int s_scan[33];
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const unsigned long long N = *raw_count < cap ? *raw_count : cap;
+    if (N <= kSigBitonicMax) {
+        if (blockIdx.x != 0)
+            return;
+        unsigned long long P2 = 1;
+        while (P2 < N)
+            P2 <<= 1;
+        for (unsigned long long i = tid; i < P2; i += nt)
+            if (i >= N)
+                raw[3 * i] = raw[3 * i + 1] = raw[3 * i + 2] = ~0ull;
         __syncthreads();
-        for (unsigned int t0 = 0; t0 < n; t0 += blockDim.x) {
-            const unsigned int i = t0 + threadIdx.x;
-            const bool valid = i < n;
+        for (unsigned long long k = 2; k <= P2; k <<= 1) {
+            for (unsigned long long j = k >> 1; j > 0; j >>= 1) {
+                for (unsigned long long i = tid; i < P2; i += nt) {
+                    const unsigned long long ixj = i ^ j;
+                    if (ixj > i) {
+                        unsigned long long *a = raw + 3 * i, *c = raw + 3 * ixj;
+                        const bool up = (i & k) == 0;
+                        if (up ? sg_less(c, a) : sg_less(a, c)) {
+                            for (int w = 0; w < 3; ++w) {
+                                const unsigned long long v = a[w];
+                                a[w] = c[w];
+                                c[w] = v;
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        const unsigned long long u = sg_unique_decode(raw, 0, N, 0, l, b, letters, out, s_scan);
+        if (tid == 0)
+            *unique_count = u;
+        return;
+    }
+
+    const unsigned int G = gridDim.x, cta = blockIdx.x;
+    unsigned int *hist = grid.hist;        // [256][G]: digit counts, then their exclusive offsets
+    unsigned int *tot = hist + 256 * G;    // [256]: keys per digit
+    unsigned int *ucount = tot + 256;      // [G]: first occurrences per tile
+    const int nw = nt >> 5, lane = tid & 31, warp = tid >> 5;
+    const unsigned int lt = (1u << lane) - 1u;
+    unsigned int *cnt = sg_sort_smem;              // [nw][256] per-warp digit counts of a group of keys
+    unsigned int *off = sg_sort_smem + nw * 256;   // [nw][256] per-warp digit offsets of a group
+    unsigned int *bin = sg_sort_smem + 2 * nw * 256;
+    const unsigned long long tile = (N + G - 1) / G;
+    const unsigned long long lo = min(N, (unsigned long long)cta * tile), hi = min(N, lo + tile);
+    unsigned int k = 0;   // grid barriers passed
+    unsigned long long *src = raw, *dst = tmp;
+    const int bits = l * b;
+    for (int shift = 0; shift < bits; shift += 8) {
+        const int word = 2 - (shift >> 6), sh = shift & 63;
+        for (int i = tid; i < 2 * nw * 256 + 256; i += nt)
+            sg_sort_smem[i] = 0u;
+        __syncthreads();
+        for (unsigned long long i = lo + tid; i < hi; i += nt)
+            atomicAdd(&bin[(unsigned int)(__ldcg(src + 3 * i + word) >> sh) & 255u], 1u);
+        __syncthreads();
+        if (tid < 256)
+            hist[tid * G + cta] = bin[tid];
+        if (!sg_grid_barrier(grid.bar, k, &s_ok))
+            return;
+        for (unsigned int t = cta; t < 256u; t += G) {
+            unsigned int run = 0;
+            for (unsigned int c0 = 0; c0 < G; c0 += nt) {
+                const unsigned int c = c0 + tid;
+                const unsigned int v = c < G ? __ldcg(hist + t * G + c) : 0u;
+                unsigned int sum;
+                const unsigned int ex = sg_block_scan(v, s_scan, &sum);
+                if (c < G)
+                    hist[t * G + c] = run + ex;
+                run += sum;
+            }
+            if (tid == 0)
+                tot[t] = run;
+        }
+        if (!sg_grid_barrier(grid.bar, k, &s_ok))
+            return;
+        {
+            // this tile's first slot of digit t: the keys of smaller digits,
+            // then the keys of digit t in earlier tiles
+            const unsigned int v = tid < 256 ? __ldcg(tot + tid) : 0u;
+            unsigned int sum;
+            const unsigned int ex = sg_block_scan(v, s_scan, &sum);
+            if (tid < 256)
+                bin[tid] = ex + __ldcg(hist + tid * G + cta);
+        }
+        __syncthreads();
+        for (unsigned long long t0 = lo; t0 < hi; t0 += nt) {
+            const unsigned long long i = t0 + tid;
+            const bool valid = i < hi;
             unsigned long long k0 = 0, k1 = 0, k2 = 0;
             unsigned int dig = 256u;
             if (valid) {
-                k0 = src[3 * i];
-                k1 = src[3 * i + 1];
-                k2 = src[3 * i + 2];
+                k0 = __ldcg(src + 3 * i);
+                k1 = __ldcg(src + 3 * i + 1);
+                k2 = __ldcg(src + 3 * i + 2);
                 const unsigned long long w = word == 0 ? k0 : (word == 1 ? k1 : k2);
                 dig = (unsigned int)(w >> sh) & 255u;
             }
@@ -1027,117 +1221,46 @@ __device__ unsigned long long *sg_radix_sort(unsigned long long *a, unsigned lon
             if (valid && rank == 0)
                 cnt[warp * 256 + dig] = __popc(peers);
             __syncthreads();
-            if (threadIdx.x < 256) {
-                unsigned int run = bin[threadIdx.x];
+            if (tid < 256) {
+                unsigned int run = bin[tid];
                 for (int w = 0; w < nw; ++w) {
-                    off[w * 256 + threadIdx.x] = run;
-                    run += cnt[w * 256 + threadIdx.x];
-                    cnt[w * 256 + threadIdx.x] = 0u;
+                    off[w * 256 + tid] = run;
+                    run += cnt[w * 256 + tid];
+                    cnt[w * 256 + tid] = 0u;
                 }
-                bin[threadIdx.x] = run;
+                bin[tid] = run;
             }
             __syncthreads();
             if (valid) {
                 const unsigned int at = off[warp * 256 + dig] + rank;
-                dst[3 * at] = k0;
-                dst[3 * at + 1] = k1;
-                dst[3 * at + 2] = k2;
+                dst[3 * (unsigned long long)at] = k0;
+                dst[3 * (unsigned long long)at + 1] = k1;
+                dst[3 * (unsigned long long)at + 2] = k2;
             }
             __syncthreads();
         }
+        if (!sg_grid_barrier(grid.bar, k, &s_ok))
+            return;
         unsigned long long *x = src;
         src = dst;
         dst = x;
     }
-    return src;
-}
-
-// One CTA: the raw keys sorted (up to kSigBitonicMax keys by a bitonic
-// network padded with all-ones keys to a power of two, within the buffer's
-// power-of-two capacity; more by the radix sort through tmp, the buffer's
-// second half), then unique + decode into l letters per motif.
-__global__ void __launch_bounds__(kSigSortThreads) sigma_sort_unique_kernel(
-    unsigned long long *raw, unsigned long long *tmp, const unsigned long long *__restrict__ raw_count, unsigned long long cap, int l, int b, SigmaMap letters,
-    uint8_t *__restrict__ out, unsigned long long *__restrict__ unique_count)
-{
-    extern __shared__ unsigned int sg_sort_smem[];
-    __shared__ unsigned int s_warp[kSigSortThreads / 32];
-    __shared__ unsigned int s_total;
-    __shared__ unsigned long long s_base;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const unsigned long long N = *raw_count < cap ? *raw_count : cap;
-    if (N > kSigBitonicMax)
-        raw = sg_radix_sort(raw, tmp, (unsigned int)N, l * b, sg_sort_smem);
-    unsigned long long P2 = 1;
-    while (P2 < N && N <= kSigBitonicMax)
-        P2 <<= 1;
-    if (N > kSigBitonicMax)
-        P2 = 1;   // sorted already: no network
-    for (unsigned long long i = tid; i < P2; i += nt)
-        if (i >= N)
-            raw[3 * i] = raw[3 * i + 1] = raw[3 * i + 2] = ~0ull;
-    __syncthreads();
-    for (unsigned long long k = 2; k <= P2; k <<= 1) {
-        for (unsigned long long j = k >> 1; j > 0; j >>= 1) {
-            for (unsigned long long i = tid; i < P2; i += nt) {
-                const unsigned long long ixj = i ^ j;
-                if (ixj > i) {
-                    unsigned long long *a = raw + 3 * i, *c = raw + 3 * ixj;
-                    const bool up = (i & k) == 0;
-                    if (up ? sg_less(c, a) : sg_less(a, c)) {
-                        for (int w = 0; w < 3; ++w) {
-                            const unsigned long long v = a[w];
-                            a[w] = c[w];
-                            c[w] = v;
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
+    // unique + decode: each tile's first occurrences, placed after those of the earlier tiles
+    const unsigned long long mine = sg_count_unique(src, lo, hi, s_scan);
     if (tid == 0)
-        s_base = 0;
-    __syncthreads();
-    const int lane = tid & 31, wid = tid >> 5;
-    for (unsigned long long start = 0; start < N; start += nt) {
-        const unsigned long long i = start + tid;
-        const bool f = i < N && (i == 0 || raw[3 * i] != raw[3 * i - 3] || raw[3 * i + 1] != raw[3 * i - 2] ||
-                                 raw[3 * i + 2] != raw[3 * i - 1]);
-        const unsigned bal = __ballot_sync(0xFFFFFFFFu, f);
-        if (lane == 0)
-            s_warp[wid] = __popc(bal);
-        __syncthreads();
-        if (tid == 0) {
-            unsigned acc = 0;
-            for (int w = 0; w < nt / 32; ++w) {
-                const unsigned v = s_warp[w];
-                s_warp[w] = acc;
-                acc += v;
-            }
-            s_total = acc;
-        }
-        __syncthreads();
-        if (f) {
-            const unsigned long long idx = s_base + s_warp[wid] + __popc(bal & ((1u << lane) - 1u));
-            const unsigned long long key[3] = {raw[3 * i], raw[3 * i + 1], raw[3 * i + 2]};
-            for (int p = 0; p < l; ++p) {
-                const int s = b * (l - 1 - p);
-                int a = 0;
-                for (int j = 0; j < b; ++j) {
-                    const int bit = s + j;
-                    a |= (int)((key[2 - (bit >> 6)] >> (bit & 63)) & 1ull) << j;
-                }
-                out[idx * l + p] = letters.v[a];
-            }
-        }
-        __syncthreads();
-        if (tid == 0)
-            s_base += s_total;
-        __syncthreads();
+        ucount[cta] = (unsigned int)mine;
+    if (!sg_grid_barrier(grid.bar, k, &s_ok))
+        return;
+    unsigned long long base = 0;
+    for (unsigned int c0 = 0; c0 < cta; c0 += nt) {
+        const unsigned int c = c0 + tid;
+        unsigned int sum;
+        sg_block_scan(c < cta ? __ldcg(ucount + c) : 0u, s_scan, &sum);
+        base += sum;
     }
-    if (tid == 0)
-        *unique_count = s_base;
+    sg_unique_decode(src, lo, hi, base, l, b, letters, out, s_scan);
+    if (cta == G - 1 && tid == 0)
+        *unique_count = base + mine;
 }
 
 // --------------------------------------------------------------------- host side
@@ -1197,14 +1320,44 @@ cudaError_t launch_sigma_main(const SigmaParams &p, int blocks, cudaStream_t st)
     return cudaGetLastError();
 }
 
+size_t sigma_sort_hist_words(int ctas)
+{
+    return (size_t)257 * ctas + 256;
+}
+
+cudaError_t sigma_sort_ctas(int *ctas)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sigma_sort_unique_kernel, kSigSortThreads,
+                                                          kSigSortSmem);
+    if (e != cudaSuccess)
+        return e;
+    *ctas = per_sm > 0 ? sms : 1;   // one CTA per SM, all resident
+    return cudaSuccess;
+}
+
 cudaError_t launch_sigma_sort_unique(unsigned long long *raw, unsigned long long *tmp,
                                      const unsigned long long *raw_count, unsigned long long cap, int l, int b,
                                      const SigmaMap &letters, uint8_t *out, unsigned long long *unique_count,
-                                     cudaStream_t st)
+                                     const SigSortGrid &grid, cudaStream_t st)
 {
-    sigma_sort_unique_kernel<<<1, kSigSortThreads, kSigSortSmem, st>>>(raw, tmp, raw_count, cap, l, b, letters, out,
-                                                                       unique_count);
-    return cudaGetLastError();
+    // a cooperative launch: it fails rather than start CTAs that could not all be resident
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned int)grid.ctas);
+    cfg.blockDim = dim3(kSigSortThreads);
+    cfg.dynamicSmemBytes = kSigSortSmem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sigma_sort_unique_kernel, raw, tmp, raw_count, cap, l, b, letters, out,
+                              unique_count, grid);
 }
 
 }  // namespace pms

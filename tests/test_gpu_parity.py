@@ -233,6 +233,21 @@ def test_errors(ctx):
     assert int(status[2].item()) & 1
 
 
+@pytest.mark.parametrize("n,m,l,d,i,k", [(20, 600, 9, 2, 0, 0), (20, 600, 9, 2, 19, 599), (20, 600, 15, 4, 7, 300),
+                                         (1, 40, 8, 2, 0, 39), (3, 17, 17, 3, 2, 16)])
+def test_invalid_byte_found_anywhere(ctx, n, m, l, d, i, k):
+    # the packing kernels find the byte; the host then names it
+    seqs = pi.random_sequences(n, m, 11)
+    bad = seqs.copy()
+    bad[i, k] = ord("N")
+    with pytest.raises(pms.PMSError) as e:
+        ctx.solve(bad, l, d)
+    assert e.value.code == pms.PMS_EINVAL
+    assert f"byte {i * m + k} (0x4e)" in str(e.value)
+    # the context stays usable
+    assert np.array_equal(ctx.solve(seqs, l, d), ctx.solve(seqs.copy(), l, d))
+
+
 def test_too_many_motifs_reported(ctx):
     c = pms.Context(0)
     c.set_options(max_motifs=16)

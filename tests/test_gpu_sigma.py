@@ -144,6 +144,23 @@ def test_large_output_with_keys_over_two_words(ctx, oracle_):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("alpha,seq,l,d", [
+    ("ACGT", "A" * 20, 8, 3),          # 13 equal windows: 23,257 raw keys, each value 13 times, across CTA tiles
+    ("ACDEF", None, 7, 2),             # 13 windows: 4,745 raw keys, just above the one-CTA network's 4,096
+    ("ACDEFGHIKLMNPQRSTVWY", "ACACACACACACACACAC", 9, 2),   # two window kinds, five times each
+])
+def test_sort_across_the_grid(ctx, oracle_, alpha, seq, l, d):
+    # n = 1: the motif set is the union of the windows' spheres; the raw keys exceed what
+    # one CTA's network sorts, so every CTA of the sort takes a tile
+    if seq is None:
+        rng = np.random.default_rng(5)
+        seq = bytes(rng.choice(np.frombuffer(alpha.encode(), np.uint8), 19)).decode()
+    seqs = np.frombuffer(seq.encode(), np.uint8).reshape(1, -1)
+    want = oracle_.sigma_solve(seqs, l, d, alpha, cap=1 << 22)
+    got = ctx.solve_sigma(seqs, l, d, alpha)
+    assert np.array_equal(got, want)
+
+
 def test_invalid_inputs(ctx):
     import paper_2403_00306_gb300 as pms
     inst = pi.planted_instance_sigma(4, 30, 6, 2, 3)
