@@ -11,11 +11,14 @@ as little-endian 64-bit words.
 
 Entries:
   batch2024_{0..255}  every instance of the batched workload (master seed 2024)
-  serve7_r{k}         32 requests of the served stream (master seed 7, 10,000 requests,
-                      m in [200, 1200]) drawn uniformly at random (generator seed 7007) from
-                      requests 16..9999 (requests 0..15 are checked whole in whole_sets.json)
+  serve7_r{k}         requests of the served stream (master seed 7, 10,000 requests,
+                      m in [200, 1200]) in a uniformly random order of requests 16..9999
+                      (requests 0..15 are checked whole in whole_sets.json): first 32 drawn
+                      with generator seed 7007, then the others in a random permutation
+                      (generator seed 7008). The file holds a prefix of that order; a longer
+                      run extends it (--serve N: the first N of the order).
 
-Usage: python tests/golden/make_set_hashes.py [name-prefix ...]
+Usage: python tests/golden/make_set_hashes.py [--serve N] [--threads T] [name-prefix ...]
 (entries already in the file are kept unless their prefix is named).
 """
 from __future__ import annotations
@@ -48,26 +51,39 @@ def set_hash(codes) -> str:
     return hashlib.sha256(np.asarray(codes, dtype="<u8").tobytes()).hexdigest()
 
 
-def served_sample() -> list[int]:
+def served_order() -> list[int]:
+    """Requests 16..9999 in the order the served sample takes them."""
     rng = np.random.default_rng(SERVE_SAMPLE_SEED)
-    return sorted(int(k) for k in rng.choice(np.arange(16, 10000), size=SERVE_SAMPLE, replace=False))
+    first = sorted(int(k) for k in rng.choice(np.arange(16, 10000), size=SERVE_SAMPLE, replace=False))
+    taken = set(first)
+    rest = np.array([k for k in range(16, 10000) if k not in taken])
+    return first + [int(k) for k in np.random.default_rng(SERVE_SAMPLE_SEED + 1).permutation(rest)]
 
 
-def entries():
+def entries(serve: int):
     for k, inst in enumerate(pi.batch_instances(count=256, master_seed=2024)):
         yield f"batch2024_{k}", {"kind": "batch", "index": k, "master_seed": 2024}, inst
     reqs = list(pi.serve_requests(count=10000, master_seed=7))
-    for k in served_sample():
-        yield f"serve7_r{k}", {"kind": "serve", "index": k, "master_seed": 7}, reqs[k][1]
+    for rank, k in enumerate(served_order()[:serve]):
+        yield f"serve7_r{k}", {"kind": "serve", "index": k, "rank": rank, "master_seed": 7}, reqs[k][1]
 
 
 def main(argv):
-    redo = argv[1:]
+    args = argv[1:]
+    serve, threads = SERVE_SAMPLE, os.cpu_count() or 1
+    while args and args[0] in ("--serve", "--threads"):
+        if args[0] == "--serve":
+            serve = int(args[1])
+        else:
+            threads = int(args[1])
+        args = args[2:]
+    redo = args
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     o = oracle.Oracle()
-    threads = os.cpu_count() or 1
-    for name, desc, inst in entries():
+    for name, desc, inst in entries(serve):
         if name in data and not any(name.startswith(p) for p in redo):
+            if "rank" in desc and data[name].get("rank") != desc["rank"]:
+                data[name]["rank"] = desc["rank"]   # entries written before ranks were recorded
             continue
         t0 = time.perf_counter()
         codes = o.solve_packed(inst.seqs, inst.l, inst.d, threads=threads, cap=1 << 24)
