@@ -83,6 +83,45 @@ DEEP = [
 _DEEP_WANT = {}
 
 
+@pytest.mark.parametrize("m", [4103, 4200])
+def test_long_sequences_match_oracle(ctx, oracle_, m):
+    # W = m - l + 1 = 4096 is the most windows the fused packing + masks kernel stages in
+    # shared memory; at W = 4193 the plan takes the separate packing and masks kernels
+    inst = pi.planted_instance(3, m, 8, 1, 40)
+    want = oracle_.solve(inst.seqs, 8, 1, cap=1 << 24)
+    got = ctx.solve(inst.seqs, 8, 1)
+    assert len(want) > 30000
+    assert np.array_equal(got, want)
+
+
+def _window_keys(codes_row: np.ndarray, l: int) -> np.ndarray:
+    # every l-mer of one sequence as its key (2 bits per base, position 0 most significant)
+    k = np.zeros(len(codes_row) - l + 1, dtype=np.uint64)
+    for p in range(l):
+        k = (k << np.uint64(2)) | codes_row[p:p + len(k)].astype(np.uint64)
+    return k
+
+
+def test_maximum_sequence_length(ctx, oracle_):
+    # m = 65536, the largest the boundary accepts. d = 0: the motifs are exactly the
+    # l-mers common to both sequences (a set intersection). d = 1: sampled seeds
+    # against the oracle, and the planted motif.
+    l = 12
+    inst = pi.planted_instance(2, 65536, l, 0, 41)
+    codes = seq_codes(inst.seqs)
+    want = np.intersect1d(_window_keys(codes[0], l), _window_keys(codes[1], l))
+    assert np.array_equal(ctx.solve(inst.seqs, l, 0), want)
+    inst = pi.planted_instance(2, 65536, l, 1, 42)
+    got = ctx.solve(inst.seqs, l, 1)
+    assert np.all(np.diff(got.astype(np.int64)) > 0)
+    assert py_key(inst.motif.decode()) in set(int(k) for k in got)
+    codes = seq_codes(inst.seqs[0])
+    rng = np.random.default_rng(42)
+    seeds = sorted(set(rng.choice(65536 - l + 1, size=5, replace=False).tolist()) | {int(inst.positions[0])})
+    for j, w in oracle_per_seed(oracle_, inst.seqs, l, 1, seeds).items():
+        assert np.array_equal(keys_within(got, codes[j:j + l], l, 1), w), j
+
+
 @pytest.mark.parametrize("partial_rows", [-1, 1, 2, 5])
 @pytest.mark.parametrize("case", DEEP, ids=lambda c: "n{}_m{}_l{}_d{}".format(*c[:4]))
 def test_partial_level_matches_oracle(oracle_, case, partial_rows):
@@ -218,9 +257,14 @@ def test_errors(ctx):
     with pytest.raises(pms.PMSError) as e:
         ctx.solve(bad, 9, 2)
     assert e.value.code == pms.PMS_EINVAL
-    for (l, d) in [(0, 0), (9, 9), (33, 2), (601, 1)]:
+    for (l, d) in [(0, 0), (9, 9), (33, 2), (601, 1), (9, -1)]:
         with pytest.raises(pms.PMSError):
             ctx.solve(inst.seqs, l, d)
+    # empty input (n = 0), sequences shorter than l, more sequences than the boundary takes
+    for seqs, l in [(np.zeros((0, 40), np.uint8), 9), (inst.seqs[:, :8], 9), (np.full((65, 20), ord("A"), np.uint8), 5)]:
+        with pytest.raises(pms.PMSError) as e:
+            ctx.solve(seqs, l, 1)
+        assert e.value.code == pms.PMS_EINVAL
     # device path reports an invalid byte in its status flags
     import torch
     d_seqs = torch.from_numpy(bad).cuda()
