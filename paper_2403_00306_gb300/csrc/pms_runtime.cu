@@ -208,8 +208,10 @@ struct pms_ctx {
     void *h_sg = nullptr;       // pinned: counters block, then the input letters
     size_t h_sg_cap = 0;
     std::vector<uint8_t> owned_sigma;   // letters returned by the last pms_solve_sigma
-    void *h_result = nullptr;   // pinned
+    void *h_result = nullptr;   // pinned, mapped: results of host-memory solves
     size_t h_result_cap = 0;
+    void *h_in = nullptr;       // pinned, mapped: inputs of host-memory solves
+    size_t h_in_cap = 0;
     void *h_meta = nullptr;     // pinned staging for descriptors and inputs
     size_t h_meta_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm0 = nullptr, evm1 = nullptr;
@@ -367,7 +369,7 @@ struct pms_ctx {
         b.p = p;
         return PMS_OK;
     }
-    int ensure_host(void *&p, size_t &cap, size_t bytes)
+    int ensure_host(void *&p, size_t &cap, size_t bytes, unsigned int flags = cudaHostAllocDefault)
     {
         if (cap >= bytes)
             return PMS_OK;
@@ -378,7 +380,7 @@ struct pms_ctx {
             cap = 0;
         }
         bytes = round_up(std::max(bytes, cap * 2), 4096);
-        cudaError_t e = cudaHostAlloc(&p, bytes, cudaHostAllocDefault);
+        cudaError_t e = cudaHostAlloc(&p, bytes, flags);
         if (e != cudaSuccess) {
             p = nullptr;
             return cuda_fail(e, "cudaHostAlloc");
@@ -1189,6 +1191,10 @@ static int status_code(const StatusDev &s)
 
 // Runs a plan whose inputs come from host memory and downloads all results
 // into h->h_result. On return (PMS_OK) statuses and codes are on the host.
+// Largest input, and largest result block, that host-memory solves keep in
+// mapped pinned memory for the kernels to read or write directly.
+constexpr size_t kZeroCopyBytes = (size_t)1 << 20;
+
 static int run_host_plan(pms_ctx *h, const Plan &P, const std::vector<InstSpec> &specs, double t0)
 {
     const size_t k = P.inst.size();
@@ -1202,26 +1208,38 @@ static int run_host_plan(pms_ctx *h, const Plan &P, const std::vector<InstSpec> 
     ResLayout rl(k, dense_keys);
     if ((rc = h->ensure(h->d_result, rl.total)))
         return rc;
-    // stage inputs (pinned) and upload in one copy
+    // Inputs are staged in mapped pinned memory. Small ones are read there by
+    // the packing kernel itself and small result blocks are written straight
+    // into mapped pinned memory, so such a solve makes no copy calls.
+    const bool zc_in = P.seq_bytes <= kZeroCopyBytes, zc_out = rl.total <= kZeroCopyBytes;
     const size_t inline_bytes = rl.dense + (size_t)kInlineKeys * 8;
-    if ((rc = h->ensure_host(h->h_result, h->h_result_cap, std::max(inline_bytes, P.seq_bytes))))
+    if ((rc = h->ensure_host(h->h_in, h->h_in_cap, P.seq_bytes, cudaHostAllocMapped)) ||
+        (rc = h->ensure_host(h->h_result, h->h_result_cap, zc_out ? rl.total : inline_bytes, cudaHostAllocMapped)))
         return rc;
-    char *stage = (char *)h->h_result;
+    char *stage = (char *)h->h_in;
     for (size_t i = 0; i < k; ++i)
         std::memcpy(stage + P.inst[i].seq_off, specs[i].host_seqs, (size_t)specs[i].n * specs[i].m);
     cudaStream_t st = h->stream;
     if (h->inject(PMS_FAULT_UPLOAD))
         return h->fail(PMS_ECUDA, "upload sequences: failure injected by pms_inject_fault");
-    cudaError_t e = cudaMemcpyAsync(h->d_seqs.p, stage, P.seq_bytes, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess)
-        return h->cuda_fail(e, "upload sequences");
-    char *dr = (char *)h->d_result.p;
-    if ((rc = enqueue_plan_graph(h, P, (const uint8_t *)h->d_seqs.p, (StatusDev *)(dr + rl.status),
+    cudaError_t e;
+    void *in_dev = nullptr, *res_dev = nullptr;
+    if ((e = cudaHostGetDevicePointer(&in_dev, h->h_in, 0)) != cudaSuccess ||
+        (e = cudaHostGetDevicePointer(&res_dev, h->h_result, 0)) != cudaSuccess)
+        return h->cuda_fail(e, "mapped host buffers");
+    if (!zc_in) {
+        if ((e = cudaMemcpyAsync(h->d_seqs.p, stage, P.seq_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return h->cuda_fail(e, "upload sequences");
+        in_dev = h->d_seqs.p;
+    }
+    char *dr = zc_out ? (char *)res_dev : (char *)h->d_result.p;
+    if ((rc = enqueue_plan_graph(h, P, (const uint8_t *)in_dev, (StatusDev *)(dr + rl.status),
                                  (uint64_t *)(dr + rl.dense), rl.dense_cap, count_mode)))
         return rc;
-    // statuses and the first codes in one download
-    const size_t first = std::min(inline_bytes, rl.total);
-    if ((e = cudaMemcpyAsync(h->h_result, dr, first, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    // otherwise statuses and the first codes in one download
+    if (!zc_out &&
+        (e = cudaMemcpyAsync(h->h_result, dr, std::min(inline_bytes, rl.total), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess)
         return h->cuda_fail(e, "download results");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
         return h->cuda_fail(e, "solve");
@@ -1229,12 +1247,12 @@ static int run_host_plan(pms_ctx *h, const Plan &P, const std::vector<InstSpec> 
     uint64_t total = 0;
     for (size_t i = 0; i < k; ++i)
         total = std::max<uint64_t>(total, (uint64_t)sd[i].dense_off + sd[i].unique_count);
-    if (total > kInlineKeys) {
+    if (!zc_out && total > kInlineKeys) {
         const size_t need = rl.dense + total * 8;
         if (need > h->h_result_cap) {
             std::vector<char> keep((const char *)h->h_result, (const char *)h->h_result + rl.dense);
             void *np = nullptr;
-            if ((e = cudaHostAlloc(&np, round_up(need, 4096), cudaHostAllocDefault)) != cudaSuccess)
+            if ((e = cudaHostAlloc(&np, round_up(need, 4096), cudaHostAllocMapped)) != cudaSuccess)
                 return h->cuda_fail(e, "cudaHostAlloc");
             cudaFreeHost(h->h_result);
             h->h_result = np;
@@ -2648,6 +2666,8 @@ void pms_destroy(pms_ctx *h)
         h->dev_free(b->p, b->cap);
     if (h->h_result)
         cudaFreeHost(h->h_result);
+    if (h->h_in)
+        cudaFreeHost(h->h_in);
     if (h->h_meta)
         cudaFreeHost(h->h_meta);
     if (h->h_sg)
