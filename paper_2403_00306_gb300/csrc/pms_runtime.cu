@@ -205,8 +205,10 @@ struct pms_ctx {
     DBuf d_sg_seqs, d_sg_planes, d_sg_ctr, d_sg_raw, d_sg_out, d_sg_scratch, d_sg_lists, d_sg_hist;
     bool sigma_ready = false;   // binomial table and kernel attributes loaded on the device
     int sg_sort_ctas = 1;       // CTAs of the sort/unique grid
-    void *h_sg = nullptr;       // pinned: counters block, then the input letters
+    void *h_sg = nullptr;       // pinned, mapped: counters block, then the input letters
     size_t h_sg_cap = 0;
+    void *h_sg_out = nullptr;   // pinned, mapped: decoded motifs of small outputs
+    size_t h_sg_out_cap = 0;
     std::vector<uint8_t> owned_sigma;   // letters returned by the last pms_solve_sigma
     void *h_result = nullptr;   // pinned, mapped: results of host-memory solves
     size_t h_result_cap = 0;
@@ -2548,10 +2550,19 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
         list_cap = 0;
         h->err.clear();
     }
-    if ((rc = h->ensure_host(h->h_sg, h->h_sg_cap, 256 + nm)))
+    if ((rc = h->ensure_host(h->h_sg, h->h_sg_cap, 256 + nm, cudaHostAllocMapped)))
         return rc;
     char *h_ctr = (char *)h->h_sg;
     memcpy(h_ctr + 256, seqs, nm);
+    // inputs of up to 1 MiB are read by the packing kernel in the mapped
+    // staging buffer, and outputs of up to 1 MiB written by the sort kernel
+    // into a mapped buffer: no copy each way
+    void *sg_dev = nullptr, *out_dev = nullptr;
+    if ((e = cudaHostGetDevicePointer(&sg_dev, h->h_sg, 0)) != cudaSuccess)
+        return h->cuda_fail(e, "mapped host buffers");
+    const bool zc_in = nm <= kZeroCopyBytes;
+    const uint8_t *seq_src = zc_in ? (const uint8_t *)sg_dev + 256 : (const uint8_t *)h->d_sg_seqs.p;
+    bool zc_out = false;
     unsigned long long raw = 0, uniq = 0, ctr[kSgCntNum] = {};
     uint32_t flags = 0, bar[2] = {};
     cudaStream_t st = h->stream;
@@ -2559,6 +2570,14 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
         // raw keys (three words each) and, after them, the sort's second buffer
         if ((rc = h->ensure(h->d_sg_raw, (size_t)48 * cap)) || (rc = h->ensure(h->d_sg_out, (size_t)l * cap)))
             return rc;
+        zc_out = (size_t)l * cap <= kZeroCopyBytes;
+        if (zc_out) {
+            if ((rc = h->ensure_host(h->h_sg_out, h->h_sg_out_cap, (size_t)l * cap, cudaHostAllocMapped)))
+                return rc;
+            if ((e = cudaHostGetDevicePointer(&out_dev, h->h_sg_out, 0)) != cudaSuccess)
+                return h->cuda_fail(e, "mapped host buffers");
+        }
+        uint8_t *out_ptr = zc_out ? (uint8_t *)out_dev : (uint8_t *)h->d_sg_out.p;
         char *c = (char *)h->d_sg_ctr.p;
         SigmaParams p{};
         p.planes = (const uint32_t *)h->d_sg_planes.p;
@@ -2582,14 +2601,15 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
         p.smem_rows = smem_rows;
         p.lists = list_cap > 0 ? (uint32_t *)h->d_sg_lists.p : nullptr;
         p.list_cap = list_cap;
-        if ((e = cudaMemcpyAsync(h->d_sg_seqs.p, h_ctr + 256, nm, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        if ((!zc_in &&
+             (e = cudaMemcpyAsync(h->d_sg_seqs.p, h_ctr + 256, nm, cudaMemcpyHostToDevice, st)) != cudaSuccess) ||
             (e = cudaMemsetAsync(c, 0, ctr_bytes, st)) != cudaSuccess || (e = cudaEventRecord(h->ev0, st)) != cudaSuccess ||
-            (e = launch_sigma_pack((const uint8_t *)h->d_sg_seqs.p, n, m, l, b, map, (uint32_t *)h->d_sg_planes.p,
+            (e = launch_sigma_pack(seq_src, n, m, l, b, map, (uint32_t *)h->d_sg_planes.p,
                                    (uint32_t *)(c + 24), st)) != cudaSuccess ||
             (e = cudaEventRecord(h->evm0, st)) != cudaSuccess || (e = launch_sigma_main(p, blocks, st)) != cudaSuccess ||
             (e = cudaEventRecord(h->evm1, st)) != cudaSuccess ||
             (e = launch_sigma_sort_unique(p.raw, p.raw + 3 * cap, p.raw_count, cap, l, b, letters,
-                                          (uint8_t *)h->d_sg_out.p, (unsigned long long *)(c + 16),
+                                          out_ptr, (unsigned long long *)(c + 16),
                                           SigSortGrid{(unsigned int *)h->d_sg_hist.p, (unsigned int *)(c + bar_off),
                                                       h->sg_sort_ctas},
                                           st)) != cudaSuccess ||
@@ -2614,9 +2634,11 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
         return h->fail(PMS_EINVAL, "byte outside the alphabet");
     const size_t keep = (size_t)std::min(uniq, cap);
     h->owned_sigma.resize(std::max<size_t>(keep * l, 1));
-    if (keep && ((e = cudaMemcpyAsync(h->owned_sigma.data(), h->d_sg_out.p, keep * l, cudaMemcpyDeviceToHost, st)) !=
-                     cudaSuccess ||
-                 (e = cudaStreamSynchronize(st)) != cudaSuccess))
+    if (keep && zc_out)
+        memcpy(h->owned_sigma.data(), h->h_sg_out, keep * l);
+    else if (keep && ((e = cudaMemcpyAsync(h->owned_sigma.data(), h->d_sg_out.p, keep * l, cudaMemcpyDeviceToHost,
+                                           st)) != cudaSuccess ||
+                      (e = cudaStreamSynchronize(st)) != cudaSuccess))
         return h->cuda_fail(e, "result copy");
     pms_stats s{};
     double nb = 0;
@@ -2672,6 +2694,8 @@ void pms_destroy(pms_ctx *h)
         cudaFreeHost(h->h_meta);
     if (h->h_sg)
         cudaFreeHost(h->h_sg);
+    if (h->h_sg_out)
+        cudaFreeHost(h->h_sg_out);
     if (h->ev0)
         cudaEventDestroy(h->ev0);
     if (h->ev1)
