@@ -8,8 +8,9 @@ step. `value` is solves/s with the inputs already in device memory, timed
 with CUDA events on the library's stream, L2 flushed between steps (outside
 the timed events). `e2e` times the host-buffer C-ABI call (pms_solve):
 the transfer of the input from pinned host memory, all kernels and the
-transfer of the result back inside the clock (for inputs and results of
-up to 1 MiB the kernels read and write the pinned host buffers directly).
+transfer of the result back inside the clock (for small inputs and
+results, such as these, the kernels read and write the pinned host buffers
+directly).
 
 Other workloads (--workload): plain9_2, plain17_5, plain19_6 (single
 instances), quorum15_4_q10 (the quorum form), protein9_3 / protein9_4 (the

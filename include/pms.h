@@ -208,9 +208,10 @@ int pms_get_options(const pms_ctx *h, pms_options *opt);
  * Bytes other than A/C/G/T are detected by the packing kernel: the call
  * then returns PMS_EINVAL, with *count = 0, and pms_last_error names the
  * first such byte. The bytes are copied into a pinned host buffer of the
- * context; up to 1 MiB of input the packing kernel reads them there, and up
- * to 1 MiB of results the sort kernel writes them into another one, so such
- * a call issues no copy of its own. */
+ * context. For small instances (n*m*max(l, (m-l+1)/16) up to 1 MiB) the
+ * packing kernel reads them there, and result blocks of up to 1 MiB are
+ * written by the sort kernel into another pinned buffer, so such a call
+ * issues no copy of its own; larger ones are copied each way. */
 int pms_solve(pms_ctx *h, const uint8_t *seqs, int n, int m, int l, int d,
               const uint64_t **motifs, size_t *count);
 

@@ -1193,8 +1193,10 @@ static int status_code(const StatusDev &s)
 
 // Runs a plan whose inputs come from host memory and downloads all results
 // into h->h_result. On return (PMS_OK) statuses and codes are on the host.
-// Largest input, and largest result block, that host-memory solves keep in
-// mapped pinned memory for the kernels to read or write directly.
+// Most bytes that the kernels of a host-memory solve read from, or write
+// to, mapped pinned memory instead of a copy. The packing kernels read each
+// input byte several times (once per CTA of a sequence's seed blocks, or once
+// per window that covers it), so inputs count with that factor.
 constexpr size_t kZeroCopyBytes = (size_t)1 << 20;
 
 static int run_host_plan(pms_ctx *h, const Plan &P, const std::vector<InstSpec> &specs, double t0)
@@ -1213,7 +1215,10 @@ static int run_host_plan(pms_ctx *h, const Plan &P, const std::vector<InstSpec> 
     // Inputs are staged in mapped pinned memory. Small ones are read there by
     // the packing kernel itself and small result blocks are written straight
     // into mapped pinned memory, so such a solve makes no copy calls.
-    const bool zc_in = P.seq_bytes <= kZeroCopyBytes, zc_out = rl.total <= kZeroCopyBytes;
+    size_t host_reads = 0;
+    for (const InstSpec &s : specs)
+        host_reads += (size_t)s.n * s.m * (size_t)std::max(s.l, (s.m - s.l + 1 + 15) / 16);
+    const bool zc_in = host_reads <= kZeroCopyBytes, zc_out = rl.total <= kZeroCopyBytes;
     const size_t inline_bytes = rl.dense + (size_t)kInlineKeys * 8;
     if ((rc = h->ensure_host(h->h_in, h->h_in_cap, P.seq_bytes, cudaHostAllocMapped)) ||
         (rc = h->ensure_host(h->h_result, h->h_result_cap, zc_out ? rl.total : inline_bytes, cudaHostAllocMapped)))
@@ -2560,7 +2565,7 @@ int pms_solve_sigma(pms_ctx *h, const uint8_t *alphabet, int sigma, const uint8_
     void *sg_dev = nullptr, *out_dev = nullptr;
     if ((e = cudaHostGetDevicePointer(&sg_dev, h->h_sg, 0)) != cudaSuccess)
         return h->cuda_fail(e, "mapped host buffers");
-    const bool zc_in = nm <= kZeroCopyBytes;
+    const bool zc_in = nm * (size_t)l <= kZeroCopyBytes;   // every window's l letters
     const uint8_t *seq_src = zc_in ? (const uint8_t *)sg_dev + 256 : (const uint8_t *)h->d_sg_seqs.p;
     bool zc_out = false;
     unsigned long long raw = 0, uniq = 0, ctr[kSgCntNum] = {};
